@@ -1,0 +1,350 @@
+#!/usr/bin/env python
+"""Benchmark of the pass-through connectivity hot path (FastCod, arXiv
+2302.09247, Section 2 / Algorithm 2) on GB300.
+
+One step = one whole pass of the hot path over one subject: zero C and C_end,
+prefilter + compaction over the full vertex stream, walk + dedup + accumulate
+of the survivors, and the exact overflow path.  The default workload is the
+HCP-shaped subject (145x174x145 @ 1.25 mm, two thalami, M = 70, 2,000,000
+streamlines), inputs resident in HBM, larger than L2 (2.4 GB vertex stream).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun (N > 1) every rank processes its own subject of the same shape
+(weak scaling, no data-path collective); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "DDA voxel-steps/s & subjects/s for C, bit-exact; batched vs plain; p50/p99 latency"
+UNIT = "voxel-steps/s"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.out = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=self.out, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.out.close()
+        sm, smax, reasons, samples = [], [], set(), 0
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                p = [x.strip() for x in line.split(",")]
+                if len(p) < 9:
+                    continue
+                try:
+                    sm.append(float(p[1]))
+                    smax.append(float(p[2]))
+                except ValueError:
+                    continue
+                samples += 1
+                for n, v in zip(names, p[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": samples}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _barrier_max(ws, x: float) -> float:
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _barrier_sum(ws, x: float) -> float:
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def _barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def cpu_baseline(vols, tr, n_sample: int):
+    """The oracle as it stands, single-threaded, on the first n_sample
+    streamlines of the same subject (test infrastructure, timed here only)."""
+    import oracle
+    n = min(n_sample, tr.n_streamlines)
+    off = tr.offsets[: n + 1]
+    xyz = tr.xyz[: off[-1]]
+    oracle.lib()  # build/load outside the timed region
+    t0 = time.perf_counter()
+    _, _, st = oracle.connectivity(vols.roi, vols.lab, vols.dims, vols.n_roi, vols.n_targets, xyz, off)
+    dt = time.perf_counter() - t0
+    return {"value": st["voxel_steps"] / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"first {n:,} of the subject's streamlines ({int(off[-1]):,} vertices, "
+                      f"{st['voxel_steps']:,} voxel-steps) in {dt:.2f} s, one thread"}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    import oracle
+    import synth
+    sample = args.ref_sample
+    vols, tr = synth.make_subject(args.config, n_streamlines=sample)
+    oracle.lib()
+    times, steps = [], 0
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        _, _, st = oracle.connectivity(vols.roi, vols.lab, vols.dims, vols.n_roi, vols.n_targets, tr.xyz,
+                                       tr.offsets)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt)
+            steps = st["voxel_steps"]
+    total = sum(times)
+    value = steps * len(times) / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1000 * total / len(times), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": _config(args.config, vols, tr, sample_note=f"bounded sample: first {sample:,} streamlines per step"),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"first {sample:,} streamlines of the subject per step, one thread"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def _config(cfg, vols, tr, sample_note=None):
+    names = {0: "tiny 32^3 @ 1 mm, one ROI ellipsoid, M=8",
+             1: "HCP-shaped 145x174x145 @ 1.25 mm, two thalami, M=70",
+             2: "high-res 260x311x260 @ 0.7 mm, two thalami, M=360"}
+    c = {"workload": f"{names.get(cfg, cfg)}: N={vols.n_roi}, M={vols.n_targets}, "
+                     f"{tr.n_streamlines:,} streamlines, {tr.n_vertices:,} vertices",
+         "grid": list(vols.dims), "N": vols.n_roi, "M": vols.n_targets, "streamlines": tr.n_streamlines,
+         "vertices": tr.n_vertices, "parallelism": "one subject per GPU",
+         "l2": "inputs larger than L2 (vertex stream %.2f GB per step)" % (tr.n_vertices * 12 / 1e9)}
+    if sample_note:
+        c["sample"] = sample_note
+    return c
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="fastcod", choices=["fastcod", "reference"])
+    ap.add_argument("--config", type=int, default=1, choices=[0, 1, 2])
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--cpu-sample", type=int, default=1_000_000)
+    ap.add_argument("--ref-sample", type=int, default=200_000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+
+    import synth
+    from paper_2302_09247_gb300 import fastcod as fc
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if dist.is_nccl_available() else "gloo")
+    dev = torch.device("cuda", local)
+
+    # one subject per rank: the preset's shape, a per-rank seed
+    vs = synth.volume_spec(args.config)
+    ss = synth.streamline_spec(args.config)
+    if rank:
+        ss.seed = ss.seed + 7919 * rank
+    vols = synth.make_volumes(vs)
+    tr = synth.make_tractogram(vs, ss, vols)
+
+    stream = torch.cuda.Stream(device=dev)
+    ctx = fc.Context(local)
+    fc.fastcod_set_stream(ctx.ctx, stream)
+    roi_d = torch.from_numpy(vols.roi).to(dev)
+    lab_d = torch.from_numpy(vols.lab.view(np.int16)).to(dev)
+    ctx.set_volumes(roi_d, lab_d, vols.dims, vols.n_roi, vols.n_targets)
+    xyz_d = torch.from_numpy(tr.xyz).to(dev)
+    off_d = torch.from_numpy(tr.offsets).to(dev)
+    torch.cuda.synchronize()
+
+    def step():
+        fc.fastcod_reset(ctx.ctx)
+        fc.fastcod_add_streamlines(ctx.ctx, xyz_d, off_d)
+
+    for _ in range(args.warmup):
+        step()
+    ctx.sync()
+    st = ctx.stats()
+    C_first = ctx.connectivity()
+
+    # ---------------------------------------------------------- timed region
+    ctx.set_option(fc.FASTCOD_OPT_PROFILE, 1)
+    launches0 = ctx.profile()["kernel_launches"]
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    _barrier(ws)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    _barrier(ws)
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    prof = ctx.profile()
+    ctx.set_option(fc.FASTCOD_OPT_PROFILE, 0)
+    st_last = ctx.stats()
+    C_last = ctx.connectivity()
+    assert np.array_equal(C_first, C_last), "C changed between identical steps"
+    assert st_last["voxel_steps"] == st["voxel_steps"]
+
+    ms_max = _barrier_max(ws, ms)
+    steps_total = _barrier_sum(ws, float(st["voxel_steps"])) * args.steps
+    value = steps_total / (ms_max / 1000.0)
+    streamlines_s = _barrier_sum(ws, float(tr.n_streamlines)) * args.steps / (ms_max / 1000.0)
+    subjects_s = ws * args.steps / (ms_max / 1000.0)
+
+    # roofline of the dominant kernel (prefilter: the full vertex stream)
+    peaks, peak_kind = _peaks()
+    alg_bytes = 12 * tr.n_vertices + 8 * (tr.n_streamlines + 1)
+    k2_ms = prof["ms_prefilter"] / max(prof["calls"], 1)
+    achieved = alg_bytes / (k2_ms / 1000.0) / 1e9
+    roofline = {"bound": "hbm", "kernel": "prefilter_tma_kernel", "achieved": achieved,
+                "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
+                "peak_source": f"{peak_kind} hbm_gbs (copy bandwidth)", "traffic": None,
+                "algorithmic_bytes_per_launch": alg_bytes,
+                "stage_ms_per_step": {"prefilter": k2_ms, "walk": prof["ms_walk"] / max(prof["calls"], 1),
+                                      "overflow": prof["ms_overflow"] / max(prof["calls"], 1)}}
+    gpu_launches = prof["kernel_launches"] - launches0
+
+    # ------------------------------------------------ end to end, host buffers
+    xyz_h = torch.from_numpy(tr.xyz).pin_memory()
+    off_h = torch.from_numpy(tr.offsets).pin_memory()
+    N, M = ctx.shape()
+    C_h = torch.empty((N, M), dtype=torch.int32).pin_memory()
+    Ce_h = torch.empty((N, M), dtype=torch.int32).pin_memory()
+    for _ in range(2):
+        fc.fastcod_reset(ctx.ctx)
+        fc.fastcod_add_streamlines(ctx.ctx, xyz_h, off_h)
+        fc.fastcod_connectivity(ctx.ctx, C_h)
+        fc.fastcod_endpoint_connectivity(ctx.ctx, Ce_h)
+    _barrier(ws)
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        fc.fastcod_reset(ctx.ctx)
+        fc.fastcod_add_streamlines(ctx.ctx, xyz_h, off_h)
+        fc.fastcod_connectivity(ctx.ctx, C_h)
+        fc.fastcod_endpoint_connectivity(ctx.ctx, Ce_h)
+    e2e_s = time.perf_counter() - t0
+    assert np.array_equal(C_h.numpy(), C_first)
+    e2e_max = _barrier_max(ws, e2e_s)
+    e2e_value = _barrier_sum(ws, float(st["voxel_steps"])) * args.e2e_steps / e2e_max
+    h2d = xyz_h.numel() * 4 + off_h.numel() * 8
+    d2h = 2 * N * M * 4
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(vols, tr, args.cpu_sample)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": _config(args.config, vols, tr),
+            "subjects_per_s": subjects_s, "streamlines_per_s": streamlines_s,
+            "voxel_steps_per_step": st["voxel_steps"], "survivors_per_step": st["survivors"],
+            "overflow_per_step": st["overflow"], "pairs_per_step": st["pairs"],
+            "C_sum": int(C_first.sum()),
+            "roofline": roofline,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "ms_per_step": 1000 * e2e_max / args.e2e_steps, "steps": args.e2e_steps},
+            "cpu_baseline": cpu,
+            "gpu_launches": gpu_launches,
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,182 @@
+/*
+ * fastcod.h - C ABI of libfastcod, a GB300 (sm_103a) implementation of the
+ * pass-through brain connectivity matrix of FastCod (Bian et al., "FastCod:
+ * Fast Brain Connectivity in Diffusion Imaging", arXiv 2302.09247).
+ *
+ * What is computed (Section 2, Algorithm 2): for ROI voxels v_1..v_N and
+ * target regions R_1..R_M, a streamline l = {p^1..p^T} adds exactly 1 to
+ * C[v][t] when it passes through ROI voxel v and through target region t,
+ * wherever it starts or ends.  "Passes through" is the exact continuous
+ * polyline: the voxels whose half-open boxes meet any of its closed segments
+ * (a single-vertex streamline is its one point).  Each streamline counts
+ * once per (v, t) pair.  The traditional seed-to-endpoint count of
+ * Algorithm 1 (first vertex = seed, region of the last vertex) is kept beside
+ * it as C_end.  All counts are exact integers.
+ *
+ * Units and layouts:
+ *   - vertices are int32 fixed point, 1 unit = 1/1024 voxel; voxel (i,j,k)
+ *     covers [1024 i, 1024 i + 1024) x [1024 j, ..) x [1024 k, ..), so the
+ *     voxel of a vertex is its coordinates shifted right by 10 (floor, also
+ *     for negative values); |coordinate| < 2^24 is required;
+ *   - xyz is [n_vertices][3] (x, y, z interleaved); offsets is int64
+ *     [n_streamlines + 1] with offsets[0] = 0, non-decreasing,
+ *     offsets[n_streamlines] = n_vertices; streamline s is vertices
+ *     offsets[s] .. offsets[s+1]-1;
+ *   - volumes are x-fastest: lin(i,j,k) = i + Dx*(j + Dy*k);
+ *     roi_index_map[lin] is the ROI row of the voxel (-1 = not in the ROI;
+ *     several voxels may share a row); target_labels[lin] is the target
+ *     region 1..M (0 = none); a voxel may be both;
+ *   - C and C_end are int32 [N][M] row-major; C[r][t-1] is the count for row
+ *     r and label t.
+ *
+ * Pointers: every input and output pointer may be host memory (pageable or
+ * page-locked) or device memory of the context's device; the library tells
+ * them apart with cudaPointerGetAttributes.  Device xyz pointers must be
+ * 16-byte aligned.  The caller owns every buffer it passes.  Work is ordered
+ * on the context's stream; device inputs and page-locked host inputs must
+ * stay unchanged until the next synchronising call (fastcod_connectivity,
+ * fastcod_endpoint_connectivity, fastcod_get_stats, fastcod_sync) or a sync
+ * of that stream; pageable host inputs may be reused when the call returns.
+ *
+ * Errors: every function returns FASTCOD_OK (0) or a negative FASTCOD_E*
+ * code and records a message readable with fastcod_last_error.  Errors found
+ * on the device (invalid offsets or coordinates in device inputs, a bounded
+ * wait that ran out) are reported by the next synchronising call; after one,
+ * C and C_end are undefined until fastcod_reset.  No C++ exception crosses
+ * this interface.  A context is not thread-safe: one thread at a time.
+ */
+#ifndef FASTCOD_H
+#define FASTCOD_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define FASTCOD_API __attribute__((visibility("default")))
+#else
+#define FASTCOD_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  FASTCOD_OK = 0,
+  FASTCOD_EINVAL = -1,    /* invalid argument or input data */
+  FASTCOD_ENOMEM = -2,    /* device or host allocation failed */
+  FASTCOD_ECUDA = -3,     /* a CUDA runtime call failed */
+  FASTCOD_ESTATE = -4,    /* call out of order (e.g. streamlines before volumes) */
+  FASTCOD_EOVERFLOW = -5, /* more than 2^31 - 1 streamlines since the last reset */
+  FASTCOD_ETIMEOUT = -6,  /* a bounded device-side wait gave up */
+  FASTCOD_ECANCELED = -7  /* request cancelled (serving) */
+};
+
+/* fastcod_create flags */
+#define FASTCOD_SYNC 1u /* every call waits for its GPU work before returning */
+
+/* fastcod_set_option keys */
+enum {
+  /* 1 (default): drop streamlines that touch no ROI brick or no target brick
+   * before the walk; 0: walk every streamline.  Results are identical. */
+  FASTCOD_OPT_PREFILTER = 1,
+  /* target rule: 0 (default) = every label the streamline passes through;
+   * 1 = only the label of the last vertex (Algorithm 2 taken literally,
+   * r_j = loc2region(p^T)).  Takes effect for streamlines added afterwards. */
+  FASTCOD_OPT_TARGET_MODE = 2,
+  /* voxel rule: 0 (default) = continuous segments; 1 = vertices only (the
+   * point-sampled reading behind the paper's upsampling rule, Section 3). */
+  FASTCOD_OPT_SAMPLING = 3,
+  /* vertex staging of the prefilter: 0 = direct loads, 1 (default) = TMA
+   * bulk copies into shared memory. Results are identical. */
+  FASTCOD_OPT_STAGING = 4,
+  /* 1: record CUDA events around every stage on the context's stream and
+   * accumulate their durations (fastcod_get_profile); 0 (default): off. */
+  FASTCOD_OPT_PROFILE = 5
+};
+
+typedef struct fastcod_ctx fastcod_ctx;
+
+typedef struct {
+  int64_t streamlines;  /* streamlines added since the last reset */
+  int64_t vertices;     /* vertices added since the last reset */
+  int64_t voxel_steps;  /* sum over segments of 1 + sum_a |floor(p1_a) - floor(p0_a)|,
+                           a single-vertex streamline counting 1 */
+  int64_t survivors;    /* streamlines that passed the prefilter and were walked */
+  int64_t overflow;     /* walked streamlines whose sets exceeded the on-chip
+                           tables and took the exact global-memory path */
+  int64_t pairs;        /* sum over streamlines of |V_s| * |T_s| (increments of C) */
+} fastcod_stats;
+
+/* Per-stage device time accumulated while FASTCOD_OPT_PROFILE is 1 (CUDA
+ * events on the context's stream), and the library's kernel launches. */
+typedef struct {
+  int64_t calls;           /* fastcod_add_streamlines calls profiled */
+  int64_t kernel_launches; /* kernels this library launched (all calls, profiled or not) */
+  double ms_h2d;           /* host-to-device copies of streamline inputs */
+  double ms_prefilter;     /* K2: prefilter + compaction */
+  double ms_walk;          /* K3: walk + dedup + accumulate */
+  double ms_overflow;      /* exact global-memory path for oversized sets */
+} fastcod_profile;
+
+/* Create a context on CUDA device cuda_device.  Allocates only small state;
+ * volumes and streamline buffers are sized by the calls that need them.
+ * *out receives the context (NULL on error). */
+FASTCOD_API int fastcod_create(fastcod_ctx** out, int cuda_device, uint32_t flags);
+
+/* Free the context and every device buffer it owns.  NULL-safe. */
+FASTCOD_API int fastcod_destroy(fastcod_ctx* ctx);
+
+/* Order the context's work on cuda_stream (a cudaStream_t of the context's
+ * device; NULL = the context's own non-blocking stream). */
+FASTCOD_API int fastcod_set_stream(fastcod_ctx* ctx, void* cuda_stream);
+
+/* Install the volumes (Section 2: the ROI voxel set V = {v_1..v_N} and the
+ * target regions R = {R_1..R_M}; loc2region).  dims are Dx, Dy, Dz (> 0,
+ * product < 2^31).  n_roi = N (0: max(roi)+1); n_targets = M (0: max label).
+ * Requires -1 <= roi < N, label <= M, N < 2^30, M < 65536.  Zeroes C,
+ * C_end and the statistics.  Blocks until the volumes are validated. */
+FASTCOD_API int fastcod_set_volumes(fastcod_ctx* ctx, const int32_t* roi_index_map,
+                                    const uint16_t* target_labels, int32_t dim_x, int32_t dim_y,
+                                    int32_t dim_z, int32_t n_roi, int32_t n_targets);
+
+/* Accumulate streamlines into C and C_end (the passthrough count of
+ * Algorithm 2 for every streamline; Algorithm 1's count for C_end).  May be called many times;
+ * the result depends only on the multiset of streamlines added. */
+FASTCOD_API int fastcod_add_streamlines(fastcod_ctx* ctx, const int32_t* xyz, int64_t n_vertices,
+                                        const int64_t* offsets, int64_t n_streamlines);
+
+/* Wait for all queued work and copy C (int32 [N][M]) to C_out. */
+FASTCOD_API int fastcod_connectivity(fastcod_ctx* ctx, int32_t* C_out);
+
+/* Wait for all queued work and copy C_end (int32 [N][M]) to Cend_out. */
+FASTCOD_API int fastcod_endpoint_connectivity(fastcod_ctx* ctx, int32_t* Cend_out);
+
+/* Zero C, C_end and the statistics; keep the volumes.  Stream-ordered: it
+ * does not wait for queued work. */
+FASTCOD_API int fastcod_reset(fastcod_ctx* ctx);
+
+/* N and M of the installed volumes (ESTATE before fastcod_set_volumes). */
+FASTCOD_API int fastcod_get_shape(const fastcod_ctx* ctx, int32_t* n_roi, int32_t* n_targets);
+
+/* Wait for all queued work and read the statistics. */
+FASTCOD_API int fastcod_get_stats(fastcod_ctx* ctx, fastcod_stats* out);
+
+/* Wait for all queued work and report any device-detected error. */
+FASTCOD_API int fastcod_sync(fastcod_ctx* ctx);
+
+/* Wait for all queued work and read the profile (zeroed when profiling is
+ * switched on; fastcod_reset keeps it). */
+FASTCOD_API int fastcod_get_profile(fastcod_ctx* ctx, fastcod_profile* out);
+
+/* Set an option (FASTCOD_OPT_*). */
+FASTCOD_API int fastcod_set_option(fastcod_ctx* ctx, int32_t key, int64_t value);
+
+/* Message of the last error on this context ("" if none); owned by ctx,
+ * valid until the next call on it.  NULL ctx: message of the last failed
+ * fastcod_create on this thread. */
+FASTCOD_API const char* fastcod_last_error(const fastcod_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FASTCOD_H */

@@ -1,0 +1,571 @@
+// libfastcod C ABI: context, validation, buffers, launches (see fastcod.h).
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/fastcod.h"
+#include "fc_internal.cuh"
+
+using fc::DevState;
+
+struct fastcod_ctx {
+  int device = 0;
+  uint32_t flags = 0;
+  int num_sms = 0;
+  cudaStream_t own_stream = nullptr;
+  cudaStream_t stream = nullptr;
+
+  // volumes
+  bool has_vol = false;
+  int32_t dims[3] = {0, 0, 0};
+  int32_t bdims[3] = {0, 0, 0};
+  int32_t N = 0, M = 0;
+  uint32_t* d_code = nullptr;
+  uint16_t* d_lab = nullptr;
+  uint32_t* d_bricks = nullptr;
+  int32_t* d_C = nullptr;
+  int32_t* d_Cend = nullptr;
+  uint32_t* d_scratch = nullptr;
+  int32_t scratch_ctas = 0;
+
+  // staging of host inputs and per-call lists
+  void* d_vstage = nullptr;
+  size_t vstage_bytes = 0;
+  int32_t* d_xyz = nullptr;
+  size_t xyz_bytes = 0;
+  int64_t* d_off = nullptr;
+  size_t off_bytes = 0;
+  int32_t* d_surv = nullptr;
+  size_t surv_bytes = 0;
+  int32_t* d_ovf = nullptr;
+  size_t ovf_bytes = 0;
+
+  DevState* d_state = nullptr;
+
+  int64_t total_streamlines = 0;
+  int64_t total_vertices = 0;
+  int prefilter = 1;
+  uint32_t mode = 0;
+  int staging_tma = 1;
+  int profile = 0;
+  struct EvSet {
+    cudaEvent_t e[5];
+  };
+  std::vector<EvSet> ev_pool;  // event sets of profiled calls
+  size_t ev_used = 0;          // sets recorded and not yet folded into prof
+  EvSet* ev_cur = nullptr;
+  fastcod_profile prof = {0, 0, 0.0, 0.0, 0.0, 0.0};
+
+  std::string err;
+};
+
+namespace {
+
+thread_local std::string g_create_err;
+
+int fail(fastcod_ctx* c, int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (c) c->err = buf;
+  return code;
+}
+
+#define CU(call)                                                                                   \
+  do {                                                                                             \
+    cudaError_t e_ = (call);                                                                       \
+    if (e_ != cudaSuccess) {                                                                       \
+      (void)cudaGetLastError();                                                                    \
+      return fail(c, e_ == cudaErrorMemoryAllocation ? FASTCOD_ENOMEM : FASTCOD_ECUDA, "%s: %s",   \
+                  #call, cudaGetErrorString(e_));                                                  \
+    }                                                                                              \
+  } while (0)
+
+// 0 = host memory, 1 = device memory of dev, -1 = device memory elsewhere
+int ptr_kind(const void* p, int dev) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return 0;
+  }
+  if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return a.device == dev ? 1 : -1;
+  return 0;
+}
+
+int grow(fastcod_ctx* c, void** p, size_t* cap, size_t need) {
+  if (need <= *cap && *p) return FASTCOD_OK;
+  size_t n = need < 256 ? 256 : need;
+  if (*p) {
+    CU(cudaStreamSynchronize(c->stream));
+    CU(cudaFree(*p));
+    *p = nullptr;
+    *cap = 0;
+  }
+  CU(cudaMalloc(p, n));
+  *cap = n;
+  return FASTCOD_OK;
+}
+
+void free_volumes(fastcod_ctx* c) {
+  cudaFree(c->d_code);
+  cudaFree(c->d_lab);
+  cudaFree(c->d_bricks);
+  cudaFree(c->d_C);
+  cudaFree(c->d_Cend);
+  cudaFree(c->d_scratch);
+  c->d_code = nullptr;
+  c->d_lab = nullptr;
+  c->d_bricks = nullptr;
+  c->d_C = nullptr;
+  c->d_Cend = nullptr;
+  c->d_scratch = nullptr;
+  c->has_vol = false;
+}
+
+void collect_profile(fastcod_ctx* c);
+
+int read_state(fastcod_ctx* c, DevState* h) {
+  CU(cudaMemcpyAsync(h, c->d_state, sizeof(DevState), cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  collect_profile(c);
+  return FASTCOD_OK;
+}
+
+// Synchronise and turn a device-detected error into a status.
+int sync_check(fastcod_ctx* c) {
+  DevState h;
+  int rc = read_state(c, &h);
+  if (rc) return rc;
+  switch (h.error) {
+    case fc::kErrNone:
+      return FASTCOD_OK;
+    case fc::kErrOffsets:
+      return fail(c, FASTCOD_EINVAL,
+                  "offsets invalid near streamline %d: need offsets[0]=0, non-decreasing, offsets[n]=n_vertices",
+                  h.error_info);
+    case fc::kErrCoord:
+      return fail(c, FASTCOD_EINVAL, "vertex coordinate out of range (|c| >= 2^24) in streamline %d", h.error_info);
+    case fc::kErrVolume:
+      return fail(c, FASTCOD_EINVAL, "volume value out of range at voxel %d", h.error_info);
+    case fc::kErrTimeout:
+      return fail(c, FASTCOD_ETIMEOUT, "device wait timed out (warp %d)", h.error_info);
+    default:
+      return fail(c, FASTCOD_ECUDA, "device error %d (%d)", h.error, h.error_info);
+  }
+}
+
+fc::VolView vol_view(const fastcod_ctx* c) {
+  fc::VolView v;
+  v.code = c->d_code;
+  v.lab = c->d_lab;
+  v.bricks = c->d_bricks;
+  v.dx = c->dims[0];
+  v.dy = c->dims[1];
+  v.dz = c->dims[2];
+  v.bx = c->bdims[0];
+  v.by = c->bdims[1];
+  v.bz = c->bdims[2];
+  v.n_roi = c->N;
+  v.n_lab = c->M;
+  return v;
+}
+
+// Stream-ordered zeroing of C, C_end and every device counter (the error
+// word included).
+int zero_accumulators(fastcod_ctx* c) {
+  const size_t nm = (size_t)c->N * (size_t)c->M;
+  if (nm) {
+    CU(cudaMemsetAsync(c->d_C, 0, nm * 4, c->stream));
+    CU(cudaMemsetAsync(c->d_Cend, 0, nm * 4, c->stream));
+  }
+  CU(cudaMemsetAsync(c->d_state, 0, sizeof(DevState), c->stream));
+  c->total_streamlines = 0;
+  c->total_vertices = 0;
+  return FASTCOD_OK;
+}
+
+// Fold the events of the profiled calls into the totals (the stream has been
+// synchronised).
+void collect_profile(fastcod_ctx* c) {
+  for (size_t k = 0; k < c->ev_used; ++k) {
+    float ms[4] = {0, 0, 0, 0};
+    for (int i = 0; i < 4; ++i)
+      if (cudaEventElapsedTime(&ms[i], c->ev_pool[k].e[i], c->ev_pool[k].e[i + 1]) != cudaSuccess) {
+        (void)cudaGetLastError();
+        ms[i] = 0;
+      }
+    c->prof.ms_h2d += ms[0];
+    c->prof.ms_prefilter += ms[1];
+    c->prof.ms_walk += ms[2];
+    c->prof.ms_overflow += ms[3];
+    c->prof.calls += 1;
+  }
+  c->ev_used = 0;
+}
+
+// Pick the event set of this call: a new one while the pool is below 256
+// sets, else fold the pending ones first (one synchronisation per 256 calls).
+int begin_profiled_call(fastcod_ctx* c) {
+  c->ev_cur = nullptr;
+  if (!c->profile) return FASTCOD_OK;
+  if (c->ev_used == c->ev_pool.size()) {
+    if (c->ev_pool.size() < 256) {
+      fastcod_ctx::EvSet set;
+      for (int i = 0; i < 5; ++i) CU(cudaEventCreate(&set.e[i]));
+      c->ev_pool.push_back(set);
+    } else {
+      CU(cudaStreamSynchronize(c->stream));
+      collect_profile(c);
+    }
+  }
+  c->ev_cur = &c->ev_pool[c->ev_used++];
+  return FASTCOD_OK;
+}
+
+int record(fastcod_ctx* c, int i) {
+  if (c->ev_cur) CU(cudaEventRecord(c->ev_cur->e[i], c->stream));
+  return FASTCOD_OK;
+}
+
+int copy_out(fastcod_ctx* c, const int32_t* src, int32_t* dst) {
+  if (!c->has_vol) return fail(c, FASTCOD_ESTATE, "no volumes installed");
+  int rc = sync_check(c);
+  if (rc) return rc;
+  const size_t nm = (size_t)c->N * (size_t)c->M;
+  if (!nm) return FASTCOD_OK;
+  if (!dst) return fail(c, FASTCOD_EINVAL, "output pointer is NULL");
+  if (ptr_kind(dst, c->device) < 0) return fail(c, FASTCOD_EINVAL, "output is device memory of another device");
+  CU(cudaMemcpyAsync(dst, src, nm * 4, cudaMemcpyDefault, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  return FASTCOD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+FASTCOD_API int fastcod_create(fastcod_ctx** out, int cuda_device, uint32_t flags) {
+  if (!out) {
+    g_create_err = "out is NULL";
+    return FASTCOD_EINVAL;
+  }
+  *out = nullptr;
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess || cuda_device < 0 || cuda_device >= n) {
+    (void)cudaGetLastError();
+    g_create_err = "no such CUDA device";
+    return FASTCOD_EINVAL;
+  }
+  fastcod_ctx* c = new (std::nothrow) fastcod_ctx();
+  if (!c) {
+    g_create_err = "host allocation failed";
+    return FASTCOD_ENOMEM;
+  }
+  c->device = cuda_device;
+  c->flags = flags;
+  int rc = FASTCOD_OK;
+  do {
+    if (cudaSetDevice(cuda_device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, cuda_device) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking) != cudaSuccess) {
+      rc = FASTCOD_ECUDA;
+      break;
+    }
+    c->stream = c->own_stream;
+    if (cudaMalloc(&c->d_state, sizeof(DevState)) != cudaSuccess) {
+      rc = FASTCOD_ENOMEM;
+      break;
+    }
+    cudaMemsetAsync(c->d_state, 0, sizeof(DevState), c->stream);
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) rc = FASTCOD_ECUDA;
+  } while (0);
+  if (rc) {
+    g_create_err = std::string("CUDA initialisation failed: ") + cudaGetErrorString(cudaGetLastError());
+    fastcod_destroy(c);
+    return rc;
+  }
+  *out = c;
+  return FASTCOD_OK;
+}
+
+FASTCOD_API int fastcod_destroy(fastcod_ctx* c) {
+  if (!c) return FASTCOD_OK;
+  cudaSetDevice(c->device);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  free_volumes(c);
+  cudaFree(c->d_vstage);
+  cudaFree(c->d_xyz);
+  cudaFree(c->d_off);
+  cudaFree(c->d_surv);
+  cudaFree(c->d_ovf);
+  cudaFree(c->d_state);
+  for (auto& set : c->ev_pool)
+    for (int i = 0; i < 5; ++i) cudaEventDestroy(set.e[i]);
+  if (c->own_stream) cudaStreamDestroy(c->own_stream);
+  delete c;
+  return FASTCOD_OK;
+}
+
+FASTCOD_API int fastcod_set_stream(fastcod_ctx* c, void* s) {
+  if (!c) return FASTCOD_EINVAL;
+  CU(cudaSetDevice(c->device));
+  CU(cudaStreamSynchronize(c->stream));
+  c->stream = s ? (cudaStream_t)s : c->own_stream;
+  return FASTCOD_OK;
+}
+
+FASTCOD_API int fastcod_set_volumes(fastcod_ctx* c, const int32_t* roi, const uint16_t* lab, int32_t dx,
+                                    int32_t dy, int32_t dz, int32_t n_roi, int32_t n_targets) {
+  if (!c) return FASTCOD_EINVAL;
+  c->err.clear();
+  if (dx <= 0 || dy <= 0 || dz <= 0) return fail(c, FASTCOD_EINVAL, "grid dims must be > 0");
+  const int64_t nvox = (int64_t)dx * dy * dz;
+  if (nvox >= ((int64_t)1 << 31)) return fail(c, FASTCOD_EINVAL, "grid has >= 2^31 voxels");
+  if (!roi || !lab) return fail(c, FASTCOD_EINVAL, "volume pointer is NULL");
+  if (n_roi < 0 || n_targets < 0) return fail(c, FASTCOD_EINVAL, "N and M must be >= 0");
+  CU(cudaSetDevice(c->device));
+  CU(cudaStreamSynchronize(c->stream));
+  const int kr = ptr_kind(roi, c->device), kl = ptr_kind(lab, c->device);
+  if (kr < 0 || kl < 0) return fail(c, FASTCOD_EINVAL, "volume is device memory of another device");
+  // device copies of host volumes
+  const size_t rb = (size_t)nvox * 4, lb = (size_t)nvox * 2;
+  const int32_t* d_roi = roi;
+  const uint16_t* d_labin = lab;
+  if (!kr || !kl) {
+    int rc = grow(c, &c->d_vstage, &c->vstage_bytes, rb + lb);
+    if (rc) return rc;
+    if (!kr) {
+      CU(cudaMemcpyAsync(c->d_vstage, roi, rb, cudaMemcpyHostToDevice, c->stream));
+      d_roi = (const int32_t*)c->d_vstage;
+    }
+    if (!kl) {
+      CU(cudaMemcpyAsync((char*)c->d_vstage + rb, lab, lb, cudaMemcpyHostToDevice, c->stream));
+      d_labin = (const uint16_t*)((char*)c->d_vstage + rb);
+    }
+  }
+  free_volumes(c);
+  DevState h;
+  memset(&h, 0, sizeof h);
+  h.max_roi = -1;
+  CU(cudaMemcpyAsync(c->d_state, &h, sizeof h, cudaMemcpyHostToDevice, c->stream));
+  if (n_roi == 0 || n_targets == 0) {
+    CU(fc::launch_volume_max(d_roi, d_labin, nvox, c->d_state, c->stream));
+    int rc = read_state(c, &h);
+    if (rc) return rc;
+    if (n_roi == 0) n_roi = h.max_roi + 1;
+    if (n_targets == 0) n_targets = h.max_label;
+  }
+  if (n_roi >= (1 << 30)) return fail(c, FASTCOD_EINVAL, "N must be < 2^30");
+  if (n_targets > 65535) return fail(c, FASTCOD_EINVAL, "M must be < 65536");
+  c->dims[0] = dx;
+  c->dims[1] = dy;
+  c->dims[2] = dz;
+  for (int a = 0; a < 3; ++a) c->bdims[a] = (c->dims[a] + (1 << fc::kBrickLog2) - 1) >> fc::kBrickLog2;
+  c->N = n_roi;
+  c->M = n_targets;
+  const int64_t nbricks = (int64_t)c->bdims[0] * c->bdims[1] * c->bdims[2];
+  const size_t nm = (size_t)c->N * (size_t)c->M;
+  CU(cudaMalloc(&c->d_code, rb));
+  CU(cudaMalloc(&c->d_lab, lb));
+  CU(cudaMalloc(&c->d_bricks, (size_t)((nbricks + 15) / 16) * 4));
+  CU(cudaMalloc(&c->d_C, nm ? nm * 4 : 4));
+  CU(cudaMalloc(&c->d_Cend, nm ? nm * 4 : 4));
+  CU(cudaMemsetAsync(c->d_bricks, 0, (size_t)((nbricks + 15) / 16) * 4, c->stream));
+  // exact global-memory path for streamlines whose sets outgrow shared memory
+  const int64_t words = fc::overflow_scratch_words(c->N, c->M);
+  int64_t ctas = 64;
+  while (ctas > 1 && ctas * words * 4 > ((int64_t)256 << 20)) ctas /= 2;
+  c->scratch_ctas = (int32_t)ctas;
+  CU(cudaMalloc(&c->d_scratch, (size_t)(ctas * words * 4)));
+  CU(cudaMemsetAsync(c->d_scratch, 0, (size_t)(ctas * words * 4), c->stream));
+  fc::VolView v = vol_view(c);
+  CU(fc::launch_volume_prep(d_roi, d_labin, nvox, v, c->d_code, c->d_lab, c->d_bricks, c->d_state, c->stream));
+  int rc = sync_check(c);
+  if (rc) {
+    free_volumes(c);
+    return rc;
+  }
+  c->has_vol = true;
+  return zero_accumulators(c);
+}
+
+FASTCOD_API int fastcod_add_streamlines(fastcod_ctx* c, const int32_t* xyz, int64_t nv, const int64_t* offsets,
+                                        int64_t ns) {
+  if (!c) return FASTCOD_EINVAL;
+  c->err.clear();
+  if (!c->has_vol) return fail(c, FASTCOD_ESTATE, "fastcod_set_volumes must come first");
+  if (ns < 0 || nv < 0) return fail(c, FASTCOD_EINVAL, "negative count");
+  if (ns == 0) return nv == 0 ? FASTCOD_OK : fail(c, FASTCOD_EINVAL, "vertices without streamlines");
+  if (!offsets || (nv > 0 && !xyz)) return fail(c, FASTCOD_EINVAL, "input pointer is NULL");
+  if (c->total_streamlines + ns > 0x7fffffffLL)
+    return fail(c, FASTCOD_EOVERFLOW, "more than 2^31-1 streamlines since the last reset");
+  if (nv > ((int64_t)1 << 40)) return fail(c, FASTCOD_EINVAL, "too many vertices");
+  CU(cudaSetDevice(c->device));
+  const int kx = nv > 0 ? ptr_kind(xyz, c->device) : 1;
+  const int ko = ptr_kind(offsets, c->device);
+  if (kx < 0 || ko < 0) return fail(c, FASTCOD_EINVAL, "input is device memory of another device");
+  if (kx == 1 && nv > 0 && ((uintptr_t)xyz & 15u))
+    return fail(c, FASTCOD_EINVAL, "device xyz must be 16-byte aligned");
+  const int32_t* d_xyz = xyz;
+  const int64_t* d_off = offsets;
+  if (int rc = begin_profiled_call(c)) return rc;
+  if (int rc = record(c, 0)) return rc;
+  if (kx == 0) {
+    int rc = grow(c, (void**)&c->d_xyz, &c->xyz_bytes, (size_t)nv * 12 + 16);
+    if (rc) return rc;
+    CU(cudaMemcpyAsync(c->d_xyz, xyz, (size_t)nv * 12, cudaMemcpyHostToDevice, c->stream));
+    d_xyz = c->d_xyz;
+  }
+  if (ko == 0) {
+    int rc = grow(c, (void**)&c->d_off, &c->off_bytes, (size_t)(ns + 1) * 8);
+    if (rc) return rc;
+    CU(cudaMemcpyAsync(c->d_off, offsets, (size_t)(ns + 1) * 8, cudaMemcpyHostToDevice, c->stream));
+    d_off = c->d_off;
+  }
+  {
+    int rc = grow(c, (void**)&c->d_surv, &c->surv_bytes, (size_t)ns * 4);
+    if (rc) return rc;
+    rc = grow(c, (void**)&c->d_ovf, &c->ovf_bytes, (size_t)ns * 4);
+    if (rc) return rc;
+  }
+  // per-call counters: n_survivors, n_overflow, work_next
+  CU(cudaMemsetAsync(&c->d_state->n_survivors, 0, 3 * sizeof(uint32_t), c->stream));
+  fc::Tract t;
+  t.xyz = d_xyz;
+  t.off = d_off;
+  t.nv = nv;
+  t.ns = ns;
+  fc::VolView v = vol_view(c);
+  fc::Accum acc;
+  acc.C = c->d_C;
+  acc.Cend = c->d_Cend;
+  if (int rc = record(c, 1)) return rc;
+  CU(fc::launch_prefilter(t, v, c->prefilter != 0, c->mode, c->staging_tma != 0, c->d_surv, c->d_state,
+                          c->num_sms, c->stream));
+  if (int rc = record(c, 2)) return rc;
+  CU(fc::launch_walk(t, v, c->d_surv, acc, c->mode, c->d_ovf, c->d_state, c->num_sms, c->stream));
+  if (int rc = record(c, 3)) return rc;
+  CU(fc::launch_walk_overflow(t, v, c->d_ovf, acc, c->mode, c->d_scratch, c->scratch_ctas, c->d_state,
+                              c->stream));
+  if (int rc = record(c, 4)) return rc;
+  c->prof.kernel_launches += 3;
+  c->total_streamlines += ns;
+  c->total_vertices += nv;
+  if (c->flags & FASTCOD_SYNC) return sync_check(c);
+  return FASTCOD_OK;
+}
+
+FASTCOD_API int fastcod_connectivity(fastcod_ctx* c, int32_t* C_out) {
+  if (!c) return FASTCOD_EINVAL;
+  c->err.clear();
+  CU(cudaSetDevice(c->device));
+  return copy_out(c, c->d_C, C_out);
+}
+
+FASTCOD_API int fastcod_endpoint_connectivity(fastcod_ctx* c, int32_t* Cend_out) {
+  if (!c) return FASTCOD_EINVAL;
+  c->err.clear();
+  CU(cudaSetDevice(c->device));
+  return copy_out(c, c->d_Cend, Cend_out);
+}
+
+FASTCOD_API int fastcod_reset(fastcod_ctx* c) {
+  if (!c) return FASTCOD_EINVAL;
+  c->err.clear();
+  if (!c->has_vol) return fail(c, FASTCOD_ESTATE, "no volumes installed");
+  CU(cudaSetDevice(c->device));
+  return zero_accumulators(c);
+}
+
+FASTCOD_API int fastcod_get_shape(const fastcod_ctx* c, int32_t* n_roi, int32_t* n_targets) {
+  if (!c) return FASTCOD_EINVAL;
+  if (!c->has_vol) return FASTCOD_ESTATE;
+  if (n_roi) *n_roi = c->N;
+  if (n_targets) *n_targets = c->M;
+  return FASTCOD_OK;
+}
+
+FASTCOD_API int fastcod_get_stats(fastcod_ctx* c, fastcod_stats* out) {
+  if (!c || !out) return FASTCOD_EINVAL;
+  c->err.clear();
+  CU(cudaSetDevice(c->device));
+  DevState h;
+  int rc = read_state(c, &h);
+  if (rc) return rc;
+  out->streamlines = c->total_streamlines;
+  out->vertices = c->total_vertices;
+  out->voxel_steps = (int64_t)h.voxel_steps;
+  out->survivors = (int64_t)h.survivors;
+  out->overflow = (int64_t)h.overflow;
+  out->pairs = (int64_t)h.pairs;
+  return FASTCOD_OK;
+}
+
+FASTCOD_API int fastcod_get_profile(fastcod_ctx* c, fastcod_profile* out) {
+  if (!c || !out) return FASTCOD_EINVAL;
+  c->err.clear();
+  CU(cudaSetDevice(c->device));
+  CU(cudaStreamSynchronize(c->stream));
+  collect_profile(c);
+  *out = c->prof;
+  return FASTCOD_OK;
+}
+
+FASTCOD_API int fastcod_sync(fastcod_ctx* c) {
+  if (!c) return FASTCOD_EINVAL;
+  c->err.clear();
+  CU(cudaSetDevice(c->device));
+  return sync_check(c);
+}
+
+FASTCOD_API int fastcod_set_option(fastcod_ctx* c, int32_t key, int64_t value) {
+  if (!c) return FASTCOD_EINVAL;
+  c->err.clear();
+  switch (key) {
+    case FASTCOD_OPT_PREFILTER:
+      if (value != 0 && value != 1) break;
+      c->prefilter = (int)value;
+      return FASTCOD_OK;
+    case FASTCOD_OPT_TARGET_MODE:
+      if (value != 0 && value != 1) break;
+      c->mode = (c->mode & ~fc::kModeTargetEndpoint) | (value ? fc::kModeTargetEndpoint : 0u);
+      return FASTCOD_OK;
+    case FASTCOD_OPT_SAMPLING:
+      if (value != 0 && value != 1) break;
+      c->mode = (c->mode & ~fc::kModeVertexSampled) | (value ? fc::kModeVertexSampled : 0u);
+      return FASTCOD_OK;
+    case FASTCOD_OPT_STAGING:
+      if (value != 0 && value != 1) break;
+      c->staging_tma = (int)value;
+      return FASTCOD_OK;
+    case FASTCOD_OPT_PROFILE:
+      if (value != 0 && value != 1) break;
+      CU(cudaSetDevice(c->device));
+      CU(cudaStreamSynchronize(c->stream));
+      collect_profile(c);
+      if (value && !c->profile) {
+        // switching on starts a fresh profile
+        const int64_t launches = c->prof.kernel_launches;
+        c->prof = fastcod_profile{0, launches, 0.0, 0.0, 0.0, 0.0};
+      }
+      c->profile = (int)value;
+      return FASTCOD_OK;
+    default:
+      return fail(c, FASTCOD_EINVAL, "unknown option %d", key);
+  }
+  return fail(c, FASTCOD_EINVAL, "invalid value %lld for option %d", (long long)value, key);
+}
+
+FASTCOD_API const char* fastcod_last_error(const fastcod_ctx* c) {
+  if (!c) return g_create_err.c_str();
+  return c->err.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,166 @@
+// Device-side building blocks: error word, voxel lookup, integer segment walk
+// and the per-warp shared-memory sets.
+#pragma once
+
+#include "fc_internal.cuh"
+
+namespace fc {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+__host__ __device__ constexpr int ilog2(int x) { return x <= 1 ? 0 : 1 + ilog2(x >> 1); }
+
+__device__ __forceinline__ void set_error(DevState* st, int32_t code, int32_t info = 0) {
+  if (atomicCAS(&st->error, 0, code) == 0) atomicExch(&st->error_info, info);
+}
+
+__device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+  unsigned m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+__device__ __forceinline__ bool coord_ok(int32_t c) { return c > -kCoordLimit && c < kCoordLimit; }
+
+// ROI row (-1 = none) and label (0 = none) of voxel (x, y, z); voxels off the
+// grid have neither (loc2region outside every region).
+__device__ __forceinline__ void voxel_lookup(const VolView& v, int32_t x, int32_t y, int32_t z,
+                                             int32_t& row, int32_t& lab) {
+  row = -1;
+  lab = 0;
+  if ((unsigned)x < (unsigned)v.dx && (unsigned)y < (unsigned)v.dy && (unsigned)z < (unsigned)v.dz) {
+    const int32_t lin = x + v.dx * (y + v.dy * z);
+    const uint32_t code = __ldg(v.code + lin);
+    if (code & kCodeRoi) {
+      row = (int32_t)(code & kCodeRowMask);
+      if (code & kCodeRoiLabelled) lab = (int32_t)__ldg(v.lab + lin);
+    } else {
+      lab = (int32_t)code;
+    }
+  }
+}
+
+// Brick bits (bit 0 ROI, bit 1 label) of brick (bx, by, bz), in range.
+__device__ __forceinline__ uint32_t brick_bits(const VolView& v, int32_t bx, int32_t by, int32_t bz) {
+  const int32_t b = bx + v.bx * (by + v.by * bz);
+  return (__ldg(v.bricks + (b >> 4)) >> ((b & 15) * 2)) & 3u;
+}
+
+// Conservative occupancy of the voxel box [lo, hi] (inclusive): the OR of the
+// brick bits over every in-grid brick the box overlaps.  Boxes spanning more
+// than two bricks on an axis report both bits (long segments are rare and
+// walking them is always exact).
+__device__ __forceinline__ uint32_t box_bits(const VolView& v, int32_t lx, int32_t ly, int32_t lz,
+                                             int32_t hx, int32_t hy, int32_t hz) {
+  if (hx < 0 || hy < 0 || hz < 0 || lx >= v.dx || ly >= v.dy || lz >= v.dz) return 0u;
+  const int32_t bx0 = max(lx, 0) >> kBrickLog2, bx1 = min(hx, v.dx - 1) >> kBrickLog2;
+  const int32_t by0 = max(ly, 0) >> kBrickLog2, by1 = min(hy, v.dy - 1) >> kBrickLog2;
+  const int32_t bz0 = max(lz, 0) >> kBrickLog2, bz1 = min(hz, v.dz - 1) >> kBrickLog2;
+  if (bx1 - bx0 > 1 || by1 - by0 > 1 || bz1 - bz0 > 1) return 3u;
+  uint32_t bits = 0;
+  for (int32_t z = bz0; z <= bz1; ++z)
+    for (int32_t y = by0; y <= by1; ++y)
+      for (int32_t x = bx0; x <= bx1; ++x) bits |= brick_bits(v, x, y, z);
+  return bits;
+}
+
+// ---------------------------------------------------------------------------
+// Integer walk of one segment P0 -> P1 (Amanatides & Woo, exact rational
+// events).  For axis a with d_a != 0 the next plane crossing is at
+// t = num_a / den_a, den_a = |d_a|.  An increasing axis moves into the next
+// voxel AT its crossing (allowed while t <= 1: a segment ending on a plane
+// reaches the upper voxel); a decreasing axis moves JUST AFTER it (allowed
+// while t < 1).  At the earliest crossing the increasing axes tied there move
+// first; tied decreasing axes move on the following step, which finds the
+// same t again.  Every move enters one new voxel.
+//
+// P is uint32_t when every den < 2^16 (compared numerators never exceed
+// their den, so products stay below 2^32) and unsigned long long otherwise
+// (|coordinate| < 2^24 keeps products below 2^52).
+template <typename P>
+struct SegWalk {
+  int32_t c[3];
+  P num[3], den[3];
+  int32_t sgn[3];
+
+  __device__ __forceinline__ void init(const int32_t p0[3], const int32_t p1[3]) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const int32_t d = p1[a] - p0[a];
+      c[a] = p0[a] >> kUnitLog2;
+      if (d > 0) {
+        sgn[a] = 1;
+        den[a] = (P)d;
+        num[a] = (P)(((c[a] + 1) << kUnitLog2) - p0[a]);
+      } else if (d < 0) {
+        sgn[a] = -1;
+        den[a] = (P)(-d);
+        num[a] = (P)(p0[a] - (c[a] << kUnitLog2));
+      } else {
+        sgn[a] = 0;
+        den[a] = 1;
+        num[a] = 0;
+      }
+    }
+  }
+
+  __device__ __forceinline__ bool pending(int a) const {
+    return sgn[a] > 0 ? (num[a] <= den[a]) : (sgn[a] < 0 ? (num[a] < den[a]) : false);
+  }
+
+  // crossing of axis a strictly before / at the same t as axis b
+  __device__ __forceinline__ bool before(int a, int b) const { return num[a] * den[b] < num[b] * den[a]; }
+  __device__ __forceinline__ bool same(int a, int b) const { return num[a] * den[b] == num[b] * den[a]; }
+
+  // Enter the next voxel; false when the segment has no crossing left.
+  __device__ __forceinline__ bool step() {
+    const bool q0 = pending(0), q1 = pending(1), q2 = pending(2);
+    if (!(q0 || q1 || q2)) return false;
+    int b = q0 ? 0 : (q1 ? 1 : 2);
+    if (q1 && b != 1 && before(1, b)) b = 1;
+    if (q2 && b != 2 && before(2, b)) b = 2;
+    const bool t0 = q0 && (b == 0 || same(0, b));
+    const bool t1 = q1 && (b == 1 || same(1, b));
+    const bool t2 = q2 && (b == 2 || same(2, b));
+    const bool up = (t0 && sgn[0] > 0) || (t1 && sgn[1] > 0) || (t2 && sgn[2] > 0);
+    const int32_t want = up ? 1 : -1;
+    if (t0 && sgn[0] == want) { c[0] += want; num[0] += (P)(1 << kUnitLog2); }
+    if (t1 && sgn[1] == want) { c[1] += want; num[1] += (P)(1 << kUnitLog2); }
+    if (t2 && sgn[2] == want) { c[2] += want; num[2] += (P)(1 << kUnitLog2); }
+    return true;
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Per-warp open-addressing set in shared memory (keys >= 0, empty = -1).
+// Lanes holding the same key are merged with __match_any_sync first; the
+// lowest lane of each group inserts with atomicCAS.  New keys are appended to
+// list[n..] in lane order.  Returns the new size; sets *fail when a probe
+// sequence found no slot (cannot happen while size < H).
+template <int H>
+__device__ __forceinline__ int set_insert(int32_t* tab, int32_t* list, int n, int32_t key, bool& fail) {
+  const unsigned want = __ballot_sync(kFull, key >= 0);
+  if (want == 0u) return n;
+  bool fresh = false;
+  if (key >= 0) {
+    const unsigned peers = __match_any_sync(want, key);
+    if ((peers & lanemask_lt()) == 0u) {
+      uint32_t h = ((uint32_t)key * 0x9E3779B1u) >> (32 - ilog2(H));
+      int probe = 0;
+      for (; probe < H; ++probe) {
+        const int32_t old = atomicCAS(tab + h, -1, key);
+        if (old == -1) { fresh = true; break; }
+        if (old == key) break;
+        h = (h + 1) & (H - 1);
+      }
+      if (probe == H) fail = true;
+    }
+  }
+  const unsigned fm = __ballot_sync(kFull, fresh);
+  if (fresh) list[n + __popc(fm & lanemask_lt())] = key;
+  return n + __popc(fm);
+}
+
+}  // namespace fc

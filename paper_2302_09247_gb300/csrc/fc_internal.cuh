@@ -1,0 +1,102 @@
+// Internal declarations shared by the CUDA translation units of libfastcod.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace fc {
+
+// 1 unit = 1/1024 voxel; the voxel of a coordinate is (c >> kUnitLog2).
+constexpr int kUnitLog2 = 10;
+constexpr int32_t kCoordLimit = 1 << 24;
+
+// Brick occupancy grid: bricks of (1 << kBrickLog2)^3 voxels, two bits per
+// brick (bit 0: some voxel has an ROI row, bit 1: some voxel has a label),
+// sixteen bricks per 32-bit word.
+constexpr int kBrickLog2 = 2;
+
+// Per-voxel code: bit 31 set -> ROI voxel, bits 0..29 = row, bit 30 = the
+// voxel also carries a label (read it from the label volume); bit 31 clear
+// -> the code is the label (0 = none).
+constexpr uint32_t kCodeRoi = 0x80000000u;
+constexpr uint32_t kCodeRoiLabelled = 0x40000000u;
+constexpr uint32_t kCodeRowMask = 0x3fffffffu;
+
+// Device-detected error codes (first one wins).
+enum DevError : int32_t {
+  kErrNone = 0,
+  kErrOffsets = 1,      // offsets not monotone, out of [0, n_vertices], or bad ends
+  kErrCoord = 2,        // |coordinate| >= 2^24
+  kErrVolume = 3,       // roi or label value out of range
+  kErrTimeout = 4,      // a bounded wait gave up
+  kErrOverflowList = 5  // overflow list capacity exceeded (cannot happen by construction)
+};
+
+// Cumulative and per-call counters in device memory.
+struct DevState {
+  int32_t error;
+  int32_t error_info;
+  uint32_t n_survivors;   // this call: entries in the survivor list
+  uint32_t n_overflow;    // this call: entries in the overflow list
+  uint32_t work_next;     // this call: dynamic work counter of the walk kernel
+  uint32_t pad0;
+  unsigned long long voxel_steps;
+  unsigned long long survivors;
+  unsigned long long overflow;
+  unsigned long long pairs;
+  int32_t max_roi;        // set_volumes: max(roi) over the volume
+  int32_t max_label;      // set_volumes: max(label)
+};
+
+// Read-only view of the installed volumes.
+struct VolView {
+  const uint32_t* code;   // [nvox] per-voxel code
+  const uint16_t* lab;    // [nvox] labels (read for labelled ROI voxels)
+  const uint32_t* bricks; // brick occupancy words
+  int32_t dx, dy, dz;     // grid
+  int32_t bx, by, bz;     // brick grid
+  int32_t n_roi, n_lab;   // N, M
+};
+
+// One batch of streamlines on the device.
+struct Tract {
+  const int32_t* xyz;     // [nv][3]
+  const int64_t* off;     // [ns + 1]
+  int64_t nv, ns;
+};
+
+struct Accum {
+  int32_t* C;             // [N][M]
+  int32_t* Cend;          // [N][M]
+};
+
+// Mode bits of the walk.
+constexpr uint32_t kModeTargetEndpoint = 1u;
+constexpr uint32_t kModeVertexSampled = 2u;
+
+// ---------------------------------------------------------------- launchers
+// Each returns the cudaError_t of the launch.
+
+// K1: per-voxel code, label copy and brick bits from the caller's volumes.
+cudaError_t launch_volume_max(const int32_t* roi, const uint16_t* lab, int64_t nvox, DevState* st,
+                              cudaStream_t s);
+cudaError_t launch_volume_prep(const int32_t* roi, const uint16_t* lab, int64_t nvox, VolView v,
+                               uint32_t* code, uint16_t* lab_out, uint32_t* bricks, DevState* st,
+                               cudaStream_t s);
+
+// K2: prefilter + compaction (+ validation and voxel-step count).
+cudaError_t launch_prefilter(const Tract& t, const VolView& v, bool prefilter, uint32_t mode,
+                             bool tma, int32_t* survivors, DevState* st, int num_sms,
+                             cudaStream_t s);
+
+// K3: warp-per-streamline walk, dedup, accumulate; overflow path.
+cudaError_t launch_walk(const Tract& t, const VolView& v, const int32_t* survivors, Accum acc,
+                        uint32_t mode, int32_t* overflow_list, DevState* st, int num_sms,
+                        cudaStream_t s);
+cudaError_t launch_walk_overflow(const Tract& t, const VolView& v, const int32_t* overflow_list,
+                                 Accum acc, uint32_t mode, uint32_t* scratch,
+                                 int32_t scratch_ctas, DevState* st, cudaStream_t s);
+// words of global scratch one overflow CTA needs for N rows and M labels
+int64_t overflow_scratch_words(int32_t n_roi, int32_t n_lab);
+
+}  // namespace fc

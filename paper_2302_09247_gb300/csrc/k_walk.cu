@@ -1,0 +1,265 @@
+// K3: walk, dedup and accumulate (Section 2, Algorithm 2 for each surviving
+// streamline: passthrough, then C(v, r) += 1 for every pass-through v and
+// target r).
+//
+// One warp per surviving streamline, lanes over its segments.  Each lane
+// walks its segment with the exact integer walk and looks up the ROI row and
+// label of every voxel it enters (the per-voxel code is read through the
+// read-only cache and stays L2-resident).  The first voxel of a segment is the
+// last voxel of the previous one, so only the streamline's first segment
+// visits its start voxel.  Rows and labels are deduplicated per streamline in
+// two shared-memory open-addressing sets (V_s and T_s) after merging equal
+// keys across lanes with __match_any_sync.  The outer product V_s x T_s is
+// then added to C with one L2 reduction per pair, and the seed/endpoint pair
+// to C_end.  A streamline whose sets outgrow the tables is handed, whole, to
+// an exact CTA-per-streamline path with global-memory bitmaps.
+#include "fc_device.cuh"
+
+namespace fc {
+
+constexpr int kWalkWarps = 8;
+constexpr int kHV = 512, kLimV = 256;  // V_s table slots / size limit
+constexpr int kHT = 128, kLimT = 64;   // T_s table slots / size limit
+
+struct WalkWarpSmem {
+  int32_t tabV[kHV];
+  int32_t listV[kLimV + 32];
+  int32_t tabT[kHT];
+  int32_t listT[kLimT + 32];
+};
+
+__device__ __forceinline__ void load_vertex(const int32_t* xyz, int64_t j, int32_t p[3]) {
+  p[0] = __ldg(xyz + 3 * j);
+  p[1] = __ldg(xyz + 3 * j + 1);
+  p[2] = __ldg(xyz + 3 * j + 2);
+}
+
+template <typename P>
+__device__ __forceinline__ void walk_window(const VolView& v, WalkWarpSmem& sm, const int32_t p0[3],
+                                            const int32_t p1[3], bool has, bool first, bool endpoint_mode,
+                                            int& nV, int& nT, bool& fail) {
+  SegWalk<P> w;
+  bool pend = false;
+  if (has) {
+    w.init(p0, p1);
+    pend = first ? true : w.step();
+  }
+  while (__any_sync(kFull, pend)) {
+    int32_t row = -1, lab = 0;
+    if (pend) voxel_lookup(v, w.c[0], w.c[1], w.c[2], row, lab);
+    if (endpoint_mode) lab = 0;
+    nV = set_insert<kHV>(sm.tabV, sm.listV, nV, row, fail);
+    nT = set_insert<kHT>(sm.tabT, sm.listT, nT, lab > 0 ? lab : -1, fail);
+    if (nV > kLimV || nT > kLimT) { fail = true; break; }
+    if (pend) pend = w.step();
+  }
+}
+
+__global__ void __launch_bounds__(kWalkWarps * 32) walk_kernel(Tract t, VolView v, const int32_t* __restrict__ surv,
+                                                              Accum acc, uint32_t mode, int32_t* __restrict__ ovf,
+                                                              DevState* st) {
+  __shared__ WalkWarpSmem smem_all[kWalkWarps];
+  WalkWarpSmem& sm = smem_all[threadIdx.x >> 5];
+  const unsigned lane = lane_id();
+  for (int i = lane; i < kHV; i += 32) sm.tabV[i] = -1;
+  for (int i = lane; i < kHT; i += 32) sm.tabT[i] = -1;
+  __syncwarp();
+  const bool endpoint_mode = (mode & kModeTargetEndpoint) != 0;
+  const bool point_mode = (mode & kModeVertexSampled) != 0;
+  const uint32_t n = st->n_survivors;
+  const int64_t M = v.n_lab;
+  unsigned long long pairs_acc = 0;
+  for (;;) {
+    uint32_t idx = 0;
+    if (lane == 0) idx = atomicAdd(&st->work_next, 1u);
+    idx = __shfl_sync(kFull, idx, 0);
+    if (idx >= n) break;
+    const int32_t s = surv[idx];
+    const int64_t a = t.off[s], b = t.off[s + 1];
+    const int64_t T = b - a;
+    int nV = 0, nT = 0;
+    bool fail = false;
+    if (T == 1 || point_mode) {
+      for (int64_t i0 = 0; i0 < T && !fail; i0 += 32) {
+        const int64_t j = a + i0 + lane;
+        int32_t row = -1, lab = 0;
+        if (j < b) {
+          int32_t p[3];
+          load_vertex(t.xyz, j, p);
+          voxel_lookup(v, p[0] >> kUnitLog2, p[1] >> kUnitLog2, p[2] >> kUnitLog2, row, lab);
+        }
+        if (endpoint_mode) lab = 0;
+        nV = set_insert<kHV>(sm.tabV, sm.listV, nV, row, fail);
+        nT = set_insert<kHT>(sm.tabT, sm.listT, nT, lab > 0 ? lab : -1, fail);
+        if (nV > kLimV || nT > kLimT) fail = true;
+        fail = __any_sync(kFull, fail);
+      }
+    } else {
+      for (int64_t i0 = 0; i0 < T - 1 && !fail; i0 += 32) {
+        const int64_t j = a + i0 + lane;
+        const int64_t jhi = min(a + i0 + 32, b - 1);
+        int32_t p0[3] = {0, 0, 0}, p1[3];
+        if (j <= jhi) load_vertex(t.xyz, j, p0);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) p1[k] = __shfl_down_sync(kFull, p0[k], 1);
+        if (lane == 31 && j + 1 <= jhi) load_vertex(t.xyz, j + 1, p1);
+        const bool has = j < b - 1;
+        const bool small = !has || (abs(p1[0] - p0[0]) < 65536 && abs(p1[1] - p0[1]) < 65536 &&
+                                    abs(p1[2] - p0[2]) < 65536);
+        if (__all_sync(kFull, small))
+          walk_window<uint32_t>(v, sm, p0, p1, has, j == a, endpoint_mode, nV, nT, fail);
+        else
+          walk_window<unsigned long long>(v, sm, p0, p1, has, j == a, endpoint_mode, nV, nT, fail);
+        fail = __any_sync(kFull, fail);
+      }
+    }
+    if (endpoint_mode && !fail) {
+      // T_s = {label of the last vertex}
+      int32_t row = -1, lab = 0;
+      if (lane == 0) {
+        int32_t p[3];
+        load_vertex(t.xyz, b - 1, p);
+        voxel_lookup(v, p[0] >> kUnitLog2, p[1] >> kUnitLog2, p[2] >> kUnitLog2, row, lab);
+      }
+      nT = set_insert<kHT>(sm.tabT, sm.listT, nT, lab > 0 ? lab : -1, fail);
+      fail = __any_sync(kFull, fail);
+    }
+    __syncwarp();
+    if (fail) {
+      if (lane == 0) ovf[atomicAdd(&st->n_overflow, 1u)] = s;
+    } else {
+      const int pairs = nV * nT;
+      for (int p = lane; p < pairs; p += 32) {
+        const int i = p / nT, k = p - i * nT;
+        atomicAdd(acc.C + (int64_t)sm.listV[i] * M + (sm.listT[k] - 1), 1);
+      }
+      pairs_acc += (unsigned long long)pairs;
+      if (lane == 0) {
+        int32_t p[3], r0, l0, r1, l1;
+        load_vertex(t.xyz, a, p);
+        voxel_lookup(v, p[0] >> kUnitLog2, p[1] >> kUnitLog2, p[2] >> kUnitLog2, r0, l0);
+        load_vertex(t.xyz, b - 1, p);
+        voxel_lookup(v, p[0] >> kUnitLog2, p[1] >> kUnitLog2, p[2] >> kUnitLog2, r1, l1);
+        if (r0 >= 0 && l1 >= 1) atomicAdd(acc.Cend + (int64_t)r0 * M + (l1 - 1), 1);
+      }
+    }
+    __syncwarp();
+    for (int i = lane; i < kHV; i += 32) sm.tabV[i] = -1;
+    for (int i = lane; i < kHT; i += 32) sm.tabT[i] = -1;
+    __syncwarp();
+  }
+  if (lane == 0 && pairs_acc) atomicAdd(&st->pairs, pairs_acc);
+}
+
+// ---------------------------------------------------------------- overflow
+// One CTA per overflowed streamline.  Sets are bitmaps over all N rows and
+// M+1 labels in the CTA's slice of global scratch, with append lists; the
+// bitmaps are cleared through the lists after each streamline, so they are
+// all-zero between streamlines (the scratch is zeroed once when allocated).
+
+int64_t overflow_scratch_words(int32_t n_roi, int32_t n_lab) {
+  return ((int64_t)n_roi + 31) / 32 + ((int64_t)n_lab + 1 + 31) / 32 + n_roi + (int64_t)n_lab + 1;
+}
+
+struct OvfSets {
+  uint32_t* rowbits;
+  uint32_t* labbits;
+  int32_t* rowlist;
+  int32_t* lablist;
+};
+
+__device__ __forceinline__ void ovf_add(uint32_t* bits, int32_t* list, int* n, int32_t key) {
+  const uint32_t m = 1u << (key & 31);
+  if (!(atomicOr(bits + (key >> 5), m) & m)) list[atomicAdd(n, 1)] = key;
+}
+
+__device__ __forceinline__ void ovf_visit(const VolView& v, const OvfSets& z, int* nV, int* nT, bool endpoint_mode,
+                                          int32_t x, int32_t y, int32_t zz) {
+  int32_t row, lab;
+  voxel_lookup(v, x, y, zz, row, lab);
+  if (row >= 0) ovf_add(z.rowbits, z.rowlist, nV, row);
+  if (!endpoint_mode && lab >= 1) ovf_add(z.labbits, z.lablist, nT, lab);
+}
+
+__global__ void __launch_bounds__(256) walk_overflow_kernel(Tract t, VolView v, const int32_t* __restrict__ ovf,
+                                                            Accum acc, uint32_t mode, uint32_t* scratch,
+                                                            int64_t words_per_cta, DevState* st) {
+  __shared__ int nV, nT;
+  OvfSets z;
+  z.rowbits = scratch + blockIdx.x * words_per_cta;
+  z.labbits = z.rowbits + ((int64_t)v.n_roi + 31) / 32;
+  z.rowlist = reinterpret_cast<int32_t*>(z.labbits + ((int64_t)v.n_lab + 1 + 31) / 32);
+  z.lablist = z.rowlist + v.n_roi;
+  const bool endpoint_mode = (mode & kModeTargetEndpoint) != 0;
+  const bool point_mode = (mode & kModeVertexSampled) != 0;
+  const uint32_t n = st->n_overflow;
+  const int64_t M = v.n_lab;
+  for (uint32_t i = blockIdx.x; i < n; i += gridDim.x) {
+    if (threadIdx.x == 0) { nV = 0; nT = 0; }
+    __syncthreads();
+    const int32_t s = ovf[i];
+    const int64_t a = t.off[s], b = t.off[s + 1], T = b - a;
+    const bool pts = T == 1 || point_mode;
+    const int64_t units = pts ? T : T - 1;
+    for (int64_t u = threadIdx.x; u < units; u += blockDim.x) {
+      int32_t p0[3];
+      load_vertex(t.xyz, a + u, p0);
+      if (pts) {
+        ovf_visit(v, z, &nV, &nT, endpoint_mode, p0[0] >> kUnitLog2, p0[1] >> kUnitLog2, p0[2] >> kUnitLog2);
+      } else {
+        int32_t p1[3];
+        load_vertex(t.xyz, a + u + 1, p1);
+        SegWalk<unsigned long long> w;
+        w.init(p0, p1);
+        ovf_visit(v, z, &nV, &nT, endpoint_mode, w.c[0], w.c[1], w.c[2]);
+        while (w.step()) ovf_visit(v, z, &nV, &nT, endpoint_mode, w.c[0], w.c[1], w.c[2]);
+      }
+    }
+    if (endpoint_mode && threadIdx.x == 0 && T >= 1) {
+      int32_t p[3], row, lab;
+      load_vertex(t.xyz, b - 1, p);
+      voxel_lookup(v, p[0] >> kUnitLog2, p[1] >> kUnitLog2, p[2] >> kUnitLog2, row, lab);
+      if (lab >= 1) ovf_add(z.labbits, z.lablist, &nT, lab);
+    }
+    __syncthreads();
+    const int64_t pairs = (int64_t)nV * nT;
+    for (int64_t p = threadIdx.x; p < pairs; p += blockDim.x) {
+      const int64_t r = p / nT, k = p - r * nT;
+      atomicAdd(acc.C + (int64_t)z.rowlist[r] * M + (z.lablist[k] - 1), 1);
+    }
+    if (threadIdx.x == 0) {
+      if (pairs) atomicAdd(&st->pairs, (unsigned long long)pairs);
+      atomicAdd(&st->overflow, 1ull);
+      if (T >= 1) {
+        int32_t p[3], r0, l0, r1, l1;
+        load_vertex(t.xyz, a, p);
+        voxel_lookup(v, p[0] >> kUnitLog2, p[1] >> kUnitLog2, p[2] >> kUnitLog2, r0, l0);
+        load_vertex(t.xyz, b - 1, p);
+        voxel_lookup(v, p[0] >> kUnitLog2, p[1] >> kUnitLog2, p[2] >> kUnitLog2, r1, l1);
+        if (r0 >= 0 && l1 >= 1) atomicAdd(acc.Cend + (int64_t)r0 * M + (l1 - 1), 1);
+      }
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < nV; k += blockDim.x) z.rowbits[z.rowlist[k] >> 5] = 0u;
+    for (int k = threadIdx.x; k < nT; k += blockDim.x) z.labbits[z.lablist[k] >> 5] = 0u;
+    __syncthreads();
+  }
+}
+
+cudaError_t launch_walk(const Tract& t, const VolView& v, const int32_t* survivors, Accum acc, uint32_t mode,
+                        int32_t* overflow_list, DevState* st, int num_sms, cudaStream_t s) {
+  if (t.ns <= 0) return cudaSuccess;
+  walk_kernel<<<num_sms * 4, kWalkWarps * 32, 0, s>>>(t, v, survivors, acc, mode, overflow_list, st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_walk_overflow(const Tract& t, const VolView& v, const int32_t* overflow_list, Accum acc,
+                                 uint32_t mode, uint32_t* scratch, int32_t scratch_ctas, DevState* st,
+                                 cudaStream_t s) {
+  if (t.ns <= 0) return cudaSuccess;
+  walk_overflow_kernel<<<scratch_ctas, 256, 0, s>>>(t, v, overflow_list, acc, mode, scratch,
+                                                    overflow_scratch_words(v.n_roi, v.n_lab), st);
+  return cudaGetLastError();
+}
+
+}  // namespace fc

@@ -1,0 +1,246 @@
+"""Thin ctypes binding of libfastcod (include/fastcod.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  Functions keep the C names; array arguments may be numpy arrays
+(host memory), torch tensors (host, pinned or CUDA) or raw integer addresses.
+There is no CPU fallback: importing this module fails loudly when the library
+has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libfastcod.so")
+
+FASTCOD_OK = 0
+FASTCOD_EINVAL = -1
+FASTCOD_ENOMEM = -2
+FASTCOD_ECUDA = -3
+FASTCOD_ESTATE = -4
+FASTCOD_EOVERFLOW = -5
+FASTCOD_ETIMEOUT = -6
+FASTCOD_ECANCELED = -7
+
+FASTCOD_SYNC = 1
+
+FASTCOD_OPT_PREFILTER = 1
+FASTCOD_OPT_TARGET_MODE = 2
+FASTCOD_OPT_SAMPLING = 3
+FASTCOD_OPT_STAGING = 4
+FASTCOD_OPT_PROFILE = 5
+
+EXPORTED = [
+    "fastcod_create", "fastcod_destroy", "fastcod_set_stream", "fastcod_set_volumes",
+    "fastcod_add_streamlines", "fastcod_connectivity", "fastcod_endpoint_connectivity",
+    "fastcod_reset", "fastcod_get_shape", "fastcod_get_stats", "fastcod_get_profile", "fastcod_sync",
+    "fastcod_set_option", "fastcod_last_error",
+]
+
+
+class FastCodError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"fastcod error {code}: {msg}")
+        self.code = code
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("streamlines", ctypes.c_int64), ("vertices", ctypes.c_int64),
+                ("voxel_steps", ctypes.c_int64), ("survivors", ctypes.c_int64),
+                ("overflow", ctypes.c_int64), ("pairs", ctypes.c_int64)]
+
+
+class Profile(ctypes.Structure):
+    _fields_ = [("calls", ctypes.c_int64), ("kernel_launches", ctypes.c_int64), ("ms_h2d", ctypes.c_double),
+                ("ms_prefilter", ctypes.c_double), ("ms_walk", ctypes.c_double),
+                ("ms_overflow", ctypes.c_double)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is not built; run paper_2302_09247_gb300.build.build()")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i32, i64, u32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32
+    sig = {
+        "fastcod_create": ([ctypes.POINTER(vp), ctypes.c_int, u32], ctypes.c_int),
+        "fastcod_destroy": ([vp], ctypes.c_int),
+        "fastcod_set_stream": ([vp, vp], ctypes.c_int),
+        "fastcod_set_volumes": ([vp, vp, vp, i32, i32, i32, i32, i32], ctypes.c_int),
+        "fastcod_add_streamlines": ([vp, vp, i64, vp, i64], ctypes.c_int),
+        "fastcod_connectivity": ([vp, vp], ctypes.c_int),
+        "fastcod_endpoint_connectivity": ([vp, vp], ctypes.c_int),
+        "fastcod_reset": ([vp], ctypes.c_int),
+        "fastcod_get_shape": ([vp, ctypes.POINTER(i32), ctypes.POINTER(i32)], ctypes.c_int),
+        "fastcod_get_stats": ([vp, ctypes.POINTER(Stats)], ctypes.c_int),
+        "fastcod_get_profile": ([vp, ctypes.POINTER(Profile)], ctypes.c_int),
+        "fastcod_sync": ([vp], ctypes.c_int),
+        "fastcod_set_option": ([vp, i32, i64], ctypes.c_int),
+        "fastcod_last_error": ([vp], ctypes.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = res
+    return L
+
+
+lib = _load()
+
+
+def _ptr(x):
+    """Address of a contiguous numpy array / torch tensor, or an int address."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return x.ctypes.data
+    raise TypeError(f"cannot take the address of {type(x)}")
+
+
+def _check(ctx, rc):
+    if rc != FASTCOD_OK:
+        raise FastCodError(rc, lib.fastcod_last_error(ctx).decode())
+    return rc
+
+
+def fastcod_create(device: int = 0, flags: int = 0):
+    out = ctypes.c_void_p()
+    rc = lib.fastcod_create(ctypes.byref(out), device, flags)
+    if rc != FASTCOD_OK:
+        raise FastCodError(rc, lib.fastcod_last_error(None).decode())
+    return out
+
+
+def fastcod_destroy(ctx):
+    return lib.fastcod_destroy(ctx)
+
+
+def fastcod_set_stream(ctx, stream):
+    s = getattr(stream, "cuda_stream", stream)
+    return _check(ctx, lib.fastcod_set_stream(ctx, s))
+
+
+def fastcod_set_volumes(ctx, roi, lab, dims, n_roi: int = 0, n_targets: int = 0):
+    dx, dy, dz = (int(d) for d in dims)
+    return _check(ctx, lib.fastcod_set_volumes(ctx, _ptr(roi), _ptr(lab), dx, dy, dz, n_roi, n_targets))
+
+
+def fastcod_add_streamlines(ctx, xyz, offsets, n_vertices: int | None = None, n_streamlines: int | None = None):
+    nv = int(xyz.shape[0]) if n_vertices is None else int(n_vertices)
+    ns = int(offsets.shape[0]) - 1 if n_streamlines is None else int(n_streamlines)
+    return _check(ctx, lib.fastcod_add_streamlines(ctx, _ptr(xyz), nv, _ptr(offsets), ns))
+
+
+def fastcod_connectivity(ctx, out):
+    return _check(ctx, lib.fastcod_connectivity(ctx, _ptr(out)))
+
+
+def fastcod_endpoint_connectivity(ctx, out):
+    return _check(ctx, lib.fastcod_endpoint_connectivity(ctx, _ptr(out)))
+
+
+def fastcod_reset(ctx):
+    return _check(ctx, lib.fastcod_reset(ctx))
+
+
+def fastcod_get_shape(ctx):
+    n, m = ctypes.c_int32(), ctypes.c_int32()
+    _check(ctx, lib.fastcod_get_shape(ctx, ctypes.byref(n), ctypes.byref(m)))
+    return n.value, m.value
+
+
+def fastcod_get_stats(ctx) -> dict:
+    s = Stats()
+    _check(ctx, lib.fastcod_get_stats(ctx, ctypes.byref(s)))
+    return {k: int(getattr(s, k)) for k, _ in Stats._fields_}
+
+
+def fastcod_get_profile(ctx) -> dict:
+    p = Profile()
+    _check(ctx, lib.fastcod_get_profile(ctx, ctypes.byref(p)))
+    return {k: (float(getattr(p, k)) if k.startswith("ms_") else int(getattr(p, k))) for k, _ in Profile._fields_}
+
+
+def fastcod_sync(ctx):
+    return _check(ctx, lib.fastcod_sync(ctx))
+
+
+def fastcod_set_option(ctx, key: int, value: int):
+    return _check(ctx, lib.fastcod_set_option(ctx, key, value))
+
+
+def fastcod_last_error(ctx) -> str:
+    return lib.fastcod_last_error(ctx).decode()
+
+
+class Context:
+    """Convenience owner of a fastcod context."""
+
+    def __init__(self, device: int = 0, flags: int = 0):
+        self.ctx = fastcod_create(device, flags)
+
+    def close(self):
+        if self.ctx is not None:
+            fastcod_destroy(self.ctx)
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_volumes(self, roi, lab, dims, n_roi: int = 0, n_targets: int = 0):
+        fastcod_set_volumes(self.ctx, roi, lab, dims, n_roi, n_targets)
+        return self.shape()
+
+    def add_streamlines(self, xyz, offsets):
+        fastcod_add_streamlines(self.ctx, xyz, offsets)
+
+    def shape(self):
+        return fastcod_get_shape(self.ctx)
+
+    def connectivity(self, out=None):
+        if out is None:
+            n, m = self.shape()
+            out = np.empty((n, m), dtype=np.int32)
+        fastcod_connectivity(self.ctx, out)
+        return out
+
+    def endpoint_connectivity(self, out=None):
+        if out is None:
+            n, m = self.shape()
+            out = np.empty((n, m), dtype=np.int32)
+        fastcod_endpoint_connectivity(self.ctx, out)
+        return out
+
+    def stats(self) -> dict:
+        return fastcod_get_stats(self.ctx)
+
+    def profile(self) -> dict:
+        return fastcod_get_profile(self.ctx)
+
+    def set_option(self, key: int, value: int):
+        fastcod_set_option(self.ctx, key, value)
+
+    def reset(self):
+        fastcod_reset(self.ctx)
+
+    def sync(self):
+        fastcod_sync(self.ctx)

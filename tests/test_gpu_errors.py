@@ -1,0 +1,143 @@
+"""Error conventions of the C ABI on a GPU: invalid inputs found on the host
+and on the device, call order, and a context that stays usable after reset."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests.gpu_helpers import as_device
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture
+def fc():
+    from paper_2302_09247_gb300 import fastcod
+    return fastcod
+
+
+@pytest.fixture(scope="module")
+def tiny0():
+    return synth.make_subject(0, n_streamlines=500)
+
+
+def _ctx_with_volumes(fc, vols, where="device"):
+    ctx = fc.Context(0)
+    if where == "device":
+        ctx.set_volumes(as_device(vols.roi), as_device(vols.lab), vols.dims, vols.n_roi, vols.n_targets)
+    else:
+        ctx.set_volumes(vols.roi, vols.lab, vols.dims, vols.n_roi, vols.n_targets)
+    return ctx
+
+
+def test_state_and_argument_errors(fc, tiny0):
+    vols, tr = tiny0
+    with fc.Context(0) as ctx:
+        with pytest.raises(fc.FastCodError) as e:
+            ctx.add_streamlines(tr.xyz, tr.offsets)
+        assert e.value.code == fc.FASTCOD_ESTATE
+        with pytest.raises(fc.FastCodError) as e:
+            ctx.shape()
+        assert e.value.code == fc.FASTCOD_ESTATE
+        with pytest.raises(fc.FastCodError) as e:
+            fc.fastcod_set_volumes(ctx.ctx, vols.roi, vols.lab, (0, 1, 1))
+        assert e.value.code == fc.FASTCOD_EINVAL
+        with pytest.raises(fc.FastCodError):
+            fc.fastcod_set_option(ctx.ctx, 999, 1)
+
+
+@pytest.mark.parametrize("where", ["device", "host"])
+def test_volume_values_rejected(fc, tiny0, where):
+    vols, _ = tiny0
+    with fc.Context(0) as ctx:
+        lab = vols.lab.copy()
+        lab.reshape(-1)[123] = vols.n_targets + 1
+        src = as_device(lab) if where == "device" else lab
+        roi = as_device(vols.roi) if where == "device" else vols.roi
+        with pytest.raises(fc.FastCodError) as e:
+            ctx.set_volumes(roi, src, vols.dims, vols.n_roi, vols.n_targets)
+        assert e.value.code == fc.FASTCOD_EINVAL
+        bad = vols.roi.copy()
+        bad.reshape(-1)[5] = vols.n_roi
+        src = as_device(bad) if where == "device" else bad
+        with pytest.raises(fc.FastCodError) as e:
+            ctx.set_volumes(src, vols.lab if where == "host" else as_device(vols.lab), vols.dims,
+                            vols.n_roi, vols.n_targets)
+        assert e.value.code == fc.FASTCOD_EINVAL
+        # N and M inferred from the volumes
+        n, m = ctx.set_volumes(vols.roi, vols.lab, vols.dims)
+        assert (n, m) == (int(vols.roi.max()) + 1, int(vols.lab.max()))
+
+
+@pytest.mark.parametrize("where", ["device", "host"])
+@pytest.mark.parametrize("staging", [0, 1])
+def test_device_detected_input_errors_then_reset(fc, tiny0, where, staging):
+    vols, tr = tiny0
+    ctx = _ctx_with_volumes(fc, vols)
+    ctx.set_option(fc.FASTCOD_OPT_STAGING, staging)
+    put = as_device if where == "device" else (lambda a: np.ascontiguousarray(a))
+    try:
+        # non-monotone offsets
+        off = tr.offsets.copy()
+        off[10], off[11] = off[11], off[10]
+        ctx.add_streamlines(put(tr.xyz), put(off))
+        with pytest.raises(fc.FastCodError) as e:
+            ctx.connectivity()
+        assert e.value.code == fc.FASTCOD_EINVAL and "offsets" in str(e.value)
+        ctx.reset()
+        # last offset != n_vertices
+        off = tr.offsets.copy()
+        off[-1] -= 1
+        ctx.add_streamlines(put(tr.xyz), put(off), ) if False else fc.fastcod_add_streamlines(
+            ctx.ctx, put(tr.xyz), put(off), n_vertices=tr.n_vertices)
+        with pytest.raises(fc.FastCodError) as e:
+            ctx.sync()
+        assert e.value.code == fc.FASTCOD_EINVAL
+        ctx.reset()
+        # coordinate out of range
+        xyz = tr.xyz.copy()
+        xyz[37, 1] = 1 << 24
+        ctx.add_streamlines(put(xyz), put(tr.offsets))
+        with pytest.raises(fc.FastCodError) as e:
+            ctx.connectivity()
+        assert e.value.code == fc.FASTCOD_EINVAL and "coordinate" in str(e.value)
+        # the context is usable again after reset
+        ctx.reset()
+        ctx.add_streamlines(put(tr.xyz), put(tr.offsets))
+        C = ctx.connectivity()
+        Cr, _, _ = oracle.connectivity(vols.roi, vols.lab, vols.dims, vols.n_roi, vols.n_targets, tr.xyz,
+                                       tr.offsets)
+        np.testing.assert_array_equal(C, Cr)
+    finally:
+        ctx.close()
+
+
+def test_misaligned_device_xyz_rejected(fc, tiny0):
+    import torch
+    vols, tr = tiny0
+    with _ctx_with_volumes(fc, vols) as ctx:
+        flat = torch.from_numpy(np.concatenate([np.zeros(1, np.int32), tr.xyz.reshape(-1)])).cuda()
+        off = as_device(tr.offsets)
+        with pytest.raises(fc.FastCodError) as e:
+            fc.fastcod_add_streamlines(ctx.ctx, flat.data_ptr() + 4, off, n_vertices=tr.n_vertices,
+                                       n_streamlines=tr.n_streamlines)
+        assert e.value.code == fc.FASTCOD_EINVAL
+
+
+def test_user_stream_and_reset(fc, tiny0):
+    import torch
+    vols, tr = tiny0
+    s = torch.cuda.Stream()
+    with _ctx_with_volumes(fc, vols) as ctx:
+        fc.fastcod_set_stream(ctx.ctx, s)
+        x, o = as_device(tr.xyz), as_device(tr.offsets)
+        ctx.add_streamlines(x, o)
+        ctx.add_streamlines(x, o)
+        C2 = ctx.connectivity()
+        ctx.reset()
+        assert ctx.connectivity().sum() == 0
+        ctx.add_streamlines(x, o)
+        C1 = ctx.connectivity()
+        np.testing.assert_array_equal(C2, 2 * C1)
+        st = ctx.stats()
+        assert st["streamlines"] == tr.n_streamlines and st["vertices"] == tr.n_vertices

@@ -1,0 +1,133 @@
+"""GPU parity: the CUDA path through the C ABI against the oracle, bit-exact
+(integer counts, tolerance 0), on the golden worked example, adversarial tiny
+grids (ties, off-grid points, T = 0/1, long segments, set overflow), the tiny
+and HCP-shaped synthetic subjects, every loader / prefilter / mode option, and
+host, page-locked and device inputs."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from synth import tiny
+from tests.gpu_helpers import run_gpu
+
+pytestmark = pytest.mark.gpu
+
+U = 1024
+
+
+def _opts(prefilter, staging, target=0, sampling=0):
+    from paper_2302_09247_gb300 import fastcod as fc
+    return {fc.FASTCOD_OPT_PREFILTER: prefilter, fc.FASTCOD_OPT_STAGING: staging,
+            fc.FASTCOD_OPT_TARGET_MODE: target, fc.FASTCOD_OPT_SAMPLING: sampling}
+
+
+def _oracle_flags(target, sampling):
+    return (oracle.TARGET_ENDPOINT if target else 0) | (oracle.VERTEX_SAMPLED if sampling else 0)
+
+
+def _check(roi, lab, dims, N, M, xyz, off, where="device", opts=None, chunks=1, flags=0):
+    C, Ce, st = run_gpu(roi, lab, dims, N, M, xyz, off, where, opts, chunks)
+    Cr, Cer, sr = oracle.connectivity(roi, lab, dims, N, M, xyz, off, flags)
+    np.testing.assert_array_equal(C, Cr)
+    np.testing.assert_array_equal(Ce, Cer)
+    assert st["voxel_steps"] == sr["voxel_steps"]
+    assert st["pairs"] == sr["pairs"]
+    assert st["streamlines"] == len(off) - 1
+    return st, sr
+
+
+def test_golden_toy():
+    d, roi, lab, xyz, off = tiny.toy_fixture(os.path.join(tiny.GOLDEN, "toy_passthrough.json"))
+    for where in ("device", "host"):
+        for staging in (0, 1):
+            C, Ce, _ = run_gpu(roi, lab, d["dims"], d["N"], d["M"], xyz, off, where, _opts(1, staging))
+            assert C.tolist() == d["C_expected"]
+            assert Ce.tolist() == d["C_end_expected"]
+
+
+@pytest.mark.parametrize("seed", range(6))
+@pytest.mark.parametrize("prefilter,staging", [(1, 1), (1, 0), (0, 1)])
+@pytest.mark.parametrize("target,sampling", [(0, 0), (1, 0), (0, 1)])
+def test_adversarial_tiny(seed, prefilter, staging, target, sampling):
+    rng = np.random.default_rng(1000 + seed)
+    dims = tuple(int(v) for v in rng.integers(3, 10, size=3))
+    roi, lab, N, M = tiny.random_volumes(rng, dims, n_roi=6, n_labels=int(rng.integers(1, 7)),
+                                         many_to_one=bool(seed % 2))
+    xyz, off = tiny.random_streamlines(rng, dims, 300, max_len=40)
+    _check(roi, lab, dims, N, M, xyz, off, "device", _opts(prefilter, staging, target, sampling),
+           flags=_oracle_flags(target, sampling))
+
+
+def test_long_segments_wide_walk():
+    # segment extents >= 2^16 units take the 64-bit walk; coordinates near 2^23
+    rng = np.random.default_rng(7)
+    dims = (40, 30, 20)
+    roi, lab, N, M = tiny.random_volumes(rng, dims, n_roi=0, n_labels=5, p_roi=0.05, p_lab=0.1)
+    n = 200
+    pts = []
+    counts = []
+    for _ in range(n):
+        T = int(rng.integers(2, 6))
+        v = rng.integers(-(1 << 23), 1 << 23, size=(T, 3))
+        v[:, :] = np.clip(v, -60 * U, 60 * U) if rng.random() < 0.7 else v
+        pts.append(v)
+        counts.append(T)
+    off = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(counts, out=off[1:])
+    xyz = np.concatenate(pts).astype(np.int32)
+    for staging in (0, 1):
+        _check(roi, lab, dims, N, M, xyz, off, "device", _opts(1, staging))
+
+
+def test_set_overflow_path():
+    # every voxel is its own ROI row and carries one of 200 labels; straight
+    # streamlines across the grid meet more rows and labels than the on-chip
+    # tables hold, so the exact global-memory path runs
+    rng = np.random.default_rng(8)
+    dims = (64, 40, 24)
+    nvox = dims[0] * dims[1] * dims[2]
+    roi = np.arange(nvox, dtype=np.int32).reshape(dims[2], dims[1], dims[0])
+    lab = rng.integers(0, 201, size=nvox).astype(np.uint16).reshape(roi.shape)
+    n, T = 150, 9
+    xyz = rng.integers(0, np.array(dims) * U, size=(n, T, 3)).reshape(-1, 3).astype(np.int32)
+    off = np.arange(0, T * n + 1, T, dtype=np.int64)
+    st, _ = _check(roi, lab, dims, nvox, 200, xyz, off, "device", _opts(1, 1))
+    assert st["overflow"] > 0
+
+
+@pytest.mark.parametrize("where", ["device", "host", "pinned"])
+def test_cfg0_full(where):
+    vols, tr = synth.make_subject(0)
+    st, sr = _check(vols.roi, vols.lab, vols.dims, vols.n_roi, vols.n_targets, tr.xyz, tr.offsets, where)
+    assert sr["n_contributing"] <= st["survivors"] <= tr.n_streamlines
+
+
+def test_cfg0_chunked_and_options():
+    vols, tr = synth.make_subject(0)
+    for prefilter, staging in ((1, 1), (0, 0), (1, 0)):
+        _check(vols.roi, vols.lab, vols.dims, vols.n_roi, vols.n_targets, tr.xyz, tr.offsets, "device",
+               _opts(prefilter, staging), chunks=7)
+
+
+def test_cfg1_subset_all_modes():
+    vols, tr = synth.make_subject(1, n_streamlines=200_000)
+    for target, sampling in ((0, 0), (1, 0), (0, 1)):
+        _check(vols.roi, vols.lab, vols.dims, vols.n_roi, vols.n_targets, tr.xyz, tr.offsets, "device",
+               _opts(1, 1, target, sampling), flags=_oracle_flags(target, sampling))
+
+
+def test_cfg1_full_bench_configuration():
+    # HCP-shaped subject, 2,000,000 streamlines, device-resident inputs and the
+    # default loader: the configuration the benchmark times
+    vols, tr = synth.make_subject(1)
+    C, Ce, st = run_gpu(vols.roi, vols.lab, vols.dims, vols.n_roi, vols.n_targets, tr.xyz, tr.offsets, "device")
+    Cr, Cer, sr = oracle.connectivity_chunked(vols.roi, vols.lab, vols.dims, vols.n_roi, vols.n_targets, tr.xyz,
+                                              tr.offsets)
+    np.testing.assert_array_equal(C, Cr)
+    np.testing.assert_array_equal(Ce, Cer)
+    assert st["voxel_steps"] == sr["voxel_steps"]
+    assert st["pairs"] == sr["pairs"]
+    assert sr["n_contributing"] <= st["survivors"]
