@@ -17,7 +17,7 @@
  *   - vertices are int32 fixed point, 1 unit = 1/1024 voxel; voxel (i,j,k)
  *     covers [1024 i, 1024 i + 1024) x [1024 j, ..) x [1024 k, ..), so the
  *     voxel of a vertex is its coordinates shifted right by 10 (floor, also
- *     for negative values); |coordinate| < 2^24 is required;
+ *     for negative values); every coordinate must lie in [-2^24, 2^24);
  *   - xyz is [n_vertices][3] (x, y, z interleaved); offsets is int64
  *     [n_streamlines + 1] with offsets[0] = 0, non-decreasing,
  *     offsets[n_streamlines] = n_vertices; streamline s is vertices
@@ -86,12 +86,22 @@ enum {
   /* voxel rule: 0 (default) = continuous segments; 1 = vertices only (the
    * point-sampled reading behind the paper's upsampling rule, Section 3). */
   FASTCOD_OPT_SAMPLING = 3,
-  /* vertex staging of the prefilter: 0 = direct loads, 1 (default) = TMA
-   * bulk copies into shared memory. Results are identical. */
+  /* vertex staging of the prefilter: 0 (default) = direct vectorised
+   * streaming loads, 1 = 1-D TMA bulk copies into a per-warp shared-memory
+   * ring.  Results are identical. */
   FASTCOD_OPT_STAGING = 4,
   /* 1: record CUDA events around every stage on the context's stream and
    * accumulate their durations (fastcod_get_profile); 0 (default): off. */
-  FASTCOD_OPT_PROFILE = 5
+  FASTCOD_OPT_PROFILE = 5,
+  /* CTAs per SM the prefilter is compiled for: 3 (default, up to 80
+   * registers per thread) or 4 (64 registers, more resident warps).  Results
+   * are identical. */
+  FASTCOD_OPT_PREFILTER_CTAS = 6,
+  /* cell of the prefilter's near grid: (1 << value)^3 voxels, 0..3 (default
+   * 1).  Coarser cells keep the grid in L1 and let more streamlines through
+   * to the exact walk.  Results are identical.  Applies to volumes installed
+   * afterwards. */
+  FASTCOD_OPT_NEAR_LOG2 = 7
 };
 
 typedef struct fastcod_ctx fastcod_ctx;
@@ -140,8 +150,9 @@ FASTCOD_API int fastcod_set_volumes(fastcod_ctx* ctx, const int32_t* roi_index_m
                                     int32_t dim_z, int32_t n_roi, int32_t n_targets);
 
 /* Accumulate streamlines into C and C_end (the passthrough count of
- * Algorithm 2 for every streamline; Algorithm 1's count for C_end).  May be called many times;
- * the result depends only on the multiset of streamlines added. */
+ * Algorithm 2 for every streamline; Algorithm 1's count for C_end).  May be
+ * called many times; the result depends only on the multiset of streamlines
+ * added.  At most 2^31 - 1 vertices per call. */
 FASTCOD_API int fastcod_add_streamlines(fastcod_ctx* ctx, const int32_t* xyz, int64_t n_vertices,
                                         const int64_t* offsets, int64_t n_streamlines);
 

@@ -2,9 +2,9 @@
  * ORACLE - TEST INFRASTRUCTURE ONLY (see oracle.h).
  *
  * Plain single-threaded C99.  Every quantity is an integer; rational
- * comparisons are exact int64 cross-multiplications.  With |coordinate| <
- * 2^24 every numerator is below 2^26 and every denominator below 2^25, so
- * the products stay below 2^51.
+ * comparisons are exact int64 cross-multiplications.  With coordinates in
+ * [-2^24, 2^24) every numerator is at most 2^25 + 1024 and every denominator
+ * at most 2^25, so the products stay below 2^51.
  */
 #include "oracle.h"
 
@@ -248,7 +248,7 @@ static int validate(const int32_t* roi, const uint16_t* lab, const int32_t dims[
   for (int64_t s = 0; s < ns; ++s)
     if (offsets[s + 1] < offsets[s]) return -1;
   for (int64_t i = 0; i < 3 * offsets[ns]; ++i)
-    if (xyz[i] <= -COORD_LIMIT || xyz[i] >= COORD_LIMIT) return -1;
+    if (xyz[i] < -COORD_LIMIT || xyz[i] >= COORD_LIMIT) return -1;
   return 0;
 }
 

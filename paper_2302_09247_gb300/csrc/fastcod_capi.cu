@@ -8,7 +8,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/fastcod.h"
+#include "fastcod.h"
 #include "fc_internal.cuh"
 
 using fc::DevState;
@@ -25,9 +25,11 @@ struct fastcod_ctx {
   int32_t dims[3] = {0, 0, 0};
   int32_t bdims[3] = {0, 0, 0};
   int32_t N = 0, M = 0;
+  int32_t near_shift = 1;  // cell size of the installed near grid
   uint32_t* d_code = nullptr;
   uint16_t* d_lab = nullptr;
   uint32_t* d_bricks = nullptr;
+  uint32_t* d_near = nullptr;
   int32_t* d_C = nullptr;
   int32_t* d_Cend = nullptr;
   uint32_t* d_scratch = nullptr;
@@ -51,7 +53,9 @@ struct fastcod_ctx {
   int64_t total_vertices = 0;
   int prefilter = 1;
   uint32_t mode = 0;
-  int staging_tma = 1;
+  int staging_tma = 0;
+  int prefilter_ctas = 3;
+  int near_log2 = 1;       // near grid cell: (1 << near_log2)^3 voxels
   int profile = 0;
   struct EvSet {
     cudaEvent_t e[5];
@@ -117,12 +121,14 @@ void free_volumes(fastcod_ctx* c) {
   cudaFree(c->d_code);
   cudaFree(c->d_lab);
   cudaFree(c->d_bricks);
+  cudaFree(c->d_near);
   cudaFree(c->d_C);
   cudaFree(c->d_Cend);
   cudaFree(c->d_scratch);
   c->d_code = nullptr;
   c->d_lab = nullptr;
   c->d_bricks = nullptr;
+  c->d_near = nullptr;
   c->d_C = nullptr;
   c->d_Cend = nullptr;
   c->d_scratch = nullptr;
@@ -151,7 +157,7 @@ int sync_check(fastcod_ctx* c) {
                   "offsets invalid near streamline %d: need offsets[0]=0, non-decreasing, offsets[n]=n_vertices",
                   h.error_info);
     case fc::kErrCoord:
-      return fail(c, FASTCOD_EINVAL, "vertex coordinate out of range (|c| >= 2^24) in streamline %d", h.error_info);
+      return fail(c, FASTCOD_EINVAL, "vertex coordinate outside [-2^24, 2^24) (warp range %d)", h.error_info);
     case fc::kErrVolume:
       return fail(c, FASTCOD_EINVAL, "volume value out of range at voxel %d", h.error_info);
     case fc::kErrTimeout:
@@ -166,12 +172,18 @@ fc::VolView vol_view(const fastcod_ctx* c) {
   v.code = c->d_code;
   v.lab = c->d_lab;
   v.bricks = c->d_bricks;
+  v.near = c->d_near;
   v.dx = c->dims[0];
   v.dy = c->dims[1];
   v.dz = c->dims[2];
   v.bx = c->bdims[0];
   v.by = c->bdims[1];
   v.bz = c->bdims[2];
+  v.nsh = c->near_shift;
+  const int32_t cs = 1 << v.nsh;
+  v.nwx = ((c->dims[0] + 2 + cs - 1) / cs + 15) / 16;
+  v.nny = (c->dims[1] + 2 + cs - 1) / cs;
+  v.nnz = (c->dims[2] + 2 + cs - 1) / cs;
   v.n_roi = c->N;
   v.n_lab = c->M;
   return v;
@@ -385,12 +397,26 @@ FASTCOD_API int fastcod_set_volumes(fastcod_ctx* c, const int32_t* roi, const ui
   c->scratch_ctas = (int32_t)ctas;
   CU(cudaMalloc(&c->d_scratch, (size_t)(ctas * words * 4)));
   CU(cudaMemsetAsync(c->d_scratch, 0, (size_t)(ctas * words * 4), c->stream));
+  // near grid (the prefilter's dilated occupancy)
+  c->near_shift = c->near_log2;
   fc::VolView v = vol_view(c);
+  const int64_t near_words = (int64_t)v.nwx * v.nny * v.nnz;
+  const int64_t pad_vox = (int64_t)(dx + 2) * (dy + 2) * (dz + 2);
+  CU(cudaMalloc(&c->d_near, (size_t)near_words * 4));
+  v.near = c->d_near;
   CU(fc::launch_volume_prep(d_roi, d_labin, nvox, v, c->d_code, c->d_lab, c->d_bricks, c->d_state, c->stream));
   int rc = sync_check(c);
   if (rc) {
     free_volumes(c);
     return rc;
+  }
+  {
+    uint8_t* tmp = nullptr;
+    CU(cudaMalloc(&tmp, (size_t)pad_vox * 2));
+    cudaError_t e = fc::launch_near(v, tmp, c->d_near, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    cudaFree(tmp);
+    CU(e);
   }
   c->has_vol = true;
   return zero_accumulators(c);
@@ -406,7 +432,7 @@ FASTCOD_API int fastcod_add_streamlines(fastcod_ctx* c, const int32_t* xyz, int6
   if (!offsets || (nv > 0 && !xyz)) return fail(c, FASTCOD_EINVAL, "input pointer is NULL");
   if (c->total_streamlines + ns > 0x7fffffffLL)
     return fail(c, FASTCOD_EOVERFLOW, "more than 2^31-1 streamlines since the last reset");
-  if (nv > ((int64_t)1 << 40)) return fail(c, FASTCOD_EINVAL, "too many vertices");
+  if (nv > 0x7fffffffLL) return fail(c, FASTCOD_EINVAL, "more than 2^31-1 vertices in one call: split the call");
   CU(cudaSetDevice(c->device));
   const int kx = nv > 0 ? ptr_kind(xyz, c->device) : 1;
   const int ko = ptr_kind(offsets, c->device);
@@ -447,8 +473,8 @@ FASTCOD_API int fastcod_add_streamlines(fastcod_ctx* c, const int32_t* xyz, int6
   acc.C = c->d_C;
   acc.Cend = c->d_Cend;
   if (int rc = record(c, 1)) return rc;
-  CU(fc::launch_prefilter(t, v, c->prefilter != 0, c->mode, c->staging_tma != 0, c->d_surv, c->d_state,
-                          c->num_sms, c->stream));
+  CU(fc::launch_prefilter(t, v, c->prefilter != 0, c->mode, c->staging_tma != 0, c->prefilter_ctas, c->d_surv,
+                          c->d_state, c->num_sms, c->stream));
   if (int rc = record(c, 2)) return rc;
   CU(fc::launch_walk(t, v, c->d_surv, acc, c->mode, c->d_ovf, c->d_state, c->num_sms, c->stream));
   if (int rc = record(c, 3)) return rc;
@@ -544,6 +570,14 @@ FASTCOD_API int fastcod_set_option(fastcod_ctx* c, int32_t key, int64_t value) {
     case FASTCOD_OPT_STAGING:
       if (value != 0 && value != 1) break;
       c->staging_tma = (int)value;
+      return FASTCOD_OK;
+    case FASTCOD_OPT_PREFILTER_CTAS:
+      if (value != 3 && value != 4) break;
+      c->prefilter_ctas = (int)value;
+      return FASTCOD_OK;
+    case FASTCOD_OPT_NEAR_LOG2:
+      if (value < 0 || value > 3) break;
+      c->near_log2 = (int)value;
       return FASTCOD_OK;
     case FASTCOD_OPT_PROFILE:
       if (value != 0 && value != 1) break;

@@ -26,7 +26,7 @@ constexpr uint32_t kCodeRowMask = 0x3fffffffu;
 enum DevError : int32_t {
   kErrNone = 0,
   kErrOffsets = 1,      // offsets not monotone, out of [0, n_vertices], or bad ends
-  kErrCoord = 2,        // |coordinate| >= 2^24
+  kErrCoord = 2,        // coordinate outside [-2^24, 2^24)
   kErrVolume = 3,       // roi or label value out of range
   kErrTimeout = 4,      // a bounded wait gave up
   kErrOverflowList = 5  // overflow list capacity exceeded (cannot happen by construction)
@@ -53,10 +53,23 @@ struct VolView {
   const uint32_t* code;   // [nvox] per-voxel code
   const uint16_t* lab;    // [nvox] labels (read for labelled ROI voxels)
   const uint32_t* bricks; // brick occupancy words
+  const uint32_t* near;   // dilated occupancy (see below)
   int32_t dx, dy, dz;     // grid
   int32_t bx, by, bz;     // brick grid
+  int32_t nwx, nny, nnz;  // near grid: words per x-row, rows, planes (in cells)
+  int32_t nsh;            // near grid cell = (1 << nsh)^3 padded voxels
   int32_t n_roi, n_lab;   // N, M
 };
+
+// Near grid: for every voxel v of the grid grown by one voxel on each side,
+// two bits (bit 0: some voxel within Chebyshev distance 1 of v has an ROI row,
+// bit 1: ... has a label), ORed over cells of (1 << nsh)^3 padded voxels,
+// sixteen cells along x per 32-bit word.  Voxel (x, y, z) sits at padded
+// position (x+1, y+1, z+1), in cell (cx, cy, cz) = padded >> nsh:
+//   word = (cx >> 4) + nwx * (cy + nny * cz),  shift = (cx & 15) * 2.
+// A segment whose end voxels differ by at most one on every axis lies in the
+// 3x3x3 block around either end, so the near bits of its end voxel (and of
+// the cell holding it) cover it.
 
 // One batch of streamlines on the device.
 struct Tract {
@@ -83,10 +96,13 @@ cudaError_t launch_volume_max(const int32_t* roi, const uint16_t* lab, int64_t n
 cudaError_t launch_volume_prep(const int32_t* roi, const uint16_t* lab, int64_t nvox, VolView v,
                                uint32_t* code, uint16_t* lab_out, uint32_t* bricks, DevState* st,
                                cudaStream_t s);
+// Near grid from the per-voxel code; tmp: two byte planes of the padded grid.
+cudaError_t launch_near(const VolView& v, uint8_t* tmp, uint32_t* near, cudaStream_t s);
 
 // K2: prefilter + compaction (+ validation and voxel-step count).
+// ctas_per_sm: 3 or 4 (the register budget the kernel is compiled for).
 cudaError_t launch_prefilter(const Tract& t, const VolView& v, bool prefilter, uint32_t mode,
-                             bool tma, int32_t* survivors, DevState* st, int num_sms,
+                             bool tma, int ctas_per_sm, int32_t* survivors, DevState* st, int num_sms,
                              cudaStream_t s);
 
 // K3: warp-per-streamline walk, dedup, accumulate; overflow path.

@@ -14,7 +14,8 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_lib", "libfastcod.so")
+# FASTCOD_LIBRARY overrides the in-tree build (e.g. a custom build of the same sources)
+LIB_PATH = os.environ.get("FASTCOD_LIBRARY") or os.path.join(_HERE, "_lib", "libfastcod.so")
 
 FASTCOD_OK = 0
 FASTCOD_EINVAL = -1
@@ -32,6 +33,8 @@ FASTCOD_OPT_TARGET_MODE = 2
 FASTCOD_OPT_SAMPLING = 3
 FASTCOD_OPT_STAGING = 4
 FASTCOD_OPT_PROFILE = 5
+FASTCOD_OPT_PREFILTER_CTAS = 6
+FASTCOD_OPT_NEAR_LOG2 = 7
 
 EXPORTED = [
     "fastcod_create", "fastcod_destroy", "fastcod_set_stream", "fastcod_set_volumes",

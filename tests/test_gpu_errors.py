@@ -101,6 +101,12 @@ def test_device_detected_input_errors_then_reset(fc, tiny0, where, staging):
         with pytest.raises(fc.FastCodError) as e:
             ctx.connectivity()
         assert e.value.code == fc.FASTCOD_EINVAL and "coordinate" in str(e.value)
+        ctx.reset()
+        # the lower end of [-2^24, 2^24) is valid
+        xyz = tr.xyz.copy()
+        xyz[37, 1] = -(1 << 24)
+        ctx.add_streamlines(put(xyz), put(tr.offsets))
+        ctx.sync()
         # the context is usable again after reset
         ctx.reset()
         ctx.add_streamlines(put(tr.xyz), put(tr.offsets))

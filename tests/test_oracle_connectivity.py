@@ -262,6 +262,12 @@ def test_invalid_inputs_rejected():
     bad[0, 0] = 1 << 24
     with pytest.raises(ValueError):
         oracle.connectivity(roi, lab, (2, 2, 2), 1, 1, bad, good)
+    edge = xyz.copy()
+    edge[0, 0] = -(1 << 24)  # the lower end of [-2^24, 2^24) is allowed
+    oracle.connectivity(roi, lab, (2, 2, 2), 1, 1, edge, good)
+    edge[0, 0] = -(1 << 24) - 1
+    with pytest.raises(ValueError):
+        oracle.connectivity(roi, lab, (2, 2, 2), 1, 1, edge, good)
     lab2 = lab.copy()
     lab2[0, 0, 0] = 2
     with pytest.raises(ValueError):
