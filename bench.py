@@ -199,7 +199,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="fastcod", choices=["fastcod", "reference"])
     ap.add_argument("--config", type=int, default=1, choices=[0, 1, 2])
-    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--e2e-steps", type=int, default=10, help="0 skips the end-to-end leg")
+    ap.add_argument("--streamlines", type=int, default=None,
+                    help="use only the first N streamlines of the subject (small profiling cases)")
     ap.add_argument("--cpu-sample", type=int, default=1_000_000)
     ap.add_argument("--ref-sample", type=int, default=200_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -226,6 +228,8 @@ def main():
     ss = synth.streamline_spec(args.config)
     if rank:
         ss.seed = ss.seed + 7919 * rank
+    if args.streamlines is not None:
+        ss.n_streamlines = min(ss.n_streamlines, args.streamlines)
     vols = synth.make_volumes(vs)
     tr = synth.make_tractogram(vs, ss, vols)
 
@@ -293,29 +297,32 @@ def main():
     gpu_launches = prof["kernel_launches"] - launches0
 
     # ------------------------------------------------ end to end, host buffers
-    xyz_h = torch.from_numpy(tr.xyz).pin_memory()
-    off_h = torch.from_numpy(tr.offsets).pin_memory()
-    N, M = ctx.shape()
-    C_h = torch.empty((N, M), dtype=torch.int32).pin_memory()
-    Ce_h = torch.empty((N, M), dtype=torch.int32).pin_memory()
-    for _ in range(2):
-        fc.fastcod_reset(ctx.ctx)
-        fc.fastcod_add_streamlines(ctx.ctx, xyz_h, off_h)
-        fc.fastcod_connectivity(ctx.ctx, C_h)
-        fc.fastcod_endpoint_connectivity(ctx.ctx, Ce_h)
-    _barrier(ws)
-    t0 = time.perf_counter()
-    for _ in range(args.e2e_steps):
-        fc.fastcod_reset(ctx.ctx)
-        fc.fastcod_add_streamlines(ctx.ctx, xyz_h, off_h)
-        fc.fastcod_connectivity(ctx.ctx, C_h)
-        fc.fastcod_endpoint_connectivity(ctx.ctx, Ce_h)
-    e2e_s = time.perf_counter() - t0
-    assert np.array_equal(C_h.numpy(), C_first)
-    e2e_max = _barrier_max(ws, e2e_s)
-    e2e_value = _barrier_sum(ws, float(st["voxel_steps"])) * args.e2e_steps / e2e_max
-    h2d = xyz_h.numel() * 4 + off_h.numel() * 8
-    d2h = 2 * N * M * 4
+    e2e = None
+    if args.e2e_steps > 0:
+        xyz_h = torch.from_numpy(tr.xyz).pin_memory()
+        off_h = torch.from_numpy(tr.offsets).pin_memory()
+        N, M = ctx.shape()
+        C_h = torch.empty((N, M), dtype=torch.int32).pin_memory()
+        Ce_h = torch.empty((N, M), dtype=torch.int32).pin_memory()
+        for _ in range(2):
+            fc.fastcod_reset(ctx.ctx)
+            fc.fastcod_add_streamlines(ctx.ctx, xyz_h, off_h)
+            fc.fastcod_connectivity(ctx.ctx, C_h)
+            fc.fastcod_endpoint_connectivity(ctx.ctx, Ce_h)
+        _barrier(ws)
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            fc.fastcod_reset(ctx.ctx)
+            fc.fastcod_add_streamlines(ctx.ctx, xyz_h, off_h)
+            fc.fastcod_connectivity(ctx.ctx, C_h)
+            fc.fastcod_endpoint_connectivity(ctx.ctx, Ce_h)
+        e2e_s = time.perf_counter() - t0
+        assert np.array_equal(C_h.numpy(), C_first)
+        e2e_max = _barrier_max(ws, e2e_s)
+        e2e_value = _barrier_sum(ws, float(st["voxel_steps"])) * args.e2e_steps / e2e_max
+        e2e = {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": xyz_h.numel() * 4 + off_h.numel() * 8,
+               "d2h_bytes_per_step": 2 * N * M * 4, "ms_per_step": 1000 * e2e_max / args.e2e_steps,
+               "steps": args.e2e_steps}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -332,8 +339,7 @@ def main():
             "overflow_per_step": st["overflow"], "pairs_per_step": st["pairs"],
             "C_sum": int(C_first.sum()),
             "roofline": roofline,
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                    "ms_per_step": 1000 * e2e_max / args.e2e_steps, "steps": args.e2e_steps},
+            "e2e": e2e,
             "cpu_baseline": cpu,
             "gpu_launches": gpu_launches,
             "clocks": clk,

@@ -101,7 +101,12 @@ enum {
    * 1).  Coarser cells keep the grid in L1 and let more streamlines through
    * to the exact walk.  Results are identical.  Applies to volumes installed
    * afterwards. */
-  FASTCOD_OPT_NEAR_LOG2 = 7
+  FASTCOD_OPT_NEAR_LOG2 = 7,
+  /* 1 (default): fastcod_batch_run picks the prefilter's CTAs per SM and
+   * near-grid cell per batch shape by timed trials on the first batch of that
+   * shape (cached in the context, and in the file named by the environment
+   * variable FASTCOD_TUNE_CACHE when set); 0: use the options as set. */
+  FASTCOD_OPT_AUTOTUNE = 8
 };
 
 typedef struct fastcod_ctx fastcod_ctx;
@@ -142,7 +147,7 @@ FASTCOD_API int fastcod_set_stream(fastcod_ctx* ctx, void* cuda_stream);
 
 /* Install the volumes (Section 2: the ROI voxel set V = {v_1..v_N} and the
  * target regions R = {R_1..R_M}; loc2region).  dims are Dx, Dy, Dz (> 0,
- * product < 2^31).  n_roi = N (0: max(roi)+1); n_targets = M (0: max label).
+ * product < 2^31, Dy and Dz <= 65533).  n_roi = N (0: max(roi)+1); n_targets = M (0: max label).
  * Requires -1 <= roi < N, label <= M, N < 2^30, M < 65536.  Zeroes C,
  * C_end and the statistics.  Blocks until the volumes are validated. */
 FASTCOD_API int fastcod_set_volumes(fastcod_ctx* ctx, const int32_t* roi_index_map,
@@ -181,6 +186,50 @@ FASTCOD_API int fastcod_get_profile(fastcod_ctx* ctx, fastcod_profile* out);
 
 /* Set an option (FASTCOD_OPT_*). */
 FASTCOD_API int fastcod_set_option(fastcod_ctx* ctx, int32_t key, int64_t value);
+
+/* ---------------------------------------------------------------- batched
+ * Many subjects in one pass: every subject's volumes are prepared, all
+ * subjects' streamlines are prefiltered in one launch (dynamic tasks of one
+ * subject's streamline range each), all survivors walked in one launch, the
+ * whole sequence captured once per batch shape as a CUDA graph and replayed.
+ * Each subject's C and C_end are computed from zero, exactly as
+ * fastcod_set_volumes + fastcod_add_streamlines would, and written to its
+ * caller-allocated outputs.  Pointers follow the same host/device rules as
+ * the single-subject calls.  The context's installed volumes and
+ * accumulators are not touched. */
+typedef struct {
+  const int32_t* roi_index_map;   /* [Dz][Dy][Dx], -1 or a row < n_roi */
+  const uint16_t* target_labels;  /* [Dz][Dy][Dx], 0 or a label <= n_targets */
+  int32_t dims[3];                /* Dx, Dy, Dz */
+  int32_t n_roi;                  /* N (> 0, given explicitly) */
+  int32_t n_targets;              /* M (> 0, given explicitly) */
+  const int32_t* xyz;             /* [n_vertices][3], 16-byte aligned if on the device */
+  int64_t n_vertices;
+  const int64_t* offsets;         /* [n_streamlines + 1] */
+  int64_t n_streamlines;
+  int32_t* C_out;                 /* [N][M] */
+  int32_t* Cend_out;              /* [N][M] */
+} fastcod_subject;
+
+typedef struct {
+  int32_t n_subjects;
+  int32_t tasks;          /* prefilter tasks of the last batch */
+  int32_t prefilter_ctas; /* configuration the last batch ran with */
+  int32_t near_log2;
+  int32_t graph_reused;   /* 1: the last batch replayed a captured graph */
+  int32_t tuned;          /* 1: the last batch ran the autotuner's trials */
+  double ms_graph;        /* device time of the last batch's graph (CUDA events) */
+} fastcod_batch_info;
+
+/* Run a batch of 1..128 subjects (the sum of their streamlines < 2^31).
+ * Blocks until every output is written; errors name the subject. */
+FASTCOD_API int fastcod_batch_run(fastcod_ctx* ctx, const fastcod_subject* subjects, int32_t n_subjects);
+
+/* Statistics of subject i of the last batch. */
+FASTCOD_API int fastcod_batch_get_stats(fastcod_ctx* ctx, int32_t subject, fastcod_stats* out);
+
+/* Shape and configuration of the last batch. */
+FASTCOD_API int fastcod_batch_get_info(fastcod_ctx* ctx, fastcod_batch_info* out);
 
 /* Message of the last error on this context ("" if none); owned by ctx,
  * valid until the next call on it.  NULL ctx: message of the last failed

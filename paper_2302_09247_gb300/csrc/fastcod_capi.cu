@@ -8,69 +8,9 @@
 #include <string>
 #include <vector>
 
-#include "fastcod.h"
-#include "fc_internal.cuh"
+#include "fc_ctx.h"
 
-using fc::DevState;
-
-struct fastcod_ctx {
-  int device = 0;
-  uint32_t flags = 0;
-  int num_sms = 0;
-  cudaStream_t own_stream = nullptr;
-  cudaStream_t stream = nullptr;
-
-  // volumes
-  bool has_vol = false;
-  int32_t dims[3] = {0, 0, 0};
-  int32_t bdims[3] = {0, 0, 0};
-  int32_t N = 0, M = 0;
-  int32_t near_shift = 1;  // cell size of the installed near grid
-  uint32_t* d_code = nullptr;
-  uint16_t* d_lab = nullptr;
-  uint32_t* d_bricks = nullptr;
-  uint32_t* d_near = nullptr;
-  int32_t* d_C = nullptr;
-  int32_t* d_Cend = nullptr;
-  uint32_t* d_scratch = nullptr;
-  int32_t scratch_ctas = 0;
-
-  // staging of host inputs and per-call lists
-  void* d_vstage = nullptr;
-  size_t vstage_bytes = 0;
-  int32_t* d_xyz = nullptr;
-  size_t xyz_bytes = 0;
-  int64_t* d_off = nullptr;
-  size_t off_bytes = 0;
-  int32_t* d_surv = nullptr;
-  size_t surv_bytes = 0;
-  int32_t* d_ovf = nullptr;
-  size_t ovf_bytes = 0;
-
-  DevState* d_state = nullptr;
-
-  int64_t total_streamlines = 0;
-  int64_t total_vertices = 0;
-  int prefilter = 1;
-  uint32_t mode = 0;
-  int staging_tma = 0;
-  int prefilter_ctas = 3;
-  int near_log2 = 1;       // near grid cell: (1 << near_log2)^3 voxels
-  int profile = 0;
-  struct EvSet {
-    cudaEvent_t e[5];
-  };
-  std::vector<EvSet> ev_pool;  // event sets of profiled calls
-  size_t ev_used = 0;          // sets recorded and not yet folded into prof
-  EvSet* ev_cur = nullptr;
-  fastcod_profile prof = {0, 0, 0.0, 0.0, 0.0, 0.0};
-
-  std::string err;
-};
-
-namespace {
-
-thread_local std::string g_create_err;
+namespace fcapi {
 
 int fail(fastcod_ctx* c, int code, const char* fmt, ...) {
   char buf[512];
@@ -82,17 +22,6 @@ int fail(fastcod_ctx* c, int code, const char* fmt, ...) {
   return code;
 }
 
-#define CU(call)                                                                                   \
-  do {                                                                                             \
-    cudaError_t e_ = (call);                                                                       \
-    if (e_ != cudaSuccess) {                                                                       \
-      (void)cudaGetLastError();                                                                    \
-      return fail(c, e_ == cudaErrorMemoryAllocation ? FASTCOD_ENOMEM : FASTCOD_ECUDA, "%s: %s",   \
-                  #call, cudaGetErrorString(e_));                                                  \
-    }                                                                                              \
-  } while (0)
-
-// 0 = host memory, 1 = device memory of dev, -1 = device memory elsewhere
 int ptr_kind(const void* p, int dev) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
@@ -116,6 +45,16 @@ int grow(fastcod_ctx* c, void** p, size_t* cap, size_t need) {
   *cap = n;
   return FASTCOD_OK;
 }
+
+}  // namespace fcapi
+
+namespace {
+
+using fcapi::fail;
+using fcapi::grow;
+using fcapi::ptr_kind;
+
+thread_local std::string g_create_err;
 
 void free_volumes(fastcod_ctx* c) {
   cudaFree(c->d_code);
@@ -317,6 +256,7 @@ FASTCOD_API int fastcod_destroy(fastcod_ctx* c) {
   cudaFree(c->d_off);
   cudaFree(c->d_surv);
   cudaFree(c->d_ovf);
+  fcapi::batch_free(c);
   cudaFree(c->d_state);
   for (auto& set : c->ev_pool)
     for (int i = 0; i < 5; ++i) cudaEventDestroy(set.e[i]);
@@ -340,6 +280,7 @@ FASTCOD_API int fastcod_set_volumes(fastcod_ctx* c, const int32_t* roi, const ui
   if (dx <= 0 || dy <= 0 || dz <= 0) return fail(c, FASTCOD_EINVAL, "grid dims must be > 0");
   const int64_t nvox = (int64_t)dx * dy * dz;
   if (nvox >= ((int64_t)1 << 31)) return fail(c, FASTCOD_EINVAL, "grid has >= 2^31 voxels");
+  if (dy > 65533 || dz > 65533) return fail(c, FASTCOD_EINVAL, "Dy and Dz must be <= 65533");
   if (!roi || !lab) return fail(c, FASTCOD_EINVAL, "volume pointer is NULL");
   if (n_roi < 0 || n_targets < 0) return fail(c, FASTCOD_EINVAL, "N and M must be >= 0");
   CU(cudaSetDevice(c->device));
@@ -461,8 +402,8 @@ FASTCOD_API int fastcod_add_streamlines(fastcod_ctx* c, const int32_t* xyz, int6
     rc = grow(c, (void**)&c->d_ovf, &c->ovf_bytes, (size_t)ns * 4);
     if (rc) return rc;
   }
-  // per-call counters: n_survivors, n_overflow, work_next
-  CU(cudaMemsetAsync(&c->d_state->n_survivors, 0, 3 * sizeof(uint32_t), c->stream));
+  // per-call counters: n_survivors, n_overflow, work_next, work_task
+  CU(cudaMemsetAsync(&c->d_state->n_survivors, 0, 4 * sizeof(uint32_t), c->stream));
   fc::Tract t;
   t.xyz = d_xyz;
   t.off = d_off;
@@ -578,6 +519,10 @@ FASTCOD_API int fastcod_set_option(fastcod_ctx* c, int32_t key, int64_t value) {
     case FASTCOD_OPT_NEAR_LOG2:
       if (value < 0 || value > 3) break;
       c->near_log2 = (int)value;
+      return FASTCOD_OK;
+    case FASTCOD_OPT_AUTOTUNE:
+      if (value != 0 && value != 1) break;
+      c->autotune = (int)value;
       return FASTCOD_OK;
     case FASTCOD_OPT_PROFILE:
       if (value != 0 && value != 1) break;

@@ -1,0 +1,92 @@
+// Host-side internals of libfastcod shared by the C-ABI translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "fastcod.h"
+#include "fc_internal.cuh"
+
+using fc::DevState;
+
+struct BatchState;
+
+struct fastcod_ctx {
+  int device = 0;
+  uint32_t flags = 0;
+  int num_sms = 0;
+  cudaStream_t own_stream = nullptr;
+  cudaStream_t stream = nullptr;
+
+  // volumes
+  bool has_vol = false;
+  int32_t dims[3] = {0, 0, 0};
+  int32_t bdims[3] = {0, 0, 0};
+  int32_t N = 0, M = 0;
+  int32_t near_shift = 1;  // cell size of the installed near grid
+  uint32_t* d_code = nullptr;
+  uint16_t* d_lab = nullptr;
+  uint32_t* d_bricks = nullptr;
+  uint32_t* d_near = nullptr;
+  int32_t* d_C = nullptr;
+  int32_t* d_Cend = nullptr;
+  uint32_t* d_scratch = nullptr;
+  int32_t scratch_ctas = 0;
+
+  // staging of host inputs and per-call lists
+  void* d_vstage = nullptr;
+  size_t vstage_bytes = 0;
+  int32_t* d_xyz = nullptr;
+  size_t xyz_bytes = 0;
+  int64_t* d_off = nullptr;
+  size_t off_bytes = 0;
+  int32_t* d_surv = nullptr;
+  size_t surv_bytes = 0;
+  int32_t* d_ovf = nullptr;
+  size_t ovf_bytes = 0;
+
+  DevState* d_state = nullptr;
+
+  int64_t total_streamlines = 0;
+  int64_t total_vertices = 0;
+  int prefilter = 1;
+  uint32_t mode = 0;
+  int staging_tma = 0;
+  int prefilter_ctas = 3;
+  int near_log2 = 1;       // near grid cell: (1 << near_log2)^3 voxels
+  int autotune = 1;        // batched form: tune per batch shape
+  int profile = 0;
+  struct EvSet {
+    cudaEvent_t e[5];
+  };
+  std::vector<EvSet> ev_pool;  // event sets of profiled calls
+  size_t ev_used = 0;          // sets recorded and not yet folded into prof
+  EvSet* ev_cur = nullptr;
+  fastcod_profile prof = {0, 0, 0.0, 0.0, 0.0, 0.0};
+
+  std::string err;
+  BatchState* batch = nullptr;  // batched form (batch.cu)
+};
+
+namespace fcapi {
+// Record a message on ctx (if any) and return code.
+int fail(fastcod_ctx* c, int code, const char* fmt, ...);
+// 0 = host memory, 1 = device memory of dev, -1 = device memory elsewhere.
+int ptr_kind(const void* p, int dev);
+// Grow a device buffer to at least need bytes (synchronises before freeing).
+int grow(fastcod_ctx* c, void** p, size_t* cap, size_t need);
+// Release the batched form's state (batch.cu).
+void batch_free(fastcod_ctx* c);
+}  // namespace fcapi
+
+#define CU(call)                                                                                   \
+  do {                                                                                             \
+    cudaError_t e_ = (call);                                                                       \
+    if (e_ != cudaSuccess) {                                                                       \
+      (void)cudaGetLastError();                                                                    \
+      return fcapi::fail(c, e_ == cudaErrorMemoryAllocation ? FASTCOD_ENOMEM : FASTCOD_ECUDA,       \
+                         "%s: %s", #call, cudaGetErrorString(e_));                                  \
+    }                                                                                              \
+  } while (0)

@@ -39,7 +39,7 @@ struct DevState {
   uint32_t n_survivors;   // this call: entries in the survivor list
   uint32_t n_overflow;    // this call: entries in the overflow list
   uint32_t work_next;     // this call: dynamic work counter of the walk kernel
-  uint32_t pad0;
+  uint32_t work_task;     // this call: dynamic task counter of the batched prefilter
   unsigned long long voxel_steps;
   unsigned long long survivors;
   unsigned long long overflow;
@@ -83,6 +83,31 @@ struct Accum {
   int32_t* Cend;          // [N][M]
 };
 
+// One subject of a batch: its volumes, streamlines, accumulators, counters,
+// and the global id of its first streamline (survivor lists hold global ids).
+struct BatchSubject {
+  VolView v;
+  Tract t;
+  Accum acc;
+  DevState* st;
+  int64_t sbase;
+};
+
+// Up to kMaxBatch subjects travel as one kernel parameter (constant bank).
+constexpr int kMaxBatch = 128;
+struct BatchTable {
+  int32_t n;
+  int32_t pad;
+  BatchSubject s[kMaxBatch];
+};
+
+// A prefilter task: streamlines [s_lo, s_hi) of one subject.
+struct BatchTask {
+  int32_t subject;
+  int32_t pad;
+  int64_t s_lo, s_hi;
+};
+
 // Mode bits of the walk.
 constexpr uint32_t kModeTargetEndpoint = 1u;
 constexpr uint32_t kModeVertexSampled = 2u;
@@ -104,6 +129,15 @@ cudaError_t launch_near(const VolView& v, uint8_t* tmp, uint32_t* near, cudaStre
 cudaError_t launch_prefilter(const Tract& t, const VolView& v, bool prefilter, uint32_t mode,
                              bool tma, int ctas_per_sm, int32_t* survivors, DevState* st, int num_sms,
                              cudaStream_t s);
+
+// Batched forms: every subject of the table in one launch each.
+cudaError_t launch_prefilter_batch(const BatchTable& tbl, const BatchTask* tasks, int32_t ntasks, bool prefilter,
+                                   int ctas_per_sm, int32_t* survivors, DevState* gst, int num_sms, cudaStream_t s);
+cudaError_t launch_walk_batch(const BatchTable& tbl, const int32_t* survivors, uint32_t mode, int32_t* overflow_list,
+                              DevState* gst, int num_sms, cudaStream_t s);
+cudaError_t launch_walk_overflow_batch(const BatchTable& tbl, const int32_t* overflow_list, uint32_t mode,
+                                       uint32_t* scratch, int32_t scratch_ctas, int64_t words_per_cta, DevState* gst,
+                                       cudaStream_t s);
 
 // K3: warp-per-streamline walk, dedup, accumulate; overflow path.
 cudaError_t launch_walk(const Tract& t, const VolView& v, const int32_t* survivors, Accum acc,

@@ -93,12 +93,15 @@ struct Scan {
   uint32_t singles, kept;
   int nbuf;
   bool bad;
+  int64_t id_base;          // survivor ids are id_base + streamline index
+  DevState* sst;            // the subject's counters and error word
 };
 
-__device__ __forceinline__ void flush_survivors(Scan& sc, int32_t* sbuf, int32_t* surv, DevState* st) {
+// gst holds the survivor list's counter (one list per launch).
+__device__ __forceinline__ void flush_survivors(Scan& sc, int32_t* sbuf, int32_t* surv, DevState* gst) {
   __syncwarp();
   uint32_t base = 0;
-  if (lane_id() == 0 && sc.nbuf > 0) base = atomicAdd(&st->n_survivors, (uint32_t)sc.nbuf);
+  if (lane_id() == 0 && sc.nbuf > 0) base = atomicAdd(&gst->n_survivors, (uint32_t)sc.nbuf);
   base = __shfl_sync(kFull, base, 0);
   const int l = (int)lane_id();
   if (l < sc.nbuf) surv[base + l] = sbuf[l];
@@ -111,7 +114,7 @@ __device__ __forceinline__ void flush_survivors(Scan& sc, int32_t* sbuf, int32_t
 // p: the lane's 12 words = vertices 4l..4l+3 of the window (meaningful where
 // inside [0, len)).
 __device__ __forceinline__ void scan_window(Scan& sc, const VolView& v, int32_t Wr, const int32_t p[12],
-                                            bool prefilter, int32_t* sbuf, int32_t* surv, DevState* st) {
+                                            bool prefilter, int32_t* sbuf, int32_t* surv, DevState* gst) {
   const int32_t lane = (int32_t)lane_id();
 
   // 1. boundaries x <= Wr + 128, 32 per round: start mask of this window
@@ -198,10 +201,10 @@ __device__ __forceinline__ void scan_window(Scan& sc, const VolView& v, int32_t 
     const bool pass = in && (!prefilter || (cR > pR && cT > pT)) && (bx > px) && !sc.bad;
     if (in && bx - px == 1) sc.singles += 1u;
     const uint32_t pm = __ballot_sync(kFull, pass);
-    if (pass) sbuf[sc.nbuf + __popc(pm & lanemask_lt())] = (int32_t)(s_round + lane - 1);
+    if (pass) sbuf[sc.nbuf + __popc(pm & lanemask_lt())] = (int32_t)(sc.id_base + s_round + lane - 1);
     sc.nbuf += __popc(pm);
     sc.kept += __popc(pm);
-    if (sc.nbuf >= 32) flush_survivors(sc, sbuf, surv, st);
+    if (sc.nbuf >= 32) flush_survivors(sc, sbuf, surv, gst);
     sc.lastR = __shfl_sync(kFull, cR, nb - 1);
     sc.lastT = __shfl_sync(kFull, cT, nb - 1);
     sc.last_x = __shfl_sync(kFull, bx, nb - 1);
@@ -217,19 +220,19 @@ __device__ __forceinline__ void scan_window(Scan& sc, const VolView& v, int32_t 
   sc.cumT += __popc(mt[0]) + __popc(mt[1]) + __popc(mt[2]) + __popc(mt[3]);
 }
 
-// Streamline range of warp gw and its validation; false when the warp has
-// nothing to do (or found invalid offsets).
-__device__ __forceinline__ bool warp_range(const Tract& t, int64_t gw, int64_t nw, Scan& sc, DevState* st) {
+// Set up the scan of streamlines [s_lo, s_hi) of t after validating their
+// offsets; false when there is nothing to do (or the offsets are invalid).
+__device__ __forceinline__ bool warp_init(const Tract& t, int64_t s_lo, int64_t s_hi, Scan& sc, DevState* sst,
+                                          int64_t id_base) {
   const unsigned lane = lane_id();
-  if (gw == 0 && lane == 0 && (t.off[0] != 0 || t.off[t.ns] != t.nv)) set_error(st, kErrOffsets, -1);
-  const int64_t s_lo = t.ns * gw / nw, s_hi = t.ns * (gw + 1) / nw;
+  if (s_lo == 0 && lane == 0 && (t.off[0] != 0 || t.off[t.ns] != t.nv)) set_error(sst, kErrOffsets, -1);
   bool ok = true;
   for (int64_t s = s_lo + lane; s < s_hi; s += 32) {
     const int64_t a = t.off[s], b = t.off[s + 1];
     ok &= (a >= 0) && (a <= b) && (b <= t.nv);
   }
   if (!__all_sync(kFull, ok)) {
-    if (lane == 0) set_error(st, kErrOffsets, (int32_t)s_lo);
+    if (lane == 0) set_error(sst, kErrOffsets, (int32_t)s_lo);
     return false;
   }
   if (s_hi <= s_lo) return false;
@@ -250,18 +253,20 @@ __device__ __forceinline__ bool warp_range(const Tract& t, int64_t gw, int64_t n
   sc.singles = sc.kept = 0;
   sc.nbuf = 0;
   sc.bad = false;
+  sc.id_base = id_base;
+  sc.sst = sst;
   return true;
 }
 
-__device__ __forceinline__ void warp_finish(Scan& sc, int32_t* sbuf, int32_t* surv, DevState* st, int64_t gw) {
-  flush_survivors(sc, sbuf, surv, st);
+__device__ __forceinline__ void warp_finish(Scan& sc, int32_t* sbuf, int32_t* surv, DevState* gst) {
+  flush_survivors(sc, sbuf, surv, gst);
   unsigned long long s = sc.steps64 + sc.steps + sc.singles;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
   if (lane_id() == 0) {
-    atomicAdd(&st->voxel_steps, s);
-    atomicAdd(&st->survivors, (unsigned long long)sc.kept);
-    if (sc.bad) set_error(st, kErrCoord, (int32_t)gw);
+    atomicAdd(&sc.sst->voxel_steps, s);
+    atomicAdd(&sc.sst->survivors, (unsigned long long)sc.kept);
+    if (sc.bad) set_error(sc.sst, kErrCoord, (int32_t)(sc.s_cur - 1));
   }
 }
 
@@ -275,15 +280,10 @@ __device__ __forceinline__ void ldcs4(const int32_t* g, int32_t* d) {
 
 // ------------------------------------------------------------------ direct
 
-template <int kMinBlocks>
-__global__ void __launch_bounds__(kWarps * 32, kMinBlocks) prefilter_direct_kernel(Tract t, VolView v, int prefilter,
-                                                                                  int32_t* surv, DevState* st) {
-  __shared__ int32_t sbuf_all[kWarps][64];
-  int32_t* sbuf = sbuf_all[threadIdx.x >> 5];
+// Window loop of the direct loader over the scan's vertex range.
+__device__ __forceinline__ void scan_range_direct(Scan& sc, const VolView& v, const Tract& t, bool prefilter,
+                                                  int32_t* sbuf, int32_t* surv, DevState* gst) {
   const int32_t lane = (int32_t)lane_id();
-  const int64_t gw = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
-  Scan sc;
-  if (!warp_range(t, gw, (int64_t)gridDim.x * kWarps, sc, st)) return;
   const int64_t q0 = sc.V0 >> kPieceLog2, q1 = (sc.V0 + sc.len - 1) >> kPieceLog2;
   for (int64_t q = q0; q <= q1; ++q) {
     const int64_t g = (q << kPieceLog2) + 4 * lane;  // absolute index of the lane's first vertex
@@ -297,11 +297,44 @@ __global__ void __launch_bounds__(kWarps * 32, kMinBlocks) prefilter_direct_kern
 #pragma unroll
       for (int w = 0; w < 12; ++w) p[w] = (g + w / 3 < t.nv) ? __ldcs(t.xyz + 3 * g + w) : 0;
     }
-    scan_window(sc, v, (int32_t)((q << kPieceLog2) - sc.V0), p, prefilter != 0, sbuf, surv, st);
+    scan_window(sc, v, (int32_t)((q << kPieceLog2) - sc.V0), p, prefilter, sbuf, surv, gst);
     sc.steps64 += sc.steps;
     sc.steps = 0;
   }
-  warp_finish(sc, sbuf, surv, st, gw);
+}
+
+template <int kMinBlocks>
+__global__ void __launch_bounds__(kWarps * 32, kMinBlocks) prefilter_direct_kernel(Tract t, VolView v, int prefilter,
+                                                                                  int32_t* surv, DevState* st) {
+  __shared__ int32_t sbuf_all[kWarps][64];
+  int32_t* sbuf = sbuf_all[threadIdx.x >> 5];
+  const int64_t gw = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
+  const int64_t nw = (int64_t)gridDim.x * kWarps;
+  Scan sc;
+  if (!warp_init(t, t.ns * gw / nw, t.ns * (gw + 1) / nw, sc, st, 0)) return;
+  scan_range_direct(sc, v, t, prefilter != 0, sbuf, surv, st);
+  warp_finish(sc, sbuf, surv, st);
+}
+
+// Batched form: warps take (subject, streamline range) tasks dynamically.
+template <int kMinBlocks>
+__global__ void __launch_bounds__(kWarps * 32, kMinBlocks)
+    prefilter_batch_kernel(const __grid_constant__ BatchTable tbl, const BatchTask* __restrict__ tasks,
+                           int32_t ntasks, int prefilter, int32_t* surv, DevState* gst) {
+  __shared__ int32_t sbuf_all[kWarps][64];
+  int32_t* sbuf = sbuf_all[threadIdx.x >> 5];
+  for (;;) {
+    int32_t task = 0;
+    if (lane_id() == 0) task = (int32_t)atomicAdd(&gst->work_task, 1u);
+    task = __shfl_sync(kFull, task, 0);
+    if (task >= ntasks) break;
+    const BatchTask tk = tasks[task];
+    const BatchSubject& S = tbl.s[tk.subject];
+    Scan sc;
+    if (!warp_init(S.t, tk.s_lo, tk.s_hi, sc, S.st, S.sbase)) continue;
+    scan_range_direct(sc, S.v, S.t, prefilter != 0, sbuf, surv, gst);
+    warp_finish(sc, sbuf, surv, gst);
+  }
 }
 
 // --------------------------------------------------------------------- tma
@@ -347,8 +380,9 @@ __global__ void __launch_bounds__(kWarps * 32, kMinBlocks) prefilter_tma_kernel(
   WarpSmem* sm = reinterpret_cast<WarpSmem*>(smem_raw) + (threadIdx.x >> 5);
   const int32_t lane = (int32_t)lane_id();
   const int64_t gw = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
+  const int64_t nw = (int64_t)gridDim.x * kWarps;
   Scan sc;
-  if (!warp_range(t, gw, (int64_t)gridDim.x * kWarps, sc, st)) return;
+  if (!warp_init(t, t.ns * gw / nw, t.ns * (gw + 1) / nw, sc, st, 0)) return;
 
   Ring r;
   r.sm = sm;
@@ -402,7 +436,7 @@ __global__ void __launch_bounds__(kWarps * 32, kMinBlocks) prefilter_tma_kernel(
     for (int64_t q = waited + 1; q < r.next_issue; ++q)
       if (!r.wait(q)) break;
   }
-  warp_finish(sc, sm->sbuf, surv, st, gw);
+  warp_finish(sc, sm->sbuf, surv, st);
 }
 
 constexpr size_t kTmaSmemBytes = sizeof(WarpSmem) * kWarps;
@@ -442,7 +476,25 @@ cudaError_t launch_one(const Tract& t, const VolView& v, bool prefilter, bool tm
   return cudaGetLastError();
 }
 
+template <int kMinBlocks>
+cudaError_t launch_batch_one(const BatchTable& tbl, const BatchTask* tasks, int32_t ntasks, bool prefilter,
+                             int32_t* survivors, DevState* gst, int num_sms, cudaStream_t s) {
+  auto k = prefilter_batch_kernel<kMinBlocks>;
+  int grid = 0;
+  cudaError_t e = resident_grid(k, 0, num_sms, &grid);
+  if (e != cudaSuccess) return e;
+  k<<<grid, kWarps * 32, 0, s>>>(tbl, tasks, ntasks, prefilter ? 1 : 0, survivors, gst);
+  return cudaGetLastError();
+}
+
 }  // namespace
+
+cudaError_t launch_prefilter_batch(const BatchTable& tbl, const BatchTask* tasks, int32_t ntasks, bool prefilter,
+                                   int ctas_per_sm, int32_t* survivors, DevState* gst, int num_sms, cudaStream_t s) {
+  if (ntasks <= 0) return cudaSuccess;
+  if (ctas_per_sm == 4) return launch_batch_one<4>(tbl, tasks, ntasks, prefilter, survivors, gst, num_sms, s);
+  return launch_batch_one<3>(tbl, tasks, ntasks, prefilter, survivors, gst, num_sms, s);
+}
 
 cudaError_t launch_prefilter(const Tract& t, const VolView& v, bool prefilter, uint32_t mode, bool tma,
                              int ctas_per_sm, int32_t* survivors, DevState* st, int num_sms, cudaStream_t s) {

@@ -55,100 +55,146 @@ __device__ __forceinline__ void walk_window(const VolView& v, WalkWarpSmem& sm, 
   }
 }
 
+// Walk surviving streamline s of (v, t) with the whole warp and add its
+// pairs to acc.  Returns |V_s| |T_s| (warp-uniform), or -1 when its sets
+// outgrew the tables: then `id` is appended to the overflow list instead.
+__device__ __forceinline__ int walk_one(const VolView& v, const Tract& t, const Accum& acc, uint32_t mode,
+                                        WalkWarpSmem& sm, int32_t s, int32_t id, int32_t* __restrict__ ovf,
+                                        DevState* gst) {
+  const unsigned lane = lane_id();
+  const bool endpoint_mode = (mode & kModeTargetEndpoint) != 0;
+  const bool point_mode = (mode & kModeVertexSampled) != 0;
+  const int64_t M = v.n_lab;
+  const int64_t a = t.off[s], b = t.off[s + 1];
+  const int64_t T = b - a;
+  int nV = 0, nT = 0;
+  bool fail = false;
+  if (T == 1 || point_mode) {
+    for (int64_t i0 = 0; i0 < T && !fail; i0 += 32) {
+      const int64_t j = a + i0 + lane;
+      int32_t row = -1, lab = 0;
+      if (j < b) {
+        int32_t p[3];
+        load_vertex(t.xyz, j, p);
+        voxel_lookup(v, p[0] >> kUnitLog2, p[1] >> kUnitLog2, p[2] >> kUnitLog2, row, lab);
+      }
+      if (endpoint_mode) lab = 0;
+      nV = set_insert<kHV>(sm.tabV, sm.listV, nV, row, fail);
+      nT = set_insert<kHT>(sm.tabT, sm.listT, nT, lab > 0 ? lab : -1, fail);
+      if (nV > kLimV || nT > kLimT) fail = true;
+      fail = __any_sync(kFull, fail);
+    }
+  } else {
+    for (int64_t i0 = 0; i0 < T - 1 && !fail; i0 += 32) {
+      const int64_t j = a + i0 + lane;
+      const int64_t jhi = min(a + i0 + 32, b - 1);
+      int32_t p0[3] = {0, 0, 0}, p1[3];
+      if (j <= jhi) load_vertex(t.xyz, j, p0);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) p1[k] = __shfl_down_sync(kFull, p0[k], 1);
+      if (lane == 31 && j + 1 <= jhi) load_vertex(t.xyz, j + 1, p1);
+      const bool has = j < b - 1;
+      const bool small = !has || (abs(p1[0] - p0[0]) < 65536 && abs(p1[1] - p0[1]) < 65536 &&
+                                  abs(p1[2] - p0[2]) < 65536);
+      if (__all_sync(kFull, small))
+        walk_window<uint32_t>(v, sm, p0, p1, has, j == a, endpoint_mode, nV, nT, fail);
+      else
+        walk_window<unsigned long long>(v, sm, p0, p1, has, j == a, endpoint_mode, nV, nT, fail);
+      fail = __any_sync(kFull, fail);
+    }
+  }
+  if (endpoint_mode && !fail) {
+    // T_s = {label of the last vertex}
+    int32_t row = -1, lab = 0;
+    if (lane == 0) {
+      int32_t p[3];
+      load_vertex(t.xyz, b - 1, p);
+      voxel_lookup(v, p[0] >> kUnitLog2, p[1] >> kUnitLog2, p[2] >> kUnitLog2, row, lab);
+    }
+    nT = set_insert<kHT>(sm.tabT, sm.listT, nT, lab > 0 ? lab : -1, fail);
+    fail = __any_sync(kFull, fail);
+  }
+  __syncwarp();
+  int pairs = -1;
+  if (fail) {
+    if (lane == 0) ovf[atomicAdd(&gst->n_overflow, 1u)] = id;
+  } else {
+    pairs = nV * nT;
+    for (int p = lane; p < pairs; p += 32) {
+      const int i = p / nT, k = p - i * nT;
+      atomicAdd(acc.C + (int64_t)sm.listV[i] * M + (sm.listT[k] - 1), 1);
+    }
+    if (lane == 0) {
+      int32_t p[3], r0, l0, r1, l1;
+      load_vertex(t.xyz, a, p);
+      voxel_lookup(v, p[0] >> kUnitLog2, p[1] >> kUnitLog2, p[2] >> kUnitLog2, r0, l0);
+      load_vertex(t.xyz, b - 1, p);
+      voxel_lookup(v, p[0] >> kUnitLog2, p[1] >> kUnitLog2, p[2] >> kUnitLog2, r1, l1);
+      if (r0 >= 0 && l1 >= 1) atomicAdd(acc.Cend + (int64_t)r0 * M + (l1 - 1), 1);
+    }
+  }
+  __syncwarp();
+  for (int i = lane; i < kHV; i += 32) sm.tabV[i] = -1;
+  for (int i = lane; i < kHT; i += 32) sm.tabT[i] = -1;
+  __syncwarp();
+  return pairs;
+}
+
+__device__ __forceinline__ void clear_tables(WalkWarpSmem& sm) {
+  for (int i = lane_id(); i < kHV; i += 32) sm.tabV[i] = -1;
+  for (int i = lane_id(); i < kHT; i += 32) sm.tabT[i] = -1;
+  __syncwarp();
+}
+
+__device__ __forceinline__ uint32_t next_survivor(DevState* gst) {
+  uint32_t idx = 0;
+  if (lane_id() == 0) idx = atomicAdd(&gst->work_next, 1u);
+  return __shfl_sync(kFull, idx, 0);
+}
+
 __global__ void __launch_bounds__(kWalkWarps * 32) walk_kernel(Tract t, VolView v, const int32_t* __restrict__ surv,
                                                               Accum acc, uint32_t mode, int32_t* __restrict__ ovf,
                                                               DevState* st) {
   __shared__ WalkWarpSmem smem_all[kWalkWarps];
   WalkWarpSmem& sm = smem_all[threadIdx.x >> 5];
-  const unsigned lane = lane_id();
-  for (int i = lane; i < kHV; i += 32) sm.tabV[i] = -1;
-  for (int i = lane; i < kHT; i += 32) sm.tabT[i] = -1;
-  __syncwarp();
-  const bool endpoint_mode = (mode & kModeTargetEndpoint) != 0;
-  const bool point_mode = (mode & kModeVertexSampled) != 0;
+  clear_tables(sm);
   const uint32_t n = st->n_survivors;
-  const int64_t M = v.n_lab;
   unsigned long long pairs_acc = 0;
   for (;;) {
-    uint32_t idx = 0;
-    if (lane == 0) idx = atomicAdd(&st->work_next, 1u);
-    idx = __shfl_sync(kFull, idx, 0);
+    const uint32_t idx = next_survivor(st);
     if (idx >= n) break;
     const int32_t s = surv[idx];
-    const int64_t a = t.off[s], b = t.off[s + 1];
-    const int64_t T = b - a;
-    int nV = 0, nT = 0;
-    bool fail = false;
-    if (T == 1 || point_mode) {
-      for (int64_t i0 = 0; i0 < T && !fail; i0 += 32) {
-        const int64_t j = a + i0 + lane;
-        int32_t row = -1, lab = 0;
-        if (j < b) {
-          int32_t p[3];
-          load_vertex(t.xyz, j, p);
-          voxel_lookup(v, p[0] >> kUnitLog2, p[1] >> kUnitLog2, p[2] >> kUnitLog2, row, lab);
-        }
-        if (endpoint_mode) lab = 0;
-        nV = set_insert<kHV>(sm.tabV, sm.listV, nV, row, fail);
-        nT = set_insert<kHT>(sm.tabT, sm.listT, nT, lab > 0 ? lab : -1, fail);
-        if (nV > kLimV || nT > kLimT) fail = true;
-        fail = __any_sync(kFull, fail);
-      }
-    } else {
-      for (int64_t i0 = 0; i0 < T - 1 && !fail; i0 += 32) {
-        const int64_t j = a + i0 + lane;
-        const int64_t jhi = min(a + i0 + 32, b - 1);
-        int32_t p0[3] = {0, 0, 0}, p1[3];
-        if (j <= jhi) load_vertex(t.xyz, j, p0);
-#pragma unroll
-        for (int k = 0; k < 3; ++k) p1[k] = __shfl_down_sync(kFull, p0[k], 1);
-        if (lane == 31 && j + 1 <= jhi) load_vertex(t.xyz, j + 1, p1);
-        const bool has = j < b - 1;
-        const bool small = !has || (abs(p1[0] - p0[0]) < 65536 && abs(p1[1] - p0[1]) < 65536 &&
-                                    abs(p1[2] - p0[2]) < 65536);
-        if (__all_sync(kFull, small))
-          walk_window<uint32_t>(v, sm, p0, p1, has, j == a, endpoint_mode, nV, nT, fail);
-        else
-          walk_window<unsigned long long>(v, sm, p0, p1, has, j == a, endpoint_mode, nV, nT, fail);
-        fail = __any_sync(kFull, fail);
-      }
-    }
-    if (endpoint_mode && !fail) {
-      // T_s = {label of the last vertex}
-      int32_t row = -1, lab = 0;
-      if (lane == 0) {
-        int32_t p[3];
-        load_vertex(t.xyz, b - 1, p);
-        voxel_lookup(v, p[0] >> kUnitLog2, p[1] >> kUnitLog2, p[2] >> kUnitLog2, row, lab);
-      }
-      nT = set_insert<kHT>(sm.tabT, sm.listT, nT, lab > 0 ? lab : -1, fail);
-      fail = __any_sync(kFull, fail);
-    }
-    __syncwarp();
-    if (fail) {
-      if (lane == 0) ovf[atomicAdd(&st->n_overflow, 1u)] = s;
-    } else {
-      const int pairs = nV * nT;
-      for (int p = lane; p < pairs; p += 32) {
-        const int i = p / nT, k = p - i * nT;
-        atomicAdd(acc.C + (int64_t)sm.listV[i] * M + (sm.listT[k] - 1), 1);
-      }
-      pairs_acc += (unsigned long long)pairs;
-      if (lane == 0) {
-        int32_t p[3], r0, l0, r1, l1;
-        load_vertex(t.xyz, a, p);
-        voxel_lookup(v, p[0] >> kUnitLog2, p[1] >> kUnitLog2, p[2] >> kUnitLog2, r0, l0);
-        load_vertex(t.xyz, b - 1, p);
-        voxel_lookup(v, p[0] >> kUnitLog2, p[1] >> kUnitLog2, p[2] >> kUnitLog2, r1, l1);
-        if (r0 >= 0 && l1 >= 1) atomicAdd(acc.Cend + (int64_t)r0 * M + (l1 - 1), 1);
-      }
-    }
-    __syncwarp();
-    for (int i = lane; i < kHV; i += 32) sm.tabV[i] = -1;
-    for (int i = lane; i < kHT; i += 32) sm.tabT[i] = -1;
-    __syncwarp();
+    const int pairs = walk_one(v, t, acc, mode, sm, s, s, ovf, st);
+    if (pairs > 0) pairs_acc += (unsigned long long)pairs;
   }
-  if (lane == 0 && pairs_acc) atomicAdd(&st->pairs, pairs_acc);
+  if (lane_id() == 0 && pairs_acc) atomicAdd(&st->pairs, pairs_acc);
+}
+
+// Subject of global streamline id g (subjects' sbase ascend).
+__device__ __forceinline__ int subject_of(const BatchTable& tbl, int64_t g) {
+  int lo = 0, hi = tbl.n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (tbl.s[mid].sbase <= g) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__global__ void __launch_bounds__(kWalkWarps * 32)
+    walk_batch_kernel(const __grid_constant__ BatchTable tbl, const int32_t* __restrict__ surv, uint32_t mode,
+                      int32_t* __restrict__ ovf, DevState* gst) {
+  __shared__ WalkWarpSmem smem_all[kWalkWarps];
+  WalkWarpSmem& sm = smem_all[threadIdx.x >> 5];
+  clear_tables(sm);
+  const uint32_t n = gst->n_survivors;
+  for (;;) {
+    const uint32_t idx = next_survivor(gst);
+    if (idx >= n) break;
+    const int32_t g = surv[idx];
+    const BatchSubject& S = tbl.s[subject_of(tbl, g)];
+    const int pairs = walk_one(S.v, S.t, S.acc, mode, sm, (int32_t)(g - S.sbase), g, ovf, gst);
+    if (pairs > 0 && lane_id() == 0) atomicAdd(&S.st->pairs, (unsigned long long)pairs);
+  }
 }
 
 // ---------------------------------------------------------------- overflow
@@ -181,68 +227,86 @@ __device__ __forceinline__ void ovf_visit(const VolView& v, const OvfSets& z, in
   if (!endpoint_mode && lab >= 1) ovf_add(z.labbits, z.lablist, nT, lab);
 }
 
-__global__ void __launch_bounds__(256) walk_overflow_kernel(Tract t, VolView v, const int32_t* __restrict__ ovf,
-                                                            Accum acc, uint32_t mode, uint32_t* scratch,
-                                                            int64_t words_per_cta, DevState* st) {
-  __shared__ int nV, nT;
+// The whole CTA handles streamline s of (v, t): walk every segment, sets as
+// bitmaps + lists in this CTA's scratch slice, then pairs and C_end.
+__device__ __forceinline__ void overflow_one(const VolView& v, const Tract& t, const Accum& acc, uint32_t mode,
+                                             uint32_t* slice, int32_t s, DevState* sst, int* nV, int* nT) {
   OvfSets z;
-  z.rowbits = scratch + blockIdx.x * words_per_cta;
+  z.rowbits = slice;
   z.labbits = z.rowbits + ((int64_t)v.n_roi + 31) / 32;
   z.rowlist = reinterpret_cast<int32_t*>(z.labbits + ((int64_t)v.n_lab + 1 + 31) / 32);
   z.lablist = z.rowlist + v.n_roi;
   const bool endpoint_mode = (mode & kModeTargetEndpoint) != 0;
   const bool point_mode = (mode & kModeVertexSampled) != 0;
-  const uint32_t n = st->n_overflow;
   const int64_t M = v.n_lab;
-  for (uint32_t i = blockIdx.x; i < n; i += gridDim.x) {
-    if (threadIdx.x == 0) { nV = 0; nT = 0; }
-    __syncthreads();
-    const int32_t s = ovf[i];
-    const int64_t a = t.off[s], b = t.off[s + 1], T = b - a;
-    const bool pts = T == 1 || point_mode;
-    const int64_t units = pts ? T : T - 1;
-    for (int64_t u = threadIdx.x; u < units; u += blockDim.x) {
-      int32_t p0[3];
-      load_vertex(t.xyz, a + u, p0);
-      if (pts) {
-        ovf_visit(v, z, &nV, &nT, endpoint_mode, p0[0] >> kUnitLog2, p0[1] >> kUnitLog2, p0[2] >> kUnitLog2);
-      } else {
-        int32_t p1[3];
-        load_vertex(t.xyz, a + u + 1, p1);
-        SegWalk<unsigned long long> w;
-        w.init(p0, p1);
-        ovf_visit(v, z, &nV, &nT, endpoint_mode, w.c[0], w.c[1], w.c[2]);
-        while (w.step()) ovf_visit(v, z, &nV, &nT, endpoint_mode, w.c[0], w.c[1], w.c[2]);
-      }
+  if (threadIdx.x == 0) { *nV = 0; *nT = 0; }
+  __syncthreads();
+  const int64_t a = t.off[s], b = t.off[s + 1], T = b - a;
+  const bool pts = T == 1 || point_mode;
+  const int64_t units = pts ? T : T - 1;
+  for (int64_t u = threadIdx.x; u < units; u += blockDim.x) {
+    int32_t p0[3];
+    load_vertex(t.xyz, a + u, p0);
+    if (pts) {
+      ovf_visit(v, z, nV, nT, endpoint_mode, p0[0] >> kUnitLog2, p0[1] >> kUnitLog2, p0[2] >> kUnitLog2);
+    } else {
+      int32_t p1[3];
+      load_vertex(t.xyz, a + u + 1, p1);
+      SegWalk<unsigned long long> w;
+      w.init(p0, p1);
+      ovf_visit(v, z, nV, nT, endpoint_mode, w.c[0], w.c[1], w.c[2]);
+      while (w.step()) ovf_visit(v, z, nV, nT, endpoint_mode, w.c[0], w.c[1], w.c[2]);
     }
-    if (endpoint_mode && threadIdx.x == 0 && T >= 1) {
-      int32_t p[3], row, lab;
+  }
+  if (endpoint_mode && threadIdx.x == 0 && T >= 1) {
+    int32_t p[3], row, lab;
+    load_vertex(t.xyz, b - 1, p);
+    voxel_lookup(v, p[0] >> kUnitLog2, p[1] >> kUnitLog2, p[2] >> kUnitLog2, row, lab);
+    if (lab >= 1) ovf_add(z.labbits, z.lablist, nT, lab);
+  }
+  __syncthreads();
+  const int64_t pairs = (int64_t)(*nV) * (*nT);
+  for (int64_t p = threadIdx.x; p < pairs; p += blockDim.x) {
+    const int64_t r = p / *nT, k = p - r * *nT;
+    atomicAdd(acc.C + (int64_t)z.rowlist[r] * M + (z.lablist[k] - 1), 1);
+  }
+  if (threadIdx.x == 0) {
+    if (pairs) atomicAdd(&sst->pairs, (unsigned long long)pairs);
+    atomicAdd(&sst->overflow, 1ull);
+    if (T >= 1) {
+      int32_t p[3], r0, l0, r1, l1;
+      load_vertex(t.xyz, a, p);
+      voxel_lookup(v, p[0] >> kUnitLog2, p[1] >> kUnitLog2, p[2] >> kUnitLog2, r0, l0);
       load_vertex(t.xyz, b - 1, p);
-      voxel_lookup(v, p[0] >> kUnitLog2, p[1] >> kUnitLog2, p[2] >> kUnitLog2, row, lab);
-      if (lab >= 1) ovf_add(z.labbits, z.lablist, &nT, lab);
+      voxel_lookup(v, p[0] >> kUnitLog2, p[1] >> kUnitLog2, p[2] >> kUnitLog2, r1, l1);
+      if (r0 >= 0 && l1 >= 1) atomicAdd(acc.Cend + (int64_t)r0 * M + (l1 - 1), 1);
     }
-    __syncthreads();
-    const int64_t pairs = (int64_t)nV * nT;
-    for (int64_t p = threadIdx.x; p < pairs; p += blockDim.x) {
-      const int64_t r = p / nT, k = p - r * nT;
-      atomicAdd(acc.C + (int64_t)z.rowlist[r] * M + (z.lablist[k] - 1), 1);
-    }
-    if (threadIdx.x == 0) {
-      if (pairs) atomicAdd(&st->pairs, (unsigned long long)pairs);
-      atomicAdd(&st->overflow, 1ull);
-      if (T >= 1) {
-        int32_t p[3], r0, l0, r1, l1;
-        load_vertex(t.xyz, a, p);
-        voxel_lookup(v, p[0] >> kUnitLog2, p[1] >> kUnitLog2, p[2] >> kUnitLog2, r0, l0);
-        load_vertex(t.xyz, b - 1, p);
-        voxel_lookup(v, p[0] >> kUnitLog2, p[1] >> kUnitLog2, p[2] >> kUnitLog2, r1, l1);
-        if (r0 >= 0 && l1 >= 1) atomicAdd(acc.Cend + (int64_t)r0 * M + (l1 - 1), 1);
-      }
-    }
-    __syncthreads();
-    for (int k = threadIdx.x; k < nV; k += blockDim.x) z.rowbits[z.rowlist[k] >> 5] = 0u;
-    for (int k = threadIdx.x; k < nT; k += blockDim.x) z.labbits[z.lablist[k] >> 5] = 0u;
-    __syncthreads();
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < *nV; k += blockDim.x) z.rowbits[z.rowlist[k] >> 5] = 0u;
+  for (int k = threadIdx.x; k < *nT; k += blockDim.x) z.labbits[z.lablist[k] >> 5] = 0u;
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(256) walk_overflow_kernel(Tract t, VolView v, const int32_t* __restrict__ ovf,
+                                                            Accum acc, uint32_t mode, uint32_t* scratch,
+                                                            int64_t words_per_cta, DevState* st) {
+  __shared__ int nV, nT;
+  const uint32_t n = st->n_overflow;
+  for (uint32_t i = blockIdx.x; i < n; i += gridDim.x)
+    overflow_one(v, t, acc, mode, scratch + blockIdx.x * words_per_cta, ovf[i], st, &nV, &nT);
+}
+
+__global__ void __launch_bounds__(256)
+    walk_overflow_batch_kernel(const __grid_constant__ BatchTable tbl, const int32_t* __restrict__ ovf, uint32_t mode,
+                               uint32_t* scratch, int64_t words_per_cta, DevState* gst) {
+  __shared__ int nV, nT;
+  const uint32_t n = gst->n_overflow;
+  for (uint32_t i = blockIdx.x; i < n; i += gridDim.x) {
+    const int32_t g = ovf[i];
+    const BatchSubject& S = tbl.s[subject_of(tbl, g)];
+    overflow_one(S.v, S.t, S.acc, mode, scratch + blockIdx.x * words_per_cta, (int32_t)(g - S.sbase), S.st, &nV,
+                 &nT);
   }
 }
 
@@ -259,6 +323,19 @@ cudaError_t launch_walk_overflow(const Tract& t, const VolView& v, const int32_t
   if (t.ns <= 0) return cudaSuccess;
   walk_overflow_kernel<<<scratch_ctas, 256, 0, s>>>(t, v, overflow_list, acc, mode, scratch,
                                                     overflow_scratch_words(v.n_roi, v.n_lab), st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_walk_batch(const BatchTable& tbl, const int32_t* survivors, uint32_t mode, int32_t* overflow_list,
+                              DevState* gst, int num_sms, cudaStream_t s) {
+  walk_batch_kernel<<<num_sms * 4, kWalkWarps * 32, 0, s>>>(tbl, survivors, mode, overflow_list, gst);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_walk_overflow_batch(const BatchTable& tbl, const int32_t* overflow_list, uint32_t mode,
+                                       uint32_t* scratch, int32_t scratch_ctas, int64_t words_per_cta, DevState* gst,
+                                       cudaStream_t s) {
+  walk_overflow_batch_kernel<<<scratch_ctas, 256, 0, s>>>(tbl, overflow_list, mode, scratch, words_per_cta, gst);
   return cudaGetLastError();
 }
 

@@ -35,12 +35,14 @@ FASTCOD_OPT_STAGING = 4
 FASTCOD_OPT_PROFILE = 5
 FASTCOD_OPT_PREFILTER_CTAS = 6
 FASTCOD_OPT_NEAR_LOG2 = 7
+FASTCOD_OPT_AUTOTUNE = 8
 
 EXPORTED = [
     "fastcod_create", "fastcod_destroy", "fastcod_set_stream", "fastcod_set_volumes",
     "fastcod_add_streamlines", "fastcod_connectivity", "fastcod_endpoint_connectivity",
     "fastcod_reset", "fastcod_get_shape", "fastcod_get_stats", "fastcod_get_profile", "fastcod_sync",
-    "fastcod_set_option", "fastcod_last_error",
+    "fastcod_set_option", "fastcod_last_error", "fastcod_batch_run", "fastcod_batch_get_stats",
+    "fastcod_batch_get_info",
 ]
 
 
@@ -60,6 +62,19 @@ class Profile(ctypes.Structure):
     _fields_ = [("calls", ctypes.c_int64), ("kernel_launches", ctypes.c_int64), ("ms_h2d", ctypes.c_double),
                 ("ms_prefilter", ctypes.c_double), ("ms_walk", ctypes.c_double),
                 ("ms_overflow", ctypes.c_double)]
+
+
+class Subject(ctypes.Structure):
+    _fields_ = [("roi_index_map", ctypes.c_void_p), ("target_labels", ctypes.c_void_p),
+                ("dims", ctypes.c_int32 * 3), ("n_roi", ctypes.c_int32), ("n_targets", ctypes.c_int32),
+                ("xyz", ctypes.c_void_p), ("n_vertices", ctypes.c_int64), ("offsets", ctypes.c_void_p),
+                ("n_streamlines", ctypes.c_int64), ("C_out", ctypes.c_void_p), ("Cend_out", ctypes.c_void_p)]
+
+
+class BatchInfo(ctypes.Structure):
+    _fields_ = [("n_subjects", ctypes.c_int32), ("tasks", ctypes.c_int32), ("prefilter_ctas", ctypes.c_int32),
+                ("near_log2", ctypes.c_int32), ("graph_reused", ctypes.c_int32), ("tuned", ctypes.c_int32),
+                ("ms_graph", ctypes.c_double)]
 
 
 def _load():
@@ -82,6 +97,9 @@ def _load():
         "fastcod_sync": ([vp], ctypes.c_int),
         "fastcod_set_option": ([vp, i32, i64], ctypes.c_int),
         "fastcod_last_error": ([vp], ctypes.c_char_p),
+        "fastcod_batch_run": ([vp, ctypes.POINTER(Subject), i32], ctypes.c_int),
+        "fastcod_batch_get_stats": ([vp, i32, ctypes.POINTER(Stats)], ctypes.c_int),
+        "fastcod_batch_get_info": ([vp, ctypes.POINTER(BatchInfo)], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -184,6 +202,41 @@ def fastcod_set_option(ctx, key: int, value: int):
 
 def fastcod_last_error(ctx) -> str:
     return lib.fastcod_last_error(ctx).decode()
+
+
+def make_subject(roi, lab, dims, n_roi, n_targets, xyz, offsets, C_out, Cend_out) -> Subject:
+    """A fastcod_subject from arrays / tensors (the caller keeps them alive)."""
+    s = Subject()
+    s.roi_index_map = _ptr(roi)
+    s.target_labels = _ptr(lab)
+    for a in range(3):
+        s.dims[a] = int(dims[a])
+    s.n_roi = int(n_roi)
+    s.n_targets = int(n_targets)
+    s.xyz = _ptr(xyz)
+    s.n_vertices = int(xyz.shape[0])
+    s.offsets = _ptr(offsets)
+    s.n_streamlines = int(offsets.shape[0]) - 1
+    s.C_out = _ptr(C_out)
+    s.Cend_out = _ptr(Cend_out)
+    return s
+
+
+def fastcod_batch_run(ctx, subjects):
+    arr = (Subject * len(subjects))(*subjects)
+    return _check(ctx, lib.fastcod_batch_run(ctx, arr, len(subjects)))
+
+
+def fastcod_batch_get_stats(ctx, subject: int) -> dict:
+    st = Stats()
+    _check(ctx, lib.fastcod_batch_get_stats(ctx, subject, ctypes.byref(st)))
+    return {k: int(getattr(st, k)) for k, _ in Stats._fields_}
+
+
+def fastcod_batch_get_info(ctx) -> dict:
+    info = BatchInfo()
+    _check(ctx, lib.fastcod_batch_get_info(ctx, ctypes.byref(info)))
+    return {k: getattr(info, k) for k, _ in BatchInfo._fields_}
 
 
 class Context:
