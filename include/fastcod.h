@@ -231,6 +231,67 @@ FASTCOD_API int fastcod_batch_get_stats(fastcod_ctx* ctx, int32_t subject, fastc
 /* Shape and configuration of the last batch. */
 FASTCOD_API int fastcod_batch_get_info(fastcod_ctx* ctx, fastcod_batch_info* out);
 
+/* ---------------------------------------------------------------- served
+ * A request loop with continuous batching.  A request names its volumes and
+ * outputs (a fastcod_subject whose xyz / offsets fields are ignored) and then
+ * receives its streamlines in chunks.  A worker thread admits waiting
+ * requests in arrival order while a slot is free and the HBM reserved for
+ * admitted requests (volumes, partial C and C_end, chunk staging) stays
+ * within the budget; admitted requests keep their volumes and partial C on
+ * the device.  Each iteration of the loop runs one batched pass over the next
+ * chunk of every active request, so requests that arrive while others run
+ * join the next pass and their work overlaps on the device; chunk uploads
+ * run on a copy stream beside the compute stream.  When a request's last
+ * chunk is done its C and C_end are written to its outputs.  The result of a
+ * request does not depend on the other requests in the mix.
+ *
+ * Chunk buffers (host or device) must stay valid and unchanged until the
+ * request is done.  Server calls are thread-safe; the context must outlive
+ * the server and is only read (device, options) at creation. */
+typedef struct fastcod_server fastcod_server;
+
+typedef struct {
+  int32_t status;       /* FASTCOD_OK, an error, or FASTCOD_ECANCELED (valid when done) */
+  int32_t done;
+  int64_t streamlines;  /* streamlines processed */
+  int64_t chunks;       /* chunks processed */
+  double t_submit;      /* seconds since the server was created */
+  double t_admit;
+  double t_done;
+} fastcod_request_info;
+
+/* max_slots: 1..128 requests on the device at once; hbm_budget_bytes: device
+ * memory the server may reserve for admitted requests (0: 90% of the free
+ * memory at creation). */
+FASTCOD_API int fastcod_server_create(fastcod_ctx* ctx, int32_t max_slots, int64_t hbm_budget_bytes,
+                                      fastcod_server** out);
+
+/* Queue a request; *request_id receives its id. */
+FASTCOD_API int fastcod_server_submit(fastcod_server* srv, const fastcod_subject* request_head,
+                                      uint64_t* request_id);
+
+/* Append a chunk of streamlines (offsets relative to the chunk: offsets[0] =
+ * 0, offsets[n_streamlines] = n_vertices); last = 1 marks the final chunk
+ * (an empty last chunk is allowed). */
+FASTCOD_API int fastcod_server_push_chunk(fastcod_server* srv, uint64_t request_id, const int32_t* xyz,
+                                          int64_t n_vertices, const int64_t* offsets, int64_t n_streamlines,
+                                          int32_t last);
+
+/* *done = 1 once the request finished; returns its status then. */
+FASTCOD_API int fastcod_server_poll(fastcod_server* srv, uint64_t request_id, int32_t* done);
+
+/* Block until the request finished or timeout_s passed (ETIMEOUT). */
+FASTCOD_API int fastcod_server_wait(fastcod_server* srv, uint64_t request_id, double timeout_s);
+
+/* Cancel a request (its outputs are not written; status ECANCELED). */
+FASTCOD_API int fastcod_server_cancel(fastcod_server* srv, uint64_t request_id);
+
+/* Timing and counts of a request. */
+FASTCOD_API int fastcod_server_request_info(fastcod_server* srv, uint64_t request_id, fastcod_request_info* out);
+
+/* Finish all admitted and queued work, stop the worker, free everything. */
+FASTCOD_API int fastcod_server_destroy(fastcod_server* srv);
+
 /* Message of the last error on this context ("" if none); owned by ctx,
  * valid until the next call on it.  NULL ctx: message of the last failed
  * fastcod_create on this thread. */

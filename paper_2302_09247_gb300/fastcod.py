@@ -42,7 +42,9 @@ EXPORTED = [
     "fastcod_add_streamlines", "fastcod_connectivity", "fastcod_endpoint_connectivity",
     "fastcod_reset", "fastcod_get_shape", "fastcod_get_stats", "fastcod_get_profile", "fastcod_sync",
     "fastcod_set_option", "fastcod_last_error", "fastcod_batch_run", "fastcod_batch_get_stats",
-    "fastcod_batch_get_info",
+    "fastcod_batch_get_info", "fastcod_server_create", "fastcod_server_submit", "fastcod_server_push_chunk",
+    "fastcod_server_poll", "fastcod_server_wait", "fastcod_server_cancel", "fastcod_server_request_info",
+    "fastcod_server_destroy",
 ]
 
 
@@ -77,6 +79,12 @@ class BatchInfo(ctypes.Structure):
                 ("ms_graph", ctypes.c_double)]
 
 
+class RequestInfo(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("done", ctypes.c_int32), ("streamlines", ctypes.c_int64),
+                ("chunks", ctypes.c_int64), ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double),
+                ("t_done", ctypes.c_double)]
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError(f"{LIB_PATH} is not built; run paper_2302_09247_gb300.build.build()")
@@ -100,6 +108,14 @@ def _load():
         "fastcod_batch_run": ([vp, ctypes.POINTER(Subject), i32], ctypes.c_int),
         "fastcod_batch_get_stats": ([vp, i32, ctypes.POINTER(Stats)], ctypes.c_int),
         "fastcod_batch_get_info": ([vp, ctypes.POINTER(BatchInfo)], ctypes.c_int),
+        "fastcod_server_create": ([vp, i32, i64, ctypes.POINTER(vp)], ctypes.c_int),
+        "fastcod_server_submit": ([vp, ctypes.POINTER(Subject), ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
+        "fastcod_server_push_chunk": ([vp, ctypes.c_uint64, vp, i64, vp, i64, i32], ctypes.c_int),
+        "fastcod_server_poll": ([vp, ctypes.c_uint64, ctypes.POINTER(i32)], ctypes.c_int),
+        "fastcod_server_wait": ([vp, ctypes.c_uint64, ctypes.c_double], ctypes.c_int),
+        "fastcod_server_cancel": ([vp, ctypes.c_uint64], ctypes.c_int),
+        "fastcod_server_request_info": ([vp, ctypes.c_uint64, ctypes.POINTER(RequestInfo)], ctypes.c_int),
+        "fastcod_server_destroy": ([vp], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -237,6 +253,57 @@ def fastcod_batch_get_info(ctx) -> dict:
     info = BatchInfo()
     _check(ctx, lib.fastcod_batch_get_info(ctx, ctypes.byref(info)))
     return {k: getattr(info, k) for k, _ in BatchInfo._fields_}
+
+
+def fastcod_server_create(ctx, max_slots: int = 8, hbm_budget_bytes: int = 0):
+    out = ctypes.c_void_p()
+    _check(ctx, lib.fastcod_server_create(ctx, max_slots, hbm_budget_bytes, ctypes.byref(out)))
+    return out
+
+
+def _scheck(rc):
+    if rc != FASTCOD_OK:
+        raise FastCodError(rc, "server call failed")
+    return rc
+
+
+def fastcod_server_submit(srv, head: Subject) -> int:
+    rid = ctypes.c_uint64()
+    _scheck(lib.fastcod_server_submit(srv, ctypes.byref(head), ctypes.byref(rid)))
+    return rid.value
+
+
+def fastcod_server_push_chunk(srv, rid: int, xyz, offsets, last: bool = False):
+    if xyz is None:
+        return _scheck(lib.fastcod_server_push_chunk(srv, rid, None, 0, None, 0, 1 if last else 0))
+    return _scheck(lib.fastcod_server_push_chunk(srv, rid, _ptr(xyz), int(xyz.shape[0]), _ptr(offsets),
+                                                 int(offsets.shape[0]) - 1, 1 if last else 0))
+
+
+def fastcod_server_poll(srv, rid: int):
+    """(done, status)"""
+    done = ctypes.c_int32()
+    rc = lib.fastcod_server_poll(srv, rid, ctypes.byref(done))
+    return bool(done.value), rc
+
+
+def fastcod_server_wait(srv, rid: int, timeout_s: float = 60.0) -> int:
+    """The request's status (FASTCOD_ETIMEOUT if it did not finish in time)."""
+    return lib.fastcod_server_wait(srv, rid, timeout_s)
+
+
+def fastcod_server_cancel(srv, rid: int):
+    return _scheck(lib.fastcod_server_cancel(srv, rid))
+
+
+def fastcod_server_request_info(srv, rid: int) -> dict:
+    info = RequestInfo()
+    _scheck(lib.fastcod_server_request_info(srv, rid, ctypes.byref(info)))
+    return {k: getattr(info, k) for k, _ in RequestInfo._fields_}
+
+
+def fastcod_server_destroy(srv):
+    return lib.fastcod_server_destroy(srv)
 
 
 class Context:

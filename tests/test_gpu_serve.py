@@ -1,0 +1,149 @@
+"""GPU tests of the served form (fastcod_server_*): continuous batching gives
+each request exactly its own result (bit-exact against the oracle and
+identical alone and in the mix), admission under a small HBM budget,
+cancellation and per-request errors leave the other requests intact."""
+import time
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests.gpu_helpers import as_device
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fc():
+    from paper_2302_09247_gb300 import fastcod
+    return fastcod
+
+
+@pytest.fixture(scope="module")
+def subjects():
+    out = {}
+    vols, tr = synth.make_subject(1, n_streamlines=60_000)
+    out["A"] = (vols, tr)
+    vols, tr = synth.make_subject(3, subject=2, n_streamlines=30_000)
+    out["B"] = (vols, tr)
+    vols, tr = synth.make_subject(0)
+    out["C"] = (vols, tr)
+    return out
+
+
+def _chunks(tr, n):
+    bounds = np.linspace(0, tr.n_streamlines, n + 1).astype(np.int64)
+    out = []
+    for c in range(n):
+        b, e = int(bounds[c]), int(bounds[c + 1])
+        out.append((np.ascontiguousarray(tr.xyz[tr.offsets[b]:tr.offsets[e]]),
+                    np.ascontiguousarray(tr.offsets[b:e + 1] - tr.offsets[b])))
+    return out
+
+
+class Req:
+    def __init__(self, fc, srv, vols, where="host"):
+        self.vols = vols
+        self.C = np.full((vols.n_roi, vols.n_targets), -3, dtype=np.int32)
+        self.Ce = np.full_like(self.C, -3)
+        if where == "device":
+            self.roi, self.lab = as_device(vols.roi), as_device(vols.lab)
+        else:
+            self.roi, self.lab = vols.roi, vols.lab
+        self.head = fc.make_subject(self.roi, self.lab, vols.dims, vols.n_roi, vols.n_targets,
+                                    np.zeros((0, 3), np.int32), np.zeros(1, np.int64), self.C, self.Ce)
+        self.id = fc.fastcod_server_submit(srv, self.head)
+        self.keep = []
+
+    def push(self, fc, srv, xyz, off, last=False, where="host"):
+        if where == "device":
+            xyz, off = as_device(xyz), as_device(off)
+        self.keep.append((xyz, off))
+        fc.fastcod_server_push_chunk(srv, self.id, xyz, off, last)
+
+
+def _oracle(vols, tr):
+    C, Ce, _ = oracle.connectivity(vols.roi, vols.lab, vols.dims, vols.n_roi, vols.n_targets, tr.xyz, tr.offsets)
+    return C, Ce
+
+
+def test_alone_equals_in_the_mix(fc, subjects):
+    vA, tA = subjects["A"]
+    ctx = fc.Context(0)
+    srv = fc.fastcod_server_create(ctx.ctx, 4, 0)
+    try:
+        ra = Req(fc, srv, vA)
+        for i, (x, o) in enumerate(_chunks(tA, 3)):
+            ra.push(fc, srv, x, o, last=(i == 2))
+        assert fc.fastcod_server_wait(srv, ra.id, 120.0) == fc.FASTCOD_OK
+        alone = ra.C.copy()
+        # the same request in a mix with two others, chunks interleaved
+        reqs = {k: Req(fc, srv, subjects[k][0], where=("device" if k == "B" else "host")) for k in "ABC"}
+        ch = {"A": _chunks(tA, 3), "B": _chunks(subjects["B"][1], 2), "C": _chunks(subjects["C"][1], 1)}
+        order = [("A", 0), ("B", 0), ("C", 0), ("A", 1), ("B", 1), ("A", 2)]
+        for k, i in order:
+            x, o = ch[k][i]
+            reqs[k].push(fc, srv, x, o, last=(i == len(ch[k]) - 1), where=("device" if k == "B" else "host"))
+        for k in "ABC":
+            assert fc.fastcod_server_wait(srv, reqs[k].id, 120.0) == fc.FASTCOD_OK
+            Cr, Cer = _oracle(*subjects[k])
+            np.testing.assert_array_equal(reqs[k].C, Cr, err_msg=k)
+            np.testing.assert_array_equal(reqs[k].Ce, Cer, err_msg=k)
+            info = fc.fastcod_server_request_info(srv, reqs[k].id)
+            assert info["done"] == 1 and info["streamlines"] == subjects[k][1].n_streamlines
+            assert info["t_submit"] <= info["t_admit"] <= info["t_done"]
+        np.testing.assert_array_equal(reqs["A"].C, alone)
+    finally:
+        fc.fastcod_server_destroy(srv)
+        ctx.close()
+
+
+def test_admission_under_small_budget(fc, subjects):
+    # a 1-byte budget admits one request at a time (the loop never deadlocks)
+    ctx = fc.Context(0)
+    srv = fc.fastcod_server_create(ctx.ctx, 8, 1)
+    try:
+        reqs = []
+        for k in "CBC":
+            r = Req(fc, srv, subjects[k][0])
+            x, o = _chunks(subjects[k][1], 1)[0]
+            r.push(fc, srv, x, o, last=True)
+            reqs.append((k, r))
+        infos = []
+        for k, r in reqs:
+            assert fc.fastcod_server_wait(srv, r.id, 120.0) == fc.FASTCOD_OK
+            np.testing.assert_array_equal(r.C, _oracle(*subjects[k])[0])
+            infos.append(fc.fastcod_server_request_info(srv, r.id))
+        for a, b in zip(infos, infos[1:]):
+            assert b["t_admit"] >= a["t_done"] - 1e-3
+    finally:
+        fc.fastcod_server_destroy(srv)
+        ctx.close()
+
+
+def test_cancel_and_errors_are_isolated(fc, subjects):
+    ctx = fc.Context(0)
+    srv = fc.fastcod_server_create(ctx.ctx, 4, 0)
+    try:
+        vC, tC = subjects["C"]
+        good = Req(fc, srv, vC)
+        x, o = _chunks(tC, 1)[0]
+        good.push(fc, srv, x, o, last=True)
+        cancelled = Req(fc, srv, vC)
+        cancelled.push(fc, srv, x, o)
+        fc.fastcod_server_cancel(srv, cancelled.id)
+        bad = Req(fc, srv, vC)
+        o2 = o.copy()
+        o2[5], o2[6] = o2[6], o2[5]
+        bad.push(fc, srv, x, o2, last=True)
+        assert fc.fastcod_server_wait(srv, good.id, 120.0) == fc.FASTCOD_OK
+        assert fc.fastcod_server_wait(srv, cancelled.id, 120.0) == fc.FASTCOD_ECANCELED
+        assert fc.fastcod_server_wait(srv, bad.id, 120.0) == fc.FASTCOD_EINVAL
+        np.testing.assert_array_equal(good.C, _oracle(vC, tC)[0])
+        assert (cancelled.C == -3).all()
+        done, rc = fc.fastcod_server_poll(srv, good.id)
+        assert done and rc == fc.FASTCOD_OK
+    finally:
+        fc.fastcod_server_destroy(srv)
+        ctx.close()
