@@ -30,7 +30,7 @@ struct Layout {
   size_t scratch, gstate, states, tasks, surv, ovf, staged_end;
   std::vector<size_t> roi_in, lab_in, xyz_in, off_in;  // staging of host inputs (or SIZE_MAX)
   std::vector<size_t> code, lab, bricks, C, Cend;
-  size_t near_tmp;
+  size_t planes;
   std::vector<size_t> near;
   size_t total;
   int64_t scratch_words;
@@ -86,11 +86,11 @@ Layout plan(const fastcod_subject* subs, int32_t n, const std::vector<int>& host
     o = align256(o + (bytes ? bytes : 1));
     return at;
   };
-  int64_t maxw = 1, maxpad = 1;
+  int64_t maxw = 1, maxplanes = 1;
   int32_t ntasks = 0;
   for (int32_t i = 0; i < n; ++i) {
     maxw = std::max(maxw, fc::overflow_scratch_words(subs[i].n_roi, subs[i].n_targets));
-    maxpad = std::max(maxpad, (int64_t)(subs[i].dims[0] + 2) * (subs[i].dims[1] + 2) * (subs[i].dims[2] + 2));
+    maxplanes = std::max(maxplanes, fc::plane_words(subs[i].dims[0], subs[i].dims[1], subs[i].dims[2]));
     ntasks += (int32_t)std::max<int64_t>(1, (subs[i].n_vertices + kTaskVertices - 1) / kTaskVertices);
   }
   L.scratch_words = maxw;
@@ -122,7 +122,7 @@ Layout plan(const fastcod_subject* subs, int32_t n, const std::vector<int>& host
     L.Cend.push_back(take(nm * 4));
   }
   // the configuration-dependent part last, so that the rest keeps its place
-  L.near_tmp = take((size_t)maxpad * 2);
+  L.planes = take((size_t)maxplanes * 4);
   for (int32_t i = 0; i < n; ++i) L.near.push_back(take((size_t)near_words(subs[i].dims, near_log2) * 4));
   L.total = o;
   return L;
@@ -221,8 +221,8 @@ int capture(fastcod_ctx* c, const fastcod_subject* subs, int32_t n, const Layout
     const uint16_t* lab = L.lab_in[i] != SIZE_MAX ? at<uint16_t>(A, L.lab_in[i]) : S.target_labels;
     if (e == cudaSuccess)
       e = fc::launch_volume_prep(roi, lab, nvox, bs.v, const_cast<uint32_t*>(bs.v.code), const_cast<uint16_t*>(bs.v.lab),
-                                 const_cast<uint32_t*>(bs.v.bricks), bs.st, c->stream);
-    if (e == cudaSuccess) e = fc::launch_near(bs.v, at<uint8_t>(A, L.near_tmp), const_cast<uint32_t*>(bs.v.near), c->stream);
+                                 const_cast<uint32_t*>(bs.v.bricks), at<uint32_t>(A, L.planes), bs.st, c->stream);
+    if (e == cudaSuccess) e = fc::launch_near(bs.v, at<uint32_t>(A, L.planes), const_cast<uint32_t*>(bs.v.near), c->stream);
   }
   if (e == cudaSuccess)
     e = fc::launch_prefilter_batch(tbl, at<fc::BatchTask>(A, L.tasks), L.ntasks, c->prefilter != 0, cfg.ctas,
@@ -244,7 +244,7 @@ int capture(fastcod_ctx* c, const fastcod_subject* subs, int32_t n, const Layout
   return FASTCOD_OK;
 }
 
-int kernels_per_run(int32_t n) { return 6 * n + 3; }
+int kernels_per_run(int32_t n) { return 2 * n + 3; }
 
 // Stage inputs, (re)capture when the shape changed, run the graph.
 int run_config(fastcod_ctx* c, const fastcod_subject* subs, int32_t n, const std::vector<int>& host_in,

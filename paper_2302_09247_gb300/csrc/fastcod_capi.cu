@@ -338,26 +338,24 @@ FASTCOD_API int fastcod_set_volumes(fastcod_ctx* c, const int32_t* roi, const ui
   c->scratch_ctas = (int32_t)ctas;
   CU(cudaMalloc(&c->d_scratch, (size_t)(ctas * words * 4)));
   CU(cudaMemsetAsync(c->d_scratch, 0, (size_t)(ctas * words * 4), c->stream));
-  // near grid (the prefilter's dilated occupancy)
+  // near grid (the prefilter's dilated occupancy), built from the bit planes
   c->near_shift = c->near_log2;
   fc::VolView v = vol_view(c);
   const int64_t near_words = (int64_t)v.nwx * v.nny * v.nnz;
-  const int64_t pad_vox = (int64_t)(dx + 2) * (dy + 2) * (dz + 2);
   CU(cudaMalloc(&c->d_near, (size_t)near_words * 4));
   v.near = c->d_near;
-  CU(fc::launch_volume_prep(d_roi, d_labin, nvox, v, c->d_code, c->d_lab, c->d_bricks, c->d_state, c->stream));
+  uint32_t* planes = nullptr;
+  CU(cudaMalloc(&planes, (size_t)fc::plane_words(dx, dy, dz) * 4));
+  cudaError_t e = fc::launch_volume_prep(d_roi, d_labin, nvox, v, c->d_code, c->d_lab, c->d_bricks, planes,
+                                         c->d_state, c->stream);
+  if (e == cudaSuccess) e = fc::launch_near(v, planes, c->d_near, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  cudaFree(planes);
+  CU(e);
   int rc = sync_check(c);
   if (rc) {
     free_volumes(c);
     return rc;
-  }
-  {
-    uint8_t* tmp = nullptr;
-    CU(cudaMalloc(&tmp, (size_t)pad_vox * 2));
-    cudaError_t e = fc::launch_near(v, tmp, c->d_near, c->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-    cudaFree(tmp);
-    CU(e);
   }
   c->has_vol = true;
   return zero_accumulators(c);

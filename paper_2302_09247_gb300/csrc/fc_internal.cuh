@@ -118,11 +118,13 @@ constexpr uint32_t kModeVertexSampled = 2u;
 // K1: per-voxel code, label copy and brick bits from the caller's volumes.
 cudaError_t launch_volume_max(const int32_t* roi, const uint16_t* lab, int64_t nvox, DevState* st,
                               cudaStream_t s);
+// planes: plane_words(dx, dy, dz) words, the ROI and label bit planes.
 cudaError_t launch_volume_prep(const int32_t* roi, const uint16_t* lab, int64_t nvox, VolView v,
-                               uint32_t* code, uint16_t* lab_out, uint32_t* bricks, DevState* st,
+                               uint32_t* code, uint16_t* lab_out, uint32_t* bricks, uint32_t* planes, DevState* st,
                                cudaStream_t s);
-// Near grid from the per-voxel code; tmp: two byte planes of the padded grid.
-cudaError_t launch_near(const VolView& v, uint8_t* tmp, uint32_t* near, cudaStream_t s);
+int64_t plane_words(int32_t dx, int32_t dy, int32_t dz);
+// Near grid from the bit planes written by launch_volume_prep.
+cudaError_t launch_near(const VolView& v, const uint32_t* planes, uint32_t* near, cudaStream_t s);
 
 // K2: prefilter + compaction (+ validation and voxel-step count).
 // ctas_per_sm: 3 or 4 (the register budget the kernel is compiled for).

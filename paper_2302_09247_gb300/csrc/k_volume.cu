@@ -28,74 +28,98 @@ __global__ void __launch_bounds__(256) volume_max_kernel(const int32_t* __restri
   }
 }
 
+// One thread per voxel; a warp covers 32 consecutive voxels of a row, so the
+// warp's ballots are the row's ROI / label bit-plane words (planes: two
+// planes of Dy*Dz rows of ceil(Dx/32) words).
 __global__ void __launch_bounds__(128) volume_prep_kernel(const int32_t* __restrict__ roi,
                                                           const uint16_t* __restrict__ lab, VolView v,
                                                           uint32_t* __restrict__ code,
                                                           uint16_t* __restrict__ lab_out,
-                                                          uint32_t* __restrict__ bricks, DevState* st) {
+                                                          uint32_t* __restrict__ bricks, uint32_t* __restrict__ planes,
+                                                          DevState* st) {
   const int32_t x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
-  if (x >= v.dx) return;
+  const bool in = x < v.dx;
   const int32_t i = x + v.dx * (y + v.dy * z);
-  const int32_t r = roi[i];
-  const int32_t l = (int32_t)lab[i];
-  if (r < -1 || r >= v.n_roi || l > v.n_lab) {
-    set_error(st, kErrVolume, i);
-    return;
+  int32_t r = -1, l = 0;
+  if (in) {
+    r = roi[i];
+    l = (int32_t)lab[i];
+    if (r < -1 || r >= v.n_roi || l > v.n_lab) {
+      set_error(st, kErrVolume, i);
+      r = -1;
+      l = 0;
+    }
+    code[i] = r >= 0 ? (kCodeRoi | (l > 0 ? kCodeRoiLabelled : 0u) | (uint32_t)r) : (uint32_t)l;
+    lab_out[i] = (uint16_t)l;
+    const uint32_t bits = (r >= 0 ? 1u : 0u) | (l > 0 ? 2u : 0u);
+    if (bits) {
+      const int32_t b = (x >> kBrickLog2) + v.bx * ((y >> kBrickLog2) + v.by * (z >> kBrickLog2));
+      atomicOr(bricks + (b >> 4), bits << ((b & 15) * 2));
+    }
   }
-  code[i] = r >= 0 ? (kCodeRoi | (l > 0 ? kCodeRoiLabelled : 0u) | (uint32_t)r) : (uint32_t)l;
-  lab_out[i] = (uint16_t)l;
-  const uint32_t bits = (r >= 0 ? 1u : 0u) | (l > 0 ? 2u : 0u);
-  if (bits) {
-    const int32_t b = (x >> kBrickLog2) + v.bx * ((y >> kBrickLog2) + v.by * (z >> kBrickLog2));
-    atomicOr(bricks + (b >> 4), bits << ((b & 15) * 2));
+  const uint32_t mr = __ballot_sync(kFull, r >= 0);
+  const uint32_t mt = __ballot_sync(kFull, l > 0);
+  const int32_t wb = (v.dx + 31) >> 5;
+  const int32_t w = (x >> 5);
+  if (lane_id() == 0 && w < wb) {
+    const int64_t row = (int64_t)y + (int64_t)v.dy * z;
+    const int64_t rows = (int64_t)v.dy * v.dz;
+    planes[row * wb + w] = mr;
+    planes[(rows + row) * wb + w] = mt;
   }
 }
 
 // ---------------------------------------------------------------- near grid
-// Occupancy bits of every voxel on the padded grid (zero border), then an OR
-// over +-1 along x, y and z in turn (the 3x3x3 dilation), then ORed over the
-// cells and packed sixteen cells per word.
+// One thread per near word (16 cells along x).  Cell cx covers padded voxels
+// [cs*cx, cs*cx + cs) per axis (padded = voxel + 1); its bits are the OR of
+// the grid voxels within Chebyshev distance 1 of it, i.e. the voxels
+// [cs*cx - 2, cs*cx + cs - 1] per axis.  Rows of the two bit planes are ORed
+// over the y/z range, then every cell tests its (cs + 2)-bit x window.
 
-__global__ void __launch_bounds__(128) near_seed_kernel(const uint32_t* __restrict__ code, VolView v,
-                                                        uint8_t* __restrict__ pad) {
-  const int32_t x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
-  if (x >= v.dx) return;
-  const uint32_t c = code[x + v.dx * (y + v.dy * z)];
-  const uint8_t bits = (c & kCodeRoi) ? (uint8_t)(1u | ((c & kCodeRoiLabelled) ? 2u : 0u)) : (uint8_t)(c ? 2u : 0u);
-  const int32_t px = v.dx + 2, py = v.dy + 2;
-  pad[(x + 1) + px * ((y + 1) + py * (z + 1))] = bits;
+__device__ __forceinline__ uint32_t plane_word(const uint32_t* __restrict__ rowp, int32_t w, int32_t wb) {
+  return (w >= 0 && w < wb) ? __ldg(rowp + w) : 0u;
 }
 
-// grid (x blocks, py, pz) over the padded grid
-__global__ void __launch_bounds__(128) near_dilate_kernel(const uint8_t* __restrict__ in, uint8_t* __restrict__ out,
-                                                          int32_t px, int32_t py, int32_t pz, int axis) {
-  const int32_t x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
-  if (x >= px) return;
-  const int32_t i = x + px * (y + py * z);
-  const int32_t c = axis == 0 ? x : (axis == 1 ? y : z);
-  const int32_t extent = axis == 0 ? px : (axis == 1 ? py : pz);
-  const int32_t stride = axis == 0 ? 1 : (axis == 1 ? px : px * py);
-  uint8_t b = in[i];
-  if (c > 0) b |= in[i - stride];
-  if (c + 1 < extent) b |= in[i + stride];
-  out[i] = b;
-}
-
-// grid (word blocks, nny, nnz): one thread per 16-cell word
-__global__ void __launch_bounds__(128) near_pack_kernel(const uint8_t* __restrict__ in, VolView v,
+// grid (word blocks, nny, nnz)
+__global__ void __launch_bounds__(128) near_pack_kernel(const uint32_t* __restrict__ planes, VolView v,
                                                         uint32_t* __restrict__ near) {
   const int32_t wx = blockIdx.x * blockDim.x + threadIdx.x, cy = blockIdx.y, cz = blockIdx.z;
   if (wx >= v.nwx) return;
-  const int32_t px = v.dx + 2, py = v.dy + 2, pz = v.dz + 2;
   const int32_t cs = 1 << v.nsh;
-  const int32_t y1 = min(py, (cy + 1) * cs), z1 = min(pz, (cz + 1) * cs);
+  const int32_t wb = (v.dx + 31) >> 5;
+  const int64_t rows = (int64_t)v.dy * v.dz;
+  const int32_t x_lo = cs * 16 * wx - 2;  // first voxel x of the word's window
+  const int32_t w0 = x_lo >> 5;          // floor for negative x_lo too
+  const int32_t sh = x_lo & 31;
+  uint32_t acc[2][5] = {{0u, 0u, 0u, 0u, 0u}, {0u, 0u, 0u, 0u, 0u}};  // bits x_lo .. x_lo + 159
+  const int32_t ylo = max(0, cs * cy - 2), yhi = min(v.dy - 1, cs * cy + cs - 1);
+  const int32_t zlo = max(0, cs * cz - 2), zhi = min(v.dz - 1, cs * cz + cs - 1);
+  for (int32_t z = zlo; z <= zhi; ++z)
+    for (int32_t y = ylo; y <= yhi; ++y) {
+      const int64_t row = (int64_t)y + (int64_t)v.dy * z;
+#pragma unroll
+      for (int p = 0; p < 2; ++p) {
+        const uint32_t* rowp = planes + ((int64_t)p * rows + row) * wb;
+        uint32_t w[6];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) w[k] = plane_word(rowp, w0 + k, wb);
+#pragma unroll
+        for (int k = 0; k < 5; ++k) acc[p][k] |= __funnelshift_r(w[k], w[k + 1], sh);
+      }
+    }
+  const uint32_t wmask = (1u << (cs + 2)) - 1u;
   uint32_t word = 0;
+#pragma unroll
   for (int k = 0; k < 16; ++k) {
-    const int32_t x0 = (wx * 16 + k) * cs, x1 = min(px, x0 + cs);
+    const int32_t idx = cs * k;  // window of cell 16*wx + k in acc
+    const int32_t q = idx >> 5, r = idx & 31;
     uint32_t bits = 0;
-    for (int32_t z = cz * cs; z < z1; ++z)
-      for (int32_t y = cy * cs; y < y1; ++y)
-        for (int32_t x = x0; x < x1; ++x) bits |= in[x + px * (y + py * z)];
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+      const uint32_t lo = q == 0 ? acc[p][0] : (q == 1 ? acc[p][1] : (q == 2 ? acc[p][2] : acc[p][3]));
+      const uint32_t hi = q == 0 ? acc[p][1] : (q == 1 ? acc[p][2] : (q == 2 ? acc[p][3] : acc[p][4]));
+      if (__funnelshift_r(lo, hi, r) & wmask) bits |= 1u << p;
+    }
     word |= bits << (2 * k);
   }
   near[wx + v.nwx * (cy + v.nny * cz)] = word;
@@ -113,26 +137,20 @@ cudaError_t launch_volume_max(const int32_t* roi, const uint16_t* lab, int64_t n
 }
 
 cudaError_t launch_volume_prep(const int32_t* roi, const uint16_t* lab, int64_t nvox, VolView v,
-                               uint32_t* code, uint16_t* lab_out, uint32_t* bricks, DevState* st,
+                               uint32_t* code, uint16_t* lab_out, uint32_t* bricks, uint32_t* planes, DevState* st,
                                cudaStream_t s) {
   (void)nvox;
-  volume_prep_kernel<<<dim3((v.dx + 127) / 128, v.dy, v.dz), 128, 0, s>>>(roi, lab, v, code, lab_out, bricks, st);
+  volume_prep_kernel<<<dim3((v.dx + 127) / 128, v.dy, v.dz), 128, 0, s>>>(roi, lab, v, code, lab_out, bricks, planes,
+                                                                           st);
   return cudaGetLastError();
 }
 
-cudaError_t launch_near(const VolView& v, uint8_t* tmp, uint32_t* near, cudaStream_t s) {
-  const int32_t px = v.dx + 2, py = v.dy + 2, pz = v.dz + 2;
-  const int64_t n = (int64_t)px * py * pz;
-  uint8_t* a = tmp;
-  uint8_t* b = tmp + n;
-  cudaError_t e = cudaMemsetAsync(a, 0, (size_t)n, s);
-  if (e != cudaSuccess) return e;
-  near_seed_kernel<<<dim3((v.dx + 127) / 128, v.dy, v.dz), 128, 0, s>>>(v.code, v, a);
-  const dim3 pg((px + 127) / 128, py, pz);
-  near_dilate_kernel<<<pg, 128, 0, s>>>(a, b, px, py, pz, 0);
-  near_dilate_kernel<<<pg, 128, 0, s>>>(b, a, px, py, pz, 1);
-  near_dilate_kernel<<<pg, 128, 0, s>>>(a, b, px, py, pz, 2);
-  near_pack_kernel<<<dim3((v.nwx + 127) / 128, v.nny, v.nnz), 128, 0, s>>>(b, v, near);
+int64_t plane_words(int32_t dx, int32_t dy, int32_t dz) {
+  return 2 * (int64_t)((dx + 31) / 32) * dy * dz;
+}
+
+cudaError_t launch_near(const VolView& v, const uint32_t* planes, uint32_t* near, cudaStream_t s) {
+  near_pack_kernel<<<dim3((v.nwx + 127) / 128, v.nny, v.nnz), 128, 0, s>>>(planes, v, near);
   return cudaGetLastError();
 }
 

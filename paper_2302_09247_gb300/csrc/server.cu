@@ -124,7 +124,7 @@ size_t resident_bytes(const fastcod_subject& h, int near_log2) {
 size_t chunk_bytes(const Chunk& k) { return a256((size_t)k.nv * 12 + 16) + a256((size_t)(k.ns + 1) * 8); }
 
 // Worker: allocate and prepare an admitted request's volumes (compute stream).
-cudaError_t setup_request(fastcod_server* S, Request* r, uint8_t** tmp, size_t* tmp_cap) {
+cudaError_t setup_request(fastcod_server* S, Request* r, uint32_t** tmp, size_t* tmp_cap) {
   const fastcod_subject& h = r->head;
   const int64_t nvox = (int64_t)h.dims[0] * h.dims[1] * h.dims[2];
   const int64_t nb = (int64_t)((h.dims[0] + 3) / 4) * ((h.dims[1] + 3) / 4) * ((h.dims[2] + 3) / 4);
@@ -176,15 +176,15 @@ cudaError_t setup_request(fastcod_server* S, Request* r, uint8_t** tmp, size_t* 
   if (e == cudaSuccess) e = cudaMemsetAsync(r->acc.Cend, 0, nm * 4, S->compute);
   if (e == cudaSuccess) e = cudaMemsetAsync(r->st, 0, sizeof(DevState), S->compute);
   if (e == cudaSuccess) e = cudaMemsetAsync(const_cast<uint32_t*>(v.bricks), 0, (nb + 15) / 16 * 4, S->compute);
-  if (e == cudaSuccess)
-    e = fc::launch_volume_prep(roi, lab, nvox, v, const_cast<uint32_t*>(v.code), const_cast<uint16_t*>(v.lab),
-                               const_cast<uint32_t*>(v.bricks), r->st, S->compute);
-  const size_t need = (size_t)(h.dims[0] + 2) * (h.dims[1] + 2) * (h.dims[2] + 2) * 2;
+  const size_t need = (size_t)fc::plane_words(h.dims[0], h.dims[1], h.dims[2]) * 4;
   if (e == cudaSuccess && need > *tmp_cap) {
     if (*tmp) e = cudaFreeAsync(*tmp, S->compute);
     if (e == cudaSuccess) e = cudaMallocAsync((void**)tmp, need, S->compute);
     if (e == cudaSuccess) *tmp_cap = need;
   }
+  if (e == cudaSuccess)
+    e = fc::launch_volume_prep(roi, lab, nvox, v, const_cast<uint32_t*>(v.code), const_cast<uint16_t*>(v.lab),
+                               const_cast<uint32_t*>(v.bricks), *tmp, r->st, S->compute);
   if (e == cudaSuccess) e = fc::launch_near(v, *tmp, const_cast<uint32_t*>(v.near), S->compute);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&r->done_ev, cudaEventDisableTiming);
   return e;
@@ -222,7 +222,7 @@ void fail_request(fastcod_server* S, Request* r, int status) {
 // One pass of the loop: admit, set up, run one batched pass over the next
 // chunk of every active request, complete finished requests.  Returns true
 // when it did any work.
-bool iterate(fastcod_server* S, uint8_t** tmp, size_t* tmp_cap) {
+bool iterate(fastcod_server* S, uint32_t** tmp, size_t* tmp_cap) {
   std::vector<Request*> setups, finishing;
   std::vector<std::pair<Request*, Chunk>> work;
   std::vector<std::pair<Request*, bool>> lasts;
@@ -408,7 +408,7 @@ bool iterate(fastcod_server* S, uint8_t** tmp, size_t* tmp_cap) {
 
 void worker_main(fastcod_server* S) {
   cudaSetDevice(S->device);
-  uint8_t* tmp = nullptr;
+  uint32_t* tmp = nullptr;
   size_t tmp_cap = 0;
   for (;;) {
     const bool did = iterate(S, &tmp, &tmp_cap);

@@ -131,3 +131,19 @@ def test_cfg1_full_bench_configuration():
     assert st["voxel_steps"] == sr["voxel_steps"]
     assert st["pairs"] == sr["pairs"]
     assert sr["n_contributing"] <= st["survivors"]
+
+
+@pytest.mark.parametrize("near_log2", [0, 1, 2, 3])
+@pytest.mark.parametrize("seed", range(3))
+def test_near_grid_cell_sizes(near_log2, seed):
+    # every near-grid cell size must keep the prefilter conservative: the
+    # result is the same exact C whatever the cell size
+    from paper_2302_09247_gb300 import fastcod as fc
+    rng = np.random.default_rng(3000 + seed)
+    dims = tuple(int(v) for v in rng.integers(3, 40, size=3))
+    roi, lab, N, M = tiny.random_volumes(rng, dims, n_roi=0, n_labels=5, p_roi=0.02, p_lab=0.05)
+    xyz, off = tiny.random_streamlines(rng, dims, 400, max_len=60)
+    _check(roi, lab, dims, N, M, xyz, off, "device", {fc.FASTCOD_OPT_NEAR_LOG2: near_log2})
+    vols, tr = synth.make_subject(0, n_streamlines=5000)
+    _check(vols.roi, vols.lab, vols.dims, vols.n_roi, vols.n_targets, tr.xyz, tr.offsets, "device",
+           {fc.FASTCOD_OPT_NEAR_LOG2: near_log2})
