@@ -292,9 +292,40 @@ FASTCOD_API int fastcod_server_request_info(fastcod_server* srv, uint64_t reques
 /* Finish all admitted and queued work, stop the worker, free everything. */
 FASTCOD_API int fastcod_server_destroy(fastcod_server* srv);
 
+/* ------------------------------------------------------- allocation-free
+ * C and C_end of one subject with no device allocation at all, neither by
+ * the caller nor by the library.  It serves callers that cannot allocate
+ * device memory: a host application whose own allocator owns every byte of
+ * device memory, or a process already at its memory limit, can still run the
+ * computation on buffers it already holds.  The paper has no counterpart;
+ * this is an interface of this library.
+ *
+ * Every pointer must be device memory of cuda_device: the volumes, the
+ * streamlines (xyz 16-byte alignment not required) and the outputs C_out and
+ * Cend_out (int32 [N][M], overwritten with the result).  Work is ordered on
+ * cuda_stream (NULL: the default stream) and the call returns once it is
+ * done.  Limits: 1 <= n_roi <= 16384 and 1 <= n_targets <= 1023; larger
+ * problems are rejected with FASTCOD_EINVAL (use the context API).  Other
+ * validation and results are those of fastcod_set_volumes +
+ * fastcod_add_streamlines + fastcod_connectivity /
+ * fastcod_endpoint_connectivity.
+ *
+ * Its working memory is one fixed device array of the library (2.3 MB),
+ * present on every device that loads the library until the process exits,
+ * and shared by every call on that device: each call clears it first, so
+ * calls that overlap on the GPU (on different streams or host threads) race
+ * and must not be issued.  The first call on a device looks up the array's
+ * device address with cudaGetSymbolAddress; make that first call before any
+ * stream capture.  Error messages: fastcod_last_error(NULL). */
+FASTCOD_API int fastcod_connectivity_noalloc(int cuda_device, void* cuda_stream, const int32_t* roi_index_map,
+                                             const uint16_t* target_labels, int32_t dim_x, int32_t dim_y,
+                                             int32_t dim_z, int32_t n_roi, int32_t n_targets, const int32_t* xyz,
+                                             int64_t n_vertices, const int64_t* offsets, int64_t n_streamlines,
+                                             int32_t* C_out, int32_t* Cend_out);
+
 /* Message of the last error on this context ("" if none); owned by ctx,
  * valid until the next call on it.  NULL ctx: message of the last failed
- * fastcod_create on this thread. */
+ * fastcod_create or fastcod_connectivity_noalloc on this thread. */
 FASTCOD_API const char* fastcod_last_error(const fastcod_ctx* ctx);
 
 #ifdef __cplusplus

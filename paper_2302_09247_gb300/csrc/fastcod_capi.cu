@@ -46,6 +46,11 @@ int grow(fastcod_ctx* c, void** p, size_t* cap, size_t need) {
   return FASTCOD_OK;
 }
 
+std::string& thread_error() {
+  static thread_local std::string msg;
+  return msg;
+}
+
 }  // namespace fcapi
 
 namespace {
@@ -54,7 +59,6 @@ using fcapi::fail;
 using fcapi::grow;
 using fcapi::ptr_kind;
 
-thread_local std::string g_create_err;
 
 void free_volumes(fastcod_ctx* c) {
   cudaFree(c->d_code);
@@ -204,19 +208,19 @@ extern "C" {
 
 FASTCOD_API int fastcod_create(fastcod_ctx** out, int cuda_device, uint32_t flags) {
   if (!out) {
-    g_create_err = "out is NULL";
+    fcapi::thread_error() = "out is NULL";
     return FASTCOD_EINVAL;
   }
   *out = nullptr;
   int n = 0;
   if (cudaGetDeviceCount(&n) != cudaSuccess || cuda_device < 0 || cuda_device >= n) {
     (void)cudaGetLastError();
-    g_create_err = "no such CUDA device";
+    fcapi::thread_error() = "no such CUDA device";
     return FASTCOD_EINVAL;
   }
   fastcod_ctx* c = new (std::nothrow) fastcod_ctx();
   if (!c) {
-    g_create_err = "host allocation failed";
+    fcapi::thread_error() = "host allocation failed";
     return FASTCOD_ENOMEM;
   }
   c->device = cuda_device;
@@ -238,7 +242,7 @@ FASTCOD_API int fastcod_create(fastcod_ctx** out, int cuda_device, uint32_t flag
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) rc = FASTCOD_ECUDA;
   } while (0);
   if (rc) {
-    g_create_err = std::string("CUDA initialisation failed: ") + cudaGetErrorString(cudaGetLastError());
+    fcapi::thread_error() = std::string("CUDA initialisation failed: ") + cudaGetErrorString(cudaGetLastError());
     fastcod_destroy(c);
     return rc;
   }
@@ -541,7 +545,7 @@ FASTCOD_API int fastcod_set_option(fastcod_ctx* c, int32_t key, int64_t value) {
 }
 
 FASTCOD_API const char* fastcod_last_error(const fastcod_ctx* c) {
-  if (!c) return g_create_err.c_str();
+  if (!c) return fcapi::thread_error().c_str();
   return c->err.c_str();
 }
 

@@ -79,6 +79,8 @@ int ptr_kind(const void* p, int dev);
 int grow(fastcod_ctx* c, void** p, size_t* cap, size_t need);
 // Release the batched form's state (batch.cu).
 void batch_free(fastcod_ctx* c);
+// Message of the last failed call on this thread that has no context.
+std::string& thread_error();
 }  // namespace fcapi
 
 #define CU(call)                                                                                   \

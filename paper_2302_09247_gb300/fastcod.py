@@ -44,7 +44,7 @@ EXPORTED = [
     "fastcod_set_option", "fastcod_last_error", "fastcod_batch_run", "fastcod_batch_get_stats",
     "fastcod_batch_get_info", "fastcod_server_create", "fastcod_server_submit", "fastcod_server_push_chunk",
     "fastcod_server_poll", "fastcod_server_wait", "fastcod_server_cancel", "fastcod_server_request_info",
-    "fastcod_server_destroy",
+    "fastcod_server_destroy", "fastcod_connectivity_noalloc",
 ]
 
 
@@ -116,6 +116,8 @@ def _load():
         "fastcod_server_cancel": ([vp, ctypes.c_uint64], ctypes.c_int),
         "fastcod_server_request_info": ([vp, ctypes.c_uint64, ctypes.POINTER(RequestInfo)], ctypes.c_int),
         "fastcod_server_destroy": ([vp], ctypes.c_int),
+        "fastcod_connectivity_noalloc": ([ctypes.c_int, vp, vp, vp, i32, i32, i32, i32, i32, vp, i64, vp, i64, vp,
+                                          vp], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -304,6 +306,18 @@ def fastcod_server_request_info(srv, rid: int) -> dict:
 
 def fastcod_server_destroy(srv):
     return lib.fastcod_server_destroy(srv)
+
+
+def fastcod_connectivity_noalloc(device, stream, roi, lab, dims, n_roi, n_targets, xyz, offsets, C_out, Cend_out):
+    """The allocation-free entry point: every array is device memory."""
+    s = getattr(stream, "cuda_stream", stream)
+    dx, dy, dz = (int(d) for d in dims)
+    rc = lib.fastcod_connectivity_noalloc(device, s, _ptr(roi), _ptr(lab), dx, dy, dz, int(n_roi), int(n_targets),
+                                          _ptr(xyz), int(xyz.shape[0]), _ptr(offsets), int(offsets.shape[0]) - 1,
+                                          _ptr(C_out), _ptr(Cend_out))
+    if rc != FASTCOD_OK:
+        raise FastCodError(rc, lib.fastcod_last_error(None).decode())
+    return rc
 
 
 class Context:
