@@ -192,13 +192,219 @@ def _config(cfg, vols, tr, sample_note=None):
     return c
 
 
+def run_batched(args):
+    """64 heterogeneous subjects in one fastcod_batch_run (a CUDA graph per batch
+    shape, autotuned) against one set_volumes + add_streamlines + readback per
+    subject; subjects/s of both, device-resident inputs and outputs."""
+    import torch
+
+    import synth
+    from paper_2302_09247_gb300 import fastcod as fc
+
+    ws, rank, local = _dist()
+    if rank != 0:
+        return 0
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    subs, steps_total, nv_total, ns_total = [], 0, 0, 0
+    t0 = time.perf_counter()
+    for s in range(1, args.subjects + 1):
+        d = synth.batched_subject_draws(s)
+        n = max(1000, int(d["ns"] * args.count_scale))
+        vols, tr = synth.make_subject(3, subject=s, n_streamlines=n)
+        subs.append(dict(roi=torch.from_numpy(vols.roi).to(dev), lab=torch.from_numpy(vols.lab.view(np.int16)).to(dev),
+                         dims=vols.dims, N=vols.n_roi, M=vols.n_targets, xyz=torch.from_numpy(tr.xyz).to(dev),
+                         off=torch.from_numpy(tr.offsets).to(dev),
+                         C=torch.empty((vols.n_roi, vols.n_targets), dtype=torch.int32, device=dev),
+                         Ce=torch.empty((vols.n_roi, vols.n_targets), dtype=torch.int32, device=dev)))
+        nv_total += tr.n_vertices
+        ns_total += tr.n_streamlines
+    gen_s = time.perf_counter() - t0
+    objs = [fc.make_subject(x["roi"], x["lab"], x["dims"], x["N"], x["M"], x["xyz"], x["off"], x["C"], x["Ce"])
+            for x in subs]
+    ctx = fc.Context(local)
+    for _ in range(args.warmup):
+        fc.fastcod_batch_run(ctx.ctx, objs)
+    for i in range(len(subs)):
+        steps_total += fc.fastcod_batch_get_stats(ctx.ctx, i)["voxel_steps"]
+    launches0 = ctx.profile()["kernel_launches"]
+    clocks = ClockSampler(local)
+    clocks.start()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    graph_ms = 0.0
+    for _ in range(args.steps):
+        fc.fastcod_batch_run(ctx.ctx, objs)
+        graph_ms += fc.fastcod_batch_get_info(ctx.ctx)["ms_graph"]
+    torch.cuda.synchronize()
+    batch_s = (time.perf_counter() - t0) / args.steps
+    clk = clocks.stop()
+    info = fc.fastcod_batch_get_info(ctx.ctx)
+    launches = ctx.profile()["kernel_launches"] - launches0
+    Cb = [x["C"].clone() for x in subs]
+
+    def plain():
+        for x in subs:
+            ctx.set_volumes(x["roi"], x["lab"], x["dims"], x["N"], x["M"])
+            ctx.add_streamlines(x["xyz"], x["off"])
+            fc.fastcod_connectivity(ctx.ctx, x["C"])
+            fc.fastcod_endpoint_connectivity(ctx.ctx, x["Ce"])
+
+    plain()
+    torch.cuda.synchronize()
+    k = max(1, min(args.steps, 3))
+    t0 = time.perf_counter()
+    for _ in range(k):
+        plain()
+    torch.cuda.synchronize()
+    plain_s = (time.perf_counter() - t0) / k
+    assert all(torch.equal(a, x["C"]) for a, x in zip(Cb, subs)), "batched and plain results differ"
+    n = len(subs)
+    line = {
+        "metric": METRIC, "value": n / batch_s, "unit": "subjects/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1000 * batch_s, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": f"batched: {n} subjects (grids 96^3..145x174x145, M in 8/70/360, N 1,000..12,000), "
+                               f"{ns_total:,} streamlines, {nv_total:,} vertices, one CUDA graph per batch",
+                   "subjects": n, "streamlines": ns_total, "vertices": nv_total, "count_scale": args.count_scale,
+                   "l2": "inputs larger than L2"},
+        "voxel_steps_per_s": steps_total / batch_s, "graph_ms": graph_ms / args.steps,
+        "plain_subjects_per_s": n / plain_s, "plain_ms_per_batch": 1000 * plain_s,
+        "batched_vs_plain": plain_s / batch_s, "autotuned": {"prefilter_ctas": info["prefilter_ctas"],
+                                                             "near_log2": info["near_log2"]},
+        "gpu_launches": launches, "clocks": clk, "generation_s": gen_s,
+    }
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
+def run_served(args):
+    """Poisson arrivals of HCP-shaped requests (200,000..2,000,000 streamlines in
+    250,000-streamline chunks from page-locked host memory) into the served form;
+    subjects/s and p50/p99 end-to-end latency, then a closed-loop saturation run."""
+    import threading
+
+    import torch
+
+    import synth
+    from paper_2302_09247_gb300 import fastcod as fc
+
+    ws, rank, local = _dist()
+    if rank != 0:
+        return 0
+    torch.cuda.set_device(local)
+    chunk = 250_000
+    pool = []
+    t0 = time.perf_counter()
+    for p in range(args.pool):
+        vols, tr = synth.make_subject(4, subject=p)
+        xyz = torch.from_numpy(tr.xyz).pin_memory()
+        chunks = []
+        for c in range(0, tr.n_streamlines, chunk):
+            e = min(tr.n_streamlines, c + chunk)
+            off = torch.from_numpy(tr.offsets[c:e + 1] - tr.offsets[c]).pin_memory()
+            chunks.append((int(tr.offsets[c]), off))
+        pool.append(dict(vols=vols, roi=torch.from_numpy(vols.roi).pin_memory(),
+                         lab=torch.from_numpy(vols.lab.view(np.int16)).pin_memory(), xyz=xyz, chunks=chunks,
+                         ns=tr.n_streamlines))
+    gen_s = time.perf_counter() - t0
+    rng = np.random.default_rng(20)
+    ctx = fc.Context(local)
+    srv = fc.fastcod_server_create(ctx.ctx, args.slots, 0)
+    keep = []
+
+    def submit(spec):
+        p, count = spec
+        P = pool[p]
+        vols = P["vols"]
+        C = torch.empty((vols.n_roi, vols.n_targets), dtype=torch.int32).pin_memory()
+        Ce = torch.empty_like(C).pin_memory()
+        head = fc.make_subject(P["roi"], P["lab"], vols.dims, vols.n_roi, vols.n_targets,
+                               np.zeros((0, 3), np.int32), np.zeros(1, np.int64), C, Ce)
+        rid = fc.fastcod_server_submit(srv, head)
+        left = count
+        for c, (v0, off) in enumerate(P["chunks"]):
+            n = min(chunk, left)
+            o = off[: n + 1]
+            x = P["xyz"][v0: v0 + int(o[-1])]
+            left -= n
+            fc.fastcod_server_push_chunk(srv, rid, x, o, last=(left == 0))
+            keep.append((x, o))
+            if left == 0:
+                break
+        keep.append((C, Ce, head))
+        return rid, count
+
+    def spec():
+        return int(rng.integers(len(pool))), 50_000 * int(rng.integers(4, 41))
+
+    # warm-up: one request of each pool subject
+    for p in range(len(pool)):
+        rid, _ = submit((p, 200_000))
+        fc.fastcod_server_wait(srv, rid, 120.0)
+    # open loop: Poisson arrivals
+    arrivals = np.cumsum(rng.exponential(1.0 / args.rate, size=int(args.rate * args.serve_seconds * 1.5) + 10))
+    arrivals = arrivals[arrivals < args.serve_seconds]
+    specs = [spec() for _ in arrivals]
+    clocks = ClockSampler(local)
+    clocks.start()
+    ids = []
+    t_start = time.perf_counter()
+    for at, sp in zip(arrivals, specs):
+        d = t_start + at - time.perf_counter()
+        if d > 0:
+            time.sleep(d)
+        ids.append(submit(sp))
+    for rid, _ in ids:
+        assert fc.fastcod_server_wait(srv, rid, 300.0) == fc.FASTCOD_OK
+    clk = clocks.stop()
+    infos = [fc.fastcod_server_request_info(srv, rid) for rid, _ in ids]
+    lat = np.array([i["t_done"] - i["t_submit"] for i in infos])
+    span = max(i["t_done"] for i in infos) - min(i["t_submit"] for i in infos)
+    n_streamlines = sum(c for _, c in ids)
+    # closed loop: everything at once
+    specs2 = [spec() for _ in range(4 * args.slots)]
+    t0 = time.perf_counter()
+    ids2 = [submit(sp) for sp in specs2]
+    for rid, _ in ids2:
+        assert fc.fastcod_server_wait(srv, rid, 300.0) == fc.FASTCOD_OK
+    sat_s = time.perf_counter() - t0
+    fc.fastcod_server_destroy(srv)
+    line = {
+        "metric": METRIC, "value": len(ids) / span, "unit": "subjects/s", "n_gpus": 1, "steps": len(ids),
+        "warmup": len(pool), "ms_per_step": 1000 * span / len(ids), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": f"served: Poisson {args.rate}/s for {args.serve_seconds}s of HCP-shaped requests "
+                               f"(200k..2M streamlines, 250k-streamline chunks from page-locked host memory, "
+                               f"pool of {len(pool)} subjects), {args.slots} slots",
+                   "requests": len(ids), "streamlines": n_streamlines},
+        "latency_ms": {"p50": 1000 * float(np.percentile(lat, 50)), "p99": 1000 * float(np.percentile(lat, 99)),
+                       "mean": 1000 * float(lat.mean()), "max": 1000 * float(lat.max())},
+        "offered_rate": args.rate,
+        "saturation": {"requests": len(ids2), "subjects_per_s": len(ids2) / sat_s,
+                       "streamlines_per_s": sum(c for _, c in ids2) / sat_s},
+        "clocks": clk, "generation_s": gen_s,
+    }
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="fastcod", choices=["fastcod", "reference"])
-    ap.add_argument("--config", type=int, default=1, choices=[0, 1, 2])
+    ap.add_argument("--config", type=int, default=1, choices=[0, 1, 2, 3, 4],
+                    help="0-2: one subject (default 1, HCP-shaped); 3: batched; 4: served")
+    ap.add_argument("--subjects", type=int, default=64, help="--config 3: subjects per batch")
+    ap.add_argument("--count-scale", type=float, default=1.0, help="--config 3: scale of the streamline counts")
+    ap.add_argument("--serve-seconds", type=float, default=15.0, help="--config 4: length of the arrival process")
+    ap.add_argument("--rate", type=float, default=20.0, help="--config 4: Poisson arrivals per second")
+    ap.add_argument("--pool", type=int, default=4, help="--config 4: pre-generated subjects")
+    ap.add_argument("--slots", type=int, default=16, help="--config 4: server slots")
     ap.add_argument("--e2e-steps", type=int, default=10, help="0 skips the end-to-end leg")
     ap.add_argument("--streamlines", type=int, default=None,
                     help="use only the first N streamlines of the subject (small profiling cases)")
@@ -210,6 +416,10 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.config == 3:
+        return run_batched(args)
+    if args.config == 4:
+        return run_served(args)
 
     import torch
 
