@@ -498,7 +498,7 @@ def main():
     alg_bytes = 12 * tr.n_vertices + 8 * (tr.n_streamlines + 1)
     k2_ms = prof["ms_prefilter"] / max(prof["calls"], 1)
     achieved = alg_bytes / (k2_ms / 1000.0) / 1e9
-    roofline = {"bound": "hbm", "kernel": "prefilter_direct_kernel", "achieved": achieved,
+    roofline = {"bound": "hbm", "kernel": "prefilter_kernel", "achieved": achieved,
                 "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
                 "peak_source": f"{peak_kind} hbm_gbs (copy bandwidth)", "traffic": None,
                 "algorithmic_bytes_per_launch": alg_bytes,

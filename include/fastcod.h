@@ -86,15 +86,15 @@ enum {
   /* voxel rule: 0 (default) = continuous segments; 1 = vertices only (the
    * point-sampled reading behind the paper's upsampling rule, Section 3). */
   FASTCOD_OPT_SAMPLING = 3,
-  /* vertex staging of the prefilter: 0 (default) = direct vectorised
-   * streaming loads, 1 = 1-D TMA bulk copies into a per-warp shared-memory
-   * ring.  Results are identical. */
+  /* vertex staging of the prefilter: 1 (default) = 1-D TMA bulk copies into
+   * a per-warp shared-memory ring, 0 = direct vectorised streaming loads into
+   * registers.  Results are identical. */
   FASTCOD_OPT_STAGING = 4,
   /* 1: record CUDA events around every stage on the context's stream and
    * accumulate their durations (fastcod_get_profile); 0 (default): off. */
   FASTCOD_OPT_PROFILE = 5,
-  /* CTAs per SM the prefilter is compiled for: 3 (default, up to 80
-   * registers per thread) or 4 (64 registers, more resident warps).  Results
+  /* CTAs per SM the prefilter is compiled for: 2 (default, up to 128
+   * registers per thread) or 3 (80 registers, more resident warps).  Results
    * are identical. */
   FASTCOD_OPT_PREFILTER_CTAS = 6,
   /* cell of the prefilter's near grid: (1 << value)^3 voxels, 0..3 (default

@@ -71,10 +71,13 @@ int ilog2_64(int64_t x) {
   return r;
 }
 
-int32_t near_words(const int32_t d[3], int near_log2) {
-  const int32_t cs = 1 << near_log2;
-  const int64_t nx = (d[0] + 2 + cs - 1) / cs, ny = (d[1] + 2 + cs - 1) / cs, nz = (d[2] + 2 + cs - 1) / cs;
-  return (int32_t)(((nx + 15) / 16) * ny * nz);
+int64_t near_words(const int32_t d[3], int near_log2) {
+  fc::VolView v{};
+  v.dx = d[0];
+  v.dy = d[1];
+  v.dz = d[2];
+  fc::set_near_dims(v, near_log2);
+  return fc::near_words(v);
 }
 
 Layout plan(const fastcod_subject* subs, int32_t n, const std::vector<int>& host_in, int near_log2,
@@ -154,11 +157,7 @@ void fill_table(fastcod_ctx* c, const fastcod_subject* subs, int32_t n, const La
     v.bx = (S.dims[0] + 3) / 4;
     v.by = (S.dims[1] + 3) / 4;
     v.bz = (S.dims[2] + 3) / 4;
-    v.nsh = near_log2;
-    const int32_t cs = 1 << near_log2;
-    v.nwx = ((S.dims[0] + 2 + cs - 1) / cs + 15) / 16;
-    v.nny = (S.dims[1] + 2 + cs - 1) / cs;
-    v.nnz = (S.dims[2] + 2 + cs - 1) / cs;
+    fc::set_near_dims(v, near_log2);
     v.n_roi = S.n_roi;
     v.n_lab = S.n_targets;
     B.t.xyz = L.xyz_in[i] != SIZE_MAX ? at<int32_t>(A, L.xyz_in[i]) : S.xyz;
@@ -182,7 +181,7 @@ void fill_table(fastcod_ctx* c, const fastcod_subject* subs, int32_t n, const La
   }
 }
 
-uint64_t graph_key(const fc::BatchTable& tbl, int32_t ntasks, const BatchConfig& cfg, uint32_t mode, int prefilter,
+uint64_t graph_key(const fc::BatchTable& tbl, int32_t ntasks, const BatchConfig& cfg, uint32_t mode, int prefilter, int tma,
                    const void* arena, const fastcod_subject* subs, const Layout& L) {
   uint64_t h = 1469598103934665603ull;
   for (int32_t i = 0; i < tbl.n; ++i) {  // the volume inputs K1 reads
@@ -194,7 +193,7 @@ uint64_t graph_key(const fc::BatchTable& tbl, int32_t ntasks, const BatchConfig&
   for (size_t i = 0; i < words; ++i) h = mix(h, w[i]);
   h = mix(h, (uint64_t)ntasks);
   h = mix(h, (uint64_t)cfg.ctas * 131 + (uint64_t)cfg.near_log2);
-  h = mix(h, (uint64_t)mode * 7 + (uint64_t)prefilter);
+  h = mix(h, (uint64_t)mode * 7 + (uint64_t)prefilter + 1000 * (uint64_t)(tma != 0));
   h = mix(h, (uint64_t)(uintptr_t)arena);
   return h;
 }
@@ -225,7 +224,7 @@ int capture(fastcod_ctx* c, const fastcod_subject* subs, int32_t n, const Layout
     if (e == cudaSuccess) e = fc::launch_near(bs.v, at<uint32_t>(A, L.planes), const_cast<uint32_t*>(bs.v.near), c->stream);
   }
   if (e == cudaSuccess)
-    e = fc::launch_prefilter_batch(tbl, at<fc::BatchTask>(A, L.tasks), L.ntasks, c->prefilter != 0, cfg.ctas,
+    e = fc::launch_prefilter_batch(tbl, at<fc::BatchTask>(A, L.tasks), L.ntasks, c->prefilter != 0, c->staging_tma != 0, cfg.ctas,
                                    at<int32_t>(A, L.surv), gst, c->num_sms, c->stream);
   if (e == cudaSuccess) e = fc::launch_walk_batch(tbl, at<int32_t>(A, L.surv), c->mode, at<int32_t>(A, L.ovf), gst, c->num_sms, c->stream);
   if (e == cudaSuccess)
@@ -301,7 +300,7 @@ int run_config(fastcod_ctx* c, const fastcod_subject* subs, int32_t n, const std
         break;
       }
     }
-    const uint64_t key = graph_key(*tbl, L.ntasks, cfg, c->mode, c->prefilter, A, subs, L);
+    const uint64_t key = graph_key(*tbl, L.ntasks, cfg, c->mode, c->prefilter, c->staging_tma, A, subs, L);
     B->info.graph_reused = (B->exec && key == B->graph_key) ? 1 : 0;
     if (!B->info.graph_reused) {
       if (B->exec) cudaGraphExecDestroy(B->exec);
@@ -360,7 +359,7 @@ void load_tune_cache(BatchState* B) {
   unsigned long long k;
   int ctas, nl;
   while (fscanf(f, "%llx %d %d", &k, &ctas, &nl) == 3)
-    if ((ctas == 3 || ctas == 4) && nl >= 0 && nl <= 3) B->tuned[(uint64_t)k] = BatchConfig{ctas, nl};
+    if ((ctas == 2 || ctas == 3) && nl >= 0 && nl <= 3) B->tuned[(uint64_t)k] = BatchConfig{ctas, nl};
   fclose(f);
 }
 
@@ -439,7 +438,7 @@ FASTCOD_API int fastcod_batch_run(fastcod_ctx* c, const fastcod_subject* subs, i
       cfg = it->second;
     } else {
       // timed trials: each candidate runs twice (the first run captures its graph)
-      const BatchConfig cand[4] = {{3, 1}, {4, 1}, {3, 2}, {3, 0}};
+      const BatchConfig cand[4] = {{2, 1}, {3, 1}, {2, 2}, {2, 0}};
       float best = 1e30f;
       for (const BatchConfig& k : cand) {
         float t = 0.f;

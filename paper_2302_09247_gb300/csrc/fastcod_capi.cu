@@ -122,11 +122,7 @@ fc::VolView vol_view(const fastcod_ctx* c) {
   v.bx = c->bdims[0];
   v.by = c->bdims[1];
   v.bz = c->bdims[2];
-  v.nsh = c->near_shift;
-  const int32_t cs = 1 << v.nsh;
-  v.nwx = ((c->dims[0] + 2 + cs - 1) / cs + 15) / 16;
-  v.nny = (c->dims[1] + 2 + cs - 1) / cs;
-  v.nnz = (c->dims[2] + 2 + cs - 1) / cs;
+  fc::set_near_dims(v, c->near_shift);
   v.n_roi = c->N;
   v.n_lab = c->M;
   return v;
@@ -345,8 +341,7 @@ FASTCOD_API int fastcod_set_volumes(fastcod_ctx* c, const int32_t* roi, const ui
   // near grid (the prefilter's dilated occupancy), built from the bit planes
   c->near_shift = c->near_log2;
   fc::VolView v = vol_view(c);
-  const int64_t near_words = (int64_t)v.nwx * v.nny * v.nnz;
-  CU(cudaMalloc(&c->d_near, (size_t)near_words * 4));
+  CU(cudaMalloc(&c->d_near, (size_t)fc::near_words(v) * 4));
   v.near = c->d_near;
   uint32_t* planes = nullptr;
   CU(cudaMalloc(&planes, (size_t)fc::plane_words(dx, dy, dz) * 4));
@@ -515,7 +510,7 @@ FASTCOD_API int fastcod_set_option(fastcod_ctx* c, int32_t key, int64_t value) {
       c->staging_tma = (int)value;
       return FASTCOD_OK;
     case FASTCOD_OPT_PREFILTER_CTAS:
-      if (value != 3 && value != 4) break;
+      if (value != 2 && value != 3) break;
       c->prefilter_ctas = (int)value;
       return FASTCOD_OK;
     case FASTCOD_OPT_NEAR_LOG2:

@@ -53,8 +53,8 @@ struct fastcod_ctx {
   int64_t total_vertices = 0;
   int prefilter = 1;
   uint32_t mode = 0;
-  int staging_tma = 0;
-  int prefilter_ctas = 3;
+  int staging_tma = 1;
+  int prefilter_ctas = 2;
   int near_log2 = 1;       // near grid cell: (1 << near_log2)^3 voxels
   int autotune = 1;        // batched form: tune per batch shape
   int profile = 0;

@@ -57,6 +57,7 @@ struct VolView {
   int32_t dx, dy, dz;     // grid
   int32_t bx, by, bz;     // brick grid
   int32_t nwx, nny, nnz;  // near grid: words per x-row, rows, planes (in cells)
+  int32_t cmx, cmy, cmz;  // near grid: index of the all-zero border cell per axis
   int32_t nsh;            // near grid cell = (1 << nsh)^3 padded voxels
   int32_t n_roi, n_lab;   // N, M
 };
@@ -67,9 +68,24 @@ struct VolView {
 // sixteen cells along x per 32-bit word.  Voxel (x, y, z) sits at padded
 // position (x+1, y+1, z+1), in cell (cx, cy, cz) = padded >> nsh:
 //   word = (cx >> 4) + nwx * (cy + nny * cz),  shift = (cx & 15) * 2.
+// Past the cells that cover padded positions [0, d + 2) every axis has one
+// more cell, all zero (index cmx / cmy / cmz); a lookup clamps its cell
+// coordinate, taken as unsigned, to that cell, so any voxel farther than one
+// voxel outside the grid reads zero without a bounds test.
 // A segment whose end voxels differ by at most one on every axis lies in the
-// 3x3x3 block around either end, so the near bits of its end voxel (and of
-// the cell holding it) cover it.
+// 3x3x3 block around either end, so the near bits of either end voxel (and
+// of the cell holding it) cover it.
+inline void set_near_dims(VolView& v, int32_t nsh) {
+  const int32_t cs = 1 << nsh;
+  v.nsh = nsh;
+  v.cmx = (v.dx + 2 + cs - 1) / cs;
+  v.cmy = (v.dy + 2 + cs - 1) / cs;
+  v.cmz = (v.dz + 2 + cs - 1) / cs;
+  v.nwx = (v.cmx + 1 + 15) / 16;
+  v.nny = v.cmy + 1;
+  v.nnz = v.cmz + 1;
+}
+__host__ __device__ inline int64_t near_words(const VolView& v) { return (int64_t)v.nwx * v.nny * v.nnz; }
 
 // One batch of streamlines on the device.
 struct Tract {
@@ -127,14 +143,15 @@ int64_t plane_words(int32_t dx, int32_t dy, int32_t dz);
 cudaError_t launch_near(const VolView& v, const uint32_t* planes, uint32_t* near, cudaStream_t s);
 
 // K2: prefilter + compaction (+ validation and voxel-step count).
-// ctas_per_sm: 3 or 4 (the register budget the kernel is compiled for).
+// ctas_per_sm: 2 or 3 (the register budget the kernel is compiled for).
 cudaError_t launch_prefilter(const Tract& t, const VolView& v, bool prefilter, uint32_t mode,
                              bool tma, int ctas_per_sm, int32_t* survivors, DevState* st, int num_sms,
                              cudaStream_t s);
 
 // Batched forms: every subject of the table in one launch each.
 cudaError_t launch_prefilter_batch(const BatchTable& tbl, const BatchTask* tasks, int32_t ntasks, bool prefilter,
-                                   int ctas_per_sm, int32_t* survivors, DevState* gst, int num_sms, cudaStream_t s);
+                                   bool tma, int ctas_per_sm, int32_t* survivors, DevState* gst, int num_sms,
+                                   cudaStream_t s);
 cudaError_t launch_walk_batch(const BatchTable& tbl, const int32_t* survivors, uint32_t mode, int32_t* overflow_list,
                               DevState* gst, int num_sms, cudaStream_t s);
 cudaError_t launch_walk_overflow_batch(const BatchTable& tbl, const int32_t* overflow_list, uint32_t mode,

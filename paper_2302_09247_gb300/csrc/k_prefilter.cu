@@ -5,32 +5,35 @@
 // seed and endpoint lie on the streamline) and is dropped; the ids of the
 // others are appended to a compact survivor list (one atomic per 32 survivors
 // of a warp).  The test is conservative; the walk decides exactly.  On the way
-// the kernel validates coordinates and counts voxel-steps.
+// the kernel validates offsets and coordinates and counts voxel-steps.
 //
-// The test.  The near grid holds, for every voxel, whether an ROI voxel / a
-// labelled voxel lies within Chebyshev distance 1.  A segment whose end
-// voxels differ by at most one on every axis lies in the 3x3x3 block around
-// its end voxel, so the near bits of that voxel cover the segment; over a
-// streamline, the OR of the near bits of its vertices covers all of its
-// segments (and its single point when T = 1).  A longer segment adds the
-// brick occupancy of its whole voxel box (exact, rare).
+// The test.  The near grid holds, per cell, whether an ROI voxel / a labelled
+// voxel lies within Chebyshev distance 1 of a voxel of the cell.  A segment
+// whose end voxels differ by at most one on every axis lies in the 3x3x3
+// block around either end voxel, so the near bits of either end cover it.
+// Every segment has an end vertex of even index, so the near bits of the
+// even-indexed vertices of a streamline cover all of its short segments; a
+// longer segment adds the brick occupancy of its whole voxel box (exact,
+// rare); a streamline of one vertex at an odd index is kept unconditionally
+// (the walk decides it).
 //
 // Vertex-parallel scan.  Each warp owns a contiguous range of streamlines and
-// walks its vertex range in 128-vertex windows aligned to 128; lane l takes
-// the four consecutive vertices 4l..4l+3 of the window, so every lane is busy
-// regardless of streamline boundaries:
-//   - boundaries (streamline starts, from the offsets) falling in the window
-//     are scanned first, 32 at a time, into a start mask;
-//   - per vertex: one near-grid lookup, the voxel-step count of the segment
-//     ending there (unless it starts a streamline), the long-segment check;
-//   - ballots turn the bits into four per-slot window masks; at every
-//     boundary x, a prefix popcount of the masks gives the running count of
-//     ROI / target hits, and the streamline ending at x passes when both
-//     counts grew since its start boundary.
-// Two loaders with identical results: direct vectorised streaming loads
-// (default: 3 x 16-byte loads per lane per window) and TMA (the warp streams
-// its vertex range through a 4-deep ring of 1536-byte pieces, one window each,
-// in shared memory with cp.async.bulk + mbarrier, L2 evict-first).
+// walks its vertex range in 256-vertex windows aligned to 256; lane l takes
+// the eight consecutive vertices 8l..8l+7 of the window (six 16-byte loads),
+// so every lane is busy whatever the streamline lengths, and the loads of the
+// next window are in flight while the current one is processed:
+//   - the streamline boundaries (offsets) falling in the window, kept in a
+//     two-group register cache of 64 offsets per warp, set the window's start
+//     bits (shared-memory atomics, one word per 32 vertices);
+//   - per vertex: coordinate check, voxel-step count and long-segment check of
+//     the segment ending there (unless the vertex starts a streamline), and
+//     at even vertices a near-grid lookup (shared memory when the grid fits);
+//   - a warp scan of the per-lane hit counts gives, at every boundary x, the
+//     running number of ROI / target hits before x, and the streamline ending
+//     at x passes when both counts grew since its start boundary.
+// Two loaders with identical results: direct streaming loads into registers
+// (default) and TMA (a ring of 3072-byte pieces per warp in shared memory,
+// cp.async.bulk + mbarrier, L2 evict-first).
 #include "fc_device.cuh"
 #include "fc_tma.cuh"
 
@@ -38,64 +41,116 @@ namespace fc {
 
 namespace {
 
-constexpr int kPieceV = 128;              // vertices per piece = per window
-constexpr int kPieceLog2 = 7;
-constexpr int kPieceWords = kPieceV * 3;  // 384 int32 = 1536 bytes
-constexpr int kStages = 4;                // ring depth per warp
+constexpr int kWinLog2 = 8;
+constexpr int kWin = 1 << kWinLog2;       // vertices per window (= per TMA piece)
+constexpr int kVpl = kWin / 32;           // vertices per lane
+constexpr int kLaneWords = kVpl * 3;      // 24 int32 per lane
+constexpr int kWinWords = kWin * 3;       // 768 int32 = 3072 bytes
+constexpr int kStages = 3;                // TMA ring depth per warp
 constexpr int kWarps = 8;                 // warps per CTA
 constexpr uint64_t kWaitTimeoutNs = 1000000000ull;  // 1 s
 constexpr int32_t kInf = 0x7fffffff;
+constexpr int64_t kNearSmemWords = 12288;  // direct loader: near grids up to 48 KB live in shared memory
 
 __device__ __forceinline__ uint32_t lowmask(int32_t k) { return k >= 32 ? 0xffffffffu : ((1u << k) - 1u); }
 
-// Near bits of voxel (x, y, z); 0 when the voxel is more than one voxel
-// outside the grid.
-__device__ __forceinline__ uint32_t near_bits(const VolView& v, int32_t x, int32_t y, int32_t z) {
-  const int32_t px = x + 1, py = y + 1, pz = z + 1;
-  if ((unsigned)px >= (unsigned)(v.dx + 2) || (unsigned)py >= (unsigned)(v.dy + 2) || (unsigned)pz >= (unsigned)(v.dz + 2))
-    return 0u;
-  const int32_t cx = px >> v.nsh, cy = py >> v.nsh, cz = pz >> v.nsh;
-  const int32_t w = (cx >> 4) + v.nwx * (cy + v.nny * cz);
-  return (__ldg(v.near + w) >> ((cx & 15) << 1)) & 3u;
+// Near bits of the cell holding voxel (vx, vy, vz); cells past the grown grid
+// clamp to the zero border.
+template <bool kSmem>
+__device__ __forceinline__ uint32_t near_lookup(const VolView& v, const uint32_t* nw, int32_t vx, int32_t vy,
+                                                int32_t vz) {
+  const uint32_t cx = min((uint32_t)((vx + 1) >> v.nsh), (uint32_t)v.cmx);
+  const uint32_t cy = min((uint32_t)((vy + 1) >> v.nsh), (uint32_t)v.cmy);
+  const uint32_t cz = min((uint32_t)((vz + 1) >> v.nsh), (uint32_t)v.cmz);
+  const uint32_t w = (cx >> 4) + (uint32_t)v.nwx * (cy + (uint32_t)v.nny * cz);
+  const uint32_t word = kSmem ? nw[w] : __ldg(nw + w);
+  return (word >> ((cx & 15u) << 1)) & 3u;
 }
 
-// Count of set bits of the four slot masks (vertex 4l+k = bit l of mask k)
-// at window positions below x, x in [0, 128].
-__device__ __forceinline__ uint32_t prefix4(const uint32_t m[4], int32_t x) {
-  const int32_t l = x >> 2, k = x & 3;
-  const uint32_t lm = lowmask(l);
-  uint32_t c = __popc(m[0] & lm) + __popc(m[1] & lm) + __popc(m[2] & lm) + __popc(m[3] & lm);
-  if (k > 0) c += (m[0] >> l) & 1u;
-  if (k > 1) c += (m[1] >> l) & 1u;
-  if (k > 2) c += (m[2] >> l) & 1u;
-  return c;
-}
-
-struct WarpSmem {
-  int32_t ring[kStages][kPieceWords];
-  uint64_t bar[kStages];
-  int32_t sbuf[64];
+struct WarpShared {
+  int32_t sbuf[64];          // survivors awaiting a flush
+  uint32_t st[kWin / 32];    // start bits of the current window
 };
 
-// Per-warp scan state (registers).  Vertex indices are relative to V0.
+// Per-warp scan state (registers).  Vertex positions are absolute indices
+// into the subject's vertex array (< 2^31).
 struct Scan {
-  int64_t V0;
-  int32_t len;              // V1 - V0
   const int64_t* off;
-  int64_t s_cur, s_hi;      // next boundary to scan: off[s_cur], s_cur <= s_hi
-  uint32_t cumR, cumT;      // hit counts before the current window
-  uint32_t lastR, lastT;    // hit counts at the last boundary
-  int32_t last_x;           // position of the last boundary
-  uint32_t start_carry;     // the next window's vertex 0 starts a streamline
-  int32_t qx, qy, qz;       // voxel of the previous window's last vertex
-  uint32_t steps;           // voxel steps counted by this lane (flushed to steps64)
-  unsigned long long steps64;
-  uint32_t singles, kept;
+  int32_t V0, V1;            // vertex range [V0, V1)
+  int64_t s_lo, s_cur, s_hi; // boundaries s_lo..s_hi; s_cur = next one to decide
+  int64_t cbase;             // cache: lane i holds off[cbase + i] (cA), off[cbase + 32 + i] (cB)
+  int32_t cA, cB;            // kInf past s_hi
+  uint32_t cumR, cumT;       // hit counts before the current window
+  uint32_t lastR, lastT;     // hit counts at the last decided boundary
+  int32_t last_b;            // that boundary
+  uint32_t carry;            // the current window's vertex 0 starts a streamline
+  int32_t qx, qy, qz;        // voxel of the previous window's last vertex
+  unsigned long long steps;  // voxel steps counted by this lane
+  uint32_t singles, kept, badc;
   int nbuf;
-  bool bad;
-  int64_t id_base;          // survivor ids are id_base + streamline index
-  DevState* sst;            // the subject's counters and error word
+  bool abort;
+  int64_t id_base;           // survivor ids are id_base + streamline index
+  DevState* sst;             // the subject's counters and error word
 };
+
+// Boundary base + lane (kInf past s_hi), saturated into int32 so that the
+// range check below sees any out-of-range value.
+__device__ __forceinline__ int32_t load_bnd(const Scan& sc, int64_t base) {
+  const int64_t i = base + lane_id();
+  if (i > sc.s_hi) return kInf;
+  const int64_t b = __ldg(sc.off + i);
+  return b < 0 ? -1 : (b >= kInf ? kInf : (int32_t)b);
+}
+
+// Offsets base .. base+31 (g, one per lane) lie in [V0, V1] and do not
+// decrease, starting at or after prev.  Warp-uniform; flags the error.
+__device__ __forceinline__ bool check_group(Scan& sc, int32_t g, int64_t base, int32_t prev) {
+  const int32_t lane = (int32_t)lane_id();
+  const int64_t i = base + lane;
+  const int32_t nx = __shfl_down_sync(kFull, g, 1);
+  bool ok = i > sc.s_hi || (g >= sc.V0 && g <= sc.V1);
+  ok &= lane == 31 || i + 1 > sc.s_hi || g <= nx;
+  ok &= lane != 0 || i > sc.s_hi || g >= prev;
+  if (__all_sync(kFull, ok)) return true;
+  if (lane == 0) set_error(sc.sst, kErrOffsets, (int32_t)base);
+  sc.abort = true;
+  return false;
+}
+
+// Position the cache so that s_cur lies in its first group.  A group is
+// checked when it becomes the first one (its load was issued a group
+// earlier) or when it is dropped.
+__device__ __forceinline__ void cache_seek(Scan& sc) {
+  while (sc.s_cur >= sc.cbase + 32 && !sc.abort) {
+    const int32_t a31 = __shfl_sync(kFull, sc.cA, 31);
+    if (!check_group(sc, sc.cB, sc.cbase + 32, a31)) return;
+    if (sc.s_cur < sc.cbase + 64) {
+      sc.cA = sc.cB;
+      sc.cbase += 32;
+      sc.cB = load_bnd(sc, sc.cbase + 32);
+    } else {
+      sc.cbase = sc.s_cur;
+      sc.cA = load_bnd(sc, sc.cbase);
+      sc.cB = load_bnd(sc, sc.cbase + 32);
+      check_group(sc, sc.cA, sc.cbase, sc.last_b);
+    }
+  }
+}
+
+// Boundaries s + lane for a warp-uniform s >= cbase: from the cache when
+// s < cbase + 32, else loaded and checked here (windows with more than
+// 32 boundaries).
+__device__ __forceinline__ int32_t fetch_bnd(Scan& sc, int64_t s, int32_t prev) {
+  if (s < sc.cbase + 32) {
+    const int32_t i = (int32_t)(s - sc.cbase) + (int32_t)lane_id();
+    const int32_t a = __shfl_sync(kFull, sc.cA, i & 31);
+    const int32_t b = __shfl_sync(kFull, sc.cB, i & 31);
+    return i < 32 ? a : b;
+  }
+  const int32_t g = load_bnd(sc, s);
+  check_group(sc, g, s, prev);
+  return g;
+}
 
 // gst holds the survivor list's counter (one list per launch).
 __device__ __forceinline__ void flush_survivors(Scan& sc, int32_t* sbuf, int32_t* surv, DevState* gst) {
@@ -110,219 +165,448 @@ __device__ __forceinline__ void flush_survivors(Scan& sc, int32_t* sbuf, int32_t
   sc.nbuf = 0;
 }
 
-// One window at relative position Wr (the window's first vertex minus V0).
-// p: the lane's 12 words = vertices 4l..4l+3 of the window (meaningful where
-// inside [0, len)).
-__device__ __forceinline__ void scan_window(Scan& sc, const VolView& v, int32_t Wr, const int32_t p[12],
-                                            bool prefilter, int32_t* sbuf, int32_t* surv, DevState* gst) {
-  const int32_t lane = (int32_t)lane_id();
+// Brick occupancy of the voxel box [lo, hi] of a long segment, out of line
+// (rare).
+__device__ __noinline__ uint32_t long_box(const uint32_t* bricks, int32_t dx, int32_t dy, int32_t dz, int32_t bx,
+                                          int32_t by, int32_t lx, int32_t ly, int32_t lz, int32_t hx, int32_t hy,
+                                          int32_t hz) {
+  VolView v;
+  v.bricks = bricks;
+  v.dx = dx;
+  v.dy = dy;
+  v.dz = dz;
+  v.bx = bx;
+  v.by = by;
+  return box_bits(v, lx, ly, lz, hx, hy, hz);
+}
 
-  // 1. boundaries x <= Wr + 128, 32 per round: start mask of this window
-  uint32_t sm[4] = {0u, 0u, 0u, 0u};
-  if (sc.start_carry) sm[0] |= 1u;
+// One window: first vertex W = q * kWin; p = the lane's 24 words, vertices
+// W + 8l .. W + 8l + 7 (zero past the end of the array).
+template <bool kSmem>
+__device__ __forceinline__ void scan_window(Scan& sc, const VolView& v, const uint32_t* nw, int64_t q,
+                                            const int32_t (&p)[kLaneWords], bool prefilter, WarpShared& ws,
+                                            int32_t* surv, DevState* gst) {
+  const int32_t lane = (int32_t)lane_id();
+  const int32_t W = (int32_t)(q << kWinLog2);
+
+  // 1. boundaries b with b - W <= kWin are decided in this window; those
+  //    with b - W < kWin start a streamline at a vertex of it
+  cache_seek(sc);
+  if (lane < kWin / 32) ws.st[lane] = 0u;
+  __syncwarp();
+  int32_t nbw = 0;
+  int32_t b_first = kInf;
   {
-    const int32_t x0 = -Wr;  // V0 starts the first streamline of the range
-    if (x0 >= 0 && x0 < 128) sm[x0 & 3] |= 1u << (x0 >> 2);
-  }
-  int64_t s_round = sc.s_cur;
-  int32_t bx;  // this lane's boundary of the current round
-  int32_t nb;
-  {
-    const int64_t s = sc.s_cur + lane;
-    bx = s <= sc.s_hi ? (int32_t)(sc.off[s] - sc.V0) : kInf;
-    nb = __popc(__ballot_sync(kFull, bx <= Wr + 128));
-    const int32_t r = bx - Wr;
-    const bool st_in = bx <= Wr + 128 && r < 128;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) sm[k] |= __reduce_or_sync(kFull, (st_in && (r & 3) == k) ? (1u << (r >> 2)) : 0u);
-    if (nb == 32) {
-      // more than 32 boundaries in one window: collect the rest of the starts
-      int64_t s2 = sc.s_cur + 32;
-      for (;;) {
-        const int64_t t = s2 + lane;
-        const int32_t b2 = t <= sc.s_hi ? (int32_t)(sc.off[t] - sc.V0) : kInf;
-        const int32_t n2 = __popc(__ballot_sync(kFull, b2 <= Wr + 128));
-        const int32_t r2 = b2 - Wr;
-        const bool in2 = b2 <= Wr + 128 && r2 < 128;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) sm[k] |= __reduce_or_sync(kFull, (in2 && (r2 & 3) == k) ? (1u << (r2 >> 2)) : 0u);
-        if (n2 < 32) break;
-        s2 += 32;
-      }
+    int64_t s = sc.s_cur;
+    int32_t prev = sc.last_b;
+    for (int round = 0;; ++round) {
+      const int32_t b = fetch_bnd(sc, s, prev);
+      if (round == 0) b_first = b;
+      const int32_t r = b - W;
+      if ((uint32_t)r < (uint32_t)kWin) atomicOr(&ws.st[r >> 5], 1u << (r & 31));
+      const int n = __popc(__ballot_sync(kFull, r <= kWin));
+      nbw += n;
+      if (n < 32 || sc.abort) break;
+      prev = __shfl_sync(kFull, b, 31);
+      s += 32;
     }
   }
+  __syncwarp();
+  const uint32_t st8 = ((ws.st[lane >> 2] >> ((lane & 3) << 3)) & 0xffu) | (lane == 0 ? sc.carry : 0u);
+  const int32_t lo = sc.V0 - W - kVpl * lane, hi = sc.V1 - W - kVpl * lane;
+  const uint32_t valid8 = lowmask(min(max(hi, 0), kVpl)) & ~lowmask(min(max(lo, 0), kVpl));
+  const uint32_t keep8 = valid8 & ~st8;  // slots whose incoming segment is counted
 
   // 2. vertices
-  uint32_t mr[4], mt[4];
-  uint32_t badacc = 0;
+  // every lane takes part in the shuffles; lane 0 then takes the carried voxel
+  int32_t q0x = __shfl_up_sync(kFull, p[kLaneWords - 3] >> kUnitLog2, 1);
+  int32_t q0y = __shfl_up_sync(kFull, p[kLaneWords - 2] >> kUnitLog2, 1);
+  int32_t q0z = __shfl_up_sync(kFull, p[kLaneWords - 1] >> kUnitLog2, 1);
+  if (lane == 0) {
+    q0x = sc.qx;
+    q0y = sc.qy;
+    q0z = sc.qz;
+  }
+  uint32_t h8 = 0u, lg = 0u, bad = 0u, stp = 0u;
   {
-    int32_t qx = __shfl_up_sync(kFull, p[9] >> kUnitLog2, 1);
-    int32_t qy = __shfl_up_sync(kFull, p[10] >> kUnitLog2, 1);
-    int32_t qz = __shfl_up_sync(kFull, p[11] >> kUnitLog2, 1);
-    if (lane == 0) { qx = sc.qx; qy = sc.qy; qz = sc.qz; }
-    sc.qx = __shfl_sync(kFull, p[9] >> kUnitLog2, 31);
-    sc.qy = __shfl_sync(kFull, p[10] >> kUnitLog2, 31);
-    sc.qz = __shfl_sync(kFull, p[11] >> kUnitLog2, 31);
+    int32_t qx = q0x, qy = q0y, qz = q0z;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const int32_t jr = Wr + 4 * lane + k;
-      const bool act = jr >= 0 && jr < sc.len;
+    for (int k = 0; k < kVpl; ++k) {
       const int32_t x = p[3 * k], y = p[3 * k + 1], z = p[3 * k + 2];
+      bad |= (uint32_t)(x + kCoordLimit) | (uint32_t)(y + kCoordLimit) | (uint32_t)(z + kCoordLimit);
       const int32_t vx = x >> kUnitLog2, vy = y >> kUnitLog2, vz = z >> kUnitLog2;
-      if (act) badacc |= (uint32_t)(x + kCoordLimit) | (uint32_t)(y + kCoordLimit) | (uint32_t)(z + kCoordLimit);
-      uint32_t D = act ? near_bits(v, vx, vy, vz) : 0u;
-      const int32_t ax = abs(vx - qx), ay = abs(vy - qy), az = abs(vz - qz);
-      const bool start = (sm[k] >> lane) & 1u;
-      if (act && !start) sc.steps += 1u + (uint32_t)(ax + ay + az);
-      if (act && !start && (uint32_t)(ax | ay | az) > 1u)
-        D |= box_bits(v, min(vx, qx), min(vy, qy), min(vz, qz), max(vx, qx), max(vy, qy), max(vz, qz));
-      mr[k] = __ballot_sync(kFull, D & 1u);
-      mt[k] = __ballot_sync(kFull, D & 2u);
+      const uint32_t ax = (uint32_t)abs(vx - qx), ay = (uint32_t)abs(vy - qy), az = (uint32_t)abs(vz - qz);
+      const uint32_t m = 0u - ((keep8 >> k) & 1u);
+      lg |= (ax | ay | az) & m;
+      stp += (ax + ay + az) & m;
+      if ((k & 1) == 0) h8 |= near_lookup<kSmem>(v, nw, vx, vy, vz) << k;
       qx = vx;
       qy = vy;
       qz = vz;
     }
   }
-  sc.bad |= __any_sync(kFull, (badacc >> 25) != 0u);
-
-  // 3. decisions at the boundaries of this window
-  while (nb > 0) {
-    const bool in = lane < nb;
-    uint32_t cR = 0, cT = 0;
-    if (in) {
-      const int32_t r = bx - Wr;
-      cR = sc.cumR + prefix4(mr, r);
-      cT = sc.cumT + prefix4(mt, r);
+  sc.badc |= bad;
+  sc.steps += stp + (uint32_t)__popc(keep8);
+  if (lg > 1u) {
+    // long segments (slots whose keep bit is set and whose end voxels differ
+    // by more than one on some axis): the brick occupancy of the segment's
+    // voxel box, as hits on the segment's even vertex
+    int32_t qx = q0x, qy = q0y, qz = q0z;
+#pragma unroll
+    for (int k = 0; k < kVpl; ++k) {
+      const int32_t vx = p[3 * k] >> kUnitLog2, vy = p[3 * k + 1] >> kUnitLog2, vz = p[3 * k + 2] >> kUnitLog2;
+      if (((keep8 >> k) & 1u) && (uint32_t)(abs(vx - qx) | abs(vy - qy) | abs(vz - qz)) > 1u)
+        h8 |= long_box(v.bricks, v.dx, v.dy, v.dz, v.bx, v.by, min(vx, qx), min(vy, qy), min(vz, qz), max(vx, qx),
+                       max(vy, qy), max(vz, qz))
+              << (k & ~1);
+      qx = vx;
+      qy = vy;
+      qz = vz;
     }
+  }
+  sc.qx = __shfl_sync(kFull, p[kLaneWords - 3] >> kUnitLog2, 31);
+  sc.qy = __shfl_sync(kFull, p[kLaneWords - 2] >> kUnitLog2, 31);
+  sc.qz = __shfl_sync(kFull, p[kLaneWords - 1] >> kUnitLog2, 31);
+
+  // 3. hit counts: R hits at the even bits of h8, T hits at the odd bits
+  //    (bit k + 1 for the lookup at slot k); both counts in one word
+  const uint32_t c = (uint32_t)__popc(h8 & 0x55u) | ((uint32_t)__popc(h8 & 0xaau) << 16);
+  uint32_t inc = c;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint32_t y = __shfl_up_sync(kFull, inc, d);
+    if (lane >= d) inc += y;
+  }
+  const uint32_t excl = inc - c;
+  const uint32_t tot = __shfl_sync(kFull, inc, 31);
+
+  // 4. decisions at the boundaries of this window, 32 per round
+  int64_t s = sc.s_cur;
+  int32_t prev = sc.last_b;
+  for (int round = 0; nbw > 0 && !sc.abort; ++round) {
+    const int32_t b = round == 0 ? b_first : fetch_bnd(sc, s, prev);
+    const int n = min(nbw, 32);
+    const bool in = lane < n;
+    const int32_t x = min(max(b - W, 0), kWin);
+    const int32_t src = x >> 3, o = x & 7;
+    const uint32_t e = __shfl_sync(kFull, excl, src & 31);
+    const uint32_t hh = __shfl_sync(kFull, h8, src & 31);
+    uint32_t cR, cT;
+    if (src >= 32) {
+      cR = tot & 0xffffu;
+      cT = tot >> 16;
+    } else {
+      cR = (e & 0xffffu) + (uint32_t)__popc(hh & 0x55u & lowmask(o));
+      cT = (e >> 16) + (uint32_t)__popc(hh & 0xaau & lowmask(o + 1));
+    }
+    cR += sc.cumR;
+    cT += sc.cumT;
     uint32_t pR = __shfl_up_sync(kFull, cR, 1), pT = __shfl_up_sync(kFull, cT, 1);
-    int32_t px = __shfl_up_sync(kFull, bx, 1);
-    if (lane == 0) { pR = sc.lastR; pT = sc.lastT; px = sc.last_x; }
-    // boundary s closes streamline s-1 = [px, bx)
-    const bool pass = in && (!prefilter || (cR > pR && cT > pT)) && (bx > px) && !sc.bad;
-    if (in && bx - px == 1) sc.singles += 1u;
+    int32_t pb = __shfl_up_sync(kFull, b, 1);
+    if (lane == 0) {
+      pR = sc.lastR;
+      pT = sc.lastT;
+      pb = sc.last_b;
+    }
+    // boundary s + lane closes streamline s + lane - 1 = [pb, b)
+    const bool real = in && s + lane > sc.s_lo;
+    const int32_t T = b - pb;
+    const bool near_hit = (cR != pR && cT != pT) || (T == 1 && (pb & 1));
+    const bool pass = real && T > 0 && (!prefilter || near_hit);
+    if (real && T == 1) sc.singles += 1u;
     const uint32_t pm = __ballot_sync(kFull, pass);
-    if (pass) sbuf[sc.nbuf + __popc(pm & lanemask_lt())] = (int32_t)(sc.id_base + s_round + lane - 1);
+    if (pass) ws.sbuf[sc.nbuf + __popc(pm & lanemask_lt())] = (int32_t)(sc.id_base + s + lane - 1);
     sc.nbuf += __popc(pm);
     sc.kept += __popc(pm);
-    if (sc.nbuf >= 32) flush_survivors(sc, sbuf, surv, gst);
-    sc.lastR = __shfl_sync(kFull, cR, nb - 1);
-    sc.lastT = __shfl_sync(kFull, cT, nb - 1);
-    sc.last_x = __shfl_sync(kFull, bx, nb - 1);
-    s_round += nb;
-    if (nb < 32) break;
-    const int64_t s = s_round + lane;
-    bx = s <= sc.s_hi ? (int32_t)(sc.off[s] - sc.V0) : kInf;
-    nb = __popc(__ballot_sync(kFull, bx <= Wr + 128));
+    if (sc.nbuf >= 32) flush_survivors(sc, ws.sbuf, surv, gst);
+    sc.lastR = __shfl_sync(kFull, cR, n - 1);
+    sc.lastT = __shfl_sync(kFull, cT, n - 1);
+    sc.last_b = __shfl_sync(kFull, b, n - 1);
+    prev = __shfl_sync(kFull, b, 31);
+    s += n;
+    nbw -= n;
   }
-  sc.s_cur = s_round;
-  sc.start_carry = (sc.last_x == Wr + 128) ? 1u : 0u;
-  sc.cumR += __popc(mr[0]) + __popc(mr[1]) + __popc(mr[2]) + __popc(mr[3]);
-  sc.cumT += __popc(mt[0]) + __popc(mt[1]) + __popc(mt[2]) + __popc(mt[3]);
+  sc.s_cur = s;
+  sc.carry = (sc.last_b - W == kWin) ? 1u : 0u;
+  sc.cumR += tot & 0xffffu;
+  sc.cumT += tot >> 16;
 }
 
-// Set up the scan of streamlines [s_lo, s_hi) of t after validating their
-// offsets; false when there is nothing to do (or the offsets are invalid).
+// Set up the scan of streamlines [s_lo, s_hi) of t; false when there is
+// nothing to scan (or the offsets are invalid).
 __device__ __forceinline__ bool warp_init(const Tract& t, int64_t s_lo, int64_t s_hi, Scan& sc, DevState* sst,
                                           int64_t id_base) {
-  const unsigned lane = lane_id();
-  if (s_lo == 0 && lane == 0 && (t.off[0] != 0 || t.off[t.ns] != t.nv)) set_error(sst, kErrOffsets, -1);
-  bool ok = true;
-  for (int64_t s = s_lo + lane; s < s_hi; s += 32) {
-    const int64_t a = t.off[s], b = t.off[s + 1];
-    ok &= (a >= 0) && (a <= b) && (b <= t.nv);
-  }
-  if (!__all_sync(kFull, ok)) {
-    if (lane == 0) set_error(sst, kErrOffsets, (int32_t)s_lo);
+  if (s_hi <= s_lo) return false;
+  const int64_t a = __ldg(t.off + s_lo), b = __ldg(t.off + s_hi);
+  if (a < 0 || b > t.nv || a > b || (s_lo == 0 && a != 0) || (s_hi == t.ns && b != t.nv)) {
+    if (lane_id() == 0) set_error(sst, kErrOffsets, (int32_t)s_lo);
     return false;
   }
-  if (s_hi <= s_lo) return false;
-  const int64_t V0 = t.off[s_lo], V1 = t.off[s_hi];
-  if (V1 <= V0) return false;
-  sc.V0 = V0;
-  sc.len = (int32_t)(V1 - V0);
+  if (a == b) {
+    // no vertices: every offset of the range must equal a
+    bool ok = true;
+    for (int64_t s = s_lo + lane_id(); s <= s_hi; s += 32) ok &= __ldg(t.off + s) == a;
+    if (!__all_sync(kFull, ok) && lane_id() == 0) set_error(sst, kErrOffsets, (int32_t)s_lo);
+    return false;
+  }
   sc.off = t.off;
-  sc.s_cur = s_lo + 1;
+  sc.V0 = (int32_t)a;
+  sc.V1 = (int32_t)b;
+  sc.s_lo = s_lo;
+  sc.s_cur = s_lo;
   sc.s_hi = s_hi;
   sc.cumR = sc.cumT = 0;
   sc.lastR = sc.lastT = 0;
-  sc.last_x = 0;
-  sc.start_carry = 0;
+  sc.last_b = sc.V0;
+  sc.carry = 0;
   sc.qx = sc.qy = sc.qz = 0;
   sc.steps = 0;
-  sc.steps64 = 0;
-  sc.singles = sc.kept = 0;
+  sc.singles = sc.kept = sc.badc = 0;
   sc.nbuf = 0;
-  sc.bad = false;
+  sc.abort = false;
   sc.id_base = id_base;
   sc.sst = sst;
-  return true;
+  sc.cbase = s_lo;
+  sc.cA = load_bnd(sc, s_lo);
+  sc.cB = load_bnd(sc, s_lo + 32);
+  return check_group(sc, sc.cA, s_lo, sc.V0);
 }
 
 __device__ __forceinline__ void warp_finish(Scan& sc, int32_t* sbuf, int32_t* surv, DevState* gst) {
+  // the last loaded group is checked here, and every boundary decided
+  if (!sc.abort && sc.cbase + 32 <= sc.s_hi) check_group(sc, sc.cB, sc.cbase + 32, __shfl_sync(kFull, sc.cA, 31));
+  if (!sc.abort && sc.s_cur != sc.s_hi + 1) {
+    if (lane_id() == 0) set_error(sc.sst, kErrOffsets, (int32_t)sc.s_cur);
+  }
   flush_survivors(sc, sbuf, surv, gst);
-  unsigned long long s = sc.steps64 + sc.steps + sc.singles;
+  unsigned long long s = sc.steps + sc.singles;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
+  const bool bad = __any_sync(kFull, (sc.badc >> 25) != 0u);
   if (lane_id() == 0) {
     atomicAdd(&sc.sst->voxel_steps, s);
     atomicAdd(&sc.sst->survivors, (unsigned long long)sc.kept);
-    if (sc.bad) set_error(sc.sst, kErrCoord, (int32_t)(sc.s_cur - 1));
+    if (bad) set_error(sc.sst, kErrCoord, (int32_t)sc.s_lo);
   }
 }
 
-__device__ __forceinline__ void ldcs4(const int32_t* g, int32_t* d) {
-  const int4 a = __ldcs(reinterpret_cast<const int4*>(g));
-  d[0] = a.x;
-  d[1] = a.y;
-  d[2] = a.z;
-  d[3] = a.w;
+// The lane's 24 words of window q (zero past the end of the array).
+__device__ __forceinline__ void load_window(const Tract& t, int64_t q, int32_t (&p)[kLaneWords]) {
+  const int64_t g = (q << kWinLog2) + kVpl * lane_id();  // the lane's first vertex
+  if (g + kVpl <= t.nv) {
+    const int4* e = reinterpret_cast<const int4*>(t.xyz + 3 * g);  // 96-byte chunk, 16-byte aligned
+#pragma unroll
+    for (int i = 0; i < kLaneWords / 4; ++i) {
+      const int4 a = __ldcs(e + i);
+      p[4 * i] = a.x;
+      p[4 * i + 1] = a.y;
+      p[4 * i + 2] = a.z;
+      p[4 * i + 3] = a.w;
+    }
+  } else {
+#pragma unroll
+    for (int w = 0; w < kLaneWords; ++w) p[w] = (g + w / 3 < t.nv) ? __ldcs(t.xyz + 3 * g + w) : 0;
+  }
 }
 
 // ------------------------------------------------------------------ direct
 
-// Window loop of the direct loader over the scan's vertex range.
-__device__ __forceinline__ void scan_range_direct(Scan& sc, const VolView& v, const Tract& t, bool prefilter,
-                                                  int32_t* sbuf, int32_t* surv, DevState* gst) {
-  const int32_t lane = (int32_t)lane_id();
-  const int64_t q0 = sc.V0 >> kPieceLog2, q1 = (sc.V0 + sc.len - 1) >> kPieceLog2;
-  for (int64_t q = q0; q <= q1; ++q) {
-    const int64_t g = (q << kPieceLog2) + 4 * lane;  // absolute index of the lane's first vertex
-    int32_t p[12];
-    if (g + 3 < t.nv) {
-      const int32_t* e = t.xyz + 3 * g;  // 48-byte chunk, 16-byte aligned
-      ldcs4(e, p);
-      ldcs4(e + 4, p + 4);
-      ldcs4(e + 8, p + 8);
-    } else {
-#pragma unroll
-      for (int w = 0; w < 12; ++w) p[w] = (g + w / 3 < t.nv) ? __ldcs(t.xyz + 3 * g + w) : 0;
-    }
-    scan_window(sc, v, (int32_t)((q << kPieceLog2) - sc.V0), p, prefilter, sbuf, surv, gst);
-    sc.steps64 += sc.steps;
-    sc.steps = 0;
+// Window loop of the direct loader: window q+1 is loaded while q is scanned.
+template <bool kSmem>
+__device__ __forceinline__ void scan_range_direct(Scan& sc, const VolView& v, const uint32_t* nw, const Tract& t,
+                                                  bool prefilter, WarpShared& ws, int32_t* surv, DevState* gst) {
+  const int64_t q1 = (int64_t)(sc.V1 - 1) >> kWinLog2;
+  int64_t q = (int64_t)sc.V0 >> kWinLog2;
+  int32_t pa[kLaneWords], pb[kLaneWords];
+  load_window(t, q, pa);
+  for (;;) {
+    if (q < q1) load_window(t, q + 1, pb);
+    scan_window<kSmem>(sc, v, nw, q, pa, prefilter, ws, surv, gst);
+    if (++q > q1 || sc.abort) break;
+    if (q < q1) load_window(t, q + 1, pa);
+    scan_window<kSmem>(sc, v, nw, q, pb, prefilter, ws, surv, gst);
+    if (++q > q1 || sc.abort) break;
   }
 }
 
-template <int kMinBlocks>
-__global__ void __launch_bounds__(kWarps * 32, kMinBlocks) prefilter_direct_kernel(Tract t, VolView v, int prefilter,
-                                                                                  int32_t* surv, DevState* st) {
-  __shared__ int32_t sbuf_all[kWarps][64];
-  int32_t* sbuf = sbuf_all[threadIdx.x >> 5];
-  const int64_t gw = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
-  const int64_t nw = (int64_t)gridDim.x * kWarps;
-  Scan sc;
-  if (!warp_init(t, t.ns * gw / nw, t.ns * (gw + 1) / nw, sc, st, 0)) return;
-  scan_range_direct(sc, v, t, prefilter != 0, sbuf, surv, st);
-  warp_finish(sc, sbuf, surv, st);
+// --------------------------------------------------------------------- tma
+
+// Per-warp ring of kStages window-sized slots filled by 1-D bulk copies.
+// Slots are used in a fixed cyclic order for the warp's whole life (slot,
+// phase), so ranges follow one another without re-initialising barriers:
+// a range issues its first pieces into the slots after the last one used,
+// and every piece issued is consumed (or drained) before the range ends.
+// 128-byte aligned, so every warp's ring (a bulk-copy destination) starts on
+// a 16-byte boundary.
+struct __align__(128) TmaSmem {
+  int32_t ring[kStages][kWinWords];
+  uint64_t bar[kStages];
+};
+static_assert(sizeof(TmaSmem) % 128 == 0 && (kWinWords * 4) % 16 == 0, "ring slots must stay 16-byte aligned");
+
+struct Ring {
+  TmaSmem* sm;
+  uint32_t slot, phase;   // next slot to consume, and the parity it completes
+  uint64_t policy;
+
+  __device__ __forceinline__ void init(TmaSmem* s) {
+    sm = s;
+    slot = 0;
+    phase = 0;
+    policy = policy_evict_first();
+    if (lane_id() == 0) {
+      for (int k = 0; k < kStages; ++k) mbar_init(&sm->bar[k], 1);
+      fence_mbar_init();
+    }
+    __syncwarp();
+  }
+
+  // lane 0 only: copy window q of t into slot k (the part of the array's
+  // tail that is not a multiple of 16 bytes with plain loads, the rest of a
+  // short last window zero-filled)
+  __device__ __forceinline__ void issue(const Tract& t, int64_t q, uint32_t k) {
+    const int64_t v0 = q << kWinLog2;
+    const int64_t n = min((int64_t)kWin, t.nv - v0);
+    const uint32_t bytes = (uint32_t)(n * 12);
+    const uint32_t tma = bytes & ~15u;
+    int32_t* dst = sm->ring[k];
+    const int32_t* src = t.xyz + 3 * v0;
+    for (uint32_t w = tma >> 2; w < (bytes >> 2); ++w) dst[w] = __ldcs(src + w);
+    for (uint32_t w = bytes >> 2; w < (uint32_t)kWinWords; ++w) dst[w] = 0;
+    if (tma) {
+      mbar_arrive_expect_tx(&sm->bar[k], tma);
+      bulk_g2s(dst, src, tma, &sm->bar[k], policy);
+    } else {
+      mbar_arrive(&sm->bar[k]);
+    }
+  }
+
+  // Every lane waits on the slot to consume (acquiring its bytes); the
+  // result is warp-uniform.
+  __device__ __forceinline__ bool wait() {
+    return __all_sync(kFull, mbar_wait_bounded(&sm->bar[slot], phase, kWaitTimeoutNs));
+  }
+
+  __device__ __forceinline__ void advance() {
+    if (++slot == (uint32_t)kStages) {
+      slot = 0;
+      phase ^= 1u;
+    }
+  }
+};
+
+// Window loop of the TMA loader over the scan's vertex range.  Returns false
+// when a wait timed out (the error is set and the ring may not be reused).
+template <bool kSmem>
+__device__ __forceinline__ bool scan_range_tma(Scan& sc, const VolView& v, const uint32_t* nw, const Tract& t,
+                                               bool prefilter, WarpShared& ws, Ring& r, int32_t* surv,
+                                               DevState* gst) {
+  const int32_t lane = (int32_t)lane_id();
+  const int64_t q0 = (int64_t)sc.V0 >> kWinLog2, q1 = (int64_t)(sc.V1 - 1) >> kWinLog2;
+  int64_t issued = min(q1 + 1, q0 + kStages);  // windows [q0, issued) are in flight
+  if (lane == 0) {
+    uint32_t k = r.slot;
+    for (int64_t q = q0; q < issued; ++q) {
+      r.issue(t, q, k);
+      k = (k + 1 == (uint32_t)kStages) ? 0u : k + 1;
+    }
+  }
+  __syncwarp();
+  int64_t q = q0;
+  bool ok = true;
+  for (; q <= q1; ++q) {
+    if (!r.wait()) {
+      ok = false;
+      break;
+    }
+    const int4* e = reinterpret_cast<const int4*>(r.sm->ring[r.slot]) + (kLaneWords / 4) * lane;
+    int32_t p[kLaneWords];
+#pragma unroll
+    for (int i = 0; i < kLaneWords / 4; ++i) {
+      const int4 a = e[i];
+      p[4 * i] = a.x;
+      p[4 * i + 1] = a.y;
+      p[4 * i + 2] = a.z;
+      p[4 * i + 3] = a.w;
+    }
+    // the window is in registers: refill its slot with window q + kStages
+    __syncwarp();
+    if (issued <= q1) {
+      if (lane == 0) {
+        fence_proxy_async_smem();
+        r.issue(t, issued, r.slot);
+      }
+      ++issued;
+    }
+    r.advance();
+    scan_window<kSmem>(sc, v, nw, q, p, prefilter, ws, surv, gst);
+    if (sc.abort) {
+      ++q;
+      break;
+    }
+  }
+  if (!ok) {
+    if (lane == 0) set_error(sc.sst, kErrTimeout, (int32_t)sc.s_lo);
+    sc.abort = true;
+  }
+  // no copy may be in flight when the range ends: bounded drain of the
+  // windows issued but not consumed
+  for (; q < issued; ++q) {
+    if (!r.wait()) {
+      ok = false;
+      break;
+    }
+    r.advance();
+  }
+  return ok;
 }
 
-// Batched form: warps take (subject, streamline range) tasks dynamically.
-template <int kMinBlocks>
+// Copy the near grid to shared memory (every thread of the CTA takes part).
+__device__ __forceinline__ void stage_near(const VolView& v, uint32_t* s_near) {
+  const int32_t n = (int32_t)near_words(v);
+  for (int32_t i = threadIdx.x; i < n; i += blockDim.x) s_near[i] = __ldg(v.near + i);
+  __syncthreads();
+}
+
+// Dynamic shared memory: [near grid (kSmem)] then, for the TMA loader, the
+// warps' rings at a 128-byte aligned offset.
+__host__ __device__ constexpr size_t ring_offset(size_t near_bytes) { return (near_bytes + 127) & ~(size_t)127; }
+
+template <int kMinBlocks, bool kTma, bool kSmem>
+__global__ void __launch_bounds__(kWarps * 32, kMinBlocks) prefilter_kernel(Tract t, VolView v, int prefilter,
+                                                                           int32_t* surv, DevState* st) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ WarpShared ws_all[kWarps];
+  uint32_t* s_near = reinterpret_cast<uint32_t*>(smem_raw);
+  if (kSmem) stage_near(v, s_near);
+  const uint32_t* nw = kSmem ? s_near : v.near;
+  WarpShared& ws = ws_all[threadIdx.x >> 5];
+  const int64_t gw = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
+  const int64_t nwarps = (int64_t)gridDim.x * kWarps;
+  Scan sc;
+  if (!warp_init(t, t.ns * gw / nwarps, t.ns * (gw + 1) / nwarps, sc, st, 0)) return;
+  if (kTma) {
+    const size_t off = ring_offset(kSmem ? (size_t)near_words(v) * 4 : 0);
+    Ring r;
+    r.init(reinterpret_cast<TmaSmem*>(smem_raw + off) + (threadIdx.x >> 5));
+    scan_range_tma<kSmem>(sc, v, nw, t, prefilter != 0, ws, r, surv, st);
+  } else {
+    scan_range_direct<kSmem>(sc, v, nw, t, prefilter != 0, ws, surv, st);
+  }
+  warp_finish(sc, ws.sbuf, surv, st);
+}
+
+// Batched form: warps take (subject, streamline range) tasks dynamically;
+// the near grids stay in global memory (L1-cached).
+template <int kMinBlocks, bool kTma>
 __global__ void __launch_bounds__(kWarps * 32, kMinBlocks)
     prefilter_batch_kernel(const __grid_constant__ BatchTable tbl, const BatchTask* __restrict__ tasks,
                            int32_t ntasks, int prefilter, int32_t* surv, DevState* gst) {
-  __shared__ int32_t sbuf_all[kWarps][64];
-  int32_t* sbuf = sbuf_all[threadIdx.x >> 5];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ WarpShared ws_all[kWarps];
+  WarpShared& ws = ws_all[threadIdx.x >> 5];
+  Ring r;
+  if (kTma) r.init(reinterpret_cast<TmaSmem*>(smem_raw) + (threadIdx.x >> 5));
   for (;;) {
     int32_t task = 0;
     if (lane_id() == 0) task = (int32_t)atomicAdd(&gst->work_task, 1u);
@@ -332,114 +616,17 @@ __global__ void __launch_bounds__(kWarps * 32, kMinBlocks)
     const BatchSubject& S = tbl.s[tk.subject];
     Scan sc;
     if (!warp_init(S.t, tk.s_lo, tk.s_hi, sc, S.st, S.sbase)) continue;
-    scan_range_direct(sc, S.v, S.t, prefilter != 0, sbuf, surv, gst);
-    warp_finish(sc, sbuf, surv, gst);
+    bool ring_ok = true;
+    if (kTma)
+      ring_ok = scan_range_tma<false>(sc, S.v, S.v.near, S.t, prefilter != 0, ws, r, surv, gst);
+    else
+      scan_range_direct<false>(sc, S.v, S.v.near, S.t, prefilter != 0, ws, surv, gst);
+    warp_finish(sc, ws.sbuf, surv, gst);
+    if (!ring_ok) break;  // a copy may still be in flight: this warp takes no more tasks
   }
 }
 
-// --------------------------------------------------------------------- tma
-
-struct Ring {
-  WarpSmem* sm;
-  const int32_t* xyz;
-  int64_t nv;
-  int64_t p_first, p_last, next_issue;
-  uint64_t policy;
-
-  // lane 0 only: bulk-copy piece q into its slot (the part of the array's
-  // tail that is not a multiple of 16 bytes is copied with plain loads)
-  __device__ __forceinline__ void issue(int64_t q) {
-    const int k = (int)((q - p_first) & (kStages - 1));
-    const int64_t v0 = q << kPieceLog2;
-    const int64_t n = min((int64_t)kPieceV, nv - v0);
-    const uint32_t bytes = (uint32_t)(n * 12);
-    const uint32_t tma = bytes & ~15u;
-    int32_t* dst = sm->ring[k];
-    const int32_t* src = xyz + 3 * v0;
-    if (tma) {
-      mbar_arrive_expect_tx(&sm->bar[k], tma);
-      bulk_g2s(dst, src, tma, &sm->bar[k], policy);
-    } else {
-      mbar_arrive(&sm->bar[k]);
-    }
-    for (uint32_t w = tma >> 2; w < (bytes >> 2); ++w) dst[w] = __ldcs(src + w);
-  }
-
-  // Every lane waits (acquiring the bytes); the result is warp-uniform.
-  __device__ __forceinline__ bool wait(int64_t q) {
-    const int k = (int)((q - p_first) & (kStages - 1));
-    const uint32_t parity = (uint32_t)(((q - p_first) >> 2) & 1);
-    return __all_sync(kFull, mbar_wait_bounded(&sm->bar[k], parity, kWaitTimeoutNs));
-  }
-};
-
-template <int kMinBlocks>
-__global__ void __launch_bounds__(kWarps * 32, kMinBlocks) prefilter_tma_kernel(Tract t, VolView v, int prefilter,
-                                                                               int32_t* surv, DevState* st) {
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  WarpSmem* sm = reinterpret_cast<WarpSmem*>(smem_raw) + (threadIdx.x >> 5);
-  const int32_t lane = (int32_t)lane_id();
-  const int64_t gw = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
-  const int64_t nw = (int64_t)gridDim.x * kWarps;
-  Scan sc;
-  if (!warp_init(t, t.ns * gw / nw, t.ns * (gw + 1) / nw, sc, st, 0)) return;
-
-  Ring r;
-  r.sm = sm;
-  r.xyz = t.xyz;
-  r.nv = t.nv;
-  r.p_first = sc.V0 >> kPieceLog2;
-  r.p_last = (sc.V0 + sc.len - 1) >> kPieceLog2;
-  r.next_issue = min(r.p_last + 1, r.p_first + kStages);
-  r.policy = policy_evict_first();
-  if (lane == 0) {
-    for (int k = 0; k < kStages; ++k) mbar_init(&sm->bar[k], 1);
-    fence_mbar_init();
-    for (int64_t q = r.p_first; q < r.next_issue; ++q) r.issue(q);
-  }
-  __syncwarp();
-
-  bool timed_out = false;
-  int64_t waited = r.p_first - 1;
-  for (int64_t q = r.p_first; q <= r.p_last; ++q) {
-    if (q > r.p_first) {
-      // piece q-1 is consumed: refill its slot with piece q-1+kStages
-      __syncwarp();
-      if (lane == 0 && r.next_issue <= r.p_last) {
-        fence_proxy_async_smem();
-        r.issue(r.next_issue);
-      }
-      if (r.next_issue <= r.p_last) ++r.next_issue;
-    }
-    if (!r.wait(q)) {
-      timed_out = true;
-      break;
-    }
-    waited = q;
-    const int4* e = reinterpret_cast<const int4*>(sm->ring[(q - r.p_first) & (kStages - 1)]) + 3 * lane;
-    int32_t p[12];
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      const int4 a = e[i];
-      p[4 * i] = a.x;
-      p[4 * i + 1] = a.y;
-      p[4 * i + 2] = a.z;
-      p[4 * i + 3] = a.w;
-    }
-    scan_window(sc, v, (int32_t)((q << kPieceLog2) - sc.V0), p, prefilter != 0, sm->sbuf, surv, st);
-    sc.steps64 += sc.steps;
-    sc.steps = 0;
-  }
-  if (timed_out) {
-    if (lane == 0) set_error(st, kErrTimeout, (int32_t)gw);
-    // no copy may be in flight when the warp leaves: bounded drain
-    for (int64_t q = waited + 1; q < r.next_issue; ++q)
-      if (!r.wait(q)) break;
-  }
-  warp_finish(sc, sm->sbuf, surv, st);
-}
-
-constexpr size_t kTmaSmemBytes = sizeof(WarpSmem) * kWarps;
+constexpr size_t kRingBytes = sizeof(TmaSmem) * kWarps;
 
 // Grid = every CTA resident at once (one wave), from the occupancy the
 // compiled kernel really reaches.
@@ -452,56 +639,69 @@ cudaError_t resident_grid(K kernel, size_t smem, int num_sms, int* grid) {
   return cudaSuccess;
 }
 
-template <int kMinBlocks>
-cudaError_t launch_one(const Tract& t, const VolView& v, bool prefilter, bool tma, int32_t* survivors,
-                       DevState* st, int num_sms, cudaStream_t s) {
+template <int kMinBlocks, bool kTma, bool kSmem>
+cudaError_t launch_plain(const Tract& t, const VolView& v, bool prefilter, int32_t* survivors, DevState* st,
+                         int num_sms, cudaStream_t s) {
+  auto k = prefilter_kernel<kMinBlocks, kTma, kSmem>;
+  const size_t near_bytes = kSmem ? (size_t)near_words(v) * 4 : 0;
+  const size_t bytes = kTma ? ring_offset(near_bytes) + kRingBytes : near_bytes;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   int grid = 0;
-  if (tma) {
-    auto k = prefilter_tma_kernel<kMinBlocks>;
-    static bool attr_set = false;
-    if (!attr_set) {
-      cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTmaSmemBytes);
-      if (e != cudaSuccess) return e;
-      attr_set = true;
-    }
-    cudaError_t e = resident_grid(k, kTmaSmemBytes, num_sms, &grid);
-    if (e != cudaSuccess) return e;
-    k<<<grid, kWarps * 32, kTmaSmemBytes, s>>>(t, v, prefilter ? 1 : 0, survivors, st);
-  } else {
-    auto k = prefilter_direct_kernel<kMinBlocks>;
-    cudaError_t e = resident_grid(k, 0, num_sms, &grid);
-    if (e != cudaSuccess) return e;
-    k<<<grid, kWarps * 32, 0, s>>>(t, v, prefilter ? 1 : 0, survivors, st);
-  }
+  if (e == cudaSuccess) e = resident_grid(k, bytes, num_sms, &grid);
+  if (e != cudaSuccess) return e;
+  k<<<grid, kWarps * 32, bytes, s>>>(t, v, prefilter ? 1 : 0, survivors, st);
   return cudaGetLastError();
 }
 
+// Near grids up to this many words are staged in shared memory (beside the
+// rings, two CTAs still fit on an SM).
+constexpr int64_t kNearSmemWordsTma = 8192;
+
 template <int kMinBlocks>
+cudaError_t launch_one(const Tract& t, const VolView& v, bool prefilter, bool tma, int32_t* survivors,
+                       DevState* st, int num_sms, cudaStream_t s) {
+  const int64_t nw = near_words(v);
+  if (tma) {
+    if (nw <= kNearSmemWordsTma) return launch_plain<kMinBlocks, true, true>(t, v, prefilter, survivors, st, num_sms, s);
+    return launch_plain<kMinBlocks, true, false>(t, v, prefilter, survivors, st, num_sms, s);
+  }
+  if (nw <= kNearSmemWords) return launch_plain<kMinBlocks, false, true>(t, v, prefilter, survivors, st, num_sms, s);
+  return launch_plain<kMinBlocks, false, false>(t, v, prefilter, survivors, st, num_sms, s);
+}
+
+template <int kMinBlocks, bool kTma>
 cudaError_t launch_batch_one(const BatchTable& tbl, const BatchTask* tasks, int32_t ntasks, bool prefilter,
                              int32_t* survivors, DevState* gst, int num_sms, cudaStream_t s) {
-  auto k = prefilter_batch_kernel<kMinBlocks>;
+  auto k = prefilter_batch_kernel<kMinBlocks, kTma>;
+  const size_t bytes = kTma ? kRingBytes : 0;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   int grid = 0;
-  cudaError_t e = resident_grid(k, 0, num_sms, &grid);
+  if (e == cudaSuccess) e = resident_grid(k, bytes, num_sms, &grid);
   if (e != cudaSuccess) return e;
-  k<<<grid, kWarps * 32, 0, s>>>(tbl, tasks, ntasks, prefilter ? 1 : 0, survivors, gst);
+  k<<<grid, kWarps * 32, bytes, s>>>(tbl, tasks, ntasks, prefilter ? 1 : 0, survivors, gst);
   return cudaGetLastError();
 }
 
 }  // namespace
 
 cudaError_t launch_prefilter_batch(const BatchTable& tbl, const BatchTask* tasks, int32_t ntasks, bool prefilter,
-                                   int ctas_per_sm, int32_t* survivors, DevState* gst, int num_sms, cudaStream_t s) {
+                                   bool tma, int ctas_per_sm, int32_t* survivors, DevState* gst, int num_sms,
+                                   cudaStream_t s) {
   if (ntasks <= 0) return cudaSuccess;
-  if (ctas_per_sm == 4) return launch_batch_one<4>(tbl, tasks, ntasks, prefilter, survivors, gst, num_sms, s);
-  return launch_batch_one<3>(tbl, tasks, ntasks, prefilter, survivors, gst, num_sms, s);
+  if (tma) {
+    if (ctas_per_sm >= 3) return launch_batch_one<3, true>(tbl, tasks, ntasks, prefilter, survivors, gst, num_sms, s);
+    return launch_batch_one<2, true>(tbl, tasks, ntasks, prefilter, survivors, gst, num_sms, s);
+  }
+  if (ctas_per_sm >= 3) return launch_batch_one<3, false>(tbl, tasks, ntasks, prefilter, survivors, gst, num_sms, s);
+  return launch_batch_one<2, false>(tbl, tasks, ntasks, prefilter, survivors, gst, num_sms, s);
 }
 
 cudaError_t launch_prefilter(const Tract& t, const VolView& v, bool prefilter, uint32_t mode, bool tma,
                              int ctas_per_sm, int32_t* survivors, DevState* st, int num_sms, cudaStream_t s) {
   (void)mode;  // the segment and the vertex-only rules share the near test; the walk applies the rule
   if (t.ns <= 0) return cudaSuccess;
-  if (ctas_per_sm == 3) return launch_one<3>(t, v, prefilter, tma, survivors, st, num_sms, s);
-  return launch_one<4>(t, v, prefilter, tma, survivors, st, num_sms, s);
+  if (ctas_per_sm >= 3) return launch_one<3>(t, v, prefilter, tma, survivors, st, num_sms, s);
+  return launch_one<2>(t, v, prefilter, tma, survivors, st, num_sms, s);
 }
 
 }  // namespace fc

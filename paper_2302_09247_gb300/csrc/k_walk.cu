@@ -66,6 +66,9 @@ __device__ __forceinline__ int walk_one(const VolView& v, const Tract& t, const 
   const bool point_mode = (mode & kModeVertexSampled) != 0;
   const int64_t M = v.n_lab;
   const int64_t a = t.off[s], b = t.off[s + 1];
+  // offsets the prefilter has flagged as invalid may reach this point; such
+  // a streamline is skipped (the call reports the error)
+  if (a < 0 || b > t.nv || b <= a) return 0;
   const int64_t T = b - a;
   int nV = 0, nT = 0;
   bool fail = false;
@@ -241,7 +244,8 @@ __device__ __forceinline__ void overflow_one(const VolView& v, const Tract& t, c
   const int64_t M = v.n_lab;
   if (threadIdx.x == 0) { *nV = 0; *nT = 0; }
   __syncthreads();
-  const int64_t a = t.off[s], b = t.off[s + 1], T = b - a;
+  const int64_t a = t.off[s], b = t.off[s + 1];
+  const int64_t T = (a >= 0 && b <= t.nv && a <= b) ? b - a : 0;  // invalid offsets: nothing (error reported)
   const bool pts = T == 1 || point_mode;
   const int64_t units = pts ? T : T - 1;
   for (int64_t u = threadIdx.x; u < units; u += blockDim.x) {

@@ -73,7 +73,8 @@ struct fastcod_server {
   int64_t reserved = 0;
   uint32_t mode = 0;
   int prefilter = 1;
-  int ctas = 3;
+  int ctas = 2;
+  int tma = 1;
   int near_log2 = 1;
   Clock::time_point t0;
 
@@ -106,10 +107,13 @@ namespace {
 
 double now_s(fastcod_server* S) { return std::chrono::duration<double>(Clock::now() - S->t0).count(); }
 
-int32_t near_words(const int32_t d[3], int near_log2) {
-  const int32_t cs = 1 << near_log2;
-  const int64_t nx = (d[0] + 2 + cs - 1) / cs, ny = (d[1] + 2 + cs - 1) / cs, nz = (d[2] + 2 + cs - 1) / cs;
-  return (int32_t)(((nx + 15) / 16) * ny * nz);
+int64_t near_words(const int32_t d[3], int near_log2) {
+  fc::VolView v{};
+  v.dx = d[0];
+  v.dy = d[1];
+  v.dz = d[2];
+  fc::set_near_dims(v, near_log2);
+  return fc::near_words(v);
 }
 
 // Device bytes a request holds while admitted (without chunk staging).
@@ -165,11 +169,7 @@ cudaError_t setup_request(fastcod_server* S, Request* r, uint32_t** tmp, size_t*
   v.bx = (h.dims[0] + 3) / 4;
   v.by = (h.dims[1] + 3) / 4;
   v.bz = (h.dims[2] + 3) / 4;
-  v.nsh = S->near_log2;
-  const int32_t cs = 1 << S->near_log2;
-  v.nwx = ((h.dims[0] + 2 + cs - 1) / cs + 15) / 16;
-  v.nny = (h.dims[1] + 2 + cs - 1) / cs;
-  v.nnz = (h.dims[2] + 2 + cs - 1) / cs;
+  fc::set_near_dims(v, S->near_log2);
   v.n_roi = h.n_roi;
   v.n_lab = h.n_targets;
   if (e == cudaSuccess) e = cudaMemsetAsync(r->acc.C, 0, nm * 4, S->compute);
@@ -342,7 +342,7 @@ bool iterate(fastcod_server* S, uint32_t** tmp, size_t* tmp_cap) {
                           S->compute);
     if (e == cudaSuccess) e = cudaMemsetAsync(S->gst, 0, sizeof(DevState), S->compute);
     if (e == cudaSuccess)
-      e = fc::launch_prefilter_batch(tbl, S->tasks, (int32_t)tasks.size(), S->prefilter != 0, S->ctas, S->lists, S->gst,
+      e = fc::launch_prefilter_batch(tbl, S->tasks, (int32_t)tasks.size(), S->prefilter != 0, S->tma != 0, S->ctas, S->lists, S->gst,
                                      S->num_sms, S->compute);
     if (e == cudaSuccess) e = fc::launch_walk_batch(tbl, S->lists, S->mode, S->lists + S->lists_cap, S->gst, S->num_sms, S->compute);
     if (e == cudaSuccess)
@@ -444,6 +444,7 @@ FASTCOD_API int fastcod_server_create(fastcod_ctx* c, int32_t max_slots, int64_t
   S->mode = c->mode;
   S->prefilter = c->prefilter;
   S->ctas = c->prefilter_ctas;
+  S->tma = c->staging_tma;
   S->near_log2 = c->near_log2;
   S->t0 = Clock::now();
   size_t free_b = 0, total_b = 0;
