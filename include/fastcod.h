@@ -106,7 +106,13 @@ enum {
    * near-grid cell per batch shape by timed trials on the first batch of that
    * shape (cached in the context, and in the file named by the environment
    * variable FASTCOD_TUNE_CACHE when set); 0: use the options as set. */
-  FASTCOD_OPT_AUTOTUNE = 8
+  FASTCOD_OPT_AUTOTUNE = 8,
+  /* 1: fastcod_add_streamlines reads page-locked (mapped) host xyz in place,
+   * the kernels streaming it over the host link while they compute (16-byte
+   * aligned xyz; otherwise it is copied); 0 (default): page-locked xyz is
+   * first copied to device memory (measured faster on GB300).  Host offsets
+   * and pageable host inputs are always copied.  Results are identical. */
+  FASTCOD_OPT_HOST_IN_PLACE = 9
 };
 
 typedef struct fastcod_ctx fastcod_ctx;

@@ -32,6 +32,15 @@ int ptr_kind(const void* p, int dev) {
   return 0;
 }
 
+const void* mapped_host(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 int grow(fastcod_ctx* c, void** p, size_t* cap, size_t need) {
   if (need <= *cap && *p) return FASTCOD_OK;
   size_t n = need < 256 ? 256 : need;
@@ -57,6 +66,7 @@ namespace {
 
 using fcapi::fail;
 using fcapi::grow;
+using fcapi::mapped_host;
 using fcapi::ptr_kind;
 
 
@@ -381,7 +391,17 @@ FASTCOD_API int fastcod_add_streamlines(fastcod_ctx* c, const int32_t* xyz, int6
   const int64_t* d_off = offsets;
   if (int rc = begin_profiled_call(c)) return rc;
   if (int rc = record(c, 0)) return rc;
-  if (kx == 0) {
+  // page-locked host xyz: read in place over the host link when allowed (the
+  // offsets, read with dependent loads, are always copied)
+  bool xyz_in_place = false;
+  if (kx == 0 && c->host_in_place) {
+    const void* m = mapped_host(xyz);
+    if (m && !((uintptr_t)m & 15u)) {
+      d_xyz = static_cast<const int32_t*>(m);
+      xyz_in_place = true;
+    }
+  }
+  if (kx == 0 && !xyz_in_place) {
     int rc = grow(c, (void**)&c->d_xyz, &c->xyz_bytes, (size_t)nv * 12 + 16);
     if (rc) return rc;
     CU(cudaMemcpyAsync(c->d_xyz, xyz, (size_t)nv * 12, cudaMemcpyHostToDevice, c->stream));
@@ -411,7 +431,10 @@ FASTCOD_API int fastcod_add_streamlines(fastcod_ctx* c, const int32_t* xyz, int6
   acc.C = c->d_C;
   acc.Cend = c->d_Cend;
   if (int rc = record(c, 1)) return rc;
-  CU(fc::launch_prefilter(t, v, c->prefilter != 0, c->mode, c->staging_tma != 0, c->prefilter_ctas, c->d_surv,
+  // bulk copies stage device-resident vertices; host-resident ones are read
+  // with direct loads
+  CU(fc::launch_prefilter(t, v, c->prefilter != 0, c->mode, c->staging_tma != 0 && !xyz_in_place, c->prefilter_ctas,
+                          c->d_surv,
                           c->d_state, c->num_sms, c->stream));
   if (int rc = record(c, 2)) return rc;
   CU(fc::launch_walk(t, v, c->d_surv, acc, c->mode, c->d_ovf, c->d_state, c->num_sms, c->stream));
@@ -520,6 +543,10 @@ FASTCOD_API int fastcod_set_option(fastcod_ctx* c, int32_t key, int64_t value) {
     case FASTCOD_OPT_AUTOTUNE:
       if (value != 0 && value != 1) break;
       c->autotune = (int)value;
+      return FASTCOD_OK;
+    case FASTCOD_OPT_HOST_IN_PLACE:
+      if (value != 0 && value != 1) break;
+      c->host_in_place = (int)value;
       return FASTCOD_OK;
     case FASTCOD_OPT_PROFILE:
       if (value != 0 && value != 1) break;

@@ -57,6 +57,7 @@ struct fastcod_ctx {
   int prefilter_ctas = 2;
   int near_log2 = 1;       // near grid cell: (1 << near_log2)^3 voxels
   int autotune = 1;        // batched form: tune per batch shape
+  int host_in_place = 0;   // read page-locked host xyz in place (option)
   int profile = 0;
   struct EvSet {
     cudaEvent_t e[5];
@@ -75,6 +76,8 @@ namespace fcapi {
 int fail(fastcod_ctx* c, int code, const char* fmt, ...);
 // 0 = host memory, 1 = device memory of dev, -1 = device memory elsewhere.
 int ptr_kind(const void* p, int dev);
+// Device address of page-locked (mapped) host memory; nullptr for anything else.
+const void* mapped_host(const void* p);
 // Grow a device buffer to at least need bytes (synchronises before freeing).
 int grow(fastcod_ctx* c, void** p, size_t* cap, size_t need);
 // Release the batched form's state (batch.cu).

@@ -18,22 +18,24 @@
 // (the walk decides it).
 //
 // Vertex-parallel scan.  Each warp owns a contiguous range of streamlines and
-// walks its vertex range in 256-vertex windows aligned to 256; lane l takes
-// the eight consecutive vertices 8l..8l+7 of the window (six 16-byte loads),
-// so every lane is busy whatever the streamline lengths, and the loads of the
-// next window are in flight while the current one is processed:
+// walks its vertex range in 512-vertex windows aligned to 512, each two
+// 256-vertex halves; in a half, lane l takes the eight consecutive vertices
+// 8l..8l+7 (six 16-byte words), so every lane is busy whatever the
+// streamline lengths:
 //   - the streamline boundaries (offsets) falling in the window, kept in a
 //     two-group register cache of 64 offsets per warp, set the window's start
 //     bits (shared-memory atomics, one word per 32 vertices);
 //   - per vertex: coordinate check, voxel-step count and long-segment check of
 //     the segment ending there (unless the vertex starts a streamline), and
 //     at even vertices a near-grid lookup (shared memory when the grid fits);
-//   - a warp scan of the per-lane hit counts gives, at every boundary x, the
-//     running number of ROI / target hits before x, and the streamline ending
-//     at x passes when both counts grew since its start boundary.
-// Two loaders with identical results: direct streaming loads into registers
-// (default) and TMA (a ring of 3072-byte pieces per warp in shared memory,
-// cp.async.bulk + mbarrier, L2 evict-first).
+//   - one warp scan of the per-lane hit counts of both halves gives, at every
+//     boundary x, the running number of ROI / target hits before x, and the
+//     streamline ending at x passes when both counts grew since its start
+//     boundary.
+// Two loaders with identical results: TMA (default; the halves stream through
+// a ring of three 3072-byte slots per warp in shared memory, cp.async.bulk +
+// mbarrier, L2 evict-first) and direct streaming loads into registers (the
+// next half in flight while the current one is processed).
 #include "fc_device.cuh"
 #include "fc_tma.cuh"
 
@@ -41,12 +43,14 @@ namespace fc {
 
 namespace {
 
-constexpr int kWinLog2 = 8;
-constexpr int kWin = 1 << kWinLog2;       // vertices per window (= per TMA piece)
-constexpr int kVpl = kWin / 32;           // vertices per lane
-constexpr int kLaneWords = kVpl * 3;      // 24 int32 per lane
-constexpr int kWinWords = kWin * 3;       // 768 int32 = 3072 bytes
-constexpr int kStages = 3;                // TMA ring depth per warp
+constexpr int kHalfLog2 = 8;
+constexpr int kHalf = 1 << kHalfLog2;     // vertices per half-window (= per TMA piece)
+constexpr int kWinLog2 = kHalfLog2 + 1;
+constexpr int kWin = 1 << kWinLog2;       // vertices per window
+constexpr int kVpl = kHalf / 32;          // vertices per lane per half
+constexpr int kLaneWords = kVpl * 3;      // 24 int32 per lane per half
+constexpr int kHalfWords = kHalf * 3;     // 768 int32 = 3072 bytes
+constexpr int kStages = 3;                // TMA ring depth per warp (halves)
 constexpr int kWarps = 8;                 // warps per CTA
 constexpr uint64_t kWaitTimeoutNs = 1000000000ull;  // 1 s
 constexpr int32_t kInf = 0x7fffffff;
@@ -84,7 +88,7 @@ struct Scan {
   uint32_t lastR, lastT;     // hit counts at the last decided boundary
   int32_t last_b;            // that boundary
   uint32_t carry;            // the current window's vertex 0 starts a streamline
-  int32_t qx, qy, qz;        // voxel of the previous window's last vertex
+  int32_t qx, qy, qz;        // voxel of the last vertex processed (lane 31's)
   unsigned long long steps;  // voxel steps counted by this lane
   uint32_t singles, kept, badc;
   int nbuf;
@@ -180,44 +184,48 @@ __device__ __noinline__ uint32_t long_box(const uint32_t* bricks, int32_t dx, in
   return box_bits(v, lx, ly, lz, hx, hy, hz);
 }
 
-// One window: first vertex W = q * kWin; p = the lane's 24 words, vertices
-// W + 8l .. W + 8l + 7 (zero past the end of the array).
-template <bool kSmem>
-__device__ __forceinline__ void scan_window(Scan& sc, const VolView& v, const uint32_t* nw, int64_t q,
-                                            const int32_t (&p)[kLaneWords], bool prefilter, WarpShared& ws,
-                                            int32_t* surv, DevState* gst) {
+// 1. Start of window W (first vertex, a multiple of kWin): boundaries b with
+//    b - W <= kWin are decided in this window (nbw of them, from s_cur); those
+//    with b - W < kWin start a streamline at a vertex of it (start bits in
+//    ws.st).  b_first: the lane's boundary of the first round of 32.
+__device__ __forceinline__ void window_begin(Scan& sc, WarpShared& ws, int32_t W, int32_t& nbw, int32_t& b_first) {
   const int32_t lane = (int32_t)lane_id();
-  const int32_t W = (int32_t)(q << kWinLog2);
-
-  // 1. boundaries b with b - W <= kWin are decided in this window; those
-  //    with b - W < kWin start a streamline at a vertex of it
   cache_seek(sc);
   if (lane < kWin / 32) ws.st[lane] = 0u;
   __syncwarp();
-  int32_t nbw = 0;
-  int32_t b_first = kInf;
-  {
-    int64_t s = sc.s_cur;
-    int32_t prev = sc.last_b;
-    for (int round = 0;; ++round) {
-      const int32_t b = fetch_bnd(sc, s, prev);
-      if (round == 0) b_first = b;
-      const int32_t r = b - W;
-      if ((uint32_t)r < (uint32_t)kWin) atomicOr(&ws.st[r >> 5], 1u << (r & 31));
-      const int n = __popc(__ballot_sync(kFull, r <= kWin));
-      nbw += n;
-      if (n < 32 || sc.abort) break;
-      prev = __shfl_sync(kFull, b, 31);
-      s += 32;
-    }
+  nbw = 0;
+  b_first = kInf;
+  int64_t s = sc.s_cur;
+  int32_t prev = sc.last_b;
+  for (int round = 0;; ++round) {
+    const int32_t b = fetch_bnd(sc, s, prev);
+    if (round == 0) b_first = b;
+    const int32_t r = b - W;
+    if ((uint32_t)r < (uint32_t)kWin) atomicOr(&ws.st[r >> 5], 1u << (r & 31));
+    const int n = __popc(__ballot_sync(kFull, r <= kWin));
+    nbw += n;
+    if (n < 32 || sc.abort) break;
+    prev = __shfl_sync(kFull, b, 31);
+    s += 32;
   }
   __syncwarp();
-  const uint32_t st8 = ((ws.st[lane >> 2] >> ((lane & 3) << 3)) & 0xffu) | (lane == 0 ? sc.carry : 0u);
-  const int32_t lo = sc.V0 - W - kVpl * lane, hi = sc.V1 - W - kVpl * lane;
+}
+
+// 2. Half h of window W: p = the lane's 24 words, vertices
+//    W + h*kHalf + 8l .. +7 (zero past the end of the array).  Returns the
+//    lane's hit bits (R hits at the even bits k, T hits at bits k + 1, for
+//    the lookups at the even slots k).
+template <bool kSmem>
+__device__ __forceinline__ uint32_t scan_half(Scan& sc, const VolView& v, const uint32_t* nw,
+                                              const int32_t (&p)[kLaneWords], int h, int32_t W, const WarpShared& ws) {
+  const int32_t lane = (int32_t)lane_id();
+  const uint32_t st8 = ((ws.st[h * (kHalf / 32) + (lane >> 2)] >> ((lane & 3) << 3)) & 0xffu) |
+                       ((h == 0 && lane == 0) ? sc.carry : 0u);
+  const int32_t base = W + h * kHalf + kVpl * lane;
+  const int32_t lo = sc.V0 - base, hi = sc.V1 - base;
   const uint32_t valid8 = lowmask(min(max(hi, 0), kVpl)) & ~lowmask(min(max(lo, 0), kVpl));
   const uint32_t keep8 = valid8 & ~st8;  // slots whose incoming segment is counted
 
-  // 2. vertices
   // every lane takes part in the shuffles; lane 0 then takes the carried voxel
   int32_t q0x = __shfl_up_sync(kFull, p[kLaneWords - 3] >> kUnitLog2, 1);
   int32_t q0y = __shfl_up_sync(kFull, p[kLaneWords - 2] >> kUnitLog2, 1);
@@ -267,10 +275,18 @@ __device__ __forceinline__ void scan_window(Scan& sc, const VolView& v, const ui
   sc.qx = __shfl_sync(kFull, p[kLaneWords - 3] >> kUnitLog2, 31);
   sc.qy = __shfl_sync(kFull, p[kLaneWords - 2] >> kUnitLog2, 31);
   sc.qz = __shfl_sync(kFull, p[kLaneWords - 1] >> kUnitLog2, 31);
+  return h8;
+}
 
-  // 3. hit counts: R hits at the even bits of h8, T hits at the odd bits
-  //    (bit k + 1 for the lookup at slot k); both counts in one word
-  const uint32_t c = (uint32_t)__popc(h8 & 0x55u) | ((uint32_t)__popc(h8 & 0xaau) << 16);
+// 3. End of window W: hit counts of both halves (h0, h1) and the decisions
+//    at its nbw boundaries, 32 per round.
+__device__ __forceinline__ void window_end(Scan& sc, WarpShared& ws, int32_t W, int32_t nbw, int32_t b_first,
+                                           uint32_t h0, uint32_t h1, bool prefilter, int32_t* surv, DevState* gst) {
+  const int32_t lane = (int32_t)lane_id();
+  // per-lane counts in four byte fields (R0, T0, R1, T1); a field's prefix
+  // over the warp is at most 4 * 32 = 128, so fields never carry
+  const uint32_t c = (uint32_t)__popc(h0 & 0x55u) | ((uint32_t)__popc(h0 & 0xaau) << 8) |
+                     ((uint32_t)__popc(h1 & 0x55u) << 16) | ((uint32_t)__popc(h1 & 0xaau) << 24);
   uint32_t inc = c;
 #pragma unroll
   for (int d = 1; d < 32; d <<= 1) {
@@ -279,8 +295,10 @@ __device__ __forceinline__ void scan_window(Scan& sc, const VolView& v, const ui
   }
   const uint32_t excl = inc - c;
   const uint32_t tot = __shfl_sync(kFull, inc, 31);
+  const uint32_t tR0 = tot & 0xffu, tT0 = (tot >> 8) & 0xffu;
+  const uint32_t tR = tR0 + ((tot >> 16) & 0xffu), tT = tT0 + (tot >> 24);
+  const uint32_t hh01 = h0 | (h1 << 8);
 
-  // 4. decisions at the boundaries of this window, 32 per round
   int64_t s = sc.s_cur;
   int32_t prev = sc.last_b;
   for (int round = 0; nbw > 0 && !sc.abort; ++round) {
@@ -288,16 +306,20 @@ __device__ __forceinline__ void scan_window(Scan& sc, const VolView& v, const ui
     const int n = min(nbw, 32);
     const bool in = lane < n;
     const int32_t x = min(max(b - W, 0), kWin);
-    const int32_t src = x >> 3, o = x & 7;
-    const uint32_t e = __shfl_sync(kFull, excl, src & 31);
-    const uint32_t hh = __shfl_sync(kFull, h8, src & 31);
+    const int32_t hx = x >> kHalfLog2, xi = x & (kHalf - 1);
+    const int32_t src = xi >> 3, o = xi & 7;
+    const uint32_t e = __shfl_sync(kFull, excl, src);
+    const uint32_t hh = (__shfl_sync(kFull, hh01, src) >> (hx == 1 ? 8 : 0)) & 0xffu;
     uint32_t cR, cT;
-    if (src >= 32) {
-      cR = tot & 0xffffu;
-      cT = tot >> 16;
+    if (hx >= 2) {
+      cR = tR;
+      cT = tT;
+    } else if (hx == 0) {
+      cR = (e & 0xffu) + (uint32_t)__popc(hh & 0x55u & lowmask(o));
+      cT = ((e >> 8) & 0xffu) + (uint32_t)__popc(hh & 0xaau & lowmask(o + 1));
     } else {
-      cR = (e & 0xffffu) + (uint32_t)__popc(hh & 0x55u & lowmask(o));
-      cT = (e >> 16) + (uint32_t)__popc(hh & 0xaau & lowmask(o + 1));
+      cR = tR0 + ((e >> 16) & 0xffu) + (uint32_t)__popc(hh & 0x55u & lowmask(o));
+      cT = tT0 + (e >> 24) + (uint32_t)__popc(hh & 0xaau & lowmask(o + 1));
     }
     cR += sc.cumR;
     cT += sc.cumT;
@@ -328,8 +350,8 @@ __device__ __forceinline__ void scan_window(Scan& sc, const VolView& v, const ui
   }
   sc.s_cur = s;
   sc.carry = (sc.last_b - W == kWin) ? 1u : 0u;
-  sc.cumR += tot & 0xffffu;
-  sc.cumT += tot >> 16;
+  sc.cumR += tR;
+  sc.cumT += tT;
 }
 
 // Set up the scan of streamlines [s_lo, s_hi) of t; false when there is
@@ -390,9 +412,12 @@ __device__ __forceinline__ void warp_finish(Scan& sc, int32_t* sbuf, int32_t* su
   }
 }
 
-// The lane's 24 words of window q (zero past the end of the array).
-__device__ __forceinline__ void load_window(const Tract& t, int64_t q, int32_t (&p)[kLaneWords]) {
-  const int64_t g = (q << kWinLog2) + kVpl * lane_id();  // the lane's first vertex
+// ------------------------------------------------------------------ direct
+
+// The lane's 24 words of half hq (vertices hq * kHalf + 8l ..; zero past the
+// end of the array).
+__device__ __forceinline__ void load_half(const Tract& t, int64_t hq, int32_t (&p)[kLaneWords]) {
+  const int64_t g = (hq << kHalfLog2) + kVpl * lane_id();  // the lane's first vertex
   if (g + kVpl <= t.nv) {
     const int4* e = reinterpret_cast<const int4*>(t.xyz + 3 * g);  // 96-byte chunk, 16-byte aligned
 #pragma unroll
@@ -409,29 +434,29 @@ __device__ __forceinline__ void load_window(const Tract& t, int64_t q, int32_t (
   }
 }
 
-// ------------------------------------------------------------------ direct
-
-// Window loop of the direct loader: window q+1 is loaded while q is scanned.
+// Window loop of the direct loader: the next half is loaded while the
+// current one is scanned.
 template <bool kSmem>
 __device__ __forceinline__ void scan_range_direct(Scan& sc, const VolView& v, const uint32_t* nw, const Tract& t,
                                                   bool prefilter, WarpShared& ws, int32_t* surv, DevState* gst) {
-  const int64_t q1 = (int64_t)(sc.V1 - 1) >> kWinLog2;
-  int64_t q = (int64_t)sc.V0 >> kWinLog2;
+  const int64_t q0 = (int64_t)sc.V0 >> kWinLog2, q1 = (int64_t)(sc.V1 - 1) >> kWinLog2;
   int32_t pa[kLaneWords], pb[kLaneWords];
-  load_window(t, q, pa);
-  for (;;) {
-    if (q < q1) load_window(t, q + 1, pb);
-    scan_window<kSmem>(sc, v, nw, q, pa, prefilter, ws, surv, gst);
-    if (++q > q1 || sc.abort) break;
-    if (q < q1) load_window(t, q + 1, pa);
-    scan_window<kSmem>(sc, v, nw, q, pb, prefilter, ws, surv, gst);
-    if (++q > q1 || sc.abort) break;
+  load_half(t, 2 * q0, pa);
+  for (int64_t q = q0; q <= q1 && !sc.abort; ++q) {
+    const int32_t W = (int32_t)(q << kWinLog2);
+    int32_t nbw, b_first;
+    window_begin(sc, ws, W, nbw, b_first);
+    load_half(t, 2 * q + 1, pb);
+    const uint32_t h0 = scan_half<kSmem>(sc, v, nw, pa, 0, W, ws);
+    if (q < q1) load_half(t, 2 * q + 2, pa);
+    const uint32_t h1 = scan_half<kSmem>(sc, v, nw, pb, 1, W, ws);
+    window_end(sc, ws, W, nbw, b_first, h0, h1, prefilter, surv, gst);
   }
 }
 
 // --------------------------------------------------------------------- tma
 
-// Per-warp ring of kStages window-sized slots filled by 1-D bulk copies.
+// Per-warp ring of kStages half-window slots filled by 1-D bulk copies.
 // Slots are used in a fixed cyclic order for the warp's whole life (slot,
 // phase), so ranges follow one another without re-initialising barriers:
 // a range issues its first pieces into the slots after the last one used,
@@ -439,10 +464,10 @@ __device__ __forceinline__ void scan_range_direct(Scan& sc, const VolView& v, co
 // 128-byte aligned, so every warp's ring (a bulk-copy destination) starts on
 // a 16-byte boundary.
 struct __align__(128) TmaSmem {
-  int32_t ring[kStages][kWinWords];
+  int32_t ring[kStages][kHalfWords];
   uint64_t bar[kStages];
 };
-static_assert(sizeof(TmaSmem) % 128 == 0 && (kWinWords * 4) % 16 == 0, "ring slots must stay 16-byte aligned");
+static_assert(sizeof(TmaSmem) % 128 == 0 && (kHalfWords * 4) % 16 == 0, "ring slots must stay 16-byte aligned");
 
 struct Ring {
   TmaSmem* sm;
@@ -461,18 +486,23 @@ struct Ring {
     __syncwarp();
   }
 
-  // lane 0 only: copy window q of t into slot k (the part of the array's
-  // tail that is not a multiple of 16 bytes with plain loads, the rest of a
-  // short last window zero-filled)
-  __device__ __forceinline__ void issue(const Tract& t, int64_t q, uint32_t k) {
-    const int64_t v0 = q << kWinLog2;
-    const int64_t n = min((int64_t)kWin, t.nv - v0);
-    const uint32_t bytes = (uint32_t)(n * 12);
-    const uint32_t tma = bytes & ~15u;
+  // lane 0 only: copy half hq of t into slot k.  A whole half is one bulk
+  // copy; at the end of the array the part that is not a multiple of 16 bytes
+  // is copied with plain loads and the rest of the slot zero-filled.
+  __device__ __forceinline__ void issue(const Tract& t, int64_t hq, uint32_t k) {
+    const int64_t v0 = hq << kHalfLog2;
     int32_t* dst = sm->ring[k];
     const int32_t* src = t.xyz + 3 * v0;
+    if (v0 + kHalf <= t.nv) {
+      mbar_arrive_expect_tx(&sm->bar[k], (uint32_t)(kHalfWords * 4));
+      bulk_g2s(dst, src, (uint32_t)(kHalfWords * 4), &sm->bar[k], policy);
+      return;
+    }
+    const int64_t n = max((int64_t)0, t.nv - v0);
+    const uint32_t bytes = (uint32_t)(n * 12);
+    const uint32_t tma = bytes & ~15u;
     for (uint32_t w = tma >> 2; w < (bytes >> 2); ++w) dst[w] = __ldcs(src + w);
-    for (uint32_t w = bytes >> 2; w < (uint32_t)kWinWords; ++w) dst[w] = 0;
+    for (uint32_t w = bytes >> 2; w < (uint32_t)kHalfWords; ++w) dst[w] = 0;
     if (tma) {
       mbar_arrive_expect_tx(&sm->bar[k], tma);
       bulk_g2s(dst, src, tma, &sm->bar[k], policy);
@@ -495,63 +525,79 @@ struct Ring {
   }
 };
 
+// Takes the next half from the ring into p and refills its slot with half
+// `issued` when that is still part of the range (hq_end exclusive).  False
+// when the wait timed out.
+__device__ __forceinline__ bool ring_take(Ring& r, const Tract& t, int64_t& issued, int64_t hq_end,
+                                          int32_t (&p)[kLaneWords]) {
+  if (!r.wait()) return false;
+  const int4* e = reinterpret_cast<const int4*>(r.sm->ring[r.slot]) + (kLaneWords / 4) * lane_id();
+#pragma unroll
+  for (int i = 0; i < kLaneWords / 4; ++i) {
+    const int4 a = e[i];
+    p[4 * i] = a.x;
+    p[4 * i + 1] = a.y;
+    p[4 * i + 2] = a.z;
+    p[4 * i + 3] = a.w;
+  }
+  // the half is in registers: its slot takes the next piece
+  __syncwarp();
+  if (issued < hq_end) {
+    if (lane_id() == 0) {
+      fence_proxy_async_smem();
+      r.issue(t, issued, r.slot);
+    }
+    ++issued;
+  }
+  r.advance();
+  return true;
+}
+
 // Window loop of the TMA loader over the scan's vertex range.  Returns false
 // when a wait timed out (the error is set and the ring may not be reused).
 template <bool kSmem>
 __device__ __forceinline__ bool scan_range_tma(Scan& sc, const VolView& v, const uint32_t* nw, const Tract& t,
                                                bool prefilter, WarpShared& ws, Ring& r, int32_t* surv,
                                                DevState* gst) {
-  const int32_t lane = (int32_t)lane_id();
   const int64_t q0 = (int64_t)sc.V0 >> kWinLog2, q1 = (int64_t)(sc.V1 - 1) >> kWinLog2;
-  int64_t issued = min(q1 + 1, q0 + kStages);  // windows [q0, issued) are in flight
-  if (lane == 0) {
+  const int64_t hq_end = 2 * q1 + 2;
+  int64_t taken = 2 * q0;                           // halves [2 q0, taken) consumed
+  int64_t issued = min(hq_end, 2 * q0 + kStages);   // halves [taken, issued) in flight
+  if (lane_id() == 0) {
     uint32_t k = r.slot;
-    for (int64_t q = q0; q < issued; ++q) {
-      r.issue(t, q, k);
+    for (int64_t hq = 2 * q0; hq < issued; ++hq) {
+      r.issue(t, hq, k);
       k = (k + 1 == (uint32_t)kStages) ? 0u : k + 1;
     }
   }
   __syncwarp();
-  int64_t q = q0;
   bool ok = true;
-  for (; q <= q1; ++q) {
-    if (!r.wait()) {
+  for (int64_t q = q0; q <= q1 && !sc.abort; ++q) {
+    const int32_t W = (int32_t)(q << kWinLog2);
+    int32_t nbw, b_first;
+    window_begin(sc, ws, W, nbw, b_first);
+    int32_t p[kLaneWords];
+    if (!ring_take(r, t, issued, hq_end, p)) {
       ok = false;
       break;
     }
-    const int4* e = reinterpret_cast<const int4*>(r.sm->ring[r.slot]) + (kLaneWords / 4) * lane;
-    int32_t p[kLaneWords];
-#pragma unroll
-    for (int i = 0; i < kLaneWords / 4; ++i) {
-      const int4 a = e[i];
-      p[4 * i] = a.x;
-      p[4 * i + 1] = a.y;
-      p[4 * i + 2] = a.z;
-      p[4 * i + 3] = a.w;
-    }
-    // the window is in registers: refill its slot with window q + kStages
-    __syncwarp();
-    if (issued <= q1) {
-      if (lane == 0) {
-        fence_proxy_async_smem();
-        r.issue(t, issued, r.slot);
-      }
-      ++issued;
-    }
-    r.advance();
-    scan_window<kSmem>(sc, v, nw, q, p, prefilter, ws, surv, gst);
-    if (sc.abort) {
-      ++q;
+    ++taken;
+    const uint32_t h0 = scan_half<kSmem>(sc, v, nw, p, 0, W, ws);
+    if (!ring_take(r, t, issued, hq_end, p)) {
+      ok = false;
       break;
     }
+    ++taken;
+    const uint32_t h1 = scan_half<kSmem>(sc, v, nw, p, 1, W, ws);
+    window_end(sc, ws, W, nbw, b_first, h0, h1, prefilter, surv, gst);
   }
   if (!ok) {
-    if (lane == 0) set_error(sc.sst, kErrTimeout, (int32_t)sc.s_lo);
+    if (lane_id() == 0) set_error(sc.sst, kErrTimeout, (int32_t)sc.s_lo);
     sc.abort = true;
   }
   // no copy may be in flight when the range ends: bounded drain of the
-  // windows issued but not consumed
-  for (; q < issued; ++q) {
+  // halves issued but not consumed
+  for (; taken < issued; ++taken) {
     if (!r.wait()) {
       ok = false;
       break;
@@ -653,8 +699,8 @@ cudaError_t launch_plain(const Tract& t, const VolView& v, bool prefilter, int32
   return cudaGetLastError();
 }
 
-// Near grids up to this many words are staged in shared memory (beside the
-// rings, two CTAs still fit on an SM).
+// Near grids up to this many words are staged in shared memory beside the
+// rings (two CTAs still fit on an SM).
 constexpr int64_t kNearSmemWordsTma = 8192;
 
 template <int kMinBlocks>

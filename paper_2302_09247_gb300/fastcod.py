@@ -36,6 +36,7 @@ FASTCOD_OPT_PROFILE = 5
 FASTCOD_OPT_PREFILTER_CTAS = 6
 FASTCOD_OPT_NEAR_LOG2 = 7
 FASTCOD_OPT_AUTOTUNE = 8
+FASTCOD_OPT_HOST_IN_PLACE = 9
 
 EXPORTED = [
     "fastcod_create", "fastcod_destroy", "fastcod_set_stream", "fastcod_set_volumes",

@@ -105,6 +105,30 @@ def test_cfg0_full(where):
     assert sr["n_contributing"] <= st["survivors"] <= tr.n_streamlines
 
 
+@pytest.mark.parametrize("in_place", [1, 0])
+@pytest.mark.parametrize("shift", [0, 1])
+def test_pinned_read_in_place_or_copied(in_place, shift):
+    """Page-locked inputs read in place over the host link (aligned) or
+    copied (option off, or xyz not 16-byte aligned: shift = 4 bytes)."""
+    import torch
+    from paper_2302_09247_gb300 import fastcod as fc
+    vols, tr = synth.make_subject(0)
+    buf = torch.empty(tr.xyz.size + 4, dtype=torch.int32).pin_memory()
+    xp = buf[shift:shift + tr.xyz.size].view(-1, 3)
+    xp.copy_(torch.from_numpy(tr.xyz))
+    op = torch.from_numpy(tr.offsets).pin_memory()
+    with fc.Context(0) as ctx:
+        ctx.set_option(fc.FASTCOD_OPT_HOST_IN_PLACE, in_place)
+        ctx.set_volumes(vols.roi, vols.lab, vols.dims, vols.n_roi, vols.n_targets)
+        for _ in range(2):
+            ctx.add_streamlines(xp, op)
+        C, Ce, st = ctx.connectivity(), ctx.endpoint_connectivity(), ctx.stats()
+    Cr, Cer, sr = oracle.connectivity(vols.roi, vols.lab, vols.dims, vols.n_roi, vols.n_targets, tr.xyz, tr.offsets)
+    np.testing.assert_array_equal(C, 2 * Cr)
+    np.testing.assert_array_equal(Ce, 2 * Cer)
+    assert st["voxel_steps"] == 2 * sr["voxel_steps"]
+
+
 def test_cfg0_chunked_and_options():
     vols, tr = synth.make_subject(0)
     for prefilter, staging in ((1, 1), (0, 0), (1, 0)):
