@@ -81,54 +81,72 @@ __device__ __forceinline__ uint32_t box_bits(const VolView& v, int32_t lx, int32
 // (|coordinate| < 2^24 keeps products below 2^52).
 template <typename P>
 struct SegWalk {
-  int32_t c[3];
-  P num[3], den[3];
-  int32_t sgn[3];
+  int32_t cx, cy, cz;      // current voxel
+  P nx, ny, nz;            // numerators of the next crossings
+  P ex, ey, ez;            // denominators |d_a| (1 for a still axis)
+  int32_t sx, sy, sz;      // direction of each axis (-1, 0, 1)
 
-  __device__ __forceinline__ void init(const int32_t p0[3], const int32_t p1[3]) {
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      const int32_t d = p1[a] - p0[a];
-      c[a] = p0[a] >> kUnitLog2;
-      if (d > 0) {
-        sgn[a] = 1;
-        den[a] = (P)d;
-        num[a] = (P)(((c[a] + 1) << kUnitLog2) - p0[a]);
-      } else if (d < 0) {
-        sgn[a] = -1;
-        den[a] = (P)(-d);
-        num[a] = (P)(p0[a] - (c[a] << kUnitLog2));
-      } else {
-        sgn[a] = 0;
-        den[a] = 1;
-        num[a] = 0;
-      }
+  __device__ __forceinline__ static void axis(int32_t a0, int32_t a1, int32_t& c, P& num, P& den, int32_t& sgn) {
+    const int32_t d = a1 - a0;
+    c = a0 >> kUnitLog2;
+    if (d > 0) {
+      sgn = 1;
+      den = (P)d;
+      num = (P)(((c + 1) << kUnitLog2) - a0);
+    } else if (d < 0) {
+      sgn = -1;
+      den = (P)(-d);
+      num = (P)(a0 - (c << kUnitLog2));
+    } else {
+      sgn = 0;
+      den = 1;
+      num = 0;
     }
   }
 
-  __device__ __forceinline__ bool pending(int a) const {
-    return sgn[a] > 0 ? (num[a] <= den[a]) : (sgn[a] < 0 ? (num[a] < den[a]) : false);
+  __device__ __forceinline__ void init(const int32_t p0[3], const int32_t p1[3]) {
+    axis(p0[0], p1[0], cx, nx, ex, sx);
+    axis(p0[1], p1[1], cy, ny, ey, sy);
+    axis(p0[2], p1[2], cz, nz, ez, sz);
   }
 
-  // crossing of axis a strictly before / at the same t as axis b
-  __device__ __forceinline__ bool before(int a, int b) const { return num[a] * den[b] < num[b] * den[a]; }
-  __device__ __forceinline__ bool same(int a, int b) const { return num[a] * den[b] == num[b] * den[a]; }
+  __device__ __forceinline__ static bool pending(P num, P den, int32_t sgn) {
+    return sgn > 0 ? (num <= den) : (sgn < 0 ? (num < den) : false);
+  }
 
-  // Enter the next voxel; false when the segment has no crossing left.
+  // Enter the next voxel; false when the segment has no crossing left.  The
+  // earliest pending crossing t* = bn / bd is found by exact cross-products;
+  // the axes crossing at t* are tied.
   __device__ __forceinline__ bool step() {
-    const bool q0 = pending(0), q1 = pending(1), q2 = pending(2);
+    const bool q0 = pending(nx, ex, sx), q1 = pending(ny, ey, sy), q2 = pending(nz, ez, sz);
     if (!(q0 || q1 || q2)) return false;
-    int b = q0 ? 0 : (q1 ? 1 : 2);
-    if (q1 && b != 1 && before(1, b)) b = 1;
-    if (q2 && b != 2 && before(2, b)) b = 2;
-    const bool t0 = q0 && (b == 0 || same(0, b));
-    const bool t1 = q1 && (b == 1 || same(1, b));
-    const bool t2 = q2 && (b == 2 || same(2, b));
-    const bool up = (t0 && sgn[0] > 0) || (t1 && sgn[1] > 0) || (t2 && sgn[2] > 0);
+    P bn = q0 ? nx : (q1 ? ny : nz);
+    P bd = q0 ? ex : (q1 ? ey : ez);
+    if (q1 && ny * bd < bn * ey) {
+      bn = ny;
+      bd = ey;
+    }
+    if (q2 && nz * bd < bn * ez) {
+      bn = nz;
+      bd = ez;
+    }
+    const bool t0 = q0 && nx * bd == bn * ex;
+    const bool t1 = q1 && ny * bd == bn * ey;
+    const bool t2 = q2 && nz * bd == bn * ez;
+    const bool up = (t0 && sx > 0) || (t1 && sy > 0) || (t2 && sz > 0);
     const int32_t want = up ? 1 : -1;
-    if (t0 && sgn[0] == want) { c[0] += want; num[0] += (P)(1 << kUnitLog2); }
-    if (t1 && sgn[1] == want) { c[1] += want; num[1] += (P)(1 << kUnitLog2); }
-    if (t2 && sgn[2] == want) { c[2] += want; num[2] += (P)(1 << kUnitLog2); }
+    if (t0 && sx == want) {
+      cx += want;
+      nx += (P)(1 << kUnitLog2);
+    }
+    if (t1 && sy == want) {
+      cy += want;
+      ny += (P)(1 << kUnitLog2);
+    }
+    if (t2 && sz == want) {
+      cz += want;
+      nz += (P)(1 << kUnitLog2);
+    }
     return true;
   }
 };

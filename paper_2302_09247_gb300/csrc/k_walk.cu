@@ -34,6 +34,34 @@ __device__ __forceinline__ void load_vertex(const int32_t* xyz, int64_t j, int32
   p[2] = __ldg(xyz + 3 * j + 2);
 }
 
+// Per-voxel code of in-grid voxel (x, y, z), or ~0u off the grid (no row, no
+// label).
+__device__ __forceinline__ int32_t voxel_lin(const VolView& v, int32_t x, int32_t y, int32_t z) {
+  if ((unsigned)x < (unsigned)v.dx && (unsigned)y < (unsigned)v.dy && (unsigned)z < (unsigned)v.dz)
+    return x + v.dx * (y + v.dy * z);
+  return -1;
+}
+
+__device__ __forceinline__ void decode(const VolView& v, int32_t lin, uint32_t code, int32_t& row, int32_t& lab) {
+  row = -1;
+  lab = 0;
+  if (lin < 0) return;
+  if (code & kCodeRoi) {
+    row = (int32_t)(code & kCodeRowMask);
+    if (code & kCodeRoiLabelled) lab = (int32_t)__ldg(v.lab + lin);
+  } else {
+    lab = (int32_t)code;
+  }
+}
+
+// Voxels gathered per lane before their codes are read together.
+constexpr int kGather = 4;
+
+// Walk the window's segments (one per lane, p0 -> p1 where has): every voxel
+// a segment enters (and, for the streamline's first segment, its start
+// voxel) goes into the sets.  Each round gathers up to kGather voxels per
+// lane with the integer walk, reads their codes with independent loads, then
+// inserts them; long segments take more rounds.
 template <typename P>
 __device__ __forceinline__ void walk_window(const VolView& v, WalkWarpSmem& sm, const int32_t p0[3],
                                             const int32_t p1[3], bool has, bool first, bool endpoint_mode,
@@ -45,13 +73,27 @@ __device__ __forceinline__ void walk_window(const VolView& v, WalkWarpSmem& sm, 
     pend = first ? true : w.step();
   }
   while (__any_sync(kFull, pend)) {
-    int32_t row = -1, lab = 0;
-    if (pend) voxel_lookup(v, w.c[0], w.c[1], w.c[2], row, lab);
-    if (endpoint_mode) lab = 0;
-    nV = set_insert<kHV>(sm.tabV, sm.listV, nV, row, fail);
-    nT = set_insert<kHT>(sm.tabT, sm.listT, nT, lab > 0 ? lab : -1, fail);
-    if (nV > kLimV || nT > kLimT) { fail = true; break; }
-    if (pend) pend = w.step();
+    int32_t lin[kGather];
+#pragma unroll
+    for (int i = 0; i < kGather; ++i) {
+      lin[i] = pend ? voxel_lin(v, w.cx, w.cy, w.cz) : -1;
+      if (pend) pend = w.step();
+    }
+    uint32_t code[kGather];
+#pragma unroll
+    for (int i = 0; i < kGather; ++i) code[i] = lin[i] >= 0 ? __ldg(v.code + lin[i]) : 0u;
+#pragma unroll
+    for (int i = 0; i < kGather; ++i) {
+      int32_t row, lab;
+      decode(v, lin[i], code[i], row, lab);
+      if (endpoint_mode) lab = 0;
+      nV = set_insert<kHV>(sm.tabV, sm.listV, nV, row, fail);
+      nT = set_insert<kHT>(sm.tabT, sm.listT, nT, lab > 0 ? lab : -1, fail);
+    }
+    if (nV > kLimV || nT > kLimT) {
+      fail = true;
+      break;
+    }
   }
 }
 
@@ -88,14 +130,21 @@ __device__ __forceinline__ int walk_one(const VolView& v, const Tract& t, const 
       fail = __any_sync(kFull, fail);
     }
   } else {
+    // window i0 holds segments a+i0+lane -> a+i0+lane+1; the vertices of the
+    // next window are loaded while this one is walked
+    int32_t cur[3] = {0, 0, 0};
+    if (a + lane < b) load_vertex(t.xyz, a + lane, cur);
     for (int64_t i0 = 0; i0 < T - 1 && !fail; i0 += 32) {
       const int64_t j = a + i0 + lane;
-      const int64_t jhi = min(a + i0 + 32, b - 1);
-      int32_t p0[3] = {0, 0, 0}, p1[3];
-      if (j <= jhi) load_vertex(t.xyz, j, p0);
+      int32_t nxt[3] = {0, 0, 0};
+      if (j + 32 < b) load_vertex(t.xyz, j + 32, nxt);
+      int32_t p0[3] = {cur[0], cur[1], cur[2]}, p1[3];
 #pragma unroll
-      for (int k = 0; k < 3; ++k) p1[k] = __shfl_down_sync(kFull, p0[k], 1);
-      if (lane == 31 && j + 1 <= jhi) load_vertex(t.xyz, j + 1, p1);
+      for (int k = 0; k < 3; ++k) {
+        const int32_t dn = __shfl_down_sync(kFull, p0[k], 1);
+        const int32_t wrap = __shfl_sync(kFull, nxt[k], 0);
+        p1[k] = lane == 31 ? wrap : dn;
+      }
       const bool has = j < b - 1;
       const bool small = !has || (abs(p1[0] - p0[0]) < 65536 && abs(p1[1] - p0[1]) < 65536 &&
                                   abs(p1[2] - p0[2]) < 65536);
@@ -104,6 +153,8 @@ __device__ __forceinline__ int walk_one(const VolView& v, const Tract& t, const 
       else
         walk_window<unsigned long long>(v, sm, p0, p1, has, j == a, endpoint_mode, nV, nT, fail);
       fail = __any_sync(kFull, fail);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) cur[k] = nxt[k];
     }
   }
   if (endpoint_mode && !fail) {
@@ -258,8 +309,8 @@ __device__ __forceinline__ void overflow_one(const VolView& v, const Tract& t, c
       load_vertex(t.xyz, a + u + 1, p1);
       SegWalk<unsigned long long> w;
       w.init(p0, p1);
-      ovf_visit(v, z, nV, nT, endpoint_mode, w.c[0], w.c[1], w.c[2]);
-      while (w.step()) ovf_visit(v, z, nV, nT, endpoint_mode, w.c[0], w.c[1], w.c[2]);
+      ovf_visit(v, z, nV, nT, endpoint_mode, w.cx, w.cy, w.cz);
+      while (w.step()) ovf_visit(v, z, nV, nT, endpoint_mode, w.cx, w.cy, w.cz);
     }
   }
   if (endpoint_mode && threadIdx.x == 0 && T >= 1) {
@@ -317,7 +368,13 @@ __global__ void __launch_bounds__(256)
 cudaError_t launch_walk(const Tract& t, const VolView& v, const int32_t* survivors, Accum acc, uint32_t mode,
                         int32_t* overflow_list, DevState* st, int num_sms, cudaStream_t s) {
   if (t.ns <= 0) return cudaSuccess;
-  walk_kernel<<<num_sms * 4, kWalkWarps * 32, 0, s>>>(t, v, survivors, acc, mode, overflow_list, st);
+  static int per_sm = 0;
+  if (per_sm == 0) {
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, walk_kernel, kWalkWarps * 32, 0);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+  }
+  walk_kernel<<<num_sms * per_sm, kWalkWarps * 32, 0, s>>>(t, v, survivors, acc, mode, overflow_list, st);
   return cudaGetLastError();
 }
 
@@ -332,7 +389,13 @@ cudaError_t launch_walk_overflow(const Tract& t, const VolView& v, const int32_t
 
 cudaError_t launch_walk_batch(const BatchTable& tbl, const int32_t* survivors, uint32_t mode, int32_t* overflow_list,
                               DevState* gst, int num_sms, cudaStream_t s) {
-  walk_batch_kernel<<<num_sms * 4, kWalkWarps * 32, 0, s>>>(tbl, survivors, mode, overflow_list, gst);
+  static int per_sm = 0;
+  if (per_sm == 0) {
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, walk_batch_kernel, kWalkWarps * 32, 0);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+  }
+  walk_batch_kernel<<<num_sms * per_sm, kWalkWarps * 32, 0, s>>>(tbl, survivors, mode, overflow_list, gst);
   return cudaGetLastError();
 }
 

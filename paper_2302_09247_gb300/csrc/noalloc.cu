@@ -105,8 +105,8 @@ __global__ void __launch_bounds__(256) na_walk_kernel(NaArgs a, uint32_t* scratc
       int32_t p1[3] = {a.xyz[3 * (b0 + u + 1)], a.xyz[3 * (b0 + u + 1) + 1], a.xyz[3 * (b0 + u + 1) + 2]};
       fc::SegWalk<unsigned long long> w;
       w.init(p0, p1);
-      na_visit(a, rowbits, labbits, rowlist, lablist, &nV, &nT, w.c[0], w.c[1], w.c[2]);
-      while (w.step()) na_visit(a, rowbits, labbits, rowlist, lablist, &nV, &nT, w.c[0], w.c[1], w.c[2]);
+      na_visit(a, rowbits, labbits, rowlist, lablist, &nV, &nT, w.cx, w.cy, w.cz);
+      while (w.step()) na_visit(a, rowbits, labbits, rowlist, lablist, &nV, &nT, w.cx, w.cy, w.cz);
     }
     __syncthreads();
     const int64_t M = a.n_lab;
