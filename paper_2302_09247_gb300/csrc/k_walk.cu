@@ -28,6 +28,56 @@ struct WalkWarpSmem {
   int32_t listT[kLimT + 32];
 };
 
+// The per-warp sets V_s and T_s live in tabV / tabT in one of two forms,
+// chosen per launch: an open-addressing hash set (empty = -1), or, when every
+// key fits (N <= 32 * kHV rows, M < 32 * kHT labels), a bitmap of the keys
+// (one shared-memory atomicOr per key).  Both append new keys to listV /
+// listT in lane order; a bitmap is cleared through its list.
+constexpr int32_t kBitRowsMax = 32 * kHV;
+constexpr int32_t kBitLabelsMax = 32 * kHT;  // labels 1 .. kBitLabelsMax - 1
+
+__device__ __forceinline__ int bit_insert(int32_t* tab, int32_t* list, int n, int32_t key) {
+  bool fresh = false;
+  if (key >= 0) {
+    const uint32_t m = 1u << (key & 31);
+    fresh = (atomicOr(reinterpret_cast<uint32_t*>(tab) + (key >> 5), m) & m) == 0u;
+  }
+  const unsigned fm = __ballot_sync(kFull, fresh);
+  if (fresh) list[n + __popc(fm & lanemask_lt())] = key;
+  return n + __popc(fm);
+}
+
+template <bool kBitV, bool kBitT>
+struct Sets {
+  __device__ __forceinline__ static int insV(WalkWarpSmem& sm, int n, int32_t key, bool& fail) {
+    return kBitV ? bit_insert(sm.tabV, sm.listV, n, key) : set_insert<kHV>(sm.tabV, sm.listV, n, key, fail);
+  }
+  __device__ __forceinline__ static int insT(WalkWarpSmem& sm, int n, int32_t key, bool& fail) {
+    return kBitT ? bit_insert(sm.tabT, sm.listT, n, key) : set_insert<kHT>(sm.tabT, sm.listT, n, key, fail);
+  }
+  // empty tables at kernel start
+  __device__ __forceinline__ static void init(WalkWarpSmem& sm) {
+    for (int i = lane_id(); i < kHV; i += 32) sm.tabV[i] = kBitV ? 0 : -1;
+    for (int i = lane_id(); i < kHT; i += 32) sm.tabT[i] = kBitT ? 0 : -1;
+    __syncwarp();
+  }
+  // empty them again after a streamline whose sets hold nV / nT keys
+  __device__ __forceinline__ static void clear(WalkWarpSmem& sm, int nV, int nT) {
+    __syncwarp();
+    if (kBitV) {
+      for (int k = lane_id(); k < nV; k += 32) sm.tabV[sm.listV[k] >> 5] = 0;
+    } else {
+      for (int i = lane_id(); i < kHV; i += 32) sm.tabV[i] = -1;
+    }
+    if (kBitT) {
+      for (int k = lane_id(); k < nT; k += 32) sm.tabT[sm.listT[k] >> 5] = 0;
+    } else {
+      for (int i = lane_id(); i < kHT; i += 32) sm.tabT[i] = -1;
+    }
+    __syncwarp();
+  }
+};
+
 __device__ __forceinline__ void load_vertex(const int32_t* xyz, int64_t j, int32_t p[3]) {
   p[0] = __ldg(xyz + 3 * j);
   p[1] = __ldg(xyz + 3 * j + 1);
@@ -55,14 +105,14 @@ __device__ __forceinline__ void decode(const VolView& v, int32_t lin, uint32_t c
 }
 
 // Voxels gathered per lane before their codes are read together.
-constexpr int kGather = 4;
+constexpr int kGather = 2;
 
 // Walk the window's segments (one per lane, p0 -> p1 where has): every voxel
 // a segment enters (and, for the streamline's first segment, its start
 // voxel) goes into the sets.  Each round gathers up to kGather voxels per
 // lane with the integer walk, reads their codes with independent loads, then
 // inserts them; long segments take more rounds.
-template <typename P>
+template <typename P, typename S>
 __device__ __forceinline__ void walk_window(const VolView& v, WalkWarpSmem& sm, const int32_t p0[3],
                                             const int32_t p1[3], bool has, bool first, bool endpoint_mode,
                                             int& nV, int& nT, bool& fail) {
@@ -87,8 +137,8 @@ __device__ __forceinline__ void walk_window(const VolView& v, WalkWarpSmem& sm, 
       int32_t row, lab;
       decode(v, lin[i], code[i], row, lab);
       if (endpoint_mode) lab = 0;
-      nV = set_insert<kHV>(sm.tabV, sm.listV, nV, row, fail);
-      nT = set_insert<kHT>(sm.tabT, sm.listT, nT, lab > 0 ? lab : -1, fail);
+      nV = S::insV(sm, nV, row, fail);
+      nT = S::insT(sm, nT, lab > 0 ? lab : -1, fail);
     }
     if (nV > kLimV || nT > kLimT) {
       fail = true;
@@ -100,6 +150,7 @@ __device__ __forceinline__ void walk_window(const VolView& v, WalkWarpSmem& sm, 
 // Walk surviving streamline s of (v, t) with the whole warp and add its
 // pairs to acc.  Returns |V_s| |T_s| (warp-uniform), or -1 when its sets
 // outgrew the tables: then `id` is appended to the overflow list instead.
+template <typename S>
 __device__ __forceinline__ int walk_one(const VolView& v, const Tract& t, const Accum& acc, uint32_t mode,
                                         WalkWarpSmem& sm, int32_t s, int32_t id, int32_t* __restrict__ ovf,
                                         DevState* gst) {
@@ -124,8 +175,8 @@ __device__ __forceinline__ int walk_one(const VolView& v, const Tract& t, const 
         voxel_lookup(v, p[0] >> kUnitLog2, p[1] >> kUnitLog2, p[2] >> kUnitLog2, row, lab);
       }
       if (endpoint_mode) lab = 0;
-      nV = set_insert<kHV>(sm.tabV, sm.listV, nV, row, fail);
-      nT = set_insert<kHT>(sm.tabT, sm.listT, nT, lab > 0 ? lab : -1, fail);
+      nV = S::insV(sm, nV, row, fail);
+      nT = S::insT(sm, nT, lab > 0 ? lab : -1, fail);
       if (nV > kLimV || nT > kLimT) fail = true;
       fail = __any_sync(kFull, fail);
     }
@@ -149,9 +200,9 @@ __device__ __forceinline__ int walk_one(const VolView& v, const Tract& t, const 
       const bool small = !has || (abs(p1[0] - p0[0]) < 65536 && abs(p1[1] - p0[1]) < 65536 &&
                                   abs(p1[2] - p0[2]) < 65536);
       if (__all_sync(kFull, small))
-        walk_window<uint32_t>(v, sm, p0, p1, has, j == a, endpoint_mode, nV, nT, fail);
+        walk_window<uint32_t, S>(v, sm, p0, p1, has, j == a, endpoint_mode, nV, nT, fail);
       else
-        walk_window<unsigned long long>(v, sm, p0, p1, has, j == a, endpoint_mode, nV, nT, fail);
+        walk_window<unsigned long long, S>(v, sm, p0, p1, has, j == a, endpoint_mode, nV, nT, fail);
       fail = __any_sync(kFull, fail);
 #pragma unroll
       for (int k = 0; k < 3; ++k) cur[k] = nxt[k];
@@ -165,8 +216,8 @@ __device__ __forceinline__ int walk_one(const VolView& v, const Tract& t, const 
       load_vertex(t.xyz, b - 1, p);
       voxel_lookup(v, p[0] >> kUnitLog2, p[1] >> kUnitLog2, p[2] >> kUnitLog2, row, lab);
     }
-    nT = set_insert<kHT>(sm.tabT, sm.listT, nT, lab > 0 ? lab : -1, fail);
-    fail = __any_sync(kFull, fail);
+    nT = S::insT(sm, nT, lab > 0 ? lab : -1, fail);
+    fail = __any_sync(kFull, fail) || nT > kLimT;
   }
   __syncwarp();
   int pairs = -1;
@@ -187,17 +238,8 @@ __device__ __forceinline__ int walk_one(const VolView& v, const Tract& t, const 
       if (r0 >= 0 && l1 >= 1) atomicAdd(acc.Cend + (int64_t)r0 * M + (l1 - 1), 1);
     }
   }
-  __syncwarp();
-  for (int i = lane; i < kHV; i += 32) sm.tabV[i] = -1;
-  for (int i = lane; i < kHT; i += 32) sm.tabT[i] = -1;
-  __syncwarp();
+  S::clear(sm, nV, nT);
   return pairs;
-}
-
-__device__ __forceinline__ void clear_tables(WalkWarpSmem& sm) {
-  for (int i = lane_id(); i < kHV; i += 32) sm.tabV[i] = -1;
-  for (int i = lane_id(); i < kHT; i += 32) sm.tabT[i] = -1;
-  __syncwarp();
 }
 
 __device__ __forceinline__ uint32_t next_survivor(DevState* gst) {
@@ -206,19 +248,21 @@ __device__ __forceinline__ uint32_t next_survivor(DevState* gst) {
   return __shfl_sync(kFull, idx, 0);
 }
 
+template <bool kBitV, bool kBitT>
 __global__ void __launch_bounds__(kWalkWarps * 32) walk_kernel(Tract t, VolView v, const int32_t* __restrict__ surv,
                                                               Accum acc, uint32_t mode, int32_t* __restrict__ ovf,
                                                               DevState* st) {
+  using S = Sets<kBitV, kBitT>;
   __shared__ WalkWarpSmem smem_all[kWalkWarps];
   WalkWarpSmem& sm = smem_all[threadIdx.x >> 5];
-  clear_tables(sm);
+  S::init(sm);
   const uint32_t n = st->n_survivors;
   unsigned long long pairs_acc = 0;
   for (;;) {
     const uint32_t idx = next_survivor(st);
     if (idx >= n) break;
     const int32_t s = surv[idx];
-    const int pairs = walk_one(v, t, acc, mode, sm, s, s, ovf, st);
+    const int pairs = walk_one<S>(v, t, acc, mode, sm, s, s, ovf, st);
     if (pairs > 0) pairs_acc += (unsigned long long)pairs;
   }
   if (lane_id() == 0 && pairs_acc) atomicAdd(&st->pairs, pairs_acc);
@@ -234,20 +278,22 @@ __device__ __forceinline__ int subject_of(const BatchTable& tbl, int64_t g) {
   return lo;
 }
 
+template <bool kBitV, bool kBitT>
 __global__ void __launch_bounds__(kWalkWarps * 32)
     walk_batch_kernel(const __grid_constant__ BatchTable tbl, const int32_t* __restrict__ surv, uint32_t mode,
                       int32_t* __restrict__ ovf, DevState* gst) {
+  using S = Sets<kBitV, kBitT>;
   __shared__ WalkWarpSmem smem_all[kWalkWarps];
   WalkWarpSmem& sm = smem_all[threadIdx.x >> 5];
-  clear_tables(sm);
+  S::init(sm);
   const uint32_t n = gst->n_survivors;
   for (;;) {
     const uint32_t idx = next_survivor(gst);
     if (idx >= n) break;
     const int32_t g = surv[idx];
-    const BatchSubject& S = tbl.s[subject_of(tbl, g)];
-    const int pairs = walk_one(S.v, S.t, S.acc, mode, sm, (int32_t)(g - S.sbase), g, ovf, gst);
-    if (pairs > 0 && lane_id() == 0) atomicAdd(&S.st->pairs, (unsigned long long)pairs);
+    const BatchSubject& B = tbl.s[subject_of(tbl, g)];
+    const int pairs = walk_one<S>(B.v, B.t, B.acc, mode, sm, (int32_t)(g - B.sbase), g, ovf, gst);
+    if (pairs > 0 && lane_id() == 0) atomicAdd(&B.st->pairs, (unsigned long long)pairs);
   }
 }
 
@@ -365,16 +411,41 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+// Grid: every CTA resident at once, from the compiled kernel's occupancy.
+template <typename K>
+int walk_grid(K kernel, int num_sms) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kWalkWarps * 32, 0) != cudaSuccess) {
+    (void)cudaGetLastError();
+    per_sm = 4;
+  }
+  return num_sms * (per_sm > 0 ? per_sm : 1);
+}
+
+template <bool kBitV, bool kBitT>
+cudaError_t launch_walk_k(const Tract& t, const VolView& v, const int32_t* survivors, Accum acc, uint32_t mode,
+                          int32_t* overflow_list, DevState* st, int num_sms, cudaStream_t s) {
+  static const int grid = walk_grid(walk_kernel<kBitV, kBitT>, num_sms);
+  walk_kernel<kBitV, kBitT><<<grid, kWalkWarps * 32, 0, s>>>(t, v, survivors, acc, mode, overflow_list, st);
+  return cudaGetLastError();
+}
+
+template <bool kBitV, bool kBitT>
+cudaError_t launch_walk_batch_k(const BatchTable& tbl, const int32_t* survivors, uint32_t mode,
+                                int32_t* overflow_list, DevState* gst, int num_sms, cudaStream_t s) {
+  static const int grid = walk_grid(walk_batch_kernel<kBitV, kBitT>, num_sms);
+  walk_batch_kernel<kBitV, kBitT><<<grid, kWalkWarps * 32, 0, s>>>(tbl, survivors, mode, overflow_list, gst);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_walk(const Tract& t, const VolView& v, const int32_t* survivors, Accum acc, uint32_t mode,
                         int32_t* overflow_list, DevState* st, int num_sms, cudaStream_t s) {
   if (t.ns <= 0) return cudaSuccess;
-  static int per_sm = 0;
-  if (per_sm == 0) {
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, walk_kernel, kWalkWarps * 32, 0);
-    if (e != cudaSuccess) return e;
-    if (per_sm < 1) per_sm = 1;
-  }
-  walk_kernel<<<num_sms * per_sm, kWalkWarps * 32, 0, s>>>(t, v, survivors, acc, mode, overflow_list, st);
+  const bool bv = v.n_roi <= kBitRowsMax, bt = v.n_lab < kBitLabelsMax;
+  if (bv && bt) return launch_walk_k<true, true>(t, v, survivors, acc, mode, overflow_list, st, num_sms, s);
+  if (bv) return launch_walk_k<true, false>(t, v, survivors, acc, mode, overflow_list, st, num_sms, s);
+  if (bt) return launch_walk_k<false, true>(t, v, survivors, acc, mode, overflow_list, st, num_sms, s);
+  return launch_walk_k<false, false>(t, v, survivors, acc, mode, overflow_list, st, num_sms, s);
   return cudaGetLastError();
 }
 
@@ -389,13 +460,15 @@ cudaError_t launch_walk_overflow(const Tract& t, const VolView& v, const int32_t
 
 cudaError_t launch_walk_batch(const BatchTable& tbl, const int32_t* survivors, uint32_t mode, int32_t* overflow_list,
                               DevState* gst, int num_sms, cudaStream_t s) {
-  static int per_sm = 0;
-  if (per_sm == 0) {
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, walk_batch_kernel, kWalkWarps * 32, 0);
-    if (e != cudaSuccess) return e;
-    if (per_sm < 1) per_sm = 1;
+  bool bv = true, bt = true;
+  for (int32_t i = 0; i < tbl.n; ++i) {
+    bv &= tbl.s[i].v.n_roi <= kBitRowsMax;
+    bt &= tbl.s[i].v.n_lab < kBitLabelsMax;
   }
-  walk_batch_kernel<<<num_sms * per_sm, kWalkWarps * 32, 0, s>>>(tbl, survivors, mode, overflow_list, gst);
+  if (bv && bt) return launch_walk_batch_k<true, true>(tbl, survivors, mode, overflow_list, gst, num_sms, s);
+  if (bv) return launch_walk_batch_k<true, false>(tbl, survivors, mode, overflow_list, gst, num_sms, s);
+  if (bt) return launch_walk_batch_k<false, true>(tbl, survivors, mode, overflow_list, gst, num_sms, s);
+  return launch_walk_batch_k<false, false>(tbl, survivors, mode, overflow_list, gst, num_sms, s);
   return cudaGetLastError();
 }
 

@@ -171,3 +171,44 @@ def test_near_grid_cell_sizes(near_log2, seed):
     vols, tr = synth.make_subject(0, n_streamlines=5000)
     _check(vols.roi, vols.lab, vols.dims, vols.n_roi, vols.n_targets, tr.xyz, tr.offsets, "device",
            {fc.FASTCOD_OPT_NEAR_LOG2: near_log2})
+
+
+@pytest.mark.parametrize("N,M", [(20000, 5000), (20000, 8), (100, 5000), (100, 8)])
+def test_walk_set_forms(N, M):
+    # the walk keeps V_s / T_s as bitmaps when N <= 16384 and M < 4096, else as
+    # hash sets: all four combinations against the oracle, with many distinct
+    # rows and labels along each streamline
+    rng = np.random.default_rng(N + M)
+    dims = (24, 20, 18)
+    roi, lab, N, M = tiny.random_volumes(rng, dims, n_roi=N, n_labels=M, p_roi=0.3, p_lab=0.4, many_to_one=True)
+    xyz, off = tiny.random_streamlines(rng, dims, 1500, max_len=40)
+    for target in (0, 1):
+        _check(roi, lab, dims, N, M, xyz, off, "device", _opts(1, 1, target, 0), flags=_oracle_flags(target, 0))
+
+
+def test_batch_mixed_set_forms():
+    # a batch whose subjects need the hash form (N > 16384) beside small ones
+    from paper_2302_09247_gb300 import fastcod as fc
+    from tests.gpu_helpers import as_device
+    subs = []
+    for k, (N, M) in enumerate(((20000, 8), (50, 6), (300, 4500))):
+        rng = np.random.default_rng(77 + k)
+        dims = (16 + k, 14, 12)
+        roi, lab, N, M = tiny.random_volumes(rng, dims, n_roi=N, n_labels=M, p_roi=0.3, p_lab=0.4,
+                                             many_to_one=True)
+        xyz, off = tiny.random_streamlines(rng, dims, 600, max_len=30)
+        subs.append((roi, lab, dims, N, M, xyz, off))
+    keep, objs, outs = [], [], []
+    for roi, lab, dims, N, M, xyz, off in subs:
+        r, l, x, o = as_device(roi), as_device(lab), as_device(xyz), as_device(off)
+        C = np.full((N, M), -7, dtype=np.int32)
+        Ce = np.full((N, M), -7, dtype=np.int32)
+        keep += [r, l, x, o]
+        outs.append((C, Ce))
+        objs.append(fc.make_subject(r, l, dims, N, M, x, o, C, Ce))
+    with fc.Context(0) as ctx:
+        fc.fastcod_batch_run(ctx.ctx, objs)
+    for (roi, lab, dims, N, M, xyz, off), (C, Ce) in zip(subs, outs):
+        Cr, Cer, _ = oracle.connectivity(roi, lab, dims, N, M, xyz, off)
+        np.testing.assert_array_equal(C, Cr)
+        np.testing.assert_array_equal(Ce, Cer)
