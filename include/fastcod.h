@@ -97,10 +97,12 @@ enum {
    * registers per thread) or 3 (80 registers, more resident warps).  Results
    * are identical. */
   FASTCOD_OPT_PREFILTER_CTAS = 6,
-  /* cell of the prefilter's near grid: (1 << value)^3 voxels, 0..3 (default
-   * 1).  Coarser cells keep the grid in L1 and let more streamlines through
-   * to the exact walk.  Results are identical.  Applies to volumes installed
-   * afterwards. */
+  /* cell of the near grid (the prefilter's test, and the walk's skip of
+   * segments far from every ROI and labelled voxel): (1 << value)^3 voxels,
+   * 0..3, or -1 (default): per volume, the smallest cell whose grid has at
+   * most 40960 words (160 KB).  Coarser cells keep the grid closer to the SMs
+   * and let more streamlines through to the exact walk.  Results are
+   * identical.  Applies to volumes installed afterwards. */
   FASTCOD_OPT_NEAR_LOG2 = 7,
   /* 1 (default): fastcod_batch_run picks the prefilter's CTAs per SM and
    * near-grid cell per batch shape by timed trials on the first batch of that

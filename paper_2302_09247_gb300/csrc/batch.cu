@@ -76,7 +76,7 @@ int64_t near_words(const int32_t d[3], int near_log2) {
   v.dx = d[0];
   v.dy = d[1];
   v.dz = d[2];
-  fc::set_near_dims(v, near_log2);
+  fc::set_near_dims(v, fc::resolve_near_log2(near_log2, d[0], d[1], d[2]));
   return fc::near_words(v);
 }
 
@@ -157,7 +157,7 @@ void fill_table(fastcod_ctx* c, const fastcod_subject* subs, int32_t n, const La
     v.bx = (S.dims[0] + 3) / 4;
     v.by = (S.dims[1] + 3) / 4;
     v.bz = (S.dims[2] + 3) / 4;
-    fc::set_near_dims(v, near_log2);
+    fc::set_near_dims(v, fc::resolve_near_log2(near_log2, S.dims[0], S.dims[1], S.dims[2]));
     v.n_roi = S.n_roi;
     v.n_lab = S.n_targets;
     B.t.xyz = L.xyz_in[i] != SIZE_MAX ? at<int32_t>(A, L.xyz_in[i]) : S.xyz;
@@ -359,7 +359,7 @@ void load_tune_cache(BatchState* B) {
   unsigned long long k;
   int ctas, nl;
   while (fscanf(f, "%llx %d %d", &k, &ctas, &nl) == 3)
-    if ((ctas == 2 || ctas == 3) && nl >= 0 && nl <= 3) B->tuned[(uint64_t)k] = BatchConfig{ctas, nl};
+    if ((ctas == 2 || ctas == 3) && nl >= -1 && nl <= 3) B->tuned[(uint64_t)k] = BatchConfig{ctas, nl};
   fclose(f);
 }
 

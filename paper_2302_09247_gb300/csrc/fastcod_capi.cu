@@ -349,7 +349,7 @@ FASTCOD_API int fastcod_set_volumes(fastcod_ctx* c, const int32_t* roi, const ui
   CU(cudaMalloc(&c->d_scratch, (size_t)(ctas * words * 4)));
   CU(cudaMemsetAsync(c->d_scratch, 0, (size_t)(ctas * words * 4), c->stream));
   // near grid (the prefilter's dilated occupancy), built from the bit planes
-  c->near_shift = c->near_log2;
+  c->near_shift = fc::resolve_near_log2(c->near_log2, dx, dy, dz);
   fc::VolView v = vol_view(c);
   CU(cudaMalloc(&c->d_near, (size_t)fc::near_words(v) * 4));
   v.near = c->d_near;
@@ -537,7 +537,7 @@ FASTCOD_API int fastcod_set_option(fastcod_ctx* c, int32_t key, int64_t value) {
       c->prefilter_ctas = (int)value;
       return FASTCOD_OK;
     case FASTCOD_OPT_NEAR_LOG2:
-      if (value < 0 || value > 3) break;
+      if (value < -1 || value > 3) break;
       c->near_log2 = (int)value;
       return FASTCOD_OK;
     case FASTCOD_OPT_AUTOTUNE:

@@ -55,7 +55,7 @@ struct fastcod_ctx {
   uint32_t mode = 0;
   int staging_tma = 1;
   int prefilter_ctas = 2;
-  int near_log2 = 1;       // near grid cell: (1 << near_log2)^3 voxels
+  int near_log2 = -1;      // near grid cell: (1 << near_log2)^3 voxels; -1 = per volume
   int autotune = 1;        // batched form: tune per batch shape
   int host_in_place = 0;   // read page-locked host xyz in place (option)
   int profile = 0;

@@ -66,6 +66,21 @@ __device__ __forceinline__ uint32_t box_bits(const VolView& v, int32_t lx, int32
   return bits;
 }
 
+// Near bits of the cell holding voxel (vx, vy, vz) (bit 0: an ROI voxel
+// within Chebyshev distance 1 of some voxel of the cell, bit 1: a labelled
+// one); cells past the grown grid clamp to the zero border.  nw: the grid in
+// shared memory (kSmem) or global memory.
+template <bool kSmem>
+__device__ __forceinline__ uint32_t near_lookup(const VolView& v, const uint32_t* nw, int32_t vx, int32_t vy,
+                                                int32_t vz) {
+  const uint32_t cx = min((uint32_t)((vx + 1) >> v.nsh), (uint32_t)v.cmx);
+  const uint32_t cy = min((uint32_t)((vy + 1) >> v.nsh), (uint32_t)v.cmy);
+  const uint32_t cz = min((uint32_t)((vz + 1) >> v.nsh), (uint32_t)v.cmz);
+  const uint32_t w = (cx >> 4) + (uint32_t)v.nwx * (cy + (uint32_t)v.nny * cz);
+  const uint32_t word = kSmem ? nw[w] : __ldg(nw + w);
+  return (word >> ((cx & 15u) << 1)) & 3u;
+}
+
 // ---------------------------------------------------------------------------
 // Integer walk of one segment P0 -> P1 (Amanatides & Woo, exact rational
 // events).  For axis a with d_a != 0 the next plane crossing is at

@@ -87,6 +87,22 @@ inline void set_near_dims(VolView& v, int32_t nsh) {
 }
 __host__ __device__ inline int64_t near_words(const VolView& v) { return (int64_t)v.nwx * v.nny * v.nnz; }
 
+// Cell size for a near-grid option value: 0..3 as given; -1 (automatic) the
+// smallest cell whose grid stays within 40960 words (160 KB, so that it
+// stays cached near the SMs), at most 3.
+inline int32_t resolve_near_log2(int32_t opt, int32_t dx, int32_t dy, int32_t dz) {
+  if (opt >= 0) return opt;
+  for (int32_t nsh = 0; nsh < 3; ++nsh) {
+    VolView v{};
+    v.dx = dx;
+    v.dy = dy;
+    v.dz = dz;
+    set_near_dims(v, nsh);
+    if (near_words(v) <= 40960) return nsh;
+  }
+  return 3;
+}
+
 // One batch of streamlines on the device.
 struct Tract {
   const int32_t* xyz;     // [nv][3]

@@ -58,19 +58,6 @@ constexpr int64_t kNearSmemWords = 12288;  // direct loader: near grids up to 48
 
 __device__ __forceinline__ uint32_t lowmask(int32_t k) { return k >= 32 ? 0xffffffffu : ((1u << k) - 1u); }
 
-// Near bits of the cell holding voxel (vx, vy, vz); cells past the grown grid
-// clamp to the zero border.
-template <bool kSmem>
-__device__ __forceinline__ uint32_t near_lookup(const VolView& v, const uint32_t* nw, int32_t vx, int32_t vy,
-                                                int32_t vz) {
-  const uint32_t cx = min((uint32_t)((vx + 1) >> v.nsh), (uint32_t)v.cmx);
-  const uint32_t cy = min((uint32_t)((vy + 1) >> v.nsh), (uint32_t)v.cmy);
-  const uint32_t cz = min((uint32_t)((vz + 1) >> v.nsh), (uint32_t)v.cmz);
-  const uint32_t w = (cx >> 4) + (uint32_t)v.nwx * (cy + (uint32_t)v.nny * cz);
-  const uint32_t word = kSmem ? nw[w] : __ldg(nw + w);
-  return (word >> ((cx & 15u) << 1)) & 3u;
-}
-
 struct WarpShared {
   int32_t sbuf[64];          // survivors awaiting a flush
   uint32_t st[kWin / 32];    // start bits of the current window

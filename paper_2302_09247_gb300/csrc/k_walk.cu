@@ -196,7 +196,17 @@ __device__ __forceinline__ int walk_one(const VolView& v, const Tract& t, const 
         const int32_t wrap = __shfl_sync(kFull, nxt[k], 0);
         p1[k] = lane == 31 ? wrap : dn;
       }
-      const bool has = j < b - 1;
+      // a segment whose end voxels differ by at most one on every axis stays
+      // within Chebyshev distance 1 of its start voxel: when the near grid
+      // shows no ROI and no labelled voxel there, it visits nothing that
+      // counts and is not walked
+      bool has = j < b - 1;
+      if (has) {
+        const int32_t c0x = p0[0] >> kUnitLog2, c0y = p0[1] >> kUnitLog2, c0z = p0[2] >> kUnitLog2;
+        const bool shortseg = abs((p1[0] >> kUnitLog2) - c0x) <= 1 && abs((p1[1] >> kUnitLog2) - c0y) <= 1 &&
+                              abs((p1[2] >> kUnitLog2) - c0z) <= 1;
+        if (shortseg && near_lookup<false>(v, v.near, c0x, c0y, c0z) == 0u) has = false;
+      }
       const bool small = !has || (abs(p1[0] - p0[0]) < 65536 && abs(p1[1] - p0[1]) < 65536 &&
                                   abs(p1[2] - p0[2]) < 65536);
       if (__all_sync(kFull, small))

@@ -75,7 +75,7 @@ struct fastcod_server {
   int prefilter = 1;
   int ctas = 2;
   int tma = 1;
-  int near_log2 = 1;
+  int near_log2 = -1;
   Clock::time_point t0;
 
   std::mutex mu;
@@ -112,7 +112,7 @@ int64_t near_words(const int32_t d[3], int near_log2) {
   v.dx = d[0];
   v.dy = d[1];
   v.dz = d[2];
-  fc::set_near_dims(v, near_log2);
+  fc::set_near_dims(v, fc::resolve_near_log2(near_log2, d[0], d[1], d[2]));
   return fc::near_words(v);
 }
 
@@ -169,7 +169,7 @@ cudaError_t setup_request(fastcod_server* S, Request* r, uint32_t** tmp, size_t*
   v.bx = (h.dims[0] + 3) / 4;
   v.by = (h.dims[1] + 3) / 4;
   v.bz = (h.dims[2] + 3) / 4;
-  fc::set_near_dims(v, S->near_log2);
+  fc::set_near_dims(v, fc::resolve_near_log2(S->near_log2, h.dims[0], h.dims[1], h.dims[2]));
   v.n_roi = h.n_roi;
   v.n_lab = h.n_targets;
   if (e == cudaSuccess) e = cudaMemsetAsync(r->acc.C, 0, nm * 4, S->compute);

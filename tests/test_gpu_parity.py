@@ -157,7 +157,7 @@ def test_cfg1_full_bench_configuration():
     assert sr["n_contributing"] <= st["survivors"]
 
 
-@pytest.mark.parametrize("near_log2", [0, 1, 2, 3])
+@pytest.mark.parametrize("near_log2", [-1, 0, 1, 2, 3])
 @pytest.mark.parametrize("seed", range(3))
 def test_near_grid_cell_sizes(near_log2, seed):
     # every near-grid cell size must keep the prefilter conservative: the
