@@ -102,30 +102,43 @@ def _dist():
     return ws, rank, local
 
 
-def _barrier_max(ws, x: float) -> float:
+def _allreduce(ws, x: float, op: str) -> float:
+    """x reduced over the ranks (max or sum); tensors live where the process
+    group's backend wants them (CUDA for NCCL, host memory for gloo)."""
     if ws == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
     return float(t.item())
+
+
+def _barrier_max(ws, x: float) -> float:
+    return _allreduce(ws, x, "max")
 
 
 def _barrier_sum(ws, x: float) -> float:
-    if ws == 1:
-        return x
-    import torch
-    import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.SUM)
-    return float(t.item())
+    return _allreduce(ws, x, "sum")
 
 
 def _barrier(ws):
     if ws > 1:
         import torch.distributed as dist
         dist.barrier()
+
+
+def rank_seed(seed: int, rank: int) -> int:
+    """Seed of rank r's subject: same shape on every rank, different data."""
+    return seed + 7919 * rank
+
+
+def weak_scaling(ws, units: float, seconds: float):
+    """(whole-job units/s, slowest rank's seconds): the units all ranks
+    processed over the time of the slowest rank."""
+    t = _barrier_max(ws, seconds)
+    return _barrier_sum(ws, units) / t, t
 
 
 def cpu_baseline(vols, tr, n_sample: int):
@@ -436,8 +449,7 @@ def main():
     # one subject per rank: the preset's shape, a per-rank seed
     vs = synth.volume_spec(args.config)
     ss = synth.streamline_spec(args.config)
-    if rank:
-        ss.seed = ss.seed + 7919 * rank
+    ss.seed = rank_seed(ss.seed, rank)
     if args.streamlines is not None:
         ss.n_streamlines = min(ss.n_streamlines, args.streamlines)
     vols = synth.make_volumes(vs)
@@ -487,11 +499,10 @@ def main():
     assert np.array_equal(C_first, C_last), "C changed between identical steps"
     assert st_last["voxel_steps"] == st["voxel_steps"]
 
-    ms_max = _barrier_max(ws, ms)
-    steps_total = _barrier_sum(ws, float(st["voxel_steps"])) * args.steps
-    value = steps_total / (ms_max / 1000.0)
-    streamlines_s = _barrier_sum(ws, float(tr.n_streamlines)) * args.steps / (ms_max / 1000.0)
-    subjects_s = ws * args.steps / (ms_max / 1000.0)
+    value, t_max = weak_scaling(ws, float(st["voxel_steps"]) * args.steps, ms / 1000.0)
+    ms_max = 1000.0 * t_max
+    streamlines_s = _barrier_sum(ws, float(tr.n_streamlines)) * args.steps / t_max
+    subjects_s = ws * args.steps / t_max
 
     # roofline of the dominant kernel (prefilter: the full vertex stream)
     peaks, peak_kind = _peaks()
@@ -528,8 +539,7 @@ def main():
             fc.fastcod_endpoint_connectivity(ctx.ctx, Ce_h)
         e2e_s = time.perf_counter() - t0
         assert np.array_equal(C_h.numpy(), C_first)
-        e2e_max = _barrier_max(ws, e2e_s)
-        e2e_value = _barrier_sum(ws, float(st["voxel_steps"])) * args.e2e_steps / e2e_max
+        e2e_value, e2e_max = weak_scaling(ws, float(st["voxel_steps"]) * args.e2e_steps, e2e_s)
         # the same calls with the page-locked xyz read in place by the kernels
         ctx.set_option(fc.FASTCOD_OPT_HOST_IN_PLACE, 1)
         for i in range(1 + args.e2e_steps):
