@@ -31,6 +31,32 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "DDA voxel-steps/s & subjects/s for C, bit-exact; batched vs plain; p50/p99 latency"
+
+# DRAM traffic (ncu dram__bytes_read.sum + dram__bytes_write.sum) of one
+# prefilter launch on the HCP-shaped subject, valid only while the prefilter's
+# sources are the ones it was measured on; other workloads scale it by their
+# vertex count (the stream is read once, so traffic grows with the vertices).
+PREFILTER_SOURCES = ("paper_2302_09247_gb300/csrc/k_prefilter.cu", "paper_2302_09247_gb300/csrc/fc_tma.cuh",
+                     "paper_2302_09247_gb300/csrc/fc_internal.cuh", "paper_2302_09247_gb300/csrc/fc_device.cuh")
+PREFILTER_TRAFFIC = {"sha256": "7896309ef5decc923eb4247f5752652ab922a35729b2017a5db519ad23924106",
+                     "bytes": 2499503616, "vertices": 205420297,
+                     "summary": "profiles/prefilter_kernel_hcp145x174x145.md"}
+
+
+def prefilter_traffic(n_vertices: int):
+    """(bytes per launch, note) from the recorded capture, or (None, why)."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in PREFILTER_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    if h.hexdigest() != PREFILTER_TRAFFIC["sha256"]:
+        return None, "prefilter sources changed since the ncu capture"
+    ref = PREFILTER_TRAFFIC
+    if n_vertices == ref["vertices"]:
+        return ref["bytes"], f"ncu capture of this workload ({ref['summary']})"
+    return int(round(ref["bytes"] * n_vertices / ref["vertices"])), \
+        f"ncu capture of the HCP-shaped subject ({ref['summary']}) scaled by vertex count"
 UNIT = "voxel-steps/s"
 
 
@@ -509,9 +535,11 @@ def main():
     alg_bytes = 12 * tr.n_vertices + 8 * (tr.n_streamlines + 1)
     k2_ms = prof["ms_prefilter"] / max(prof["calls"], 1)
     achieved = alg_bytes / (k2_ms / 1000.0) / 1e9
+    traffic, traffic_note = prefilter_traffic(tr.n_vertices)
     roofline = {"bound": "hbm", "kernel": "prefilter_kernel", "achieved": achieved,
                 "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
-                "peak_source": f"{peak_kind} hbm_gbs (copy bandwidth)", "traffic": None,
+                "peak_source": f"{peak_kind} hbm_gbs (copy bandwidth)", "traffic": traffic,
+                "traffic_source": traffic_note,
                 "algorithmic_bytes_per_launch": alg_bytes,
                 "stage_ms_per_step": {"prefilter": k2_ms, "walk": prof["ms_walk"] / max(prof["calls"], 1),
                                       "overflow": prof["ms_overflow"] / max(prof["calls"], 1)}}
