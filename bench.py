@@ -309,8 +309,9 @@ def run_batched(args):
                    "l2": "inputs larger than L2"},
         "voxel_steps_per_s": steps_total / batch_s, "graph_ms": graph_ms / args.steps,
         "plain_subjects_per_s": n / plain_s, "plain_ms_per_batch": 1000 * plain_s,
-        "batched_vs_plain": plain_s / batch_s, "autotuned": {"prefilter_ctas": info["prefilter_ctas"],
-                                                             "near_log2": info["near_log2"]},
+        "batched_vs_plain": plain_s / batch_s,
+        "autotuned": {"prefilter_ctas": info["prefilter_ctas"], "near_log2": info["near_log2"],
+                      "task_vertices": info["task_vertices"]},
         "gpu_launches": launches, "clocks": clk, "generation_s": gen_s,
     }
     print(json.dumps(line), flush=True)

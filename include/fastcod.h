@@ -104,10 +104,12 @@ enum {
    * and let more streamlines through to the exact walk.  Results are
    * identical.  Applies to volumes installed afterwards. */
   FASTCOD_OPT_NEAR_LOG2 = 7,
-  /* 1 (default): fastcod_batch_run picks the prefilter's CTAs per SM and
-   * near-grid cell per batch shape by timed trials on the first batch of that
-   * shape (cached in the context, and in the file named by the environment
-   * variable FASTCOD_TUNE_CACHE when set); 0: use the options as set. */
+  /* 1 (default): fastcod_batch_run picks the prefilter's CTAs per SM, the
+   * near-grid cell and the work granularity of a prefilter task (vertices per
+   * task) per batch shape by timed trials on the first batch of that shape
+   * (cached in the context, and in the file named by the environment
+   * variable FASTCOD_TUNE_CACHE when set); 0: use the options as set, with
+   * tasks of about 65,536 vertices. */
   FASTCOD_OPT_AUTOTUNE = 8,
   /* 1: fastcod_add_streamlines reads page-locked (mapped) host xyz in place,
    * the kernels streaming it over the host link while they compute (16-byte
@@ -223,10 +225,11 @@ typedef struct {
   int32_t n_subjects;
   int32_t tasks;          /* prefilter tasks of the last batch */
   int32_t prefilter_ctas; /* configuration the last batch ran with */
-  int32_t near_log2;
+  int32_t near_log2;      /* -1: the per-volume automatic cell */
   int32_t graph_reused;   /* 1: the last batch replayed a captured graph */
   int32_t tuned;          /* 1: the last batch ran the autotuner's trials */
   double ms_graph;        /* device time of the last batch's graph (CUDA events) */
+  int64_t task_vertices;  /* work granularity: about this many vertices per prefilter task */
 } fastcod_batch_info;
 
 /* Run a batch of 1..128 subjects (the sum of their streamlines < 2^31).

@@ -17,13 +17,22 @@ using fcapi::ptr_kind;
 
 namespace {
 
-constexpr int64_t kTaskVertices = 1 << 16;  // target vertices per prefilter task
+constexpr int kTaskLog2Default = 16;  // prefilter task: about 2^16 vertices of one subject
 constexpr int32_t kOverflowCtas = 64;
 
+// What the autotuner picks per batch shape: prefilter CTAs per SM, near-grid
+// cell (-1: per subject), and the work granularity of a prefilter task (about
+// 2^task_log2 vertices of one subject).
 struct BatchConfig {
   int ctas;
   int near_log2;
+  int task_log2;
 };
+
+int64_t tasks_of(int64_t n_vertices, int task_log2) {
+  const int64_t tv = (int64_t)1 << task_log2;
+  return std::max<int64_t>(1, (n_vertices + tv - 1) / tv);
+}
 
 // Sub-allocation of the batch arena (byte offsets, 256-byte aligned).
 struct Layout {
@@ -80,7 +89,7 @@ int64_t near_words(const int32_t d[3], int near_log2) {
   return fc::near_words(v);
 }
 
-Layout plan(const fastcod_subject* subs, int32_t n, const std::vector<int>& host_in, int near_log2,
+Layout plan(const fastcod_subject* subs, int32_t n, const std::vector<int>& host_in, int near_log2, int task_log2,
             int64_t total_ns) {
   Layout L;
   size_t o = 0;
@@ -94,14 +103,13 @@ Layout plan(const fastcod_subject* subs, int32_t n, const std::vector<int>& host
   for (int32_t i = 0; i < n; ++i) {
     maxw = std::max(maxw, fc::overflow_scratch_words(subs[i].n_roi, subs[i].n_targets));
     maxplanes = std::max(maxplanes, fc::plane_words(subs[i].dims[0], subs[i].dims[1], subs[i].dims[2]));
-    ntasks += (int32_t)std::max<int64_t>(1, (subs[i].n_vertices + kTaskVertices - 1) / kTaskVertices);
+    ntasks += (int32_t)tasks_of(subs[i].n_vertices, task_log2);
   }
   L.scratch_words = maxw;
   L.ntasks = ntasks;
   L.scratch = take((size_t)(kOverflowCtas * maxw * 4));
   L.gstate = take(sizeof(DevState));
   L.states = take(sizeof(DevState) * n);
-  L.tasks = take(sizeof(fc::BatchTask) * ntasks);
   L.surv = take((size_t)total_ns * 4);
   L.ovf = take((size_t)total_ns * 4);
   for (int32_t i = 0; i < n; ++i) {
@@ -124,9 +132,12 @@ Layout plan(const fastcod_subject* subs, int32_t n, const std::vector<int>& host
     L.C.push_back(take(nm * 4));
     L.Cend.push_back(take(nm * 4));
   }
-  // the configuration-dependent part last, so that the rest keeps its place
+  // the configuration-dependent part last (near grids: the cell size; tasks:
+  // the work granularity), so that the rest, staged inputs included, keeps
+  // its place from one configuration to the next
   L.planes = take((size_t)maxplanes * 4);
   for (int32_t i = 0; i < n; ++i) L.near.push_back(take((size_t)near_words(subs[i].dims, near_log2) * 4));
+  L.tasks = take(sizeof(fc::BatchTask) * ntasks);
   L.total = o;
   return L;
 }
@@ -136,7 +147,7 @@ T* at(void* base, size_t off) {
   return reinterpret_cast<T*>(static_cast<char*>(base) + off);
 }
 
-void fill_table(fastcod_ctx* c, const fastcod_subject* subs, int32_t n, const Layout& L, int near_log2,
+void fill_table(fastcod_ctx* c, const fastcod_subject* subs, int32_t n, const Layout& L, int near_log2, int task_log2,
                 fc::BatchTable& tbl, std::vector<fc::BatchTask>& tasks) {
   void* A = c->batch->arena;
   memset(&tbl, 0, sizeof tbl);
@@ -169,7 +180,7 @@ void fill_table(fastcod_ctx* c, const fastcod_subject* subs, int32_t n, const La
     B.st = at<DevState>(A, L.states) + i;
     B.sbase = sbase;
     sbase += S.n_streamlines;
-    const int64_t k = std::max<int64_t>(1, (S.n_vertices + kTaskVertices - 1) / kTaskVertices);
+    const int64_t k = tasks_of(S.n_vertices, task_log2);
     for (int64_t j = 0; j < k; ++j) {
       fc::BatchTask t;
       t.subject = i;
@@ -192,7 +203,7 @@ uint64_t graph_key(const fc::BatchTable& tbl, int32_t ntasks, const BatchConfig&
   const size_t words = (offsetof(fc::BatchTable, s) + sizeof(fc::BatchSubject) * tbl.n) / 8;
   for (size_t i = 0; i < words; ++i) h = mix(h, w[i]);
   h = mix(h, (uint64_t)ntasks);
-  h = mix(h, (uint64_t)cfg.ctas * 131 + (uint64_t)cfg.near_log2);
+  h = mix(h, (uint64_t)cfg.ctas * 131 + (uint64_t)(cfg.near_log2 + 1) * 7 + (uint64_t)cfg.task_log2 * 1009);
   h = mix(h, (uint64_t)mode * 7 + (uint64_t)prefilter + 1000 * (uint64_t)(tma != 0));
   h = mix(h, (uint64_t)(uintptr_t)arena);
   return h;
@@ -249,7 +260,7 @@ int kernels_per_run(int32_t n) { return 2 * n + 3; }
 int run_config(fastcod_ctx* c, const fastcod_subject* subs, int32_t n, const std::vector<int>& host_in,
                int64_t total_ns, const BatchConfig& cfg, bool stage, float* ms) {
   BatchState* B = c->batch;
-  Layout L = plan(subs, n, host_in, cfg.near_log2, total_ns);
+  Layout L = plan(subs, n, host_in, cfg.near_log2, cfg.task_log2, total_ns);
   if (L.total > B->arena_bytes || !B->arena) {
     if (B->exec) {
       cudaGraphExecDestroy(B->exec);
@@ -270,7 +281,7 @@ int run_config(fastcod_ctx* c, const fastcod_subject* subs, int32_t n, const std
   fc::BatchTable* tbl = new (std::nothrow) fc::BatchTable;
   if (!tbl) return fail(c, FASTCOD_ENOMEM, "host allocation failed");
   std::vector<fc::BatchTask> tasks;
-  fill_table(c, subs, n, L, cfg.near_log2, *tbl, tasks);
+  fill_table(c, subs, n, L, cfg.near_log2, cfg.task_log2, *tbl, tasks);
   int rc = FASTCOD_OK;
   do {
     if (stage) {
@@ -293,12 +304,13 @@ int run_config(fastcod_ctx* c, const fastcod_subject* subs, int32_t n, const std
         }
       }
       if (rc) break;
-      if (cudaMemcpyAsync(at<void>(A, L.tasks), tasks.data(), sizeof(fc::BatchTask) * tasks.size(),
-                          cudaMemcpyHostToDevice, c->stream) != cudaSuccess) {
-        (void)cudaGetLastError();
-        rc = fail(c, FASTCOD_ECUDA, "batch task table copy failed");
-        break;
-      }
+    }
+    // the task table depends on the configuration: uploaded on every run
+    if (cudaMemcpyAsync(at<void>(A, L.tasks), tasks.data(), sizeof(fc::BatchTask) * tasks.size(),
+                        cudaMemcpyHostToDevice, c->stream) != cudaSuccess) {
+      (void)cudaGetLastError();
+      rc = fail(c, FASTCOD_ECUDA, "batch task table copy failed");
+      break;
     }
     const uint64_t key = graph_key(*tbl, L.ntasks, cfg, c->mode, c->prefilter, c->staging_tma, A, subs, L);
     B->info.graph_reused = (B->exec && key == B->graph_key) ? 1 : 0;
@@ -332,6 +344,7 @@ int run_config(fastcod_ctx* c, const fastcod_subject* subs, int32_t n, const std
     B->info.tasks = L.ntasks;
     B->info.prefilter_ctas = cfg.ctas;
     B->info.near_log2 = cfg.near_log2;
+    B->info.task_vertices = (int64_t)1 << cfg.task_log2;
     B->info.ms_graph = *ms;
   } while (0);
   delete tbl;
@@ -357,9 +370,12 @@ void load_tune_cache(BatchState* B) {
   FILE* f = fopen(path, "r");
   if (!f) return;
   unsigned long long k;
-  int ctas, nl;
-  while (fscanf(f, "%llx %d %d", &k, &ctas, &nl) == 3)
-    if ((ctas == 2 || ctas == 3) && nl >= -1 && nl <= 3) B->tuned[(uint64_t)k] = BatchConfig{ctas, nl};
+  int ctas, nl, tl;
+  char line[256];
+  while (fgets(line, sizeof line, f))
+    if (sscanf(line, "%llx %d %d %d", &k, &ctas, &nl, &tl) == 4 && (ctas == 2 || ctas == 3) && nl >= -1 && nl <= 3 &&
+        tl >= 12 && tl <= 22)
+      B->tuned[(uint64_t)k] = BatchConfig{ctas, nl, tl};
   fclose(f);
 }
 
@@ -368,7 +384,7 @@ void save_tune_entry(uint64_t key, const BatchConfig& cfg) {
   if (!path) return;
   FILE* f = fopen(path, "a");
   if (!f) return;
-  fprintf(f, "%llx %d %d\n", (unsigned long long)key, cfg.ctas, cfg.near_log2);
+  fprintf(f, "%llx %d %d %d\n", (unsigned long long)key, cfg.ctas, cfg.near_log2, cfg.task_log2);
   fclose(f);
 }
 
@@ -428,7 +444,7 @@ FASTCOD_API int fastcod_batch_run(fastcod_ctx* c, const fastcod_subject* subs, i
   B->info = fastcod_batch_info{};
   B->info.n_subjects = n;
   float ms = 0.f;
-  BatchConfig cfg{c->prefilter_ctas, c->near_log2};
+  BatchConfig cfg{c->prefilter_ctas, c->near_log2, kTaskLog2Default};
   bool staged = false;
   if (c->autotune) {
     load_tune_cache(B);
@@ -438,7 +454,7 @@ FASTCOD_API int fastcod_batch_run(fastcod_ctx* c, const fastcod_subject* subs, i
       cfg = it->second;
     } else {
       // timed trials: each candidate runs twice (the first run captures its graph)
-      const BatchConfig cand[4] = {{2, 1}, {3, 1}, {2, 2}, {2, 0}};
+      const BatchConfig cand[6] = {{2, -1, 16}, {2, -1, 14}, {2, -1, 18}, {3, -1, 16}, {2, 2, 16}, {2, 0, 16}};
       float best = 1e30f;
       for (const BatchConfig& k : cand) {
         float t = 0.f;
@@ -459,7 +475,7 @@ FASTCOD_API int fastcod_batch_run(fastcod_ctx* c, const fastcod_subject* subs, i
   if (int rc = run_config(c, subs, n, host_in, total_ns, cfg, true, &ms)) return rc;
   // outputs and per-subject state
   void* A = B->arena;
-  Layout L = plan(subs, n, host_in, cfg.near_log2, total_ns);
+  Layout L = plan(subs, n, host_in, cfg.near_log2, cfg.task_log2, total_ns);
   for (int32_t i = 0; i < n; ++i) {
     const size_t nm = (size_t)subs[i].n_roi * (size_t)subs[i].n_targets;
     CU(cudaMemcpyAsync(subs[i].C_out, at<int32_t>(A, L.C[i]), nm * 4, cudaMemcpyDefault, c->stream));

@@ -77,7 +77,7 @@ class Subject(ctypes.Structure):
 class BatchInfo(ctypes.Structure):
     _fields_ = [("n_subjects", ctypes.c_int32), ("tasks", ctypes.c_int32), ("prefilter_ctas", ctypes.c_int32),
                 ("near_log2", ctypes.c_int32), ("graph_reused", ctypes.c_int32), ("tuned", ctypes.c_int32),
-                ("ms_graph", ctypes.c_double)]
+                ("ms_graph", ctypes.c_double), ("task_vertices", ctypes.c_int64)]
 
 
 class RequestInfo(ctypes.Structure):
