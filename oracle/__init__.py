@@ -34,7 +34,8 @@ def build(force: bool = False) -> str:
     if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < max(os.path.getmtime(src),
                                                                           os.path.getmtime(hdr)):
         tmp = _SO + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-o", tmp, src])
+        subprocess.check_call(["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fPIC", "-shared", "-o", tmp, src,
+                               "-lm"])
         os.replace(tmp, _SO)
     return _SO
 
@@ -66,6 +67,16 @@ def lib():
         L.oracle_bruteforce_connectivity.argtypes = [vp, vp, vp, i32, i32, vp, vp, i64, u32, vp, vp]
         L.oracle_streamline_sets.restype = ctypes.c_int
         L.oracle_streamline_sets.argtypes = [vp, vp, vp, i32, i32, vp, i64, u32, vp, vp, vp, vp]
+        L.oracle_parcellate.restype = ctypes.c_int
+        L.oracle_parcellate.argtypes = [vp, i32, i32, vp, vp]
+        L.oracle_world_to_fixed.restype = ctypes.c_int
+        L.oracle_world_to_fixed.argtypes = [vp, i64, vp, vp]
+        L.oracle_upsample.restype = i64
+        L.oracle_upsample.argtypes = [vp, vp, i64, i32, vp, vp]
+        L.oracle_upsample_factor.restype = i32
+        L.oracle_upsample_factor.argtypes = [vp, vp, i64, i32]
+        L.oracle_rescale.restype = ctypes.c_int
+        L.oracle_rescale.argtypes = [vp, i64, vp, vp, vp, vp]
         _lib = L
     return _lib
 
@@ -173,3 +184,62 @@ def streamline_sets(roi, lab, dims, N, M, verts, flags: int = 0):
     lib().oracle_streamline_sets(_p(roi), _p(lab), _p(d), N, M, _p(v), len(v), flags, _p(V),
                                  ctypes.byref(nV), _p(Tl), ctypes.byref(nT))
     return V[:nV.value].copy(), Tl[:nT.value].copy()
+
+
+def parcellate(C):
+    """(label int32 [N], fractions float32 [N, M]) of a connectivity matrix
+    (Section 3, pie-glyphs and the single-colour display)."""
+    C = np.ascontiguousarray(C, dtype=np.int64)
+    N, M = C.shape
+    label = np.empty(N, dtype=np.int32)
+    frac = np.empty((N, M), dtype=np.float32)
+    if lib().oracle_parcellate(_p(C), N, M, _p(label), _p(frac)) != 0:
+        raise ValueError("oracle: negative count")
+    return label, frac
+
+
+def world_to_fixed(xyz_mm, affine):
+    """int32 fixed-point vertices from binary32 world-mm vertices and a 3x4
+    world -> voxel affine (binary32)."""
+    x = np.ascontiguousarray(xyz_mm, dtype=np.float32).reshape(-1, 3)
+    A = np.ascontiguousarray(affine, dtype=np.float32).reshape(12)
+    out = np.empty(x.shape, dtype=np.int32)
+    if lib().oracle_world_to_fixed(_p(x), len(x), _p(A), _p(out)) != 0:
+        raise ValueError("oracle: coordinate not finite or out of range")
+    return out
+
+
+def upsample(xyz, offsets, factor: int):
+    """(xyz, offsets) with `factor` segments per original segment."""
+    xyz = np.ascontiguousarray(xyz, dtype=np.int32).reshape(-1, 3)
+    off = np.ascontiguousarray(offsets, dtype=np.int64)
+    ns = len(off) - 1
+    nonempty = int(np.count_nonzero(np.diff(off)))
+    nv_out = (len(xyz) - nonempty) * factor + nonempty
+    out = np.empty((max(nv_out, 0), 3), dtype=np.int32)
+    oo = np.empty(ns + 1, dtype=np.int64)
+    n = lib().oracle_upsample(_p(xyz), _p(off), ns, int(factor), _p(out), _p(oo))
+    if n < 0:
+        raise ValueError("oracle: invalid input")
+    assert n == nv_out
+    return out, oo
+
+
+def upsample_factor(xyz, offsets, spacing: int) -> int:
+    xyz = np.ascontiguousarray(xyz, dtype=np.int32).reshape(-1, 3)
+    off = np.ascontiguousarray(offsets, dtype=np.int64)
+    k = lib().oracle_upsample_factor(_p(xyz), _p(off), len(off) - 1, int(spacing))
+    if k < 0:
+        raise ValueError("oracle: invalid input")
+    return int(k)
+
+
+def rescale(xyz, num, den, add):
+    xyz = np.ascontiguousarray(xyz, dtype=np.int32).reshape(-1, 3)
+    num = np.ascontiguousarray(num, dtype=np.int32)
+    den = np.ascontiguousarray(den, dtype=np.int32)
+    add = np.ascontiguousarray(add, dtype=np.int64)
+    out = np.empty_like(xyz)
+    if lib().oracle_rescale(_p(xyz), len(xyz), _p(num), _p(den), _p(add), _p(out)) != 0:
+        raise ValueError("oracle: invalid input or result out of range")
+    return out

@@ -1,13 +1,16 @@
 /*
  * ORACLE - TEST INFRASTRUCTURE ONLY (see oracle.h).
  *
- * Plain single-threaded C99.  Every quantity is an integer; rational
- * comparisons are exact int64 cross-multiplications.  With coordinates in
- * [-2^24, 2^24) every numerator is at most 2^25 + 1024 and every denominator
- * at most 2^25, so the products stay below 2^51.
+ * Plain single-threaded C99.  Every quantity of the connectivity path is an
+ * integer; rational comparisons are exact int64 cross-multiplications.  With
+ * coordinates in [-2^24, 2^24) every numerator is at most 2^25 + 1024 and
+ * every denominator at most 2^25, so the products stay below 2^51.  The
+ * floating-point steps (parcellation fractions, world-mm ingest) state their
+ * rounding and are compiled without contraction (-ffp-contract=off).
  */
 #include "oracle.h"
 
+#include <math.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -375,5 +378,127 @@ int oracle_streamline_sets(const int32_t* roi, const uint16_t* lab, const int32_
   memcpy(Tl, k.Tl, sizeof(int32_t) * (size_t)k.nT);
   *nV = k.nV; *nT = k.nT;
   ctx_free(&k);
+  return 0;
+}
+
+/* ------------------------------------------------------------ parcellation */
+
+int oracle_parcellate(const int64_t* C, int32_t N, int32_t M, int32_t* label, float* frac) {
+  for (int32_t r = 0; r < N; ++r) {
+    const int64_t* row = C + (int64_t)r * M;
+    int64_t sum = 0, best = 0;
+    int32_t arg = 0;
+    for (int32_t t = 0; t < M; ++t) {
+      if (row[t] < 0) return -1;
+      sum += row[t];
+      if (row[t] > best) {
+        best = row[t];
+        arg = t + 1;
+      }
+    }
+    label[r] = arg;
+    if (frac) {
+      for (int32_t t = 0; t < M; ++t) {
+        /* binary64 quotient of two exact integers (< 2^53), then binary32:
+           the double rounding is innocuous since 53 >= 2 * 24 + 2 */
+        frac[(int64_t)r * M + t] = sum > 0 ? (float)((double)row[t] / (double)sum) : 0.0f;
+      }
+    }
+  }
+  return 0;
+}
+
+/* ------------------------------------------------------------------ ingest */
+
+int oracle_world_to_fixed(const float* xyz_mm, int64_t nv, const float affine[12], int32_t* xyz) {
+  for (int64_t i = 0; i < nv; ++i) {
+    const float x = xyz_mm[3 * i], y = xyz_mm[3 * i + 1], z = xyz_mm[3 * i + 2];
+    for (int a = 0; a < 3; ++a) {
+      const float* A = affine + 4 * a;
+      volatile float t0 = A[0] * x; /* volatile: every product and sum rounded on its own */
+      volatile float t1 = A[1] * y;
+      volatile float s0 = t0 + t1;
+      volatile float t2 = A[2] * z;
+      volatile float s1 = s0 + t2;
+      volatile float v = s1 + A[3];
+      const float u = v * 1024.0f;
+      if (!(u >= -16777216.0f && u < 16777216.0f)) return -1;
+      const long r = lrintf(u);
+      if (r < -16777216L || r >= 16777216L) return -1;
+      xyz[3 * i + a] = (int32_t)r;
+    }
+  }
+  return 0;
+}
+
+/* --------------------------------------------------------------- upsample */
+
+static int64_t floor_div(int64_t a, int64_t b) { /* b > 0 */
+  int64_t q = a / b;
+  if ((a % b != 0) && (a < 0)) q -= 1;
+  return q;
+}
+
+int64_t oracle_upsample(const int32_t* xyz, const int64_t* offsets, int64_t ns, int32_t factor,
+                        int32_t* out_xyz, int64_t* out_offsets) {
+  if (factor < 1 || offsets[0] != 0) return -1;
+  int64_t o = 0;
+  out_offsets[0] = 0;
+  for (int64_t s = 0; s < ns; ++s) {
+    const int64_t a = offsets[s], b = offsets[s + 1];
+    if (b < a) return -1;
+    for (int64_t i = a; i + 1 < b; ++i) {
+      for (int32_t j = 0; j < factor; ++j) {
+        for (int c = 0; c < 3; ++c) {
+          const int64_t p = xyz[3 * i + c], q = xyz[3 * (i + 1) + c];
+          out_xyz[3 * o + c] = (int32_t)(p + floor_div((q - p) * j, factor));
+        }
+        ++o;
+      }
+    }
+    if (b > a) {
+      for (int c = 0; c < 3; ++c) out_xyz[3 * o + c] = xyz[3 * (b - 1) + c];
+      ++o;
+    }
+    out_offsets[s + 1] = o;
+  }
+  return o;
+}
+
+int32_t oracle_upsample_factor(const int32_t* xyz, const int64_t* offsets, int64_t ns, int32_t spacing) {
+  if (spacing < 1) return -1;
+  int64_t best = 0; /* largest squared segment length */
+  for (int64_t s = 0; s < ns; ++s) {
+    for (int64_t i = offsets[s]; i + 1 < offsets[s + 1]; ++i) {
+      int64_t l2 = 0;
+      for (int c = 0; c < 3; ++c) {
+        const int64_t d = (int64_t)xyz[3 * (i + 1) + c] - xyz[3 * i + c];
+        l2 += d * d;
+      }
+      if (l2 > best) best = l2;
+    }
+  }
+  /* r = the smallest integer with r * r >= best (binary search; best < 2^53),
+     then the smallest k with k * spacing >= r */
+  int64_t lo = 0, hi = (int64_t)1 << 27;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) / 2;
+    if (mid * mid >= best) hi = mid; else lo = mid + 1;
+  }
+  int64_t k = (lo + spacing - 1) / spacing;
+  if (k < 1) k = 1;
+  return k > (1 << 20) ? -1 : (int32_t)k;
+}
+
+int oracle_rescale(const int32_t* xyz, int64_t nv, const int32_t num[3], const int32_t den[3],
+                   const int64_t add[3], int32_t* out) {
+  for (int c = 0; c < 3; ++c)
+    if (num[c] < 1 || den[c] < 1) return -1;
+  for (int64_t i = 0; i < nv; ++i)
+    for (int c = 0; c < 3; ++c) {
+      const int64_t v = floor_div((int64_t)xyz[3 * i + c] * num[c] + add[c], den[c]);
+      if (v < -16777216LL || v >= 16777216LL) return -1;
+      out[3 * i + c] = (int32_t)v;
+    }
   return 0;
 }

@@ -21,9 +21,10 @@
  *   - C_end[r][t-1] = sum_{s : T >= 1} [row(floor p^1) = r][lab(floor p^T) = t]
  *     (Algorithm 1, the seed read as the first vertex).
  *
- * Readings where the paper is silent (half-open boxes, the first vertex as the
- * seed, points off the grid ignored, dedup by row index and label value) are
- * the ones listed in the repository's design notes.
+ * Readings where the paper is silent: half-open voxel boxes (at a shared
+ * crossing the increasing axes step at the crossing, the decreasing ones just
+ * after it), the first vertex as the seed, points off the grid ignored, dedup
+ * by row index and by label value.
  *
  * Options (flags):
  *   ORACLE_TARGET_ENDPOINT - T_s = {lab(floor p^T)} instead of the labels the
@@ -77,6 +78,48 @@ int oracle_bruteforce_connectivity(const int32_t* roi, const uint16_t* lab, cons
 int oracle_streamline_sets(const int32_t* roi, const uint16_t* lab, const int32_t dims[3],
                            int32_t N, int32_t M, const int32_t* xyz, int64_t T, uint32_t flags,
                            int32_t* V, int32_t* nV, int32_t* Tl, int32_t* nT);
+
+/* Parcellation outputs of an N x M connectivity matrix (Section 3,
+ * "Pie-glyphs": the single-colour display shows the region with the highest
+ * connectivity, the pie chart each region's relative connectivity strength):
+ *   label[r] = 1 + argmax_t C[r][t], ties to the lowest label; 0 when the row
+ *              is all zero;
+ *   frac[r][t] = C[r][t] / sum_t C[r][t] rounded to the nearest binary32
+ *              (ties to even); 0 for an all-zero row.  frac may be NULL.
+ * Returns 0, or -1 when an entry is negative. */
+int oracle_parcellate(const int64_t* C, int32_t N, int32_t M, int32_t* label, float* frac);
+
+/* World-mm streamline vertices (binary32, the form tractography writes) to
+ * this library's fixed point: v_a = ((A[a][0] x + A[a][1] y) + A[a][2] z)
+ * + A[a][3] with every product and sum rounded to binary32 (no fused
+ * multiply-add), then the coordinate is v_a * 1024 rounded to the nearest
+ * integer (ties to even).  A is the row-major 3 x 4 world -> voxel affine
+ * (voxel i spans [i, i+1)).  Returns 0, or -1 when a result is not finite or
+ * falls outside [-2^24, 2^24). */
+int oracle_world_to_fixed(const float* xyz_mm, int64_t nv, const float affine[12], int32_t* xyz);
+
+/* Streamline upsampling (Section 3, "Super-resolving connectivity features":
+ * evenly spaced points inserted between neighbouring points): every segment
+ * p -> q of a streamline becomes `factor` segments through the points
+ * p + floor((q - p) * j / factor), j = 0 .. factor-1, followed by the last
+ * vertex.  A streamline of T >= 1 vertices gets (T - 1) * factor + 1, an
+ * empty one none.  out_offsets has ns + 1 entries.  Returns the vertices
+ * written, or -1 on invalid input. */
+int64_t oracle_upsample(const int32_t* xyz, const int64_t* offsets, int64_t ns, int32_t factor,
+                        int32_t* out_xyz, int64_t* out_offsets);
+
+/* The smallest factor k >= 1 whose upsampled spacing is at most `spacing`
+ * units on every segment: |q - p|^2 <= (k * spacing)^2 (exact integers; the
+ * paper's rule of thumb takes spacing <= half the target voxel).  Returns k,
+ * or -1 on invalid input or when k would exceed 2^20. */
+int32_t oracle_upsample_factor(const int32_t* xyz, const int64_t* offsets, int64_t ns, int32_t spacing);
+
+/* Integer rescale of fixed-point vertices between grids:
+ * out_a = floor((p_a * num_a + add_a) / den_a), exact in 64-bit integers
+ * (num_a, den_a > 0).  Returns 0, or -1 when a result falls outside
+ * [-2^24, 2^24). */
+int oracle_rescale(const int32_t* xyz, int64_t nv, const int32_t num[3], const int32_t den[3],
+                   const int64_t add[3], int32_t* out);
 
 #ifdef __cplusplus
 }
