@@ -431,6 +431,106 @@ def run_served(args):
     return 0
 
 
+def run_next(args):
+    """Entry points beside the path, timed with CUDA events on the context's
+    stream over device-resident inputs, each against its HBM roofline:
+      parcellate - labels and binary32 fractions of the high-res subject's C
+                   (N = 39,708, M = 360): 8 B per entry + 4 B per row;
+      ingest     - fastcod_add_streamlines_mm of the HCP-shaped subject from
+                   binary32 world-mm vertices (conversion, 24 B per vertex,
+                   then the path, 12 B per vertex); metric voxel-steps/s;
+      upsample   - fastcod_upsample of the HCP-shaped subject by --factor:
+                   12 B read + 12 * factor B written per vertex."""
+    import torch
+
+    import synth
+    from paper_2302_09247_gb300 import fastcod as fc
+
+    ws, rank, local = _dist()
+    if rank != 0:
+        return 0
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    peaks, peak_kind = _peaks()
+    ctx = fc.Context(local)
+    stream = torch.cuda.Stream(device=dev)
+    fc.fastcod_set_stream(ctx.ctx, stream)
+    cfg = 2 if args.next == "parcellate" else 1
+    vols, tr = synth.make_subject(cfg, n_streamlines=args.streamlines)
+    xyz_d = torch.from_numpy(tr.xyz).to(dev)
+    off_d = torch.from_numpy(tr.offsets).to(dev)
+    extra = {}
+    if args.next == "parcellate":
+        ctx.set_volumes(torch.from_numpy(vols.roi).to(dev), torch.from_numpy(vols.lab.view(np.int16)).to(dev),
+                        vols.dims, vols.n_roi, vols.n_targets)
+        ctx.add_streamlines(xyz_d, off_d)
+        N, M = vols.n_roi, vols.n_targets
+        lab_out = torch.empty(N, dtype=torch.int32, device=dev)
+        frac_out = torch.empty((N, M), dtype=torch.float32, device=dev)
+
+        def step():
+            fc.fastcod_parcellate(ctx.ctx, 0, lab_out, frac_out)
+        units, unit, metric = float(N), "rows/s", "parcellation rows/s (label + fractions)"
+        alg_bytes = 8 * N * M + 4 * N
+        kernel = "parcellate_kernel"
+    elif args.next == "ingest":
+        ctx.set_volumes(torch.from_numpy(vols.roi).to(dev), torch.from_numpy(vols.lab.view(np.int16)).to(dev),
+                        vols.dims, vols.n_roi, vols.n_targets)
+        A = np.zeros((3, 4), dtype=np.float32)  # 1.25 mm voxels, origin at -90 mm
+        A[:, :3] = np.eye(3, dtype=np.float32) / np.float32(1.25)
+        A[:, 3] = np.float32(90.0) / np.float32(1.25)
+        x_mm = torch.from_numpy(((tr.xyz.astype(np.float64) / 1024.0) * 1.25 - 90.0).astype(np.float32)).to(dev)
+
+        def step():
+            fc.fastcod_reset(ctx.ctx)
+            fc.fastcod_add_streamlines_mm(ctx.ctx, x_mm, off_d, A)
+        step()
+        ctx.sync()
+        units, unit, metric = float(ctx.stats()["voxel_steps"]), UNIT, METRIC + " (world-mm binary32 input)"
+        alg_bytes = 36 * tr.n_vertices + 8 * (tr.n_streamlines + 1)
+        kernel = "world_to_fixed_kernel + prefilter_kernel (the call's two streaming passes: 24 + 12 B per vertex)"
+    else:
+        k = args.factor
+        n_out = fc.upsampled_count(tr.offsets, k)
+        ux = torch.empty((n_out, 3), dtype=torch.int32, device=dev)
+        uo = torch.empty(tr.n_streamlines + 1, dtype=torch.int64, device=dev)
+
+        def step():
+            fc.fastcod_upsample(ctx.ctx, xyz_d, off_d, k, ux, uo)
+        units, unit, metric = float(n_out), "vertices/s", f"upsampled vertices/s (factor {k})"
+        alg_bytes = 12 * tr.n_vertices + 12 * n_out + 16 * (tr.n_streamlines + 1)
+        kernel = "upsample kernels (offsets scan + vertices)"
+        extra["factor"] = k
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    line = {
+        "metric": metric, "value": units / (ms / 1000.0), "unit": unit, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int32" if args.next != "parcellate" else "int32 -> f32",
+        "data": "synthetic", "config": dict(_config(cfg, vols, tr), next=args.next, **extra),
+        "roofline": {"bound": "hbm", "kernel": kernel, "algorithmic_bytes_per_step": alg_bytes,
+                     "achieved": alg_bytes / (ms / 1000.0) / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                     "frac": alg_bytes / (ms / 1000.0) / 1e9 / peaks["hbm_gbs"],
+                     "peak_source": f"{peak_kind} hbm_gbs (copy bandwidth)", "traffic": None},
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -445,6 +545,9 @@ def main():
     ap.add_argument("--rate", type=float, default=20.0, help="--config 4: Poisson arrivals per second")
     ap.add_argument("--pool", type=int, default=4, help="--config 4: pre-generated subjects")
     ap.add_argument("--slots", type=int, default=16, help="--config 4: server slots")
+    ap.add_argument("--next", default=None, choices=["parcellate", "ingest", "upsample"],
+                    help="time an entry point beside the path instead (one JSON line of its own)")
+    ap.add_argument("--factor", type=int, default=2, help="--next upsample: upsampling factor")
     ap.add_argument("--e2e-steps", type=int, default=10, help="0 skips the end-to-end leg")
     ap.add_argument("--streamlines", type=int, default=None,
                     help="use only the first N streamlines of the subject (small profiling cases)")
@@ -456,6 +559,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.next:
+        return run_next(args)
     if args.config == 3:
         return run_batched(args)
     if args.config == 4:

@@ -303,6 +303,69 @@ FASTCOD_API int fastcod_server_request_info(fastcod_server* srv, uint64_t reques
 /* Finish all admitted and queued work, stop the worker, free everything. */
 FASTCOD_API int fastcod_server_destroy(fastcod_server* srv);
 
+/* ---------------------------------------------------- beside the path
+ * Outputs and inputs around the connectivity matrix.  Pointers may be host
+ * or device memory of the context's device; every call blocks until its
+ * outputs are written.  Errors these calls find leave C and C_end as they
+ * were. */
+
+/* Parcellation outputs of C (which = 0) or C_end (which = 1) (Section 3,
+ * "Pie-glyphs": the single-colour display shows, per source voxel, the region
+ * with the highest connectivity; the pie-glyph shows its relative
+ * connectivity strength to every region):
+ *   label_out[r]      (int32 [N]) = 1 + argmax_t C[r][t], ties to the lowest
+ *                     label; 0 for a row of zeros;
+ *   fractions_out[r][t] (binary32 [N][M], may be NULL) = C[r][t] / sum_t
+ *                     C[r][t] rounded to the nearest binary32 (ties to even);
+ *                     0 for a row of zeros.
+ * Waits for the queued work first (ESTATE without volumes). */
+FASTCOD_API int fastcod_parcellate(fastcod_ctx* ctx, int32_t which, int32_t* label_out, float* fractions_out);
+
+/* World-mm vertices (binary32 [n][3], the form tractography writes) to this
+ * library's fixed point: v_a = ((A[a][0] x + A[a][1] y) + A[a][2] z) +
+ * A[a][3], every product and sum rounded to binary32 (no fused multiply-add),
+ * then round(v_a * 1024) to the nearest integer, ties to even.  affine is the
+ * row-major 3 x 4 world -> voxel matrix in this library's voxel units (voxel
+ * i spans [i, i+1); for an image affine that maps voxel centres, add 0.5 to
+ * its translation).  EINVAL when a result is not finite or falls outside
+ * [-2^24, 2^24). */
+FASTCOD_API int fastcod_world_to_fixed(fastcod_ctx* ctx, const float* xyz_mm, int64_t n_vertices,
+                                       const float affine[12], int32_t* xyz_out);
+
+/* fastcod_world_to_fixed into the context's buffer, then
+ * fastcod_add_streamlines on it. */
+FASTCOD_API int fastcod_add_streamlines_mm(fastcod_ctx* ctx, const float* xyz_mm, int64_t n_vertices,
+                                           const int64_t* offsets, int64_t n_streamlines, const float affine[12]);
+
+/* Streamline upsampling (Section 3, "Super-resolving connectivity features":
+ * evenly spaced points inserted between neighbouring points, so that
+ * connectivity can be computed on a finer grid than the tractography's).
+ * Every segment p -> q becomes `factor` segments through the points
+ * p + floor((q - p) * j / factor), j = 0 .. factor-1, followed by the
+ * streamline's last vertex: a streamline of T >= 1 vertices gets
+ * (T - 1) * factor + 1, an empty one none.  n_vertices_out must equal that
+ * total ((n_vertices - non-empty streamlines) * factor + non-empty
+ * streamlines; EINVAL otherwise); offsets_out has n_streamlines + 1 entries.
+ * factor in [1, 2^20]. */
+FASTCOD_API int fastcod_upsample(fastcod_ctx* ctx, const int32_t* xyz, int64_t n_vertices, const int64_t* offsets,
+                                 int64_t n_streamlines, int32_t factor, int32_t* xyz_out, int64_t n_vertices_out,
+                                 int64_t* offsets_out);
+
+/* The smallest upsampling factor k >= 1 with |q - p|^2 <= (k * spacing)^2
+ * on every segment (exact integers; the paper's rule of thumb takes spacing
+ * at most half the target voxel, i.e. 512 units for the grid the vertices are
+ * in).  EINVAL when k would exceed 2^20. */
+FASTCOD_API int fastcod_upsample_factor(fastcod_ctx* ctx, const int32_t* xyz, int64_t n_vertices,
+                                        const int64_t* offsets, int64_t n_streamlines, int32_t spacing,
+                                        int32_t* factor_out);
+
+/* Integer rescale of fixed-point vertices between grids (for instance from
+ * the diffusion grid to a finer structural grid):
+ * out_a = floor((p_a * num[a] + add[a]) / den[a]), exact in 64-bit integers,
+ * num and den positive.  EINVAL when a result falls outside [-2^24, 2^24). */
+FASTCOD_API int fastcod_rescale(fastcod_ctx* ctx, const int32_t* xyz, int64_t n_vertices, const int32_t num[3],
+                                const int32_t den[3], const int64_t add[3], int32_t* xyz_out);
+
 /* ------------------------------------------------------- allocation-free
  * C and C_end of one subject with no device allocation at all, neither by
  * the caller nor by the library.  It serves callers that cannot allocate

@@ -14,7 +14,8 @@ LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libfastcod.so")
 INCLUDE = os.path.join(ROOT, "include")
 
-SOURCES = ["fastcod_capi.cu", "batch.cu", "server.cu", "noalloc.cu", "k_volume.cu", "k_prefilter.cu", "k_walk.cu"]
+SOURCES = ["fastcod_capi.cu", "batch.cu", "server.cu", "noalloc.cu", "aux_capi.cu", "k_volume.cu", "k_prefilter.cu",
+           "k_walk.cu", "k_aux.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler",
                      "-fvisibility=hidden", f"-I{INCLUDE}"]

@@ -68,6 +68,7 @@ using fcapi::fail;
 using fcapi::grow;
 using fcapi::mapped_host;
 using fcapi::ptr_kind;
+using fcapi::sync_check;
 
 
 void free_volumes(fastcod_ctx* c) {
@@ -97,8 +98,10 @@ int read_state(fastcod_ctx* c, DevState* h) {
   return FASTCOD_OK;
 }
 
+}  // namespace
+
 // Synchronise and turn a device-detected error into a status.
-int sync_check(fastcod_ctx* c) {
+int fcapi::sync_check(fastcod_ctx* c) {
   DevState h;
   int rc = read_state(c, &h);
   if (rc) return rc;
@@ -119,6 +122,8 @@ int sync_check(fastcod_ctx* c) {
       return fail(c, FASTCOD_ECUDA, "device error %d (%d)", h.error, h.error_info);
   }
 }
+
+namespace {
 
 fc::VolView vol_view(const fastcod_ctx* c) {
   fc::VolView v;
@@ -266,6 +271,7 @@ FASTCOD_API int fastcod_destroy(fastcod_ctx* c) {
   cudaFree(c->d_off);
   cudaFree(c->d_surv);
   cudaFree(c->d_ovf);
+  for (int i = 0; i < fastcod_ctx::kAuxSlots; ++i) cudaFree(c->d_aux[i]);
   fcapi::batch_free(c);
   cudaFree(c->d_state);
   for (auto& set : c->ev_pool)

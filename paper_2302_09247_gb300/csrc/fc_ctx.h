@@ -67,6 +67,11 @@ struct fastcod_ctx {
   EvSet* ev_cur = nullptr;
   fastcod_profile prof = {0, 0, 0.0, 0.0, 0.0, 0.0};
 
+  // device scratch of the entry points beside the path (aux_capi.cu)
+  static constexpr int kAuxSlots = 6;
+  void* d_aux[kAuxSlots] = {};
+  size_t aux_bytes[kAuxSlots] = {};
+
   std::string err;
   BatchState* batch = nullptr;  // batched form (batch.cu)
 };
@@ -80,6 +85,9 @@ int ptr_kind(const void* p, int dev);
 const void* mapped_host(const void* p);
 // Grow a device buffer to at least need bytes (synchronises before freeing).
 int grow(fastcod_ctx* c, void** p, size_t* cap, size_t need);
+// Synchronise the context's stream and turn a device-detected error into a
+// status.
+int sync_check(fastcod_ctx* c);
 // Release the batched form's state (batch.cu).
 void batch_free(fastcod_ctx* c);
 // Message of the last failed call on this thread that has no context.

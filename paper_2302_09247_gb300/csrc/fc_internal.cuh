@@ -184,4 +184,21 @@ cudaError_t launch_walk_overflow(const Tract& t, const VolView& v, const int32_t
 // words of global scratch one overflow CTA needs for N rows and M labels
 int64_t overflow_scratch_words(int32_t n_roi, int32_t n_lab);
 
+// Beside the path (k_aux.cu): parcellation of an N x M matrix (frac may be
+// null), world-mm ingest, offsets check, upsampling (offsets, then
+// vertices; block_tmp holds upsample_scan_blocks(ns) values), rescale.
+cudaError_t launch_parcellate(const int32_t* C, int32_t N, int32_t M, int32_t* label, float* frac, cudaStream_t s);
+cudaError_t launch_world_to_fixed(const float* xyz_mm, int64_t nv, const float affine[12], int32_t* out,
+                                  DevState* st, cudaStream_t s);
+cudaError_t launch_check_offsets(const int64_t* off, int64_t ns, int64_t nv, DevState* st, cudaStream_t s);
+cudaError_t launch_seg_max(const int32_t* xyz, const int64_t* off, int64_t ns, unsigned long long* best,
+                           cudaStream_t s);
+int64_t upsample_scan_blocks(int64_t ns);
+cudaError_t launch_upsample_offsets(const int64_t* off, int64_t ns, int32_t factor, long long* block_tmp,
+                                    int64_t* out_off, cudaStream_t s);
+cudaError_t launch_upsample_vertices(const int32_t* xyz, const int64_t* off, int64_t ns, int32_t factor,
+                                     const int64_t* out_off, int32_t* out, cudaStream_t s);
+cudaError_t launch_rescale(const int32_t* xyz, int64_t nv, const int32_t num[3], const int32_t den[3],
+                           const int64_t add[3], int32_t* out, DevState* st, cudaStream_t s);
+
 }  // namespace fc

@@ -1,0 +1,345 @@
+// Kernels beside the connectivity path: the parcellation outputs of a
+// connectivity matrix (Section 3, "Pie-glyphs"), world-mm ingest through an
+// affine, streamline upsampling and the integer rescale between grids
+// (Section 3, "Super-resolving connectivity features").  All are single
+// streaming passes (HBM-bound); every result is exact or rounds as stated.
+#include "fc_device.cuh"
+
+namespace fc {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ int64_t floor_div(int64_t a, int64_t b) {  // b > 0
+  const int64_t q = a / b;
+  return (a % b != 0 && a < 0) ? q - 1 : q;
+}
+
+int grid_for(int64_t items, int per_thread = 1) {
+  const int64_t b = (items + (int64_t)kThreads * per_thread - 1) / ((int64_t)kThreads * per_thread);
+  return (int)(b < 1 ? 1 : (b > (1 << 20) ? (1 << 20) : b));
+}
+
+// ------------------------------------------------------------ parcellation
+// One warp per row: the maximum with the lowest label on ties, the row sum
+// (64-bit), then the fractions: the binary32 nearest to count / sum.  When the
+// sum is below 2^24 both integers are exact in binary32 and one binary32
+// division (IEEE, round to nearest) gives it; otherwise the binary64 quotient
+// rounded to binary32 does (innocuous double rounding: 53 >= 2 * 24 + 2).
+__global__ void __launch_bounds__(kThreads) parcellate_kernel(const int32_t* __restrict__ C, int32_t N, int32_t M,
+                                                              int32_t* __restrict__ label, float* __restrict__ frac) {
+  const int32_t lane = (int32_t)lane_id();
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < N; r += nwarps) {
+    const int32_t* row = C + r * M;
+    long long sum = 0;
+    int32_t best = 0, arg = 0x7fffffff;
+    for (int32_t t = lane; t < M; t += 32) {
+      const int32_t v = __ldg(row + t);
+      sum += v;
+      if (v > best) {  // ascending t per lane: the first maximum stays
+        best = v;
+        arg = t;
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const int32_t ob = __shfl_xor_sync(kFull, best, o), oa = __shfl_xor_sync(kFull, arg, o);
+      if (ob > best || (ob == best && oa < arg)) {
+        best = ob;
+        arg = oa;
+      }
+      sum += __shfl_xor_sync(kFull, sum, o);
+    }
+    if (lane == 0) label[r] = best > 0 ? arg + 1 : 0;
+    if (frac) {
+      if (sum > 0 && sum < (1ll << 24)) {
+        const float s = (float)sum;
+        for (int32_t t = lane; t < M; t += 32) frac[r * M + t] = __fdiv_rn((float)__ldg(row + t), s);
+      } else {
+        const double s = (double)sum;
+        for (int32_t t = lane; t < M; t += 32)
+          frac[r * M + t] = sum > 0 ? __double2float_rn(__ddiv_rn((double)__ldg(row + t), s)) : 0.0f;
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------ ingest
+// v_a = ((A[a][0] x + A[a][1] y) + A[a][2] z) + A[a][3], every operation a
+// round-to-nearest binary32 intrinsic (no contraction), then v_a * 1024
+// rounded to the nearest integer (ties to even).
+struct Affine {
+  float a[12];
+};
+
+__global__ void __launch_bounds__(kThreads) world_to_fixed_kernel(const float* __restrict__ in, int64_t nv,
+                                                                  Affine A, int32_t* __restrict__ out,
+                                                                  DevState* st) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += stride) {
+    const float x = __ldcs(in + 3 * i), y = __ldcs(in + 3 * i + 1), z = __ldcs(in + 3 * i + 2);
+    bool ok = true;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const float v = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(A.a[4 * a], x), __fmul_rn(A.a[4 * a + 1], y)),
+                                          __fmul_rn(A.a[4 * a + 2], z)),
+                                A.a[4 * a + 3]);
+      const float u = __fmul_rn(v, 1024.0f);
+      const bool in_range = u >= -16777216.0f && u < 16777216.0f;  // false for NaN
+      const int32_t r = in_range ? __float2int_rn(u) : 0;
+      ok &= in_range && r >= -16777216 && r < 16777216;
+      out[3 * i + a] = r;
+    }
+    if (!ok) set_error(st, kErrCoord, (int32_t)min(i, (int64_t)0x7fffffff));
+  }
+}
+
+// ---------------------------------------------------------------- upsample
+
+// Largest squared segment length (warp per streamline, lanes over segments).
+__global__ void __launch_bounds__(kThreads) seg_max_kernel(const int32_t* __restrict__ xyz,
+                                                           const int64_t* __restrict__ off, int64_t ns,
+                                                           unsigned long long* best) {
+  const int32_t lane = (int32_t)lane_id();
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  unsigned long long m = 0;
+  for (int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; s < ns; s += nwarps) {
+    const int64_t a = off[s], b = off[s + 1];
+    for (int64_t i = a + lane; i + 1 < b; i += 32) {
+      long long l2 = 0;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const long long d = (long long)__ldg(xyz + 3 * (i + 1) + c) - __ldg(xyz + 3 * i + c);
+        l2 += d * d;
+      }
+      m = max(m, (unsigned long long)l2);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(kFull, m, o));
+  if (lane == 0 && m) atomicMax(best, m);
+}
+
+// Offsets of the upsampled streamlines: out[s] = factor * off[s] - (factor - 1)
+// * (non-empty streamlines before s).  Three passes: per-block counts of
+// non-empty streamlines, their exclusive scan in one block, then each block's
+// own scan.
+constexpr int kScanItems = 8;  // streamlines per thread
+
+__global__ void __launch_bounds__(kThreads) nonempty_counts_kernel(const int64_t* __restrict__ off, int64_t ns,
+                                                                   long long* __restrict__ block_sum) {
+  const int64_t base = (int64_t)blockIdx.x * kThreads * kScanItems;
+  long long c = 0;
+  for (int k = 0; k < kScanItems; ++k) {
+    const int64_t s = base + (int64_t)k * kThreads + threadIdx.x;
+    if (s < ns) c += off[s + 1] > off[s] ? 1 : 0;
+  }
+  __shared__ long long red[kThreads / 32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(kFull, c, o);
+  if (lane_id() == 0) red[threadIdx.x >> 5] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    long long t = 0;
+    for (int w = 0; w < kThreads / 32; ++w) t += red[w];
+    block_sum[blockIdx.x] = t;
+  }
+}
+
+// Exclusive scan of n block sums in place (one block of kThreads threads).
+__global__ void __launch_bounds__(kThreads) scan_blocks_kernel(long long* __restrict__ v, int32_t n) {
+  __shared__ long long part[kThreads];
+  const int32_t per = (n + kThreads - 1) / kThreads;
+  const int32_t lo = min(n, (int32_t)threadIdx.x * per), hi = min(n, lo + per);
+  long long t = 0;
+  for (int32_t i = lo; i < hi; ++i) t += v[i];
+  part[threadIdx.x] = t;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    long long run = 0;
+    for (int k = 0; k < kThreads; ++k) {
+      const long long x = part[k];
+      part[k] = run;
+      run += x;
+    }
+  }
+  __syncthreads();
+  long long run = part[threadIdx.x];
+  for (int32_t i = lo; i < hi; ++i) {
+    const long long x = v[i];
+    v[i] = run;
+    run += x;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) upsample_offsets_kernel(const int64_t* __restrict__ off, int64_t ns,
+                                                                    int32_t factor,
+                                                                    const long long* __restrict__ block_base,
+                                                                    int64_t* __restrict__ out) {
+  // each thread takes kScanItems consecutive streamlines; a block scan of
+  // the per-thread counts gives each thread its first index
+  const int64_t base = (int64_t)blockIdx.x * kThreads * kScanItems + (int64_t)threadIdx.x * kScanItems;
+  long long c = 0;
+  for (int k = 0; k < kScanItems; ++k) {
+    const int64_t s = base + k;
+    if (s < ns) c += off[s + 1] > off[s] ? 1 : 0;
+  }
+  __shared__ long long warp_tot[kThreads / 32];
+  const int32_t lane = (int32_t)lane_id();
+  long long inc = c;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const long long y = __shfl_up_sync(kFull, inc, d);
+    if (lane >= d) inc += y;
+  }
+  if (lane == 31) warp_tot[threadIdx.x >> 5] = inc;
+  __syncthreads();
+  long long before = block_base[blockIdx.x];
+  for (int w = 0; w < (int)(threadIdx.x >> 5); ++w) before += warp_tot[w];
+  long long e = before + inc - c;  // non-empty streamlines before `base`
+  for (int k = 0; k < kScanItems; ++k) {
+    const int64_t s = base + k;
+    if (s > ns) break;
+    out[s] = (int64_t)factor * off[s] - (int64_t)(factor - 1) * e;
+    if (s < ns && off[s + 1] > off[s]) ++e;
+  }
+}
+
+// Upsampled vertices: warp per streamline, lanes over its segments.  With
+// d = q - p = q0 * factor + r0 (0 <= r0 < factor), floor(d * j / factor) =
+// q0 * j + floor(r0 * j / factor): one division per segment and axis, then
+// the points follow with one carry test each.
+__global__ void __launch_bounds__(kThreads) upsample_kernel(const int32_t* __restrict__ xyz,
+                                                            const int64_t* __restrict__ off, int64_t ns,
+                                                            int32_t factor, const int64_t* __restrict__ out_off,
+                                                            int32_t* __restrict__ out) {
+  const int32_t lane = (int32_t)lane_id();
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; s < ns; s += nwarps) {
+    const int64_t a = off[s], b = off[s + 1], o = out_off[s];
+    if (b == a) continue;
+    if (lane == 0) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) out[3 * (out_off[s + 1] - 1) + c] = __ldg(xyz + 3 * (b - 1) + c);
+    }
+    for (int64_t i = a + lane; i + 1 < b; i += 32) {
+      // 64-bit: any int32 input (a point between p and q fits in 32 bits)
+      int64_t p[3], q0[3], r0[3], acc_q[3] = {0, 0, 0}, acc_r[3] = {0, 0, 0};
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        p[c] = __ldg(xyz + 3 * i + c);
+        const int64_t d = (int64_t)__ldg(xyz + 3 * (i + 1) + c) - p[c];
+        q0[c] = floor_div(d, factor);
+        r0[c] = d - q0[c] * factor;
+      }
+      int32_t* dst = out + 3 * (o + (i - a) * factor);
+      for (int32_t j = 0; j < factor; ++j) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          dst[3 * j + c] = (int32_t)(p[c] + acc_q[c]);
+          acc_q[c] += q0[c];
+          acc_r[c] += r0[c];
+          if (acc_r[c] >= factor) {
+            acc_r[c] -= factor;
+            acc_q[c] += 1;
+          }
+        }
+      }
+    }
+  }
+}
+
+// Offsets [ns + 1] start at 0, do not decrease and end at nv.
+__global__ void __launch_bounds__(kThreads) check_offsets_kernel(const int64_t* __restrict__ off, int64_t ns,
+                                                                 int64_t nv, DevState* st) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s <= ns; s += stride) {
+    const int64_t a = off[s];
+    bool ok = a >= 0 && a <= nv;
+    if (s == 0) ok &= a == 0;
+    if (s == ns) ok &= a == nv;
+    if (s < ns) ok &= off[s + 1] >= a;
+    if (!ok) set_error(st, kErrOffsets, (int32_t)min(s, (int64_t)0x7fffffff));
+  }
+}
+
+// ----------------------------------------------------------------- rescale
+struct Rescale {
+  int64_t num[3], den[3], add[3];
+};
+
+__global__ void __launch_bounds__(kThreads) rescale_kernel(const int32_t* __restrict__ xyz, int64_t n_coords,
+                                                           Rescale R, int32_t* __restrict__ out, DevState* st) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n_coords; k += stride) {
+    const int c = (int)(k % 3);
+    const int64_t v = floor_div((int64_t)__ldcs(xyz + k) * R.num[c] + R.add[c], R.den[c]);
+    const bool ok = v >= -16777216 && v < 16777216;
+    out[k] = ok ? (int32_t)v : 0;
+    if (!ok) set_error(st, kErrCoord, (int32_t)min(k / 3, (int64_t)0x7fffffff));
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_parcellate(const int32_t* C, int32_t N, int32_t M, int32_t* label, float* frac, cudaStream_t s) {
+  if (N <= 0) return cudaSuccess;
+  parcellate_kernel<<<grid_for((int64_t)N * 32), kThreads, 0, s>>>(C, N, M, label, frac);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_world_to_fixed(const float* xyz_mm, int64_t nv, const float affine[12], int32_t* out,
+                                  DevState* st, cudaStream_t s) {
+  if (nv <= 0) return cudaSuccess;
+  Affine A;
+  for (int k = 0; k < 12; ++k) A.a[k] = affine[k];
+  world_to_fixed_kernel<<<grid_for(nv, 4), kThreads, 0, s>>>(xyz_mm, nv, A, out, st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_seg_max(const int32_t* xyz, const int64_t* off, int64_t ns, unsigned long long* best,
+                           cudaStream_t s) {
+  if (ns <= 0) return cudaSuccess;
+  seg_max_kernel<<<grid_for(ns * 32, 8), kThreads, 0, s>>>(xyz, off, ns, best);
+  return cudaGetLastError();
+}
+
+int64_t upsample_scan_blocks(int64_t ns) { return (ns + 1 + (int64_t)kThreads * kScanItems - 1) / ((int64_t)kThreads * kScanItems); }
+
+cudaError_t launch_check_offsets(const int64_t* off, int64_t ns, int64_t nv, DevState* st, cudaStream_t s) {
+  check_offsets_kernel<<<grid_for(ns + 1, 4), kThreads, 0, s>>>(off, ns, nv, st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_upsample_offsets(const int64_t* off, int64_t ns, int32_t factor, long long* block_tmp,
+                                    int64_t* out_off, cudaStream_t s) {
+  const int64_t nb = upsample_scan_blocks(ns);
+  nonempty_counts_kernel<<<(unsigned)nb, kThreads, 0, s>>>(off, ns, block_tmp);
+  scan_blocks_kernel<<<1, kThreads, 0, s>>>(block_tmp, (int32_t)nb);
+  upsample_offsets_kernel<<<(unsigned)nb, kThreads, 0, s>>>(off, ns, factor, block_tmp, out_off);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_upsample_vertices(const int32_t* xyz, const int64_t* off, int64_t ns, int32_t factor,
+                                     const int64_t* out_off, int32_t* out, cudaStream_t s) {
+  if (ns <= 0) return cudaSuccess;
+  upsample_kernel<<<grid_for(ns * 32, 8), kThreads, 0, s>>>(xyz, off, ns, factor, out_off, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rescale(const int32_t* xyz, int64_t nv, const int32_t num[3], const int32_t den[3],
+                           const int64_t add[3], int32_t* out, DevState* st, cudaStream_t s) {
+  if (nv <= 0) return cudaSuccess;
+  Rescale R;
+  for (int c = 0; c < 3; ++c) {
+    R.num[c] = num[c];
+    R.den[c] = den[c];
+    R.add[c] = add[c];
+  }
+  rescale_kernel<<<grid_for(nv * 3, 4), kThreads, 0, s>>>(xyz, nv * 3, R, out, st);
+  return cudaGetLastError();
+}
+
+}  // namespace fc

@@ -45,7 +45,8 @@ EXPORTED = [
     "fastcod_set_option", "fastcod_last_error", "fastcod_batch_run", "fastcod_batch_get_stats",
     "fastcod_batch_get_info", "fastcod_server_create", "fastcod_server_submit", "fastcod_server_push_chunk",
     "fastcod_server_poll", "fastcod_server_wait", "fastcod_server_cancel", "fastcod_server_request_info",
-    "fastcod_server_destroy", "fastcod_connectivity_noalloc",
+    "fastcod_server_destroy", "fastcod_connectivity_noalloc", "fastcod_parcellate", "fastcod_world_to_fixed",
+    "fastcod_add_streamlines_mm", "fastcod_upsample", "fastcod_upsample_factor", "fastcod_rescale",
 ]
 
 
@@ -119,6 +120,12 @@ def _load():
         "fastcod_server_destroy": ([vp], ctypes.c_int),
         "fastcod_connectivity_noalloc": ([ctypes.c_int, vp, vp, vp, i32, i32, i32, i32, i32, vp, i64, vp, i64, vp,
                                           vp], ctypes.c_int),
+        "fastcod_parcellate": ([vp, i32, vp, vp], ctypes.c_int),
+        "fastcod_world_to_fixed": ([vp, vp, i64, vp, vp], ctypes.c_int),
+        "fastcod_add_streamlines_mm": ([vp, vp, i64, vp, i64, vp], ctypes.c_int),
+        "fastcod_upsample": ([vp, vp, i64, vp, i64, i32, vp, i64, vp], ctypes.c_int),
+        "fastcod_upsample_factor": ([vp, vp, i64, vp, i64, i32, ctypes.POINTER(i32)], ctypes.c_int),
+        "fastcod_rescale": ([vp, vp, i64, vp, vp, vp, vp], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -319,6 +326,57 @@ def fastcod_connectivity_noalloc(device, stream, roi, lab, dims, n_roi, n_target
     if rc != FASTCOD_OK:
         raise FastCodError(rc, lib.fastcod_last_error(None).decode())
     return rc
+
+
+def fastcod_parcellate(ctx, which: int, label_out, fractions_out=None):
+    return _check(ctx, lib.fastcod_parcellate(ctx, int(which), _ptr(label_out), _ptr(fractions_out)))
+
+
+def _affine(affine):
+    a = np.ascontiguousarray(np.asarray(affine, dtype=np.float32).reshape(-1)[:12])
+    if a.size != 12:
+        raise ValueError("affine needs 12 values (3 x 4, row-major)")
+    return a
+
+
+def fastcod_world_to_fixed(ctx, xyz_mm, affine, xyz_out):
+    a = _affine(affine)
+    return _check(ctx, lib.fastcod_world_to_fixed(ctx, _ptr(xyz_mm), int(xyz_mm.shape[0]), a.ctypes.data,
+                                                  _ptr(xyz_out)))
+
+
+def fastcod_add_streamlines_mm(ctx, xyz_mm, offsets, affine):
+    a = _affine(affine)
+    return _check(ctx, lib.fastcod_add_streamlines_mm(ctx, _ptr(xyz_mm), int(xyz_mm.shape[0]), _ptr(offsets),
+                                                      int(offsets.shape[0]) - 1, a.ctypes.data))
+
+
+def upsampled_count(offsets_host: np.ndarray, factor: int) -> int:
+    """Vertices of the upsampled tractogram (host offsets)."""
+    T = np.diff(np.asarray(offsets_host, dtype=np.int64))
+    nonempty = int(np.count_nonzero(T))
+    return (int(T.sum()) - nonempty) * int(factor) + nonempty
+
+
+def fastcod_upsample(ctx, xyz, offsets, factor: int, xyz_out, offsets_out):
+    return _check(ctx, lib.fastcod_upsample(ctx, _ptr(xyz), int(xyz.shape[0]), _ptr(offsets),
+                                            int(offsets.shape[0]) - 1, int(factor), _ptr(xyz_out),
+                                            int(xyz_out.shape[0]), _ptr(offsets_out)))
+
+
+def fastcod_upsample_factor(ctx, xyz, offsets, spacing: int) -> int:
+    k = ctypes.c_int32()
+    _check(ctx, lib.fastcod_upsample_factor(ctx, _ptr(xyz), int(xyz.shape[0]), _ptr(offsets),
+                                           int(offsets.shape[0]) - 1, int(spacing), ctypes.byref(k)))
+    return int(k.value)
+
+
+def fastcod_rescale(ctx, xyz, num, den, add, xyz_out):
+    n = np.ascontiguousarray(num, dtype=np.int32)
+    d = np.ascontiguousarray(den, dtype=np.int32)
+    a = np.ascontiguousarray(add, dtype=np.int64)
+    return _check(ctx, lib.fastcod_rescale(ctx, _ptr(xyz), int(xyz.shape[0]), n.ctypes.data, d.ctypes.data,
+                                           a.ctypes.data, _ptr(xyz_out)))
 
 
 class Context:

@@ -1,0 +1,193 @@
+"""GPU parity of the entry points beside the path, through the C ABI, against
+the oracle, bit-exact: parcellation outputs (labels and binary32 fractions),
+world-mm ingest (and connectivity from world-mm input), upsampling (offsets,
+vertices, the factor rule, and the super-resolved connectivity) and the
+integer rescale; host and device buffers; invalid input rejected."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from synth import tiny
+from tests.gpu_helpers import as_device
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fc():
+    from paper_2302_09247_gb300 import fastcod
+    return fastcod
+
+
+def _subject_with_ties(seed):
+    # tiny grids with few labels give rows with equal counts and rows of zeros
+    rng = np.random.default_rng(seed)
+    dims = (10, 9, 8)
+    roi, lab, N, M = tiny.random_volumes(rng, dims, n_roi=30, n_labels=4, p_roi=0.3, p_lab=0.3, many_to_one=True)
+    xyz, off = tiny.random_streamlines(rng, dims, 300, max_len=10)
+    return roi, lab, dims, N, M, xyz, off
+
+
+@pytest.mark.parametrize("where", ["host", "device"])
+def test_parcellate_matches_oracle(fc, where):
+    import torch
+    cases = [_subject_with_ties(s) for s in range(3)]
+    vols, tr = synth.make_subject(1, n_streamlines=100_000)
+    cases.append((vols.roi, vols.lab, vols.dims, vols.n_roi, vols.n_targets, tr.xyz, tr.offsets))
+    for roi, lab, dims, N, M, xyz, off in cases:
+        Cr, Cer, _ = oracle.connectivity(roi, lab, dims, N, M, xyz, off)
+        with fc.Context(0) as ctx:
+            ctx.set_volumes(as_device(roi), as_device(lab), dims, N, M)
+            ctx.add_streamlines(as_device(xyz), as_device(off))
+            for which, ref in ((0, Cr), (1, Cer)):
+                lr, fr = oracle.parcellate(ref)
+                if where == "host":
+                    label = np.full(N, -5, np.int32)
+                    frac = np.full((N, M), -1, np.float32)
+                    fc.fastcod_parcellate(ctx.ctx, which, label, frac)
+                else:
+                    lt = torch.full((N,), -5, dtype=torch.int32, device="cuda:0")
+                    ft = torch.full((N, M), -1.0, dtype=torch.float32, device="cuda:0")
+                    fc.fastcod_parcellate(ctx.ctx, which, lt, ft)
+                    label, frac = lt.cpu().numpy(), ft.cpu().numpy()
+                np.testing.assert_array_equal(label, lr)
+                np.testing.assert_array_equal(frac.view(np.uint32), fr.view(np.uint32))  # bit-exact
+                label2 = np.full(N, -5, np.int32)
+                fc.fastcod_parcellate(ctx.ctx, which, label2, None)  # labels only
+                np.testing.assert_array_equal(label2, lr)
+
+
+def _affine(rng):
+    A = np.zeros((3, 4), dtype=np.float32)
+    A[:, :3] = (np.eye(3) / 1.25 + rng.normal(0, 0.03, (3, 3))).astype(np.float32)
+    A[:, 3] = rng.uniform(-40, 60, 3).astype(np.float32)
+    return A
+
+
+@pytest.mark.parametrize("where", ["host", "device"])
+def test_world_to_fixed_matches_oracle(fc, where):
+    import torch
+    rng = np.random.default_rng(11)
+    A = _affine(rng)
+    x = rng.uniform(-150, 150, size=(100_003, 3)).astype(np.float32)
+    x[:7] = [[0, 0, 0], [1e-30, -1e-30, 0], [0.5, 0.25, 0.125], [-150, 150, -150], [3.9e-3, 7.81e-4, 1.0],
+             [100.0, 100.0, 100.0], [-1e-3, -2e-3, -3e-3]]
+    want = oracle.world_to_fixed(x, A)
+    with fc.Context(0) as ctx:
+        if where == "host":
+            out = np.full(x.shape, -9, np.int32)
+            fc.fastcod_world_to_fixed(ctx.ctx, x, A, out)
+        else:
+            ot = torch.full(x.shape, -9, dtype=torch.int32, device="cuda:0")
+            fc.fastcod_world_to_fixed(ctx.ctx, as_device(x), A, ot)
+            out = ot.cpu().numpy()
+        np.testing.assert_array_equal(out, want)
+        for bad in ([[np.nan, 0, 0]], [[np.inf, 0, 0]], [[1e9, 0, 0]]):
+            with pytest.raises(fc.FastCodError) as e:
+                fc.fastcod_world_to_fixed(ctx.ctx, np.array(bad, np.float32), A, np.zeros((1, 3), np.int32))
+            assert e.value.code == fc.FASTCOD_EINVAL
+
+
+def test_add_streamlines_mm_equals_fixed_point_path(fc):
+    rng = np.random.default_rng(12)
+    vols, tr = synth.make_subject(0)
+    res = np.float32(1.25)
+    A = np.zeros((3, 4), dtype=np.float32)  # world = 1.25 mm per voxel, origin at (-20, -20, -20) mm
+    A[:, :3] = np.eye(3, dtype=np.float32) / res
+    A[:, 3] = np.float32(20.0) / res
+    x_mm = ((tr.xyz.astype(np.float64) / 1024.0) * 1.25 - 20.0).astype(np.float32)
+    fixed = oracle.world_to_fixed(x_mm, A)
+    Cr, Cer, sr = oracle.connectivity(vols.roi, vols.lab, vols.dims, vols.n_roi, vols.n_targets, fixed, tr.offsets)
+    with fc.Context(0) as ctx:
+        ctx.set_volumes(vols.roi, vols.lab, vols.dims, vols.n_roi, vols.n_targets)
+        fc.fastcod_add_streamlines_mm(ctx.ctx, x_mm, tr.offsets, A)
+        fc.fastcod_add_streamlines_mm(ctx.ctx, as_device(x_mm), as_device(tr.offsets), A)
+        C, Ce, st = ctx.connectivity(), ctx.endpoint_connectivity(), ctx.stats()
+    np.testing.assert_array_equal(C, 2 * Cr)
+    np.testing.assert_array_equal(Ce, 2 * Cer)
+    assert st["voxel_steps"] == 2 * sr["voxel_steps"]
+
+
+@pytest.mark.parametrize("factor", [1, 2, 5])
+@pytest.mark.parametrize("where", ["host", "device"])
+def test_upsample_matches_oracle(fc, factor, where):
+    import torch
+    rng = np.random.default_rng(20 + factor)
+    xyz, off = tiny.random_streamlines(rng, (12, 12, 12), 5000, max_len=30)  # empty and one-vertex ones too
+    want_xyz, want_off = oracle.upsample(xyz, off, factor)
+    nv_out = fc.upsampled_count(off, factor)
+    assert nv_out == len(want_xyz)
+    with fc.Context(0) as ctx:
+        if where == "host":
+            out = np.full((nv_out, 3), -9, np.int32)
+            oo = np.full(len(off), -9, np.int64)
+            fc.fastcod_upsample(ctx.ctx, xyz, off, factor, out, oo)
+        else:
+            ot = torch.full((nv_out, 3), -9, dtype=torch.int32, device="cuda:0")
+            oot = torch.full((len(off),), -9, dtype=torch.int64, device="cuda:0")
+            fc.fastcod_upsample(ctx.ctx, as_device(xyz), as_device(off), factor, ot, oot)
+            out, oo = ot.cpu().numpy(), oot.cpu().numpy()
+        np.testing.assert_array_equal(oo, want_off)
+        np.testing.assert_array_equal(out, want_xyz)
+        with pytest.raises(fc.FastCodError):  # wrong output size
+            fc.fastcod_upsample(ctx.ctx, xyz, off, factor, np.zeros((nv_out + 1, 3), np.int32), oo)
+        bad = off.copy()
+        bad[5], bad[6] = bad[6] + 1, bad[5]
+        with pytest.raises(fc.FastCodError):  # invalid offsets
+            fc.fastcod_upsample(ctx.ctx, xyz, bad, factor, out, oo)
+
+
+def test_upsample_factor_matches_oracle(fc):
+    rng = np.random.default_rng(30)
+    with fc.Context(0) as ctx:
+        for trial in range(6):
+            xyz, off = tiny.random_streamlines(rng, (20, 20, 20), 500, max_len=20)
+            for spacing in (1, 100, 512, 1023, 100000):
+                assert fc.fastcod_upsample_factor(ctx.ctx, xyz, off, spacing) == \
+                    oracle.upsample_factor(xyz, off, spacing)
+
+
+def test_super_resolved_connectivity(fc):
+    # the paper's super-resolution: upsample so that the spacing is at most
+    # half a voxel, then count on the grid; GPU upsampling + GPU connectivity
+    # equal the oracle's upsampling + oracle connectivity, in both voxel rules
+    vols, tr = synth.make_subject(0, n_streamlines=4000)
+    with fc.Context(0) as ctx:
+        k = fc.fastcod_upsample_factor(ctx.ctx, tr.xyz, tr.offsets, 512)
+        assert k == oracle.upsample_factor(tr.xyz, tr.offsets, 512)
+        n = fc.upsampled_count(tr.offsets, k)
+        ux, uo = np.empty((n, 3), np.int32), np.empty(len(tr.offsets), np.int64)
+        fc.fastcod_upsample(ctx.ctx, tr.xyz, tr.offsets, k, ux, uo)
+    wx, wo = oracle.upsample(tr.xyz, tr.offsets, k)
+    np.testing.assert_array_equal(ux, wx)
+    for sampling in (0, 1):
+        with fc.Context(0) as ctx:
+            ctx.set_option(fc.FASTCOD_OPT_SAMPLING, sampling)
+            ctx.set_volumes(vols.roi, vols.lab, vols.dims, vols.n_roi, vols.n_targets)
+            ctx.add_streamlines(ux, uo)
+            C = ctx.connectivity()
+        Cr, _, _ = oracle.connectivity(vols.roi, vols.lab, vols.dims, vols.n_roi, vols.n_targets, wx, wo,
+                                       oracle.VERTEX_SAMPLED if sampling else 0)
+        np.testing.assert_array_equal(C, Cr)
+
+
+@pytest.mark.parametrize("where", ["host", "device"])
+def test_rescale_matches_oracle(fc, where):
+    import torch
+    rng = np.random.default_rng(40)
+    xyz = rng.integers(-300000, 300000, size=(50_001, 3)).astype(np.int32)
+    num, den, add = [25, 25, 25], [14, 14, 14], [512 * 11, 512 * 11, 512 * 11]
+    want = oracle.rescale(xyz, num, den, add)
+    with fc.Context(0) as ctx:
+        if where == "host":
+            out = np.full(xyz.shape, -9, np.int32)
+            fc.fastcod_rescale(ctx.ctx, xyz, num, den, add, out)
+        else:
+            ot = torch.full(xyz.shape, -9, dtype=torch.int32, device="cuda:0")
+            fc.fastcod_rescale(ctx.ctx, as_device(xyz), num, den, add, ot)
+            out = ot.cpu().numpy()
+        np.testing.assert_array_equal(out, want)
+        with pytest.raises(fc.FastCodError):
+            fc.fastcod_rescale(ctx.ctx, np.array([[16000000, 0, 0]], np.int32), [2, 1, 1], [1, 1, 1], [0, 0, 0],
+                               np.zeros((1, 3), np.int32))
