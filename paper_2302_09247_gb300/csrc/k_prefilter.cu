@@ -44,9 +44,12 @@ namespace fc {
 namespace {
 
 constexpr int kHalfLog2 = 8;
-constexpr int kHalf = 1 << kHalfLog2;     // vertices per half-window (= per TMA piece)
-constexpr int kWinLog2 = kHalfLog2 + 1;
+constexpr int kHalf = 1 << kHalfLog2;     // vertices per piece (= per TMA slot)
+constexpr int kPieces = 4;                // pieces per window (even)
+constexpr int kWinLog2 = kHalfLog2 + (kPieces == 4 ? 2 : 1);
 constexpr int kWin = 1 << kWinLog2;       // vertices per window
+constexpr int kCountWords = kPieces / 2;  // per-lane hit counts: two pieces (R, T bytes) per word
+static_assert(kPieces == 2 || kPieces == 4, "two or four pieces per window");
 constexpr int kVpl = kHalf / 32;          // vertices per lane per half
 constexpr int kLaneWords = kVpl * 3;      // 24 int32 per lane per half
 constexpr int kHalfWords = kHalf * 3;     // 768 int32 = 3072 bytes
@@ -265,26 +268,38 @@ __device__ __forceinline__ uint32_t scan_half(Scan& sc, const VolView& v, const 
   return h8;
 }
 
-// 3. End of window W: hit counts of both halves (h0, h1) and the decisions
-//    at its nbw boundaries, 32 per round.
+// 3. End of window W: hit counts of its pieces (hh: piece h's hit bits at
+//    bits 8h) and the decisions at its nbw boundaries, 32 per round.
 __device__ __forceinline__ void window_end(Scan& sc, WarpShared& ws, int32_t W, int32_t nbw, int32_t b_first,
-                                           uint32_t h0, uint32_t h1, bool prefilter, int32_t* surv, DevState* gst) {
+                                           uint32_t hh, bool prefilter, int32_t* surv, DevState* gst) {
   const int32_t lane = (int32_t)lane_id();
-  // per-lane counts in four byte fields (R0, T0, R1, T1); a field's prefix
-  // over the warp is at most 4 * 32 = 128, so fields never carry
-  const uint32_t c = (uint32_t)__popc(h0 & 0x55u) | ((uint32_t)__popc(h0 & 0xaau) << 8) |
-                     ((uint32_t)__popc(h1 & 0x55u) << 16) | ((uint32_t)__popc(h1 & 0xaau) << 24);
-  uint32_t inc = c;
+  // per-lane counts in byte fields (R and T of two pieces per word); a
+  // field's prefix over the warp is at most 4 * 32 = 128, so fields never
+  // carry
+  uint32_t excl[kCountWords], totw[kCountWords];
 #pragma unroll
-  for (int d = 1; d < 32; d <<= 1) {
-    const uint32_t y = __shfl_up_sync(kFull, inc, d);
-    if (lane >= d) inc += y;
+  for (int w = 0; w < kCountWords; ++w) {
+    const uint32_t b0 = (hh >> (16 * w)) & 0xffu, b1 = (hh >> (16 * w + 8)) & 0xffu;
+    const uint32_t c = (uint32_t)__popc(b0 & 0x55u) | ((uint32_t)__popc(b0 & 0xaau) << 8) |
+                       ((uint32_t)__popc(b1 & 0x55u) << 16) | ((uint32_t)__popc(b1 & 0xaau) << 24);
+    uint32_t inc = c;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t y = __shfl_up_sync(kFull, inc, d);
+      if (lane >= d) inc += y;
+    }
+    excl[w] = inc - c;
+    totw[w] = __shfl_sync(kFull, inc, 31);
   }
-  const uint32_t excl = inc - c;
-  const uint32_t tot = __shfl_sync(kFull, inc, 31);
-  const uint32_t tR0 = tot & 0xffu, tT0 = (tot >> 8) & 0xffu;
-  const uint32_t tR = tR0 + ((tot >> 16) & 0xffu), tT = tT0 + (tot >> 24);
-  const uint32_t hh01 = h0 | (h1 << 8);
+  // hit counts of the pieces before piece h, and of the whole window
+  uint32_t baseR[kPieces + 1], baseT[kPieces + 1];
+  baseR[0] = baseT[0] = 0u;
+#pragma unroll
+  for (int h = 0; h < kPieces; ++h) {
+    const uint32_t f = totw[h >> 1] >> (16 * (h & 1));
+    baseR[h + 1] = baseR[h] + (f & 0xffu);
+    baseT[h + 1] = baseT[h] + ((f >> 8) & 0xffu);
+  }
 
   int64_t s = sc.s_cur;
   int32_t prev = sc.last_b;
@@ -295,18 +310,25 @@ __device__ __forceinline__ void window_end(Scan& sc, WarpShared& ws, int32_t W, 
     const int32_t x = min(max(b - W, 0), kWin);
     const int32_t hx = x >> kHalfLog2, xi = x & (kHalf - 1);
     const int32_t src = xi >> 3, o = xi & 7;
-    const uint32_t e = __shfl_sync(kFull, excl, src);
-    const uint32_t hh = (__shfl_sync(kFull, hh01, src) >> (hx == 1 ? 8 : 0)) & 0xffu;
-    uint32_t cR, cT;
-    if (hx >= 2) {
-      cR = tR;
-      cT = tT;
-    } else if (hx == 0) {
-      cR = (e & 0xffu) + (uint32_t)__popc(hh & 0x55u & lowmask(o));
-      cT = ((e >> 8) & 0xffu) + (uint32_t)__popc(hh & 0xaau & lowmask(o + 1));
-    } else {
-      cR = tR0 + ((e >> 16) & 0xffu) + (uint32_t)__popc(hh & 0x55u & lowmask(o));
-      cT = tT0 + (e >> 24) + (uint32_t)__popc(hh & 0xaau & lowmask(o + 1));
+    uint32_t e = __shfl_sync(kFull, excl[0], src);
+#pragma unroll
+    for (int w = 1; w < kCountWords; ++w) {
+      const uint32_t ew = __shfl_sync(kFull, excl[w], src);
+      if ((hx >> 1) == w) e = ew;
+    }
+    const uint32_t hb = (__shfl_sync(kFull, hh, src) >> (8 * (hx & (kPieces - 1)))) & 0xffu;
+    uint32_t bR = baseR[kPieces], bT = baseT[kPieces];
+#pragma unroll
+    for (int h = kPieces - 1; h >= 0; --h)
+      if (hx == h) {
+        bR = baseR[h];
+        bT = baseT[h];
+      }
+    uint32_t cR = bR, cT = bT;
+    if (hx < kPieces) {
+      const int sh = 16 * (hx & 1);
+      cR += ((e >> sh) & 0xffu) + (uint32_t)__popc(hb & 0x55u & lowmask(o));
+      cT += ((e >> (sh + 8)) & 0xffu) + (uint32_t)__popc(hb & 0xaau & lowmask(o + 1));
     }
     cR += sc.cumR;
     cT += sc.cumT;
@@ -337,8 +359,8 @@ __device__ __forceinline__ void window_end(Scan& sc, WarpShared& ws, int32_t W, 
   }
   sc.s_cur = s;
   sc.carry = (sc.last_b - W == kWin) ? 1u : 0u;
-  sc.cumR += tR;
-  sc.cumT += tT;
+  sc.cumR += baseR[kPieces];
+  sc.cumT += baseT[kPieces];
 }
 
 // Set up the scan of streamlines [s_lo, s_hi) of t; false when there is
@@ -421,23 +443,29 @@ __device__ __forceinline__ void load_half(const Tract& t, int64_t hq, int32_t (&
   }
 }
 
-// Window loop of the direct loader: the next half is loaded while the
+// Window loop of the direct loader: the next piece is loaded while the
 // current one is scanned.
 template <bool kSmem>
 __device__ __forceinline__ void scan_range_direct(Scan& sc, const VolView& v, const uint32_t* nw, const Tract& t,
                                                   bool prefilter, WarpShared& ws, int32_t* surv, DevState* gst) {
   const int64_t q0 = (int64_t)sc.V0 >> kWinLog2, q1 = (int64_t)(sc.V1 - 1) >> kWinLog2;
+  const int64_t hq_end = kPieces * (q1 + 1);
   int32_t pa[kLaneWords], pb[kLaneWords];
-  load_half(t, 2 * q0, pa);
+  int64_t hq = kPieces * q0;
+  load_half(t, hq, pa);
   for (int64_t q = q0; q <= q1 && !sc.abort; ++q) {
     const int32_t W = (int32_t)(q << kWinLog2);
     int32_t nbw, b_first;
     window_begin(sc, ws, W, nbw, b_first);
-    load_half(t, 2 * q + 1, pb);
-    const uint32_t h0 = scan_half<kSmem>(sc, v, nw, pa, 0, W, ws);
-    if (q < q1) load_half(t, 2 * q + 2, pa);
-    const uint32_t h1 = scan_half<kSmem>(sc, v, nw, pb, 1, W, ws);
-    window_end(sc, ws, W, nbw, b_first, h0, h1, prefilter, surv, gst);
+    uint32_t hh = 0u;
+#pragma unroll 1
+    for (int h = 0; h < kPieces; h += 2, hq += 2) {
+      load_half(t, hq + 1, pb);
+      hh |= scan_half<kSmem>(sc, v, nw, pa, h, W, ws) << (8 * h);
+      if (hq + 2 < hq_end) load_half(t, hq + 2, pa);
+      hh |= scan_half<kSmem>(sc, v, nw, pb, h + 1, W, ws) << (8 * (h + 1));
+    }
+    window_end(sc, ws, W, nbw, b_first, hh, prefilter, surv, gst);
   }
 }
 
@@ -547,36 +575,34 @@ __device__ __forceinline__ bool scan_range_tma(Scan& sc, const VolView& v, const
                                                bool prefilter, WarpShared& ws, Ring& r, int32_t* surv,
                                                DevState* gst) {
   const int64_t q0 = (int64_t)sc.V0 >> kWinLog2, q1 = (int64_t)(sc.V1 - 1) >> kWinLog2;
-  const int64_t hq_end = 2 * q1 + 2;
-  int64_t taken = 2 * q0;                           // halves [2 q0, taken) consumed
-  int64_t issued = min(hq_end, 2 * q0 + kStages);   // halves [taken, issued) in flight
+  const int64_t hq_end = kPieces * (q1 + 1);
+  int64_t taken = kPieces * q0;                          // pieces [kPieces q0, taken) consumed
+  int64_t issued = min(hq_end, kPieces * q0 + kStages);  // pieces [taken, issued) in flight
   if (lane_id() == 0) {
     uint32_t k = r.slot;
-    for (int64_t hq = 2 * q0; hq < issued; ++hq) {
+    for (int64_t hq = kPieces * q0; hq < issued; ++hq) {
       r.issue(t, hq, k);
       k = (k + 1 == (uint32_t)kStages) ? 0u : k + 1;
     }
   }
   __syncwarp();
   bool ok = true;
-  for (int64_t q = q0; q <= q1 && !sc.abort; ++q) {
+  for (int64_t q = q0; q <= q1 && !sc.abort && ok; ++q) {
     const int32_t W = (int32_t)(q << kWinLog2);
     int32_t nbw, b_first;
     window_begin(sc, ws, W, nbw, b_first);
-    int32_t p[kLaneWords];
-    if (!ring_take(r, t, issued, hq_end, p)) {
-      ok = false;
-      break;
+    uint32_t hh = 0u;
+#pragma unroll 1
+    for (int h = 0; h < kPieces; ++h) {
+      int32_t p[kLaneWords];
+      if (!ring_take(r, t, issued, hq_end, p)) {
+        ok = false;
+        break;
+      }
+      ++taken;
+      hh |= scan_half<kSmem>(sc, v, nw, p, h, W, ws) << (8 * h);
     }
-    ++taken;
-    const uint32_t h0 = scan_half<kSmem>(sc, v, nw, p, 0, W, ws);
-    if (!ring_take(r, t, issued, hq_end, p)) {
-      ok = false;
-      break;
-    }
-    ++taken;
-    const uint32_t h1 = scan_half<kSmem>(sc, v, nw, p, 1, W, ws);
-    window_end(sc, ws, W, nbw, b_first, h0, h1, prefilter, surv, gst);
+    if (ok) window_end(sc, ws, W, nbw, b_first, hh, prefilter, surv, gst);
   }
   if (!ok) {
     if (lane_id() == 0) set_error(sc.sst, kErrTimeout, (int32_t)sc.s_lo);
