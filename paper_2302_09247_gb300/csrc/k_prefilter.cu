@@ -36,8 +36,14 @@
 // a ring of three 3072-byte slots per warp in shared memory, cp.async.bulk +
 // mbarrier, L2 evict-first) and direct streaming loads into registers (the
 // next half in flight while the current one is processed).
+#include <type_traits>
+
 #include "fc_device.cuh"
 #include "fc_tma.cuh"
+
+#ifndef PREFILTER_PIECES
+#define PREFILTER_PIECES 8
+#endif
 
 namespace fc {
 
@@ -45,11 +51,13 @@ namespace {
 
 constexpr int kHalfLog2 = 8;
 constexpr int kHalf = 1 << kHalfLog2;     // vertices per piece (= per TMA slot)
-constexpr int kPieces = 4;                // pieces per window (even)
-constexpr int kWinLog2 = kHalfLog2 + (kPieces == 4 ? 2 : 1);
+constexpr int kPieces = PREFILTER_PIECES;  // pieces per window
+constexpr int kWinLog2 = kHalfLog2 + ilog2(kPieces);
 constexpr int kWin = 1 << kWinLog2;       // vertices per window
 constexpr int kCountWords = kPieces / 2;  // per-lane hit counts: two pieces (R, T bytes) per word
-static_assert(kPieces == 2 || kPieces == 4, "two or four pieces per window");
+static_assert(kPieces == 2 || kPieces == 4 || kPieces == 8, "2, 4 or 8 pieces per window");
+// a lane's hit bits of every piece of a window, 8 per piece
+using HitWord = typename std::conditional<(kPieces > 4), unsigned long long, uint32_t>::type;
 constexpr int kVpl = kHalf / 32;          // vertices per lane per half
 constexpr int kLaneWords = kVpl * 3;      // 24 int32 per lane per half
 constexpr int kHalfWords = kHalf * 3;     // 768 int32 = 3072 bytes
@@ -181,7 +189,7 @@ __device__ __noinline__ uint32_t long_box(const uint32_t* bricks, int32_t dx, in
 __device__ __forceinline__ void window_begin(Scan& sc, WarpShared& ws, int32_t W, int32_t& nbw, int32_t& b_first) {
   const int32_t lane = (int32_t)lane_id();
   cache_seek(sc);
-  if (lane < kWin / 32) ws.st[lane] = 0u;
+  for (int i = lane; i < kWin / 32; i += 32) ws.st[i] = 0u;
   __syncwarp();
   nbw = 0;
   b_first = kInf;
@@ -271,7 +279,7 @@ __device__ __forceinline__ uint32_t scan_half(Scan& sc, const VolView& v, const 
 // 3. End of window W: hit counts of its pieces (hh: piece h's hit bits at
 //    bits 8h) and the decisions at its nbw boundaries, 32 per round.
 __device__ __forceinline__ void window_end(Scan& sc, WarpShared& ws, int32_t W, int32_t nbw, int32_t b_first,
-                                           uint32_t hh, bool prefilter, int32_t* surv, DevState* gst) {
+                                           HitWord hh, bool prefilter, int32_t* surv, DevState* gst) {
   const int32_t lane = (int32_t)lane_id();
   // per-lane counts in byte fields (R and T of two pieces per word); a
   // field's prefix over the warp is at most 4 * 32 = 128, so fields never
@@ -279,7 +287,7 @@ __device__ __forceinline__ void window_end(Scan& sc, WarpShared& ws, int32_t W, 
   uint32_t excl[kCountWords], totw[kCountWords];
 #pragma unroll
   for (int w = 0; w < kCountWords; ++w) {
-    const uint32_t b0 = (hh >> (16 * w)) & 0xffu, b1 = (hh >> (16 * w + 8)) & 0xffu;
+    const uint32_t b0 = (uint32_t)(hh >> (16 * w)) & 0xffu, b1 = (uint32_t)(hh >> (16 * w + 8)) & 0xffu;
     const uint32_t c = (uint32_t)__popc(b0 & 0x55u) | ((uint32_t)__popc(b0 & 0xaau) << 8) |
                        ((uint32_t)__popc(b1 & 0x55u) << 16) | ((uint32_t)__popc(b1 & 0xaau) << 24);
     uint32_t inc = c;
@@ -316,7 +324,7 @@ __device__ __forceinline__ void window_end(Scan& sc, WarpShared& ws, int32_t W, 
       const uint32_t ew = __shfl_sync(kFull, excl[w], src);
       if ((hx >> 1) == w) e = ew;
     }
-    const uint32_t hb = (__shfl_sync(kFull, hh, src) >> (8 * (hx & (kPieces - 1)))) & 0xffu;
+    const uint32_t hb = (uint32_t)(__shfl_sync(kFull, hh, src) >> (8 * (hx & (kPieces - 1)))) & 0xffu;
     uint32_t bR = baseR[kPieces], bT = baseT[kPieces];
 #pragma unroll
     for (int h = kPieces - 1; h >= 0; --h)
@@ -444,26 +452,30 @@ __device__ __forceinline__ void load_half(const Tract& t, int64_t hq, int32_t (&
 }
 
 // Window loop of the direct loader: the next piece is loaded while the
-// current one is scanned.
+// current one is scanned.  Pieces wholly outside the scan's vertex range
+// (at the ends of its first and last windows) are neither loaded nor scanned:
+// the range's first vertex starts a streamline, so no state carries over them.
 template <bool kSmem>
 __device__ __forceinline__ void scan_range_direct(Scan& sc, const VolView& v, const uint32_t* nw, const Tract& t,
                                                   bool prefilter, WarpShared& ws, int32_t* surv, DevState* gst) {
   const int64_t q0 = (int64_t)sc.V0 >> kWinLog2, q1 = (int64_t)(sc.V1 - 1) >> kWinLog2;
-  const int64_t hq_end = kPieces * (q1 + 1);
-  int32_t pa[kLaneWords], pb[kLaneWords];
-  int64_t hq = kPieces * q0;
-  load_half(t, hq, pa);
+  const int64_t hq_lo = (int64_t)sc.V0 >> kHalfLog2, hq_hi = ((int64_t)(sc.V1 - 1) >> kHalfLog2) + 1;
+  int32_t p[kLaneWords], nx[kLaneWords];
+  load_half(t, hq_lo, nx);
   for (int64_t q = q0; q <= q1 && !sc.abort; ++q) {
     const int32_t W = (int32_t)(q << kWinLog2);
     int32_t nbw, b_first;
     window_begin(sc, ws, W, nbw, b_first);
-    uint32_t hh = 0u;
+    HitWord hh = 0u;
+    const int h_lo = q == q0 ? (int)(hq_lo - q * kPieces) : 0;
+    const int h_hi = q == q1 ? (int)(hq_hi - q * kPieces) : kPieces;
 #pragma unroll 1
-    for (int h = 0; h < kPieces; h += 2, hq += 2) {
-      load_half(t, hq + 1, pb);
-      hh |= scan_half<kSmem>(sc, v, nw, pa, h, W, ws) << (8 * h);
-      if (hq + 2 < hq_end) load_half(t, hq + 2, pa);
-      hh |= scan_half<kSmem>(sc, v, nw, pb, h + 1, W, ws) << (8 * (h + 1));
+    for (int h = h_lo; h < h_hi; ++h) {
+      const int64_t hq = q * kPieces + h;
+#pragma unroll
+      for (int w = 0; w < kLaneWords; ++w) p[w] = nx[w];
+      if (hq + 1 < hq_hi) load_half(t, hq + 1, nx);
+      hh |= (HitWord)scan_half<kSmem>(sc, v, nw, p, h, W, ws) << (8 * h);
     }
     window_end(sc, ws, W, nbw, b_first, hh, prefilter, surv, gst);
   }
@@ -574,13 +586,15 @@ template <bool kSmem>
 __device__ __forceinline__ bool scan_range_tma(Scan& sc, const VolView& v, const uint32_t* nw, const Tract& t,
                                                bool prefilter, WarpShared& ws, Ring& r, int32_t* surv,
                                                DevState* gst) {
+  // pieces wholly outside the vertex range (at the ends of the first and last
+  // windows) are neither copied nor scanned
   const int64_t q0 = (int64_t)sc.V0 >> kWinLog2, q1 = (int64_t)(sc.V1 - 1) >> kWinLog2;
-  const int64_t hq_end = kPieces * (q1 + 1);
-  int64_t taken = kPieces * q0;                          // pieces [kPieces q0, taken) consumed
-  int64_t issued = min(hq_end, kPieces * q0 + kStages);  // pieces [taken, issued) in flight
+  const int64_t hq_lo = (int64_t)sc.V0 >> kHalfLog2, hq_end = ((int64_t)(sc.V1 - 1) >> kHalfLog2) + 1;
+  int64_t taken = hq_lo;                           // pieces [hq_lo, taken) consumed
+  int64_t issued = min(hq_end, hq_lo + kStages);   // pieces [taken, issued) in flight
   if (lane_id() == 0) {
     uint32_t k = r.slot;
-    for (int64_t hq = kPieces * q0; hq < issued; ++hq) {
+    for (int64_t hq = hq_lo; hq < issued; ++hq) {
       r.issue(t, hq, k);
       k = (k + 1 == (uint32_t)kStages) ? 0u : k + 1;
     }
@@ -591,16 +605,18 @@ __device__ __forceinline__ bool scan_range_tma(Scan& sc, const VolView& v, const
     const int32_t W = (int32_t)(q << kWinLog2);
     int32_t nbw, b_first;
     window_begin(sc, ws, W, nbw, b_first);
-    uint32_t hh = 0u;
+    HitWord hh = 0u;
+    const int h_lo = q == q0 ? (int)(hq_lo - q * kPieces) : 0;
+    const int h_hi = q == q1 ? (int)(hq_end - q * kPieces) : kPieces;
 #pragma unroll 1
-    for (int h = 0; h < kPieces; ++h) {
+    for (int h = h_lo; h < h_hi; ++h) {
       int32_t p[kLaneWords];
       if (!ring_take(r, t, issued, hq_end, p)) {
         ok = false;
         break;
       }
       ++taken;
-      hh |= scan_half<kSmem>(sc, v, nw, p, h, W, ws) << (8 * h);
+      hh |= (HitWord)scan_half<kSmem>(sc, v, nw, p, h, W, ws) << (8 * h);
     }
     if (ok) window_end(sc, ws, W, nbw, b_first, hh, prefilter, surv, gst);
   }
