@@ -67,6 +67,24 @@ __device__ __forceinline__ uint64_t policy_evict_first() {
   return pol;
 }
 
+__device__ __forceinline__ uint64_t policy_evict_last() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+
+// Read-only 32-bit load with an L2 cache-eviction hint.
+__device__ __forceinline__ uint32_t ldg_hint(const uint32_t* p, uint64_t pol) {
+  uint32_t v;
+  asm volatile("ld.global.nc.L2::cache_hint.b32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
+  return v;
+}
+
+// Fire-and-forget 32-bit add to global memory with an L2 cache-eviction hint.
+__device__ __forceinline__ void red_add_hint(int32_t* p, int32_t v, uint64_t pol) {
+  asm volatile("red.global.add.L2::cache_hint.s32 [%0], %1, %2;" ::"l"(p), "r"(v), "l"(pol) : "memory");
+}
+
 // 1-D bulk copy global -> shared completing on bar.  dst, src 16-byte
 // aligned; bytes a positive multiple of 16.
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar,

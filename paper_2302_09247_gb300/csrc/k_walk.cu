@@ -14,6 +14,7 @@
 // to C_end.  A streamline whose sets outgrow the tables is handed, whole, to
 // an exact CTA-per-streamline path with global-memory bitmaps.
 #include "fc_device.cuh"
+#include "fc_tma.cuh"
 
 namespace fc {
 
@@ -115,7 +116,7 @@ constexpr int kGather = 2;
 template <typename P, typename S>
 __device__ __forceinline__ void walk_window(const VolView& v, WalkWarpSmem& sm, const int32_t p0[3],
                                             const int32_t p1[3], bool has, bool first, bool endpoint_mode,
-                                            int& nV, int& nT, bool& fail) {
+                                            uint64_t keep, int& nV, int& nT, bool& fail) {
   SegWalk<P> w;
   bool pend = false;
   if (has) {
@@ -131,7 +132,7 @@ __device__ __forceinline__ void walk_window(const VolView& v, WalkWarpSmem& sm, 
     }
     uint32_t code[kGather];
 #pragma unroll
-    for (int i = 0; i < kGather; ++i) code[i] = lin[i] >= 0 ? __ldg(v.code + lin[i]) : 0u;
+    for (int i = 0; i < kGather; ++i) code[i] = lin[i] >= 0 ? ldg_hint(v.code + lin[i], keep) : 0u;
 #pragma unroll
     for (int i = 0; i < kGather; ++i) {
       int32_t row, lab;
@@ -157,6 +158,7 @@ __device__ __forceinline__ int walk_one(const VolView& v, const Tract& t, const 
   const unsigned lane = lane_id();
   const bool endpoint_mode = (mode & kModeTargetEndpoint) != 0;
   const bool point_mode = (mode & kModeVertexSampled) != 0;
+  const uint64_t keep = policy_evict_last();  // code gathers and C stay in L2 across the stream
   const int64_t M = v.n_lab;
   const int64_t a = t.off[s], b = t.off[s + 1];
   // offsets the prefilter has flagged as invalid may reach this point; such
@@ -210,9 +212,9 @@ __device__ __forceinline__ int walk_one(const VolView& v, const Tract& t, const 
       const bool small = !has || (abs(p1[0] - p0[0]) < 65536 && abs(p1[1] - p0[1]) < 65536 &&
                                   abs(p1[2] - p0[2]) < 65536);
       if (__all_sync(kFull, small))
-        walk_window<uint32_t, S>(v, sm, p0, p1, has, j == a, endpoint_mode, nV, nT, fail);
+        walk_window<uint32_t, S>(v, sm, p0, p1, has, j == a, endpoint_mode, keep, nV, nT, fail);
       else
-        walk_window<unsigned long long, S>(v, sm, p0, p1, has, j == a, endpoint_mode, nV, nT, fail);
+        walk_window<unsigned long long, S>(v, sm, p0, p1, has, j == a, endpoint_mode, keep, nV, nT, fail);
       fail = __any_sync(kFull, fail);
 #pragma unroll
       for (int k = 0; k < 3; ++k) cur[k] = nxt[k];
@@ -237,7 +239,7 @@ __device__ __forceinline__ int walk_one(const VolView& v, const Tract& t, const 
     pairs = nV * nT;
     for (int p = lane; p < pairs; p += 32) {
       const int i = p / nT, k = p - i * nT;
-      atomicAdd(acc.C + (int64_t)sm.listV[i] * M + (sm.listT[k] - 1), 1);
+      red_add_hint(acc.C + (int64_t)sm.listV[i] * M + (sm.listT[k] - 1), 1, keep);
     }
     if (lane == 0) {
       int32_t p[3], r0, l0, r1, l1;
@@ -259,7 +261,8 @@ __device__ __forceinline__ uint32_t next_survivor(DevState* gst) {
 }
 
 template <bool kBitV, bool kBitT>
-__global__ void __launch_bounds__(kWalkWarps * 32) walk_kernel(Tract t, VolView v, const int32_t* __restrict__ surv,
+__global__ void __launch_bounds__(kWalkWarps * 32)
+    walk_kernel(Tract t, VolView v, const int32_t* __restrict__ surv,
                                                               Accum acc, uint32_t mode, int32_t* __restrict__ ovf,
                                                               DevState* st) {
   using S = Sets<kBitV, kBitT>;
