@@ -50,7 +50,7 @@ struct Request {
   fc::VolView v{};
   fc::Accum acc{};
   DevState* st = nullptr;
-  DevState host_state{};
+  DevState* host_state = nullptr;  // page-locked, from the server's pool while admitted
   cudaEvent_t done_ev = nullptr;
   int64_t streamlines = 0, chunks_done = 0;
   double t_submit = 0, t_admit = 0, t_done = 0;
@@ -101,6 +101,15 @@ struct fastcod_server {
   uint32_t* scratch = nullptr;
   int64_t scratch_words = 0;
   fc::BatchTable* tbl = nullptr;
+  // page-locked host memory, so that no copy of the loop waits for the
+  // compute stream: the task tables of the last two iterations (reused once
+  // their copy event has passed) and one state block per slot
+  fc::BatchTask* tasks_host[2] = {nullptr, nullptr};
+  size_t tasks_host_cap[2] = {0, 0};
+  cudaEvent_t tasks_ev[2] = {nullptr, nullptr};
+  int tasks_turn = 0;
+  DevState* state_pool = nullptr;
+  std::vector<DevState*> free_states;
 };
 
 namespace {
@@ -248,6 +257,8 @@ bool iterate(fastcod_server* S, uint32_t** tmp, size_t* tmp_cap) {
       if (S->reserved + (int64_t)need > S->budget && !S->active.empty()) break;
       S->reserved += (int64_t)need;
       r->reserve = need;
+      r->host_state = S->free_states.back();  // active requests <= slots = pool size
+      S->free_states.pop_back();
       r->state = RState::Setup;
       r->t_admit = now_s(S);
       S->active.push_back(r);
@@ -337,9 +348,24 @@ bool iterate(fastcod_server* S, uint32_t** tmp, size_t* tmp_cap) {
       }
     }
     tbl.n = (int32_t)staged.size();
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(S->tasks, tasks.data(), tasks.size() * sizeof(fc::BatchTask), cudaMemcpyHostToDevice,
+    // the task table goes through one of two page-locked buffers
+    const int turn = S->tasks_turn;
+    S->tasks_turn ^= 1;
+    if (e == cudaSuccess) e = cudaEventSynchronize(S->tasks_ev[turn]);  // its copy two iterations ago is done
+    if (e == cudaSuccess && tasks.size() > S->tasks_host_cap[turn]) {
+      if (S->tasks_host[turn]) cudaFreeHost(S->tasks_host[turn]);
+      S->tasks_host[turn] = nullptr;
+      S->tasks_host_cap[turn] = 0;
+      const size_t cap = std::max(tasks.size(), (size_t)1024);
+      e = cudaMallocHost((void**)&S->tasks_host[turn], cap * sizeof(fc::BatchTask));
+      if (e == cudaSuccess) S->tasks_host_cap[turn] = cap;
+    }
+    if (e == cudaSuccess) {
+      memcpy(S->tasks_host[turn], tasks.data(), tasks.size() * sizeof(fc::BatchTask));
+      e = cudaMemcpyAsync(S->tasks, S->tasks_host[turn], tasks.size() * sizeof(fc::BatchTask), cudaMemcpyHostToDevice,
                           S->compute);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(S->tasks_ev[turn], S->compute);
     if (e == cudaSuccess) e = cudaMemsetAsync(S->gst, 0, sizeof(DevState), S->compute);
     if (e == cudaSuccess)
       e = fc::launch_prefilter_batch(tbl, S->tasks, (int32_t)tasks.size(), S->prefilter != 0, S->tma != 0, S->ctas, S->lists, S->gst,
@@ -371,7 +397,7 @@ bool iterate(fastcod_server* S, uint32_t** tmp, size_t* tmp_cap) {
       cudaMemcpyAsync(r->head.C_out, r->acc.C, nm * 4, cudaMemcpyDefault, S->compute);
       cudaMemcpyAsync(r->head.Cend_out, r->acc.Cend, nm * 4, cudaMemcpyDefault, S->compute);
     }
-    if (r->mem) cudaMemcpyAsync(&r->host_state, r->st, sizeof(DevState), cudaMemcpyDeviceToHost, S->compute);
+    if (r->mem) cudaMemcpyAsync(r->host_state, r->st, sizeof(DevState), cudaMemcpyDeviceToHost, S->compute);
     if (r->done_ev) cudaEventRecord(r->done_ev, S->compute);
   }
   // completion
@@ -389,8 +415,10 @@ bool iterate(fastcod_server* S, uint32_t** tmp, size_t* tmp_cap) {
         continue;
       }
       (void)cudaGetLastError();
-      if (r->status == FASTCOD_OK && r->host_state.error != fc::kErrNone)
-        r->status = r->host_state.error == fc::kErrTimeout ? FASTCOD_ETIMEOUT : FASTCOD_EINVAL;
+      if (r->status == FASTCOD_OK && r->mem && r->host_state->error != fc::kErrNone)
+        r->status = r->host_state->error == fc::kErrTimeout ? FASTCOD_ETIMEOUT : FASTCOD_EINVAL;
+      S->free_states.push_back(r->host_state);
+      r->host_state = nullptr;
       if (r->mem) cudaFreeAsync(r->mem, S->compute);
       r->mem = nullptr;
       if (r->done_ev) cudaEventDestroy(r->done_ev);
@@ -456,11 +484,20 @@ FASTCOD_API int fastcod_server_create(fastcod_ctx* c, int32_t max_slots, int64_t
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->copy, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&S->copied, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaMalloc(&S->gst, sizeof(DevState));
+  for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = cudaEventCreateWithFlags(&S->tasks_ev[k], cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&S->state_pool, sizeof(DevState) * (size_t)max_slots);
+  if (e == cudaSuccess) {
+    memset(S->state_pool, 0, sizeof(DevState) * (size_t)max_slots);
+    for (int32_t k = 0; k < max_slots; ++k) S->free_states.push_back(S->state_pool + k);
+  }
   if (e != cudaSuccess) {
     (void)cudaGetLastError();
     if (S->compute) cudaStreamDestroy(S->compute);
     if (S->copy) cudaStreamDestroy(S->copy);
     if (S->copied) cudaEventDestroy(S->copied);
+    for (int k = 0; k < 2; ++k)
+      if (S->tasks_ev[k]) cudaEventDestroy(S->tasks_ev[k]);
+    if (S->state_pool) cudaFreeHost(S->state_pool);
     cudaFree(S->gst);
     delete S->tbl;
     delete S;
@@ -593,6 +630,11 @@ FASTCOD_API int fastcod_server_destroy(fastcod_server* S) {
   if (S->scratch) cudaFree(S->scratch);
   cudaFree(S->gst);
   cudaEventDestroy(S->copied);
+  for (int k = 0; k < 2; ++k) {
+    cudaEventDestroy(S->tasks_ev[k]);
+    if (S->tasks_host[k]) cudaFreeHost(S->tasks_host[k]);
+  }
+  cudaFreeHost(S->state_pool);
   cudaStreamDestroy(S->compute);
   cudaStreamDestroy(S->copy);
   delete S->tbl;
