@@ -209,44 +209,102 @@ __global__ void __launch_bounds__(kThreads) upsample_offsets_kernel(const int64_
 
 // Upsampled vertices: warp per streamline, lanes over its segments.  With
 // d = q - p = q0 * factor + r0 (0 <= r0 < factor), floor(d * j / factor) =
-// q0 * j + floor(r0 * j / factor): one division per segment and axis, then
-// the points follow with one carry test each.
+// q0 * j + floor(r0 * j / factor): one division per segment and axis (a shift
+// for a power-of-two factor, 32-bit when d fits), then the points follow with
+// one carry test each.  The running sums are kept modulo 2^32: every point
+// lies between p and q, so its int32 value is exact.  A round computes the
+// points of up to 32 segments into a per-warp shared buffer; the warp then
+// writes the round's contiguous output with coalesced stores.
+constexpr int kUpCap = 256;  // points staged per warp (3 KB)
+
+__device__ __forceinline__ void seg_split(int64_t d, int32_t factor, int32_t flog2, uint32_t& q0, uint32_t& r0) {
+  if (flog2 >= 0) {  // arithmetic shift: floor division by 2^flog2
+    q0 = (uint32_t)(d >> flog2);
+    r0 = (uint32_t)d & (uint32_t)(factor - 1);
+  } else if (d == (int64_t)(int32_t)d) {
+    const int32_t dd = (int32_t)d;
+    int32_t q = dd / factor, r = dd - q * factor;
+    if (r < 0) {
+      q -= 1;
+      r += factor;
+    }
+    q0 = (uint32_t)q;
+    r0 = (uint32_t)r;
+  } else {
+    const int64_t q = floor_div(d, factor);
+    q0 = (uint32_t)q;
+    r0 = (uint32_t)(d - q * factor);
+  }
+}
+
+struct SegPoints {
+  uint32_t p[3], q0[3], r0[3], acc_q[3], acc_r[3];
+
+  __device__ __forceinline__ void init(const int32_t* __restrict__ xyz, int64_t i, int32_t factor, int32_t flog2) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const int32_t a = __ldg(xyz + 3 * i + c);
+      p[c] = (uint32_t)a;
+      seg_split((int64_t)__ldg(xyz + 3 * (i + 1) + c) - a, factor, flog2, q0[c], r0[c]);
+      acc_q[c] = 0;
+      acc_r[c] = 0;
+    }
+  }
+  // writes point j (in order j = 0, 1, ...) and advances
+  __device__ __forceinline__ void emit(int32_t* w, int32_t factor) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      w[c] = (int32_t)(p[c] + acc_q[c]);
+      acc_q[c] += q0[c];
+      acc_r[c] += r0[c];
+      if (acc_r[c] >= (uint32_t)factor) {
+        acc_r[c] -= (uint32_t)factor;
+        acc_q[c] += 1u;
+      }
+    }
+  }
+};
+
 __global__ void __launch_bounds__(kThreads) upsample_kernel(const int32_t* __restrict__ xyz,
                                                             const int64_t* __restrict__ off, int64_t ns,
-                                                            int32_t factor, const int64_t* __restrict__ out_off,
+                                                            int32_t factor, int32_t flog2,
+                                                            const int64_t* __restrict__ out_off,
                                                             int32_t* __restrict__ out) {
+  __shared__ int32_t stage[kThreads / 32][3 * kUpCap];
+  int32_t* sb = stage[threadIdx.x >> 5];
   const int32_t lane = (int32_t)lane_id();
+  const int32_t per = factor <= kUpCap ? min(32, kUpCap / factor) : 0;  // segments per round
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; s < ns; s += nwarps) {
-    const int64_t a = off[s], b = off[s + 1], o = out_off[s];
+    const int64_t a = off[s], b = off[s + 1];
     if (b == a) continue;
+    const int64_t o = out_off[s];
     if (lane == 0) {
 #pragma unroll
-      for (int c = 0; c < 3; ++c) out[3 * (out_off[s + 1] - 1) + c] = __ldg(xyz + 3 * (b - 1) + c);
+      for (int c = 0; c < 3; ++c) out[3 * (o + (b - 1 - a) * factor) + c] = __ldg(xyz + 3 * (b - 1) + c);
     }
-    for (int64_t i = a + lane; i + 1 < b; i += 32) {
-      // 64-bit: any int32 input (a point between p and q fits in 32 bits)
-      int64_t p[3], q0[3], r0[3], acc_q[3] = {0, 0, 0}, acc_r[3] = {0, 0, 0};
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        p[c] = __ldg(xyz + 3 * i + c);
-        const int64_t d = (int64_t)__ldg(xyz + 3 * (i + 1) + c) - p[c];
-        q0[c] = floor_div(d, factor);
-        r0[c] = d - q0[c] * factor;
+    if (per == 0) {  // factors above the staging capacity: each lane writes its own segments
+      for (int64_t i = a + lane; i + 1 < b; i += 32) {
+        SegPoints g;
+        g.init(xyz, i, factor, flog2);
+        int32_t* dst = out + 3 * (o + (i - a) * factor);
+        for (int32_t j = 0; j < factor; ++j) g.emit(dst + 3 * j, factor);
       }
-      int32_t* dst = out + 3 * (o + (i - a) * factor);
-      for (int32_t j = 0; j < factor; ++j) {
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          dst[3 * j + c] = (int32_t)(p[c] + acc_q[c]);
-          acc_q[c] += q0[c];
-          acc_r[c] += r0[c];
-          if (acc_r[c] >= factor) {
-            acc_r[c] -= factor;
-            acc_q[c] += 1;
-          }
-        }
+      continue;
+    }
+    for (int64_t i0 = a; i0 + 1 < b; i0 += per) {
+      const int32_t nseg = (int32_t)min((int64_t)per, b - 1 - i0);
+      if (lane < nseg) {
+        SegPoints g;
+        g.init(xyz, i0 + lane, factor, flog2);
+        int32_t* w = sb + 3 * lane * factor;
+        for (int32_t j = 0; j < factor; ++j) g.emit(w + 3 * j, factor);
       }
+      __syncwarp();
+      const int32_t nw = 3 * nseg * factor;
+      int32_t* dst = out + 3 * (o + (i0 - a) * factor);
+      for (int32_t k = lane; k < nw; k += 32) __stcs(dst + k, sb[k]);
+      __syncwarp();
     }
   }
 }
@@ -325,7 +383,8 @@ cudaError_t launch_upsample_offsets(const int64_t* off, int64_t ns, int32_t fact
 cudaError_t launch_upsample_vertices(const int32_t* xyz, const int64_t* off, int64_t ns, int32_t factor,
                                      const int64_t* out_off, int32_t* out, cudaStream_t s) {
   if (ns <= 0) return cudaSuccess;
-  upsample_kernel<<<grid_for(ns * 32, 8), kThreads, 0, s>>>(xyz, off, ns, factor, out_off, out);
+  const int32_t flog2 = (factor & (factor - 1)) == 0 ? __builtin_ctz((unsigned)factor) : -1;
+  upsample_kernel<<<grid_for(ns * 32, 8), kThreads, 0, s>>>(xyz, off, ns, factor, flog2, out_off, out);
   return cudaGetLastError();
 }
 

@@ -17,9 +17,10 @@
 // rare); a streamline of one vertex at an odd index is kept unconditionally
 // (the walk decides it).
 //
-// Vertex-parallel scan.  Each warp owns a contiguous range of streamlines and
-// walks its vertex range in 512-vertex windows aligned to 512, each two
-// 256-vertex halves; in a half, lane l takes the eight consecutive vertices
+// Vertex-parallel scan.  Each warp owns a contiguous range of streamlines
+// holding about the same number of vertices as every other warp's, and walks
+// its vertex range in 2048-vertex windows aligned to 2048, each eight
+// 256-vertex pieces; in a piece, lane l takes the eight consecutive vertices
 // 8l..8l+7 (six 16-byte words), so every lane is busy whatever the
 // streamline lengths:
 //   - the streamline boundaries (offsets) falling in the window, kept in a
@@ -28,14 +29,14 @@
 //   - per vertex: coordinate check, voxel-step count and long-segment check of
 //     the segment ending there (unless the vertex starts a streamline), and
 //     at even vertices a near-grid lookup (shared memory when the grid fits);
-//   - one warp scan of the per-lane hit counts of both halves gives, at every
-//     boundary x, the running number of ROI / target hits before x, and the
-//     streamline ending at x passes when both counts grew since its start
-//     boundary.
-// Two loaders with identical results: TMA (default; the halves stream through
+//   - one warp scan of the per-lane hit counts of the window's pieces gives,
+//     at every boundary x, the running number of ROI / target hits before x,
+//     and the streamline ending at x passes when both counts grew since its
+//     start boundary.
+// Two loaders with identical results: TMA (default; the pieces stream through
 // a ring of three 3072-byte slots per warp in shared memory, cp.async.bulk +
 // mbarrier, L2 evict-first) and direct streaming loads into registers (the
-// next half in flight while the current one is processed).
+// next piece in flight while the current one is processed).
 #include <type_traits>
 
 #include "fc_device.cuh"
@@ -371,11 +372,52 @@ __device__ __forceinline__ void window_end(Scan& sc, WarpShared& ws, int32_t W, 
   sc.cumT += baseT[kPieces];
 }
 
+// Vertex-balanced ranges.  Warp g of G scans the streamlines s with
+// split(g) <= s < split(g + 1), where split(g) is the first s with
+// off[s] >= nv * g / G (split(0) = 0, split(G) = ns), so that every warp
+// reads about the same number of vertices whatever the length mix.  Two
+// half-warp 16-ary searches (one per end of the range); the first round probes
+// every 256 streamlines around the streamline-count split, which usually
+// brackets the answer (three rounds in all).  On
+// valid offsets split() does not decrease in g; ranges that come out reversed
+// can only come from decreasing offsets and are reported by warp_init.
+__device__ __forceinline__ void vertex_split(const int64_t* off, int64_t ns, int64_t nv, int64_t g, int64_t G,
+                                             int64_t& s_lo, int64_t& s_hi) {
+  const int32_t lane = (int32_t)lane_id(), sub = lane & 15, half = lane >> 4;
+  const int64_t gg = g + half;
+  const int64_t target = nv * gg / G, guess = ns * gg / G;
+  int64_t lo = 0, hi = ns;  // the answer lies in [lo, hi]
+  if (gg == 0 || gg == G) lo = hi = gg == 0 ? 0 : ns;
+  for (int round = 0; __any_sync(kFull, lo < hi); ++round) {
+    const bool act = lo < hi;
+    const int64_t p = round == 0 ? min(max(guess + 256 * (sub - 7), (int64_t)0), ns)
+                                 : lo + ((int64_t)(sub + 1) * (hi - lo)) / 16;  // p(15) = hi
+    const bool ge = act && __ldg(off + p) >= target;
+    const uint32_t m = (__ballot_sync(kFull, ge) >> (16 * half)) & 0xffffu;
+    const int k = m ? __ffs(m) - 1 : 16;  // the first probe at or above the target
+    const int64_t pk = __shfl_sync(kFull, p, 16 * half + min(k, 15));
+    const int64_t pb = __shfl_sync(kFull, p, 16 * half + max(k - 1, 0));
+    if (act) {
+      if (k == 16) {  // every probe below the target: the answer lies above the last one
+        lo = min(pk + 1, hi);
+      } else {
+        hi = pk;  // p(0) >= lo: with k = 0 the answer lies in [lo, p(0)]
+        if (k > 0) lo = pb + 1;
+      }
+    }
+  }
+  s_lo = __shfl_sync(kFull, lo, 0);
+  s_hi = __shfl_sync(kFull, lo, 16);
+}
+
 // Set up the scan of streamlines [s_lo, s_hi) of t; false when there is
 // nothing to scan (or the offsets are invalid).
 __device__ __forceinline__ bool warp_init(const Tract& t, int64_t s_lo, int64_t s_hi, Scan& sc, DevState* sst,
                                           int64_t id_base) {
-  if (s_hi <= s_lo) return false;
+  if (s_hi <= s_lo) {
+    if (s_hi < s_lo && lane_id() == 0) set_error(sst, kErrOffsets, (int32_t)s_hi);
+    return false;
+  }
   const int64_t a = __ldg(t.off + s_lo), b = __ldg(t.off + s_hi);
   if (a < 0 || b > t.nv || a > b || (s_lo == 0 && a != 0) || (s_hi == t.ns && b != t.nv)) {
     if (lane_id() == 0) set_error(sst, kErrOffsets, (int32_t)s_lo);
@@ -658,8 +700,10 @@ __global__ void __launch_bounds__(kWarps * 32, kMinBlocks) prefilter_kernel(Trac
   WarpShared& ws = ws_all[threadIdx.x >> 5];
   const int64_t gw = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
   const int64_t nwarps = (int64_t)gridDim.x * kWarps;
+  int64_t s_lo, s_hi;
+  vertex_split(t.off, t.ns, t.nv, gw, nwarps, s_lo, s_hi);
   Scan sc;
-  if (!warp_init(t, t.ns * gw / nwarps, t.ns * (gw + 1) / nwarps, sc, st, 0)) return;
+  if (!warp_init(t, s_lo, s_hi, sc, st, 0)) return;
   if (kTma) {
     const size_t off = ring_offset(kSmem ? (size_t)near_words(v) * 4 : 0);
     Ring r;

@@ -88,8 +88,7 @@ def test_device_detected_input_errors_then_reset(fc, tiny0, where, staging):
         # last offset != n_vertices
         off = tr.offsets.copy()
         off[-1] -= 1
-        ctx.add_streamlines(put(tr.xyz), put(off), ) if False else fc.fastcod_add_streamlines(
-            ctx.ctx, put(tr.xyz), put(off), n_vertices=tr.n_vertices)
+        fc.fastcod_add_streamlines(ctx.ctx, put(tr.xyz), put(off), n_vertices=tr.n_vertices)
         with pytest.raises(fc.FastCodError) as e:
             ctx.sync()
         assert e.value.code == fc.FASTCOD_EINVAL
@@ -116,6 +115,59 @@ def test_device_detected_input_errors_then_reset(fc, tiny0, where, staging):
         np.testing.assert_array_equal(C, Cr)
     finally:
         ctx.close()
+
+
+@pytest.fixture(scope="module")
+def mid():
+    return synth.make_subject(1, n_streamlines=60_000)
+
+
+@pytest.mark.parametrize("where", ["device", "host"])
+def test_offset_patterns_across_warp_ranges(fc, mid, where):
+    # the prefilter gives every warp about the same number of vertices (a
+    # search over the offsets): invalid offsets anywhere are still reported,
+    # and valid but lopsided length mixes still count exactly
+    vols, tr = mid
+    put = as_device if where == "device" else (lambda a: np.ascontiguousarray(a))
+    ns, nv = tr.n_streamlines, tr.n_vertices
+    bad = []
+    o = tr.offsets.copy()
+    o[ns // 2] = nv + 1000  # a spike past the end
+    bad.append(o)
+    o = tr.offsets.copy()
+    o[ns // 3] = -1
+    bad.append(o)
+    o = tr.offsets.copy()
+    o[ns // 4:ns // 4 + 5000] = o[ns // 4:ns // 4 + 5000][::-1].copy()  # a decreasing block
+    bad.append(o)
+    o = tr.offsets.copy()
+    o[1:-1] = o[1:-1][::-1].copy()  # decreasing everywhere inside
+    bad.append(o)
+    with _ctx_with_volumes(fc, vols) as ctx:
+        for o in bad:
+            ctx.add_streamlines(put(tr.xyz), put(o))
+            with pytest.raises(fc.FastCodError) as e:
+                ctx.connectivity()
+            assert e.value.code == fc.FASTCOD_EINVAL and "offsets" in str(e.value)
+            ctx.reset()
+        # valid: one streamline holds every vertex among empty ones; and a
+        # few very long streamlines among short ones
+        T = np.diff(tr.offsets)
+        lop = np.zeros(ns + 1, np.int64)
+        lop[ns // 2 + 1:] = nv
+        k = np.arange(ns)
+        T2 = np.where(k % 997 == 0, 0, T)
+        T2[7] += nv - int(T2.sum())
+        for off in (lop, np.concatenate([[0], np.cumsum(T2)]).astype(np.int64)):
+            assert off[-1] == nv and (np.diff(off) >= 0).all()
+            ctx.reset()
+            ctx.add_streamlines(put(tr.xyz), put(off))
+            C, Ce, st = ctx.connectivity(), ctx.endpoint_connectivity(), ctx.stats()
+            Cr, Cer, sr = oracle.connectivity(vols.roi, vols.lab, vols.dims, vols.n_roi, vols.n_targets,
+                                              tr.xyz, off)
+            np.testing.assert_array_equal(C, Cr)
+            np.testing.assert_array_equal(Ce, Cer)
+            assert st["voxel_steps"] == sr["voxel_steps"]
 
 
 def test_misaligned_device_xyz_rejected(fc, tiny0):
