@@ -37,6 +37,7 @@ int64_t tasks_of(int64_t n_vertices, int task_log2) {
 // Sub-allocation of the batch arena (byte offsets, 256-byte aligned).
 struct Layout {
   size_t scratch, gstate, states, tasks, surv, ovf, staged_end;
+  int64_t surv_cap;  // entries of the survivor and overflow lists
   std::vector<size_t> roi_in, lab_in, xyz_in, off_in;  // staging of host inputs (or SIZE_MAX)
   std::vector<size_t> code, lab, bricks, C, Cend;
   size_t planes;
@@ -111,6 +112,7 @@ Layout plan(const fastcod_subject* subs, int32_t n, const std::vector<int>& host
   L.gstate = take(sizeof(DevState));
   L.states = take(sizeof(DevState) * n);
   L.surv = take((size_t)total_ns * 4);
+  L.surv_cap = total_ns;
   L.ovf = take((size_t)total_ns * 4);
   for (int32_t i = 0; i < n; ++i) {
     const fastcod_subject& S = subs[i];
@@ -236,8 +238,10 @@ int capture(fastcod_ctx* c, const fastcod_subject* subs, int32_t n, const Layout
   }
   if (e == cudaSuccess)
     e = fc::launch_prefilter_batch(tbl, at<fc::BatchTask>(A, L.tasks), L.ntasks, c->prefilter != 0, c->staging_tma != 0, cfg.ctas,
-                                   at<int32_t>(A, L.surv), gst, c->num_sms, c->stream);
-  if (e == cudaSuccess) e = fc::launch_walk_batch(tbl, at<int32_t>(A, L.surv), c->mode, at<int32_t>(A, L.ovf), gst, c->num_sms, c->stream);
+                                   at<int32_t>(A, L.surv), L.surv_cap, gst, c->num_sms, c->stream);
+  if (e == cudaSuccess)
+    e = fc::launch_walk_batch(tbl, at<int32_t>(A, L.surv), L.surv_cap, c->mode, at<int32_t>(A, L.ovf), gst, c->num_sms,
+                              c->stream);
   if (e == cudaSuccess)
     e = fc::launch_walk_overflow_batch(tbl, at<int32_t>(A, L.ovf), c->mode, at<uint32_t>(A, L.scratch), kOverflowCtas,
                                        L.scratch_words, gst, c->stream);

@@ -2,6 +2,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdarg>
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -426,7 +427,8 @@ FASTCOD_API int fastcod_add_streamlines(fastcod_ctx* c, const int32_t* xyz, int6
     if (rc) return rc;
   }
   // per-call counters: n_survivors, n_overflow, work_next, work_task
-  CU(cudaMemsetAsync(&c->d_state->n_survivors, 0, 4 * sizeof(uint32_t), c->stream));
+  CU(cudaMemsetAsync(&c->d_state->n_survivors, 0, offsetof(DevState, voxel_steps) - offsetof(DevState, n_survivors),
+                     c->stream));
   fc::Tract t;
   t.xyz = d_xyz;
   t.off = d_off;
@@ -440,10 +442,9 @@ FASTCOD_API int fastcod_add_streamlines(fastcod_ctx* c, const int32_t* xyz, int6
   // bulk copies stage device-resident vertices; host-resident ones are read
   // with direct loads
   CU(fc::launch_prefilter(t, v, c->prefilter != 0, c->mode, c->staging_tma != 0 && !xyz_in_place, c->prefilter_ctas,
-                          c->d_surv,
-                          c->d_state, c->num_sms, c->stream));
+                          c->d_surv, ns, c->d_state, c->num_sms, c->stream));
   if (int rc = record(c, 2)) return rc;
-  CU(fc::launch_walk(t, v, c->d_surv, acc, c->mode, c->d_ovf, c->d_state, c->num_sms, c->stream));
+  CU(fc::launch_walk(t, v, c->d_surv, ns, acc, c->mode, c->d_ovf, c->d_state, c->num_sms, c->stream));
   if (int rc = record(c, 3)) return rc;
   CU(fc::launch_walk_overflow(t, v, c->d_ovf, acc, c->mode, c->d_scratch, c->scratch_ctas, c->d_state,
                               c->stream));

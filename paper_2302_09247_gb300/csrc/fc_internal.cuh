@@ -40,6 +40,8 @@ struct DevState {
   uint32_t n_overflow;    // this call: entries in the overflow list
   uint32_t work_next;     // this call: dynamic work counter of the walk kernel
   uint32_t work_task;     // this call: dynamic task counter of the batched prefilter
+  uint32_t n_long;        // this call: entries at the far end of the survivor list
+  uint32_t spare;
   unsigned long long voxel_steps;
   unsigned long long survivors;
   unsigned long long overflow;
@@ -115,6 +117,21 @@ struct Accum {
   int32_t* Cend;          // [N][M]
 };
 
+// The survivor list of one launch, cap entries: the prefilter appends
+// streamlines of at most kLongSegments segments from the front (counter
+// n_survivors) and longer ones from the back (n_long); the walk takes the
+// long ones first, so that no long walk is left for the end of the launch.
+constexpr int32_t kLongSegments = 192;
+
+struct SurvList {
+  int32_t* ids;
+  int64_t cap;
+};
+
+__device__ __forceinline__ int32_t survivor_at(const int32_t* ids, int64_t cap, uint32_t n_long, uint32_t idx) {
+  return idx < n_long ? ids[cap - 1 - (int64_t)idx] : ids[idx - n_long];
+}
+
 // One subject of a batch: its volumes, streamlines, accumulators, counters,
 // and the global id of its first streamline (survivor lists hold global ids).
 struct BatchSubject {
@@ -161,22 +178,22 @@ cudaError_t launch_near(const VolView& v, const uint32_t* planes, uint32_t* near
 // K2: prefilter + compaction (+ validation and voxel-step count).
 // ctas_per_sm: 2 or 3 (the register budget the kernel is compiled for).
 cudaError_t launch_prefilter(const Tract& t, const VolView& v, bool prefilter, uint32_t mode,
-                             bool tma, int ctas_per_sm, int32_t* survivors, DevState* st, int num_sms,
-                             cudaStream_t s);
+                             bool tma, int ctas_per_sm, int32_t* survivors, int64_t survivor_cap, DevState* st,
+                             int num_sms, cudaStream_t s);
 
 // Batched forms: every subject of the table in one launch each.
 cudaError_t launch_prefilter_batch(const BatchTable& tbl, const BatchTask* tasks, int32_t ntasks, bool prefilter,
-                                   bool tma, int ctas_per_sm, int32_t* survivors, DevState* gst, int num_sms,
-                                   cudaStream_t s);
-cudaError_t launch_walk_batch(const BatchTable& tbl, const int32_t* survivors, uint32_t mode, int32_t* overflow_list,
-                              DevState* gst, int num_sms, cudaStream_t s);
+                                   bool tma, int ctas_per_sm, int32_t* survivors, int64_t survivor_cap,
+                                   DevState* gst, int num_sms, cudaStream_t s);
+cudaError_t launch_walk_batch(const BatchTable& tbl, const int32_t* survivors, int64_t survivor_cap, uint32_t mode,
+                              int32_t* overflow_list, DevState* gst, int num_sms, cudaStream_t s);
 cudaError_t launch_walk_overflow_batch(const BatchTable& tbl, const int32_t* overflow_list, uint32_t mode,
                                        uint32_t* scratch, int32_t scratch_ctas, int64_t words_per_cta, DevState* gst,
                                        cudaStream_t s);
 
 // K3: warp-per-streamline walk, dedup, accumulate; overflow path.
-cudaError_t launch_walk(const Tract& t, const VolView& v, const int32_t* survivors, Accum acc,
-                        uint32_t mode, int32_t* overflow_list, DevState* st, int num_sms,
+cudaError_t launch_walk(const Tract& t, const VolView& v, const int32_t* survivors, int64_t survivor_cap,
+                        Accum acc, uint32_t mode, int32_t* overflow_list, DevState* st, int num_sms,
                         cudaStream_t s);
 cudaError_t launch_walk_overflow(const Tract& t, const VolView& v, const int32_t* overflow_list,
                                  Accum acc, uint32_t mode, uint32_t* scratch,

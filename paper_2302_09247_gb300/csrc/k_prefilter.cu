@@ -71,7 +71,8 @@ constexpr int64_t kNearSmemWords = 12288;  // direct loader: near grids up to 48
 __device__ __forceinline__ uint32_t lowmask(int32_t k) { return k >= 32 ? 0xffffffffu : ((1u << k) - 1u); }
 
 struct WarpShared {
-  int32_t sbuf[64];          // survivors awaiting a flush
+  int32_t sbuf[64];          // short survivors awaiting a flush
+  int32_t lbuf[64];          // long survivors awaiting a flush
   uint32_t st[kWin / 32];    // start bits of the current window
 };
 
@@ -90,7 +91,7 @@ struct Scan {
   int32_t qx, qy, qz;        // voxel of the last vertex processed (lane 31's)
   unsigned long long steps;  // voxel steps counted by this lane
   uint32_t singles, kept, badc;
-  int nbuf;
+  int nbuf, nlong;           // entries of sbuf, lbuf
   bool abort;
   int64_t id_base;           // survivor ids are id_base + streamline index
   DevState* sst;             // the subject's counters and error word
@@ -155,17 +156,21 @@ __device__ __forceinline__ int32_t fetch_bnd(Scan& sc, int64_t s, int32_t prev) 
   return g;
 }
 
-// gst holds the survivor list's counter (one list per launch).
-__device__ __forceinline__ void flush_survivors(Scan& sc, int32_t* sbuf, int32_t* surv, DevState* gst) {
+// Appends the n buffered ids to the launch's survivor list (counters in gst):
+// short streamlines from its front, long ones from its back, so that the walk
+// can take the long ones first.
+__device__ __forceinline__ void flush_ids(int& n, const int32_t* buf, bool back, const SurvList& surv,
+                                          DevState* gst) {
   __syncwarp();
   uint32_t base = 0;
-  if (lane_id() == 0 && sc.nbuf > 0) base = atomicAdd(&gst->n_survivors, (uint32_t)sc.nbuf);
+  if (lane_id() == 0 && n > 0) base = atomicAdd(back ? &gst->n_long : &gst->n_survivors, (uint32_t)n);
   base = __shfl_sync(kFull, base, 0);
-  const int l = (int)lane_id();
-  if (l < sc.nbuf) surv[base + l] = sbuf[l];
-  if (l + 32 < sc.nbuf) surv[base + l + 32] = sbuf[l + 32];
+  for (int k = (int)lane_id(); k < n; k += 32) {  // n <= 64
+    const int64_t pos = (int64_t)base + k;
+    surv.ids[back ? surv.cap - 1 - pos : pos] = buf[k];
+  }
   __syncwarp();
-  sc.nbuf = 0;
+  n = 0;
 }
 
 // Brick occupancy of the voxel box [lo, hi] of a long segment, out of line
@@ -280,7 +285,7 @@ __device__ __forceinline__ uint32_t scan_half(Scan& sc, const VolView& v, const 
 // 3. End of window W: hit counts of its pieces (hh: piece h's hit bits at
 //    bits 8h) and the decisions at its nbw boundaries, 32 per round.
 __device__ __forceinline__ void window_end(Scan& sc, WarpShared& ws, int32_t W, int32_t nbw, int32_t b_first,
-                                           HitWord hh, bool prefilter, int32_t* surv, DevState* gst) {
+                                           HitWord hh, bool prefilter, const SurvList& surv, DevState* gst) {
   const int32_t lane = (int32_t)lane_id();
   // per-lane counts in byte fields (R and T of two pieces per word); a
   // field's prefix over the warp is at most 4 * 32 = 128, so fields never
@@ -354,11 +359,18 @@ __device__ __forceinline__ void window_end(Scan& sc, WarpShared& ws, int32_t W, 
     const bool near_hit = (cR != pR && cT != pT) || (T == 1 && (pb & 1));
     const bool pass = real && T > 0 && (!prefilter || near_hit);
     if (real && T == 1) sc.singles += 1u;
-    const uint32_t pm = __ballot_sync(kFull, pass);
-    if (pass) ws.sbuf[sc.nbuf + __popc(pm & lanemask_lt())] = (int32_t)(sc.id_base + s + lane - 1);
+    const bool lng = T - 1 > kLongSegments;
+    const uint32_t pm = __ballot_sync(kFull, pass && !lng), pl = __ballot_sync(kFull, pass && lng);
+    if (pass) {
+      const int32_t id = (int32_t)(sc.id_base + s + lane - 1);
+      if (lng) ws.lbuf[sc.nlong + __popc(pl & lanemask_lt())] = id;
+      else ws.sbuf[sc.nbuf + __popc(pm & lanemask_lt())] = id;
+    }
     sc.nbuf += __popc(pm);
-    sc.kept += __popc(pm);
-    if (sc.nbuf >= 32) flush_survivors(sc, ws.sbuf, surv, gst);
+    sc.nlong += __popc(pl);
+    sc.kept += __popc(pm | pl);
+    if (sc.nbuf >= 32) flush_ids(sc.nbuf, ws.sbuf, false, surv, gst);
+    if (sc.nlong >= 32) flush_ids(sc.nlong, ws.lbuf, true, surv, gst);
     sc.lastR = __shfl_sync(kFull, cR, n - 1);
     sc.lastT = __shfl_sync(kFull, cT, n - 1);
     sc.last_b = __shfl_sync(kFull, b, n - 1);
@@ -443,7 +455,7 @@ __device__ __forceinline__ bool warp_init(const Tract& t, int64_t s_lo, int64_t 
   sc.qx = sc.qy = sc.qz = 0;
   sc.steps = 0;
   sc.singles = sc.kept = sc.badc = 0;
-  sc.nbuf = 0;
+  sc.nbuf = sc.nlong = 0;
   sc.abort = false;
   sc.id_base = id_base;
   sc.sst = sst;
@@ -453,13 +465,14 @@ __device__ __forceinline__ bool warp_init(const Tract& t, int64_t s_lo, int64_t 
   return check_group(sc, sc.cA, s_lo, sc.V0);
 }
 
-__device__ __forceinline__ void warp_finish(Scan& sc, int32_t* sbuf, int32_t* surv, DevState* gst) {
+__device__ __forceinline__ void warp_finish(Scan& sc, WarpShared& ws, const SurvList& surv, DevState* gst) {
   // the last loaded group is checked here, and every boundary decided
   if (!sc.abort && sc.cbase + 32 <= sc.s_hi) check_group(sc, sc.cB, sc.cbase + 32, __shfl_sync(kFull, sc.cA, 31));
   if (!sc.abort && sc.s_cur != sc.s_hi + 1) {
     if (lane_id() == 0) set_error(sc.sst, kErrOffsets, (int32_t)sc.s_cur);
   }
-  flush_survivors(sc, sbuf, surv, gst);
+  flush_ids(sc.nbuf, ws.sbuf, false, surv, gst);
+  flush_ids(sc.nlong, ws.lbuf, true, surv, gst);
   unsigned long long s = sc.steps + sc.singles;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
@@ -499,7 +512,7 @@ __device__ __forceinline__ void load_half(const Tract& t, int64_t hq, int32_t (&
 // the range's first vertex starts a streamline, so no state carries over them.
 template <bool kSmem>
 __device__ __forceinline__ void scan_range_direct(Scan& sc, const VolView& v, const uint32_t* nw, const Tract& t,
-                                                  bool prefilter, WarpShared& ws, int32_t* surv, DevState* gst) {
+                                                  bool prefilter, WarpShared& ws, const SurvList& surv, DevState* gst) {
   const int64_t q0 = (int64_t)sc.V0 >> kWinLog2, q1 = (int64_t)(sc.V1 - 1) >> kWinLog2;
   const int64_t hq_lo = (int64_t)sc.V0 >> kHalfLog2, hq_hi = ((int64_t)(sc.V1 - 1) >> kHalfLog2) + 1;
   int32_t p[kLaneWords], nx[kLaneWords];
@@ -626,7 +639,7 @@ __device__ __forceinline__ bool ring_take(Ring& r, const Tract& t, int64_t& issu
 // when a wait timed out (the error is set and the ring may not be reused).
 template <bool kSmem>
 __device__ __forceinline__ bool scan_range_tma(Scan& sc, const VolView& v, const uint32_t* nw, const Tract& t,
-                                               bool prefilter, WarpShared& ws, Ring& r, int32_t* surv,
+                                               bool prefilter, WarpShared& ws, Ring& r, const SurvList& surv,
                                                DevState* gst) {
   // pieces wholly outside the vertex range (at the ends of the first and last
   // windows) are neither copied nor scanned
@@ -691,7 +704,7 @@ __host__ __device__ constexpr size_t ring_offset(size_t near_bytes) { return (ne
 
 template <int kMinBlocks, bool kTma, bool kSmem>
 __global__ void __launch_bounds__(kWarps * 32, kMinBlocks) prefilter_kernel(Tract t, VolView v, int prefilter,
-                                                                           int32_t* surv, DevState* st) {
+                                                                           SurvList surv, DevState* st) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ WarpShared ws_all[kWarps];
   uint32_t* s_near = reinterpret_cast<uint32_t*>(smem_raw);
@@ -712,7 +725,7 @@ __global__ void __launch_bounds__(kWarps * 32, kMinBlocks) prefilter_kernel(Trac
   } else {
     scan_range_direct<kSmem>(sc, v, nw, t, prefilter != 0, ws, surv, st);
   }
-  warp_finish(sc, ws.sbuf, surv, st);
+  warp_finish(sc, ws, surv, st);
 }
 
 // Batched form: warps take (subject, streamline range) tasks dynamically;
@@ -720,7 +733,7 @@ __global__ void __launch_bounds__(kWarps * 32, kMinBlocks) prefilter_kernel(Trac
 template <int kMinBlocks, bool kTma>
 __global__ void __launch_bounds__(kWarps * 32, kMinBlocks)
     prefilter_batch_kernel(const __grid_constant__ BatchTable tbl, const BatchTask* __restrict__ tasks,
-                           int32_t ntasks, int prefilter, int32_t* surv, DevState* gst) {
+                           int32_t ntasks, int prefilter, SurvList surv, DevState* gst) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ WarpShared ws_all[kWarps];
   WarpShared& ws = ws_all[threadIdx.x >> 5];
@@ -740,7 +753,7 @@ __global__ void __launch_bounds__(kWarps * 32, kMinBlocks)
       ring_ok = scan_range_tma<false>(sc, S.v, S.v.near, S.t, prefilter != 0, ws, r, surv, gst);
     else
       scan_range_direct<false>(sc, S.v, S.v.near, S.t, prefilter != 0, ws, surv, gst);
-    warp_finish(sc, ws.sbuf, surv, gst);
+    warp_finish(sc, ws, surv, gst);
     if (!ring_ok) break;  // a copy may still be in flight: this warp takes no more tasks
   }
 }
@@ -759,7 +772,7 @@ cudaError_t resident_grid(K kernel, size_t smem, int num_sms, int* grid) {
 }
 
 template <int kMinBlocks, bool kTma, bool kSmem>
-cudaError_t launch_plain(const Tract& t, const VolView& v, bool prefilter, int32_t* survivors, DevState* st,
+cudaError_t launch_plain(const Tract& t, const VolView& v, bool prefilter, const SurvList& survivors, DevState* st,
                          int num_sms, cudaStream_t s) {
   auto k = prefilter_kernel<kMinBlocks, kTma, kSmem>;
   const size_t near_bytes = kSmem ? (size_t)near_words(v) * 4 : 0;
@@ -777,7 +790,7 @@ cudaError_t launch_plain(const Tract& t, const VolView& v, bool prefilter, int32
 constexpr int64_t kNearSmemWordsTma = 8192;
 
 template <int kMinBlocks>
-cudaError_t launch_one(const Tract& t, const VolView& v, bool prefilter, bool tma, int32_t* survivors,
+cudaError_t launch_one(const Tract& t, const VolView& v, bool prefilter, bool tma, const SurvList& survivors,
                        DevState* st, int num_sms, cudaStream_t s) {
   const int64_t nw = near_words(v);
   if (tma) {
@@ -790,7 +803,7 @@ cudaError_t launch_one(const Tract& t, const VolView& v, bool prefilter, bool tm
 
 template <int kMinBlocks, bool kTma>
 cudaError_t launch_batch_one(const BatchTable& tbl, const BatchTask* tasks, int32_t ntasks, bool prefilter,
-                             int32_t* survivors, DevState* gst, int num_sms, cudaStream_t s) {
+                             const SurvList& survivors, DevState* gst, int num_sms, cudaStream_t s) {
   auto k = prefilter_batch_kernel<kMinBlocks, kTma>;
   const size_t bytes = kTma ? kRingBytes : 0;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
@@ -804,9 +817,10 @@ cudaError_t launch_batch_one(const BatchTable& tbl, const BatchTask* tasks, int3
 }  // namespace
 
 cudaError_t launch_prefilter_batch(const BatchTable& tbl, const BatchTask* tasks, int32_t ntasks, bool prefilter,
-                                   bool tma, int ctas_per_sm, int32_t* survivors, DevState* gst, int num_sms,
-                                   cudaStream_t s) {
+                                   bool tma, int ctas_per_sm, int32_t* survivor_ids, int64_t survivor_cap,
+                                   DevState* gst, int num_sms, cudaStream_t s) {
   if (ntasks <= 0) return cudaSuccess;
+  const SurvList survivors{survivor_ids, survivor_cap};
   if (tma) {
     if (ctas_per_sm >= 3) return launch_batch_one<3, true>(tbl, tasks, ntasks, prefilter, survivors, gst, num_sms, s);
     return launch_batch_one<2, true>(tbl, tasks, ntasks, prefilter, survivors, gst, num_sms, s);
@@ -816,9 +830,11 @@ cudaError_t launch_prefilter_batch(const BatchTable& tbl, const BatchTask* tasks
 }
 
 cudaError_t launch_prefilter(const Tract& t, const VolView& v, bool prefilter, uint32_t mode, bool tma,
-                             int ctas_per_sm, int32_t* survivors, DevState* st, int num_sms, cudaStream_t s) {
+                             int ctas_per_sm, int32_t* survivor_ids, int64_t survivor_cap, DevState* st, int num_sms,
+                             cudaStream_t s) {
   (void)mode;  // the segment and the vertex-only rules share the near test; the walk applies the rule
   if (t.ns <= 0) return cudaSuccess;
+  const SurvList survivors{survivor_ids, survivor_cap};
   if (ctas_per_sm >= 3) return launch_one<3>(t, v, prefilter, tma, survivors, st, num_sms, s);
   return launch_one<2>(t, v, prefilter, tma, survivors, st, num_sms, s);
 }

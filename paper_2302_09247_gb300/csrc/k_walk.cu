@@ -262,19 +262,18 @@ __device__ __forceinline__ uint32_t next_survivor(DevState* gst) {
 
 template <bool kBitV, bool kBitT>
 __global__ void __launch_bounds__(kWalkWarps * 32)
-    walk_kernel(Tract t, VolView v, const int32_t* __restrict__ surv,
-                                                              Accum acc, uint32_t mode, int32_t* __restrict__ ovf,
-                                                              DevState* st) {
+    walk_kernel(Tract t, VolView v, const int32_t* __restrict__ surv, int64_t surv_cap, Accum acc, uint32_t mode,
+                int32_t* __restrict__ ovf, DevState* st) {
   using S = Sets<kBitV, kBitT>;
   __shared__ WalkWarpSmem smem_all[kWalkWarps];
   WalkWarpSmem& sm = smem_all[threadIdx.x >> 5];
   S::init(sm);
-  const uint32_t n = st->n_survivors;
+  const uint32_t nl = st->n_long, n = st->n_survivors + nl;
   unsigned long long pairs_acc = 0;
   for (;;) {
     const uint32_t idx = next_survivor(st);
     if (idx >= n) break;
-    const int32_t s = surv[idx];
+    const int32_t s = survivor_at(surv, surv_cap, nl, idx);
     const int pairs = walk_one<S>(v, t, acc, mode, sm, s, s, ovf, st);
     if (pairs > 0) pairs_acc += (unsigned long long)pairs;
   }
@@ -293,17 +292,17 @@ __device__ __forceinline__ int subject_of(const BatchTable& tbl, int64_t g) {
 
 template <bool kBitV, bool kBitT>
 __global__ void __launch_bounds__(kWalkWarps * 32)
-    walk_batch_kernel(const __grid_constant__ BatchTable tbl, const int32_t* __restrict__ surv, uint32_t mode,
-                      int32_t* __restrict__ ovf, DevState* gst) {
+    walk_batch_kernel(const __grid_constant__ BatchTable tbl, const int32_t* __restrict__ surv, int64_t surv_cap,
+                      uint32_t mode, int32_t* __restrict__ ovf, DevState* gst) {
   using S = Sets<kBitV, kBitT>;
   __shared__ WalkWarpSmem smem_all[kWalkWarps];
   WalkWarpSmem& sm = smem_all[threadIdx.x >> 5];
   S::init(sm);
-  const uint32_t n = gst->n_survivors;
+  const uint32_t nl = gst->n_long, n = gst->n_survivors + nl;
   for (;;) {
     const uint32_t idx = next_survivor(gst);
     if (idx >= n) break;
-    const int32_t g = surv[idx];
+    const int32_t g = survivor_at(surv, surv_cap, nl, idx);
     const BatchSubject& B = tbl.s[subject_of(tbl, g)];
     const int pairs = walk_one<S>(B.v, B.t, B.acc, mode, sm, (int32_t)(g - B.sbase), g, ovf, gst);
     if (pairs > 0 && lane_id() == 0) atomicAdd(&B.st->pairs, (unsigned long long)pairs);
@@ -436,30 +435,29 @@ int walk_grid(K kernel, int num_sms) {
 }
 
 template <bool kBitV, bool kBitT>
-cudaError_t launch_walk_k(const Tract& t, const VolView& v, const int32_t* survivors, Accum acc, uint32_t mode,
-                          int32_t* overflow_list, DevState* st, int num_sms, cudaStream_t s) {
+cudaError_t launch_walk_k(const Tract& t, const VolView& v, const int32_t* survivors, int64_t surv_cap, Accum acc,
+                          uint32_t mode, int32_t* overflow_list, DevState* st, int num_sms, cudaStream_t s) {
   static const int grid = walk_grid(walk_kernel<kBitV, kBitT>, num_sms);
-  walk_kernel<kBitV, kBitT><<<grid, kWalkWarps * 32, 0, s>>>(t, v, survivors, acc, mode, overflow_list, st);
+  walk_kernel<kBitV, kBitT><<<grid, kWalkWarps * 32, 0, s>>>(t, v, survivors, surv_cap, acc, mode, overflow_list, st);
   return cudaGetLastError();
 }
 
 template <bool kBitV, bool kBitT>
-cudaError_t launch_walk_batch_k(const BatchTable& tbl, const int32_t* survivors, uint32_t mode,
+cudaError_t launch_walk_batch_k(const BatchTable& tbl, const int32_t* survivors, int64_t surv_cap, uint32_t mode,
                                 int32_t* overflow_list, DevState* gst, int num_sms, cudaStream_t s) {
   static const int grid = walk_grid(walk_batch_kernel<kBitV, kBitT>, num_sms);
-  walk_batch_kernel<kBitV, kBitT><<<grid, kWalkWarps * 32, 0, s>>>(tbl, survivors, mode, overflow_list, gst);
+  walk_batch_kernel<kBitV, kBitT><<<grid, kWalkWarps * 32, 0, s>>>(tbl, survivors, surv_cap, mode, overflow_list, gst);
   return cudaGetLastError();
 }
 
-cudaError_t launch_walk(const Tract& t, const VolView& v, const int32_t* survivors, Accum acc, uint32_t mode,
-                        int32_t* overflow_list, DevState* st, int num_sms, cudaStream_t s) {
+cudaError_t launch_walk(const Tract& t, const VolView& v, const int32_t* survivors, int64_t surv_cap, Accum acc,
+                        uint32_t mode, int32_t* overflow_list, DevState* st, int num_sms, cudaStream_t s) {
   if (t.ns <= 0) return cudaSuccess;
   const bool bv = v.n_roi <= kBitRowsMax, bt = v.n_lab < kBitLabelsMax;
-  if (bv && bt) return launch_walk_k<true, true>(t, v, survivors, acc, mode, overflow_list, st, num_sms, s);
-  if (bv) return launch_walk_k<true, false>(t, v, survivors, acc, mode, overflow_list, st, num_sms, s);
-  if (bt) return launch_walk_k<false, true>(t, v, survivors, acc, mode, overflow_list, st, num_sms, s);
-  return launch_walk_k<false, false>(t, v, survivors, acc, mode, overflow_list, st, num_sms, s);
-  return cudaGetLastError();
+  if (bv && bt) return launch_walk_k<true, true>(t, v, survivors, surv_cap, acc, mode, overflow_list, st, num_sms, s);
+  if (bv) return launch_walk_k<true, false>(t, v, survivors, surv_cap, acc, mode, overflow_list, st, num_sms, s);
+  if (bt) return launch_walk_k<false, true>(t, v, survivors, surv_cap, acc, mode, overflow_list, st, num_sms, s);
+  return launch_walk_k<false, false>(t, v, survivors, surv_cap, acc, mode, overflow_list, st, num_sms, s);
 }
 
 cudaError_t launch_walk_overflow(const Tract& t, const VolView& v, const int32_t* overflow_list, Accum acc,
@@ -471,18 +469,17 @@ cudaError_t launch_walk_overflow(const Tract& t, const VolView& v, const int32_t
   return cudaGetLastError();
 }
 
-cudaError_t launch_walk_batch(const BatchTable& tbl, const int32_t* survivors, uint32_t mode, int32_t* overflow_list,
-                              DevState* gst, int num_sms, cudaStream_t s) {
+cudaError_t launch_walk_batch(const BatchTable& tbl, const int32_t* survivors, int64_t surv_cap, uint32_t mode,
+                              int32_t* overflow_list, DevState* gst, int num_sms, cudaStream_t s) {
   bool bv = true, bt = true;
   for (int32_t i = 0; i < tbl.n; ++i) {
     bv &= tbl.s[i].v.n_roi <= kBitRowsMax;
     bt &= tbl.s[i].v.n_lab < kBitLabelsMax;
   }
-  if (bv && bt) return launch_walk_batch_k<true, true>(tbl, survivors, mode, overflow_list, gst, num_sms, s);
-  if (bv) return launch_walk_batch_k<true, false>(tbl, survivors, mode, overflow_list, gst, num_sms, s);
-  if (bt) return launch_walk_batch_k<false, true>(tbl, survivors, mode, overflow_list, gst, num_sms, s);
-  return launch_walk_batch_k<false, false>(tbl, survivors, mode, overflow_list, gst, num_sms, s);
-  return cudaGetLastError();
+  if (bv && bt) return launch_walk_batch_k<true, true>(tbl, survivors, surv_cap, mode, overflow_list, gst, num_sms, s);
+  if (bv) return launch_walk_batch_k<true, false>(tbl, survivors, surv_cap, mode, overflow_list, gst, num_sms, s);
+  if (bt) return launch_walk_batch_k<false, true>(tbl, survivors, surv_cap, mode, overflow_list, gst, num_sms, s);
+  return launch_walk_batch_k<false, false>(tbl, survivors, surv_cap, mode, overflow_list, gst, num_sms, s);
 }
 
 cudaError_t launch_walk_overflow_batch(const BatchTable& tbl, const int32_t* overflow_list, uint32_t mode,

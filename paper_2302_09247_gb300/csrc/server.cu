@@ -368,9 +368,11 @@ bool iterate(fastcod_server* S, uint32_t** tmp, size_t* tmp_cap) {
     if (e == cudaSuccess) e = cudaEventRecord(S->tasks_ev[turn], S->compute);
     if (e == cudaSuccess) e = cudaMemsetAsync(S->gst, 0, sizeof(DevState), S->compute);
     if (e == cudaSuccess)
-      e = fc::launch_prefilter_batch(tbl, S->tasks, (int32_t)tasks.size(), S->prefilter != 0, S->tma != 0, S->ctas, S->lists, S->gst,
-                                     S->num_sms, S->compute);
-    if (e == cudaSuccess) e = fc::launch_walk_batch(tbl, S->lists, S->mode, S->lists + S->lists_cap, S->gst, S->num_sms, S->compute);
+      e = fc::launch_prefilter_batch(tbl, S->tasks, (int32_t)tasks.size(), S->prefilter != 0, S->tma != 0, S->ctas,
+                                     S->lists, (int64_t)S->lists_cap, S->gst, S->num_sms, S->compute);
+    if (e == cudaSuccess)
+      e = fc::launch_walk_batch(tbl, S->lists, (int64_t)S->lists_cap, S->mode, S->lists + S->lists_cap, S->gst,
+                                S->num_sms, S->compute);
     if (e == cudaSuccess)
       e = fc::launch_walk_overflow_batch(tbl, S->lists + S->lists_cap, S->mode, S->scratch, kOverflowCtas, S->scratch_words,
                                          S->gst, S->compute);
