@@ -19,6 +19,10 @@
 namespace fc {
 
 constexpr int kWalkWarps = 8;
+// CTAs per SM the walk kernels are compiled for (at most 64 registers a
+// thread): the walk is latency-bound, and four CTAs (32 warps) per SM hide
+// more of it than three.
+constexpr int kWalkMinBlocks = 4;
 constexpr int kHV = 512, kLimV = 256;  // V_s table slots / size limit
 constexpr int kHT = 128, kLimT = 64;   // T_s table slots / size limit
 
@@ -261,7 +265,7 @@ __device__ __forceinline__ uint32_t next_survivor(DevState* gst) {
 }
 
 template <bool kBitV, bool kBitT>
-__global__ void __launch_bounds__(kWalkWarps * 32)
+__global__ void __launch_bounds__(kWalkWarps * 32, kWalkMinBlocks)
     walk_kernel(Tract t, VolView v, const int32_t* __restrict__ surv, int64_t surv_cap, Accum acc, uint32_t mode,
                 int32_t* __restrict__ ovf, DevState* st) {
   using S = Sets<kBitV, kBitT>;
@@ -291,7 +295,7 @@ __device__ __forceinline__ int subject_of(const BatchTable& tbl, int64_t g) {
 }
 
 template <bool kBitV, bool kBitT>
-__global__ void __launch_bounds__(kWalkWarps * 32)
+__global__ void __launch_bounds__(kWalkWarps * 32, kWalkMinBlocks)
     walk_batch_kernel(const __grid_constant__ BatchTable tbl, const int32_t* __restrict__ surv, int64_t surv_cap,
                       uint32_t mode, int32_t* __restrict__ ovf, DevState* gst) {
   using S = Sets<kBitV, kBitT>;
