@@ -2,17 +2,20 @@
 // streamline: passthrough, then C(v, r) += 1 for every pass-through v and
 // target r).
 //
-// One warp per surviving streamline, lanes over its segments.  Each lane
-// walks its segment with the exact integer walk and looks up the ROI row and
-// label of every voxel it enters (the per-voxel code is read through the
-// read-only cache and stays L2-resident).  The first voxel of a segment is the
-// last voxel of the previous one, so only the streamline's first segment
-// visits its start voxel.  Rows and labels are deduplicated per streamline in
-// two shared-memory open-addressing sets (V_s and T_s) after merging equal
-// keys across lanes with __match_any_sync.  The outer product V_s x T_s is
-// then added to C with one L2 reduction per pair, and the seed/endpoint pair
-// to C_end.  A streamline whose sets outgrow the tables is handed, whole, to
-// an exact CTA-per-streamline path with global-memory bitmaps.
+// One warp per surviving streamline (taken dynamically, the long ones
+// first), lanes over its segments.  Each lane walks its segment with the
+// exact integer walk and looks up the ROI row and label of every voxel it
+// enters (the per-voxel code is read through the read-only cache with an L2
+// evict-last hint).  The first voxel of a segment is the last voxel of the
+// previous one, so only the streamline's first segment visits its start
+// voxel; short segments whose start voxel lies far from every ROI and
+// labelled voxel are not walked.  Rows and labels are deduplicated per
+// streamline in two per-warp shared-memory sets (V_s and T_s): bitmaps when
+// the keys fit, else open-addressing hash sets after merging equal keys
+// across lanes with __match_any_sync.  The outer product V_s x T_s is then
+// added to C with one L2 reduction per pair, and the seed/endpoint pair to
+// C_end.  A streamline whose sets outgrow the tables is handed, whole, to an
+// exact CTA-per-streamline path with global-memory bitmaps.
 #include "fc_device.cuh"
 #include "fc_tma.cuh"
 
