@@ -77,8 +77,7 @@ void free_volumes(fastcod_ctx* c) {
   cudaFree(c->d_lab);
   cudaFree(c->d_bricks);
   cudaFree(c->d_near);
-  cudaFree(c->d_C);
-  cudaFree(c->d_Cend);
+  cudaFree(c->d_C);  // C_end shares this allocation
   cudaFree(c->d_scratch);
   c->d_code = nullptr;
   c->d_lab = nullptr;
@@ -144,14 +143,14 @@ fc::VolView vol_view(const fastcod_ctx* c) {
   return v;
 }
 
+// Bytes from C to C_end in their shared allocation.
+size_t accum_stride_bytes(size_t nm) { return nm ? (nm * 4 + 255) & ~(size_t)255 : 256; }
+
 // Stream-ordered zeroing of C, C_end and every device counter (the error
 // word included).
 int zero_accumulators(fastcod_ctx* c) {
   const size_t nm = (size_t)c->N * (size_t)c->M;
-  if (nm) {
-    CU(cudaMemsetAsync(c->d_C, 0, nm * 4, c->stream));
-    CU(cudaMemsetAsync(c->d_Cend, 0, nm * 4, c->stream));
-  }
+  if (nm) CU(cudaMemsetAsync(c->d_C, 0, accum_stride_bytes(nm) + nm * 4, c->stream));
   CU(cudaMemsetAsync(c->d_state, 0, sizeof(DevState), c->stream));
   c->total_streamlines = 0;
   c->total_vertices = 0;
@@ -345,8 +344,10 @@ FASTCOD_API int fastcod_set_volumes(fastcod_ctx* c, const int32_t* roi, const ui
   CU(cudaMalloc(&c->d_code, rb));
   CU(cudaMalloc(&c->d_lab, lb));
   CU(cudaMalloc(&c->d_bricks, (size_t)((nbricks + 15) / 16) * 4));
-  CU(cudaMalloc(&c->d_C, nm ? nm * 4 : 4));
-  CU(cudaMalloc(&c->d_Cend, nm ? nm * 4 : 4));
+  // C and C_end in one allocation (C_end at a 256-byte boundary), zeroed by
+  // one memset
+  CU(cudaMalloc(&c->d_C, 2 * accum_stride_bytes(nm)));
+  c->d_Cend = c->d_C + accum_stride_bytes(nm) / 4;
   CU(cudaMemsetAsync(c->d_bricks, 0, (size_t)((nbricks + 15) / 16) * 4, c->stream));
   // exact global-memory path for streamlines whose sets outgrow shared memory
   const int64_t words = fc::overflow_scratch_words(c->N, c->M);

@@ -707,6 +707,7 @@ __global__ void __launch_bounds__(kWarps * 32, kMinBlocks) prefilter_kernel(Trac
                                                                            SurvList surv, DevState* st) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ WarpShared ws_all[kWarps];
+  griddep_launch_dependents();  // the walk's CTAs may take SMs as this grid's CTAs end
   uint32_t* s_near = reinterpret_cast<uint32_t*>(smem_raw);
   if (kSmem) stage_near(v, s_near);
   const uint32_t* nw = kSmem ? s_near : v.near;

@@ -275,6 +275,8 @@ __global__ void __launch_bounds__(kWalkWarps * 32, kWalkMinBlocks)
   __shared__ WalkWarpSmem smem_all[kWalkWarps];
   WalkWarpSmem& sm = smem_all[threadIdx.x >> 5];
   S::init(sm);
+  griddep_launch_dependents();
+  griddep_wait();  // the prefilter's survivor list and counters
   const uint32_t nl = st->n_long, n = st->n_survivors + nl;
   unsigned long long pairs_acc = 0;
   for (;;) {
@@ -412,6 +414,7 @@ __global__ void __launch_bounds__(256) walk_overflow_kernel(Tract t, VolView v, 
                                                             Accum acc, uint32_t mode, uint32_t* scratch,
                                                             int64_t words_per_cta, DevState* st) {
   __shared__ int nV, nT;
+  griddep_wait();  // the walk's overflow list
   const uint32_t n = st->n_overflow;
   for (uint32_t i = blockIdx.x; i < n; i += gridDim.x)
     overflow_one(v, t, acc, mode, scratch + blockIdx.x * words_per_cta, ovf[i], st, &nV, &nT);
@@ -441,12 +444,30 @@ int walk_grid(K kernel, int num_sms) {
   return num_sms * (per_sm > 0 ? per_sm : 1);
 }
 
+// Launch in stream order with programmatic stream serialisation: the kernel
+// may be scheduled while the previous one ends and waits for it in
+// griddep_wait.
+template <typename... Params, typename... Args>
+cudaError_t launch_after_previous(void (*kernel)(Params...), int grid, int block, cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3((unsigned)block);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 template <bool kBitV, bool kBitT>
 cudaError_t launch_walk_k(const Tract& t, const VolView& v, const int32_t* survivors, int64_t surv_cap, Accum acc,
                           uint32_t mode, int32_t* overflow_list, DevState* st, int num_sms, cudaStream_t s) {
   static const int grid = walk_grid(walk_kernel<kBitV, kBitT>, num_sms);
-  walk_kernel<kBitV, kBitT><<<grid, kWalkWarps * 32, 0, s>>>(t, v, survivors, surv_cap, acc, mode, overflow_list, st);
-  return cudaGetLastError();
+  return launch_after_previous(walk_kernel<kBitV, kBitT>, grid, kWalkWarps * 32, s, t, v, survivors, surv_cap, acc,
+                               mode, overflow_list, st);
 }
 
 template <bool kBitV, bool kBitT>
@@ -471,9 +492,8 @@ cudaError_t launch_walk_overflow(const Tract& t, const VolView& v, const int32_t
                                  uint32_t mode, uint32_t* scratch, int32_t scratch_ctas, DevState* st,
                                  cudaStream_t s) {
   if (t.ns <= 0) return cudaSuccess;
-  walk_overflow_kernel<<<scratch_ctas, 256, 0, s>>>(t, v, overflow_list, acc, mode, scratch,
-                                                    overflow_scratch_words(v.n_roi, v.n_lab), st);
-  return cudaGetLastError();
+  return launch_after_previous(walk_overflow_kernel, scratch_ctas, 256, s, t, v, overflow_list, acc, mode, scratch,
+                               overflow_scratch_words(v.n_roi, v.n_lab), st);
 }
 
 cudaError_t launch_walk_batch(const BatchTable& tbl, const int32_t* survivors, int64_t surv_cap, uint32_t mode,
