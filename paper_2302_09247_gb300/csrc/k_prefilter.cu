@@ -50,19 +50,19 @@ namespace fc {
 
 namespace {
 
-constexpr int kHalfLog2 = 8;
-constexpr int kHalf = 1 << kHalfLog2;     // vertices per piece (= per TMA slot)
+constexpr int kPieceLog2 = 8;
+constexpr int kPiece = 1 << kPieceLog2;     // vertices per piece (= per TMA slot)
 constexpr int kPieces = PREFILTER_PIECES;  // pieces per window
-constexpr int kWinLog2 = kHalfLog2 + ilog2(kPieces);
+constexpr int kWinLog2 = kPieceLog2 + ilog2(kPieces);
 constexpr int kWin = 1 << kWinLog2;       // vertices per window
 constexpr int kCountWords = kPieces / 2;  // per-lane hit counts: two pieces (R, T bytes) per word
 static_assert(kPieces == 2 || kPieces == 4 || kPieces == 8, "2, 4 or 8 pieces per window");
 // a lane's hit bits of every piece of a window, 8 per piece
 using HitWord = typename std::conditional<(kPieces > 4), unsigned long long, uint32_t>::type;
-constexpr int kVpl = kHalf / 32;          // vertices per lane per half
-constexpr int kLaneWords = kVpl * 3;      // 24 int32 per lane per half
-constexpr int kHalfWords = kHalf * 3;     // 768 int32 = 3072 bytes
-constexpr int kStages = 3;                // TMA ring depth per warp (halves)
+constexpr int kVpl = kPiece / 32;          // vertices per lane per piece
+constexpr int kLaneWords = kVpl * 3;      // 24 int32 per lane per piece
+constexpr int kPieceWords = kPiece * 3;     // 768 int32 = 3072 bytes
+constexpr int kStages = 3;                // TMA ring depth per warp (pieces)
 constexpr int kWarps = 8;                 // warps per CTA
 constexpr uint64_t kWaitTimeoutNs = 1000000000ull;  // 1 s
 constexpr int32_t kInf = 0x7fffffff;
@@ -215,17 +215,17 @@ __device__ __forceinline__ void window_begin(Scan& sc, WarpShared& ws, int32_t W
   __syncwarp();
 }
 
-// 2. Half h of window W: p = the lane's 24 words, vertices
-//    W + h*kHalf + 8l .. +7 (zero past the end of the array).  Returns the
+// 2. Piece h of window W: p = the lane's 24 words, vertices
+//    W + h*kPiece + 8l .. +7 (zero past the end of the array).  Returns the
 //    lane's hit bits (R hits at the even bits k, T hits at bits k + 1, for
 //    the lookups at the even slots k).
 template <bool kSmem>
-__device__ __forceinline__ uint32_t scan_half(Scan& sc, const VolView& v, const uint32_t* nw,
+__device__ __forceinline__ uint32_t scan_piece(Scan& sc, const VolView& v, const uint32_t* nw,
                                               const int32_t (&p)[kLaneWords], int h, int32_t W, const WarpShared& ws) {
   const int32_t lane = (int32_t)lane_id();
-  const uint32_t st8 = ((ws.st[h * (kHalf / 32) + (lane >> 2)] >> ((lane & 3) << 3)) & 0xffu) |
+  const uint32_t st8 = ((ws.st[h * (kPiece / 32) + (lane >> 2)] >> ((lane & 3) << 3)) & 0xffu) |
                        ((h == 0 && lane == 0) ? sc.carry : 0u);
-  const int32_t base = W + h * kHalf + kVpl * lane;
+  const int32_t base = W + h * kPiece + kVpl * lane;
   const int32_t lo = sc.V0 - base, hi = sc.V1 - base;
   const uint32_t valid8 = lowmask(min(max(hi, 0), kVpl)) & ~lowmask(min(max(lo, 0), kVpl));
   const uint32_t keep8 = valid8 & ~st8;  // slots whose incoming segment is counted
@@ -322,7 +322,7 @@ __device__ __forceinline__ void window_end(Scan& sc, WarpShared& ws, int32_t W, 
     const int n = min(nbw, 32);
     const bool in = lane < n;
     const int32_t x = min(max(b - W, 0), kWin);
-    const int32_t hx = x >> kHalfLog2, xi = x & (kHalf - 1);
+    const int32_t hx = x >> kPieceLog2, xi = x & (kPiece - 1);
     const int32_t src = xi >> 3, o = xi & 7;
     uint32_t e = __shfl_sync(kFull, excl[0], src);
 #pragma unroll
@@ -486,10 +486,10 @@ __device__ __forceinline__ void warp_finish(Scan& sc, WarpShared& ws, const Surv
 
 // ------------------------------------------------------------------ direct
 
-// The lane's 24 words of half hq (vertices hq * kHalf + 8l ..; zero past the
+// The lane's 24 words of piece hq (vertices hq * kPiece + 8l ..; zero past the
 // end of the array).
-__device__ __forceinline__ void load_half(const Tract& t, int64_t hq, int32_t (&p)[kLaneWords]) {
-  const int64_t g = (hq << kHalfLog2) + kVpl * lane_id();  // the lane's first vertex
+__device__ __forceinline__ void load_piece(const Tract& t, int64_t hq, int32_t (&p)[kLaneWords]) {
+  const int64_t g = (hq << kPieceLog2) + kVpl * lane_id();  // the lane's first vertex
   if (g + kVpl <= t.nv) {
     const int4* e = reinterpret_cast<const int4*>(t.xyz + 3 * g);  // 96-byte chunk, 16-byte aligned
 #pragma unroll
@@ -514,9 +514,9 @@ template <bool kSmem>
 __device__ __forceinline__ void scan_range_direct(Scan& sc, const VolView& v, const uint32_t* nw, const Tract& t,
                                                   bool prefilter, WarpShared& ws, const SurvList& surv, DevState* gst) {
   const int64_t q0 = (int64_t)sc.V0 >> kWinLog2, q1 = (int64_t)(sc.V1 - 1) >> kWinLog2;
-  const int64_t hq_lo = (int64_t)sc.V0 >> kHalfLog2, hq_hi = ((int64_t)(sc.V1 - 1) >> kHalfLog2) + 1;
+  const int64_t hq_lo = (int64_t)sc.V0 >> kPieceLog2, hq_hi = ((int64_t)(sc.V1 - 1) >> kPieceLog2) + 1;
   int32_t p[kLaneWords], nx[kLaneWords];
-  load_half(t, hq_lo, nx);
+  load_piece(t, hq_lo, nx);
   for (int64_t q = q0; q <= q1 && !sc.abort; ++q) {
     const int32_t W = (int32_t)(q << kWinLog2);
     int32_t nbw, b_first;
@@ -529,8 +529,8 @@ __device__ __forceinline__ void scan_range_direct(Scan& sc, const VolView& v, co
       const int64_t hq = q * kPieces + h;
 #pragma unroll
       for (int w = 0; w < kLaneWords; ++w) p[w] = nx[w];
-      if (hq + 1 < hq_hi) load_half(t, hq + 1, nx);
-      hh |= (HitWord)scan_half<kSmem>(sc, v, nw, p, h, W, ws) << (8 * h);
+      if (hq + 1 < hq_hi) load_piece(t, hq + 1, nx);
+      hh |= (HitWord)scan_piece<kSmem>(sc, v, nw, p, h, W, ws) << (8 * h);
     }
     window_end(sc, ws, W, nbw, b_first, hh, prefilter, surv, gst);
   }
@@ -538,7 +538,7 @@ __device__ __forceinline__ void scan_range_direct(Scan& sc, const VolView& v, co
 
 // --------------------------------------------------------------------- tma
 
-// Per-warp ring of kStages half-window slots filled by 1-D bulk copies.
+// Per-warp ring of kStages piece slots filled by 1-D bulk copies.
 // Slots are used in a fixed cyclic order for the warp's whole life (slot,
 // phase), so ranges follow one another without re-initialising barriers:
 // a range issues its first pieces into the slots after the last one used,
@@ -546,10 +546,10 @@ __device__ __forceinline__ void scan_range_direct(Scan& sc, const VolView& v, co
 // 128-byte aligned, so every warp's ring (a bulk-copy destination) starts on
 // a 16-byte boundary.
 struct __align__(128) TmaSmem {
-  int32_t ring[kStages][kHalfWords];
+  int32_t ring[kStages][kPieceWords];
   uint64_t bar[kStages];
 };
-static_assert(sizeof(TmaSmem) % 128 == 0 && (kHalfWords * 4) % 16 == 0, "ring slots must stay 16-byte aligned");
+static_assert(sizeof(TmaSmem) % 128 == 0 && (kPieceWords * 4) % 16 == 0, "ring slots must stay 16-byte aligned");
 
 struct Ring {
   TmaSmem* sm;
@@ -568,23 +568,23 @@ struct Ring {
     __syncwarp();
   }
 
-  // lane 0 only: copy half hq of t into slot k.  A whole half is one bulk
+  // lane 0 only: copy piece hq of t into slot k.  A whole piece is one bulk
   // copy; at the end of the array the part that is not a multiple of 16 bytes
   // is copied with plain loads and the rest of the slot zero-filled.
   __device__ __forceinline__ void issue(const Tract& t, int64_t hq, uint32_t k) {
-    const int64_t v0 = hq << kHalfLog2;
+    const int64_t v0 = hq << kPieceLog2;
     int32_t* dst = sm->ring[k];
     const int32_t* src = t.xyz + 3 * v0;
-    if (v0 + kHalf <= t.nv) {
-      mbar_arrive_expect_tx(&sm->bar[k], (uint32_t)(kHalfWords * 4));
-      bulk_g2s(dst, src, (uint32_t)(kHalfWords * 4), &sm->bar[k], policy);
+    if (v0 + kPiece <= t.nv) {
+      mbar_arrive_expect_tx(&sm->bar[k], (uint32_t)(kPieceWords * 4));
+      bulk_g2s(dst, src, (uint32_t)(kPieceWords * 4), &sm->bar[k], policy);
       return;
     }
     const int64_t n = max((int64_t)0, t.nv - v0);
     const uint32_t bytes = (uint32_t)(n * 12);
     const uint32_t tma = bytes & ~15u;
     for (uint32_t w = tma >> 2; w < (bytes >> 2); ++w) dst[w] = __ldcs(src + w);
-    for (uint32_t w = bytes >> 2; w < (uint32_t)kHalfWords; ++w) dst[w] = 0;
+    for (uint32_t w = bytes >> 2; w < (uint32_t)kPieceWords; ++w) dst[w] = 0;
     if (tma) {
       mbar_arrive_expect_tx(&sm->bar[k], tma);
       bulk_g2s(dst, src, tma, &sm->bar[k], policy);
@@ -607,7 +607,7 @@ struct Ring {
   }
 };
 
-// Takes the next half from the ring into p and refills its slot with half
+// Takes the next piece from the ring into p and refills its slot with piece
 // `issued` when that is still part of the range (hq_end exclusive).  False
 // when the wait timed out.
 __device__ __forceinline__ bool ring_take(Ring& r, const Tract& t, int64_t& issued, int64_t hq_end,
@@ -622,7 +622,7 @@ __device__ __forceinline__ bool ring_take(Ring& r, const Tract& t, int64_t& issu
     p[4 * i + 2] = a.z;
     p[4 * i + 3] = a.w;
   }
-  // the half is in registers: its slot takes the next piece
+  // the piece is in registers: its slot takes the next one
   __syncwarp();
   if (issued < hq_end) {
     if (lane_id() == 0) {
@@ -644,7 +644,7 @@ __device__ __forceinline__ bool scan_range_tma(Scan& sc, const VolView& v, const
   // pieces wholly outside the vertex range (at the ends of the first and last
   // windows) are neither copied nor scanned
   const int64_t q0 = (int64_t)sc.V0 >> kWinLog2, q1 = (int64_t)(sc.V1 - 1) >> kWinLog2;
-  const int64_t hq_lo = (int64_t)sc.V0 >> kHalfLog2, hq_end = ((int64_t)(sc.V1 - 1) >> kHalfLog2) + 1;
+  const int64_t hq_lo = (int64_t)sc.V0 >> kPieceLog2, hq_end = ((int64_t)(sc.V1 - 1) >> kPieceLog2) + 1;
   int64_t taken = hq_lo;                           // pieces [hq_lo, taken) consumed
   int64_t issued = min(hq_end, hq_lo + kStages);   // pieces [taken, issued) in flight
   if (lane_id() == 0) {
@@ -671,7 +671,7 @@ __device__ __forceinline__ bool scan_range_tma(Scan& sc, const VolView& v, const
         break;
       }
       ++taken;
-      hh |= (HitWord)scan_half<kSmem>(sc, v, nw, p, h, W, ws) << (8 * h);
+      hh |= (HitWord)scan_piece<kSmem>(sc, v, nw, p, h, W, ws) << (8 * h);
     }
     if (ok) window_end(sc, ws, W, nbw, b_first, hh, prefilter, surv, gst);
   }
@@ -680,7 +680,7 @@ __device__ __forceinline__ bool scan_range_tma(Scan& sc, const VolView& v, const
     sc.abort = true;
   }
   // no copy may be in flight when the range ends: bounded drain of the
-  // halves issued but not consumed
+  // pieces issued but not consumed
   for (; taken < issued; ++taken) {
     if (!r.wait()) {
       ok = false;
