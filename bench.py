@@ -38,8 +38,8 @@ METRIC = "DDA voxel-steps/s & subjects/s for C, bit-exact; batched vs plain; p50
 # vertex count (the stream is read once, so traffic grows with the vertices).
 PREFILTER_SOURCES = ("paper_2302_09247_gb300/csrc/k_prefilter.cu", "paper_2302_09247_gb300/csrc/fc_tma.cuh",
                      "paper_2302_09247_gb300/csrc/fc_internal.cuh", "paper_2302_09247_gb300/csrc/fc_device.cuh")
-PREFILTER_TRAFFIC = {"sha256": "abf3ecdb2208d21287498ed65d61d530c6b9000dc0d47df72e6cc147783d780b",
-                     "bytes": 2491837952, "vertices": 205420297,
+PREFILTER_TRAFFIC = {"sha256": "e995f4dc86d63df4779f09f7d17520a1d21bf77965041188195eb309d85d6538",
+                     "bytes": 2491725824, "vertices": 205420297,
                      "summary": "profiles/prefilter_kernel_hcp145x174x145.md"}
 
 

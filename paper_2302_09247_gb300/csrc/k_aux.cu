@@ -214,7 +214,10 @@ __global__ void __launch_bounds__(kThreads) upsample_offsets_kernel(const int64_
 // one carry test each.  The running sums are kept modulo 2^32: every point
 // lies between p and q, so its int32 value is exact.  A round computes the
 // points of up to 32 segments into a per-warp shared buffer; the warp then
-// writes the round's contiguous output with coalesced stores.
+// writes the round's contiguous output with coalesced stores.  The next
+// round's vertices and the next streamline's offsets load while a round is
+// computed and written, so that a streamline costs about one memory round
+// trip instead of one per round.
 constexpr int kUpCap = 256;  // points staged per warp (3 KB)
 
 __device__ __forceinline__ void seg_split(int64_t d, int32_t factor, int32_t flog2, uint32_t& q0, uint32_t& r0) {
@@ -237,15 +240,25 @@ __device__ __forceinline__ void seg_split(int64_t d, int32_t factor, int32_t flo
   }
 }
 
+// Vertices i and i + 1 (the segment's ends).
+__device__ __forceinline__ void load_segment(const int32_t* __restrict__ xyz, int64_t i, int32_t (&pa)[3],
+                                             int32_t (&pb)[3]) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    pa[c] = __ldg(xyz + 3 * i + c);
+    pb[c] = __ldg(xyz + 3 * (i + 1) + c);
+  }
+}
+
 struct SegPoints {
   uint32_t p[3], q0[3], r0[3], acc_q[3], acc_r[3];
 
-  __device__ __forceinline__ void init(const int32_t* __restrict__ xyz, int64_t i, int32_t factor, int32_t flog2) {
+  __device__ __forceinline__ void init(const int32_t (&pa)[3], const int32_t (&pb)[3], int32_t factor,
+                                       int32_t flog2) {
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      const int32_t a = __ldg(xyz + 3 * i + c);
-      p[c] = (uint32_t)a;
-      seg_split((int64_t)__ldg(xyz + 3 * (i + 1) + c) - a, factor, flog2, q0[c], r0[c]);
+      p[c] = (uint32_t)pa[c];
+      seg_split((int64_t)pb[c] - pa[c], factor, flog2, q0[c], r0[c]);
       acc_q[c] = 0;
       acc_r[c] = 0;
     }
@@ -275,37 +288,63 @@ __global__ void __launch_bounds__(kThreads) upsample_kernel(const int32_t* __res
   const int32_t lane = (int32_t)lane_id();
   const int32_t per = factor <= kUpCap ? min(32, kUpCap / factor) : 0;  // segments per round
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; s < ns; s += nwarps) {
-    const int64_t a = off[s], b = off[s + 1];
-    if (b == a) continue;
-    const int64_t o = out_off[s];
-    if (lane == 0) {
+  const int64_t s0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int64_t a = 0, b = 0, o = 0;
+  if (s0 < ns) {
+    a = off[s0];
+    b = off[s0 + 1];
+    o = out_off[s0];
+  }
+  for (int64_t s = s0; s < ns; s += nwarps) {
+    int64_t an = 0, bn = 0, on = 0;  // the next streamline's offsets, in flight
+    if (s + nwarps < ns) {
+      an = off[s + nwarps];
+      bn = off[s + nwarps + 1];
+      on = out_off[s + nwarps];
+    }
+    if (b > a) {
+      if (lane == 0) {
 #pragma unroll
-      for (int c = 0; c < 3; ++c) out[3 * (o + (b - 1 - a) * factor) + c] = __ldg(xyz + 3 * (b - 1) + c);
-    }
-    if (per == 0) {  // factors above the staging capacity: each lane writes its own segments
-      for (int64_t i = a + lane; i + 1 < b; i += 32) {
-        SegPoints g;
-        g.init(xyz, i, factor, flog2);
-        int32_t* dst = out + 3 * (o + (i - a) * factor);
-        for (int32_t j = 0; j < factor; ++j) g.emit(dst + 3 * j, factor);
+        for (int c = 0; c < 3; ++c) out[3 * (o + (b - 1 - a) * factor) + c] = __ldg(xyz + 3 * (b - 1) + c);
       }
-      continue;
-    }
-    for (int64_t i0 = a; i0 + 1 < b; i0 += per) {
-      const int32_t nseg = (int32_t)min((int64_t)per, b - 1 - i0);
-      if (lane < nseg) {
-        SegPoints g;
-        g.init(xyz, i0 + lane, factor, flog2);
-        int32_t* w = sb + 3 * lane * factor;
-        for (int32_t j = 0; j < factor; ++j) g.emit(w + 3 * j, factor);
+      if (per == 0) {  // factors above the staging capacity: each lane writes its own segments
+        for (int64_t i = a + lane; i + 1 < b; i += 32) {
+          int32_t pa[3], pb[3];
+          load_segment(xyz, i, pa, pb);
+          SegPoints g;
+          g.init(pa, pb, factor, flog2);
+          int32_t* dst = out + 3 * (o + (i - a) * factor);
+          for (int32_t j = 0; j < factor; ++j) g.emit(dst + 3 * j, factor);
+        }
+      } else {
+        int32_t cp[3] = {0, 0, 0}, cq[3] = {0, 0, 0};  // this round's segment of the lane
+        if (a + lane + 1 < b && lane < per) load_segment(xyz, a + lane, cp, cq);
+        for (int64_t i0 = a; i0 + 1 < b; i0 += per) {
+          const int32_t nseg = (int32_t)min((int64_t)per, b - 1 - i0);
+          int32_t np[3] = {0, 0, 0}, nq[3] = {0, 0, 0};  // the next round's, in flight
+          if (i0 + per + lane + 1 < b && lane < per) load_segment(xyz, i0 + per + lane, np, nq);
+          if (lane < nseg) {
+            SegPoints g;
+            g.init(cp, cq, factor, flog2);
+            int32_t* w = sb + 3 * lane * factor;
+            for (int32_t j = 0; j < factor; ++j) g.emit(w + 3 * j, factor);
+          }
+          __syncwarp();
+          const int32_t nw = 3 * nseg * factor;
+          int32_t* dst = out + 3 * (o + (i0 - a) * factor);
+          for (int32_t k = lane; k < nw; k += 32) __stcs(dst + k, sb[k]);
+          __syncwarp();
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            cp[c] = np[c];
+            cq[c] = nq[c];
+          }
+        }
       }
-      __syncwarp();
-      const int32_t nw = 3 * nseg * factor;
-      int32_t* dst = out + 3 * (o + (i0 - a) * factor);
-      for (int32_t k = lane; k < nw; k += 32) __stcs(dst + k, sb[k]);
-      __syncwarp();
     }
+    a = an;
+    b = bn;
+    o = on;
   }
 }
 
