@@ -141,6 +141,10 @@ typedef struct {
   double ms_prefilter;     /* K2: prefilter + compaction */
   double ms_walk;          /* K3: walk + dedup + accumulate */
   double ms_overflow;      /* exact global-memory path for oversized sets */
+  int64_t aux_calls;       /* calls beside the path profiled (parcellate, world-mm
+                              conversion, upsample, rescale) */
+  double ms_aux;           /* their kernels' device time (the host-side checks and
+                              synchronisations between kernels excluded) */
 } fastcod_profile;
 
 /* Create a context on CUDA device cuda_device.  Allocates only small state;

@@ -84,6 +84,27 @@ int state_end(fastcod_ctx* c, const DevState* st, const char* what) {
   }
 }
 
+// Device time of a span of kernels while profiling: events before and after
+// the span; span_end waits for the stream and adds the elapsed time.
+int span_begin(fastcod_ctx* c) {
+  if (!c->profile) return FASTCOD_OK;
+  for (cudaEvent_t& e : c->aux_ev)
+    if (!e) CU(cudaEventCreate(&e));
+  CU(cudaEventRecord(c->aux_ev[0], c->stream));
+  return FASTCOD_OK;
+}
+
+int span_end(fastcod_ctx* c, bool count_call) {
+  if (!c->profile) return FASTCOD_OK;
+  CU(cudaEventRecord(c->aux_ev[1], c->stream));
+  CU(cudaEventSynchronize(c->aux_ev[1]));
+  float ms = 0.0f;
+  CU(cudaEventElapsedTime(&ms, c->aux_ev[0], c->aux_ev[1]));
+  c->prof.ms_aux += ms;
+  if (count_call) c->prof.aux_calls += 1;
+  return FASTCOD_OK;
+}
+
 int begin(fastcod_ctx* c) {
   if (!c) return FASTCOD_EINVAL;
   c->err.clear();
@@ -102,7 +123,9 @@ int check_streamlines(fastcod_ctx* c, const void* xyz, int64_t nv, const int64_t
 int validate_offsets(fastcod_ctx* c, const int64_t* d_off, int64_t ns, int64_t nv, const char* what) {
   DevState* st = nullptr;
   if (int rc = state_begin(c, &st)) return rc;
+  if (int rc = span_begin(c)) return rc;
   CU(fc::launch_check_offsets(d_off, ns, nv, st, c->stream));
+  if (int rc = span_end(c, false)) return rc;
   return state_end(c, st, what);
 }
 
@@ -111,7 +134,9 @@ int world_to_fixed_into(fastcod_ctx* c, const float* xyz_mm, int64_t nv, const f
   if (int rc = stage_in(c, kIn, xyz_mm, (size_t)nv * 12, &d_in)) return rc;
   DevState* st = nullptr;
   if (int rc = state_begin(c, &st)) return rc;
+  if (int rc = span_begin(c)) return rc;
   CU(fc::launch_world_to_fixed(static_cast<const float*>(d_in), nv, affine, d_out, st, c->stream));
+  if (int rc = span_end(c, true)) return rc;
   return state_end(c, st, "world-mm ingest");
 }
 
@@ -131,8 +156,10 @@ FASTCOD_API int fastcod_parcellate(fastcod_ctx* c, int32_t which, int32_t* label
   if (int rc = out_dst(c, kOut, label_out, (size_t)N * 4, &d_label)) return rc;
   if (fractions_out)
     if (int rc = out_dst(c, kOut2, fractions_out, (size_t)N * M * 4, &d_frac)) return rc;
+  if (int rc = span_begin(c)) return rc;
   CU(fc::launch_parcellate(which ? c->d_Cend : c->d_C, N, M, static_cast<int32_t*>(d_label),
                            static_cast<float*>(d_frac), c->stream));
+  if (int rc = span_end(c, true)) return rc;
   if (int rc = copy_out(c, label_out, d_label, (size_t)N * 4)) return rc;
   if (fractions_out)
     if (int rc = copy_out(c, fractions_out, d_frac, (size_t)N * M * 4)) return rc;
@@ -182,8 +209,10 @@ FASTCOD_API int fastcod_upsample_factor(fastcod_ctx* c, const int32_t* xyz, int6
   void* d_best = nullptr;
   if (int rc = slot(c, kTmp, 8, &d_best)) return rc;
   CU(cudaMemsetAsync(d_best, 0, 8, c->stream));
+  if (int rc = span_begin(c)) return rc;
   CU(fc::launch_seg_max(static_cast<const int32_t*>(d_xyz), off, n_streamlines,
                         static_cast<unsigned long long*>(d_best), c->stream));
+  if (int rc = span_end(c, true)) return rc;
   unsigned long long best = 0;
   CU(cudaMemcpyAsync(&best, d_best, 8, cudaMemcpyDeviceToHost, c->stream));
   CU(cudaStreamSynchronize(c->stream));
@@ -218,7 +247,9 @@ FASTCOD_API int fastcod_upsample(fastcod_ctx* c, const int32_t* xyz, int64_t n_v
   if (int rc = out_dst(c, kOut2, offsets_out, (size_t)(n_streamlines + 1) * 8, &d_oo)) return rc;
   if (int rc = slot(c, kTmp, (size_t)fc::upsample_scan_blocks(n_streamlines) * 8, &d_tmp)) return rc;
   int64_t* oo = static_cast<int64_t*>(d_oo);
+  if (int rc = span_begin(c)) return rc;
   CU(fc::launch_upsample_offsets(off, n_streamlines, factor, static_cast<long long*>(d_tmp), oo, c->stream));
+  if (int rc = span_end(c, false)) return rc;
   int64_t total = 0;
   CU(cudaMemcpyAsync(&total, oo + n_streamlines, 8, cudaMemcpyDeviceToHost, c->stream));
   CU(cudaStreamSynchronize(c->stream));
@@ -229,9 +260,13 @@ FASTCOD_API int fastcod_upsample(fastcod_ctx* c, const int32_t* xyz, int64_t n_v
   void* d_out = nullptr;
   if (total > 0) {
     if (int rc = out_dst(c, kOut, xyz_out, (size_t)total * 12, &d_out)) return rc;
+    if (int rc = span_begin(c)) return rc;
     CU(fc::launch_upsample_vertices(static_cast<const int32_t*>(d_xyz), off, n_streamlines, factor, oo,
                                     static_cast<int32_t*>(d_out), c->stream));
+    if (int rc = span_end(c, true)) return rc;
     if (int rc = copy_out(c, xyz_out, d_out, (size_t)total * 12)) return rc;
+  } else if (c->profile) {
+    c->prof.aux_calls += 1;
   }
   if (int rc = copy_out(c, offsets_out, d_oo, (size_t)(n_streamlines + 1) * 8)) return rc;
   CU(cudaStreamSynchronize(c->stream));
@@ -253,8 +288,10 @@ FASTCOD_API int fastcod_rescale(fastcod_ctx* c, const int32_t* xyz, int64_t n_ve
   if (int rc = out_dst(c, kOut, xyz_out, (size_t)n_vertices * 12, &d_out)) return rc;
   DevState* st = nullptr;
   if (int rc = state_begin(c, &st)) return rc;
+  if (int rc = span_begin(c)) return rc;
   CU(fc::launch_rescale(static_cast<const int32_t*>(d_in), n_vertices, num, den, add, static_cast<int32_t*>(d_out), st,
                         c->stream));
+  if (int rc = span_end(c, true)) return rc;
   if (int rc = state_end(c, st, "rescale")) return rc;
   if (int rc = copy_out(c, xyz_out, d_out, (size_t)n_vertices * 12)) return rc;
   CU(cudaStreamSynchronize(c->stream));

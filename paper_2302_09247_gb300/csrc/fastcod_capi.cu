@@ -276,6 +276,8 @@ FASTCOD_API int fastcod_destroy(fastcod_ctx* c) {
   cudaFree(c->d_state);
   for (auto& set : c->ev_pool)
     for (int i = 0; i < 5; ++i) cudaEventDestroy(set.e[i]);
+  for (cudaEvent_t e : c->aux_ev)
+    if (e) cudaEventDestroy(e);
   if (c->own_stream) cudaStreamDestroy(c->own_stream);
   delete c;
   return FASTCOD_OK;
@@ -564,7 +566,7 @@ FASTCOD_API int fastcod_set_option(fastcod_ctx* c, int32_t key, int64_t value) {
       if (value && !c->profile) {
         // switching on starts a fresh profile
         const int64_t launches = c->prof.kernel_launches;
-        c->prof = fastcod_profile{0, launches, 0.0, 0.0, 0.0, 0.0};
+        c->prof = fastcod_profile{0, launches, 0.0, 0.0, 0.0, 0.0, 0, 0.0};
       }
       c->profile = (int)value;
       return FASTCOD_OK;

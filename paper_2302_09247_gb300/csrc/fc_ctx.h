@@ -65,7 +65,8 @@ struct fastcod_ctx {
   std::vector<EvSet> ev_pool;  // event sets of profiled calls
   size_t ev_used = 0;          // sets recorded and not yet folded into prof
   EvSet* ev_cur = nullptr;
-  fastcod_profile prof = {0, 0, 0.0, 0.0, 0.0, 0.0};
+  fastcod_profile prof = {0, 0, 0.0, 0.0, 0.0, 0.0, 0, 0.0};
+  cudaEvent_t aux_ev[2] = {nullptr, nullptr};  // kernel spans of the calls beside the path
 
   // device scratch of the entry points beside the path (aux_capi.cu)
   static constexpr int kAuxSlots = 6;

@@ -66,6 +66,57 @@ __global__ void __launch_bounds__(kThreads) parcellate_kernel(const int32_t* __r
   }
 }
 
+// The same for rows of at most 32 * kPer entries, each lane's entries held in
+// registers: one load per entry, all issued at once, and the fractions
+// computed from the registers (the generic kernel reads the row twice).
+template <int kPer>
+__global__ void __launch_bounds__(kThreads) parcellate_rows_kernel(const int32_t* __restrict__ C, int32_t N,
+                                                                   int32_t M, int32_t* __restrict__ label,
+                                                                   float* __restrict__ frac) {
+  const int32_t lane = (int32_t)lane_id();
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < N; r += nwarps) {
+    const int32_t* row = C + r * M;
+    int32_t v[kPer];
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) v[k] = lane + 32 * k < M ? __ldg(row + lane + 32 * k) : 0;
+    long long sum = 0;
+    int32_t best = 0, arg = 0x7fffffff;
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+      sum += v[k];
+      if (v[k] > best) {  // ascending t per lane: the first maximum stays
+        best = v[k];
+        arg = lane + 32 * k;
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const int32_t ob = __shfl_xor_sync(kFull, best, o), oa = __shfl_xor_sync(kFull, arg, o);
+      if (ob > best || (ob == best && oa < arg)) {
+        best = ob;
+        arg = oa;
+      }
+      sum += __shfl_xor_sync(kFull, sum, o);
+    }
+    if (lane == 0) label[r] = best > 0 ? arg + 1 : 0;
+    if (frac) {
+      float* out = frac + r * M;
+      if (sum > 0 && sum < (1ll << 24)) {
+        const float sf = (float)sum;
+#pragma unroll
+        for (int k = 0; k < kPer; ++k)
+          if (lane + 32 * k < M) out[lane + 32 * k] = __fdiv_rn((float)v[k], sf);
+      } else {
+        const double sd = (double)sum;
+#pragma unroll
+        for (int k = 0; k < kPer; ++k)
+          if (lane + 32 * k < M) out[lane + 32 * k] = sum > 0 ? __double2float_rn(__ddiv_rn((double)v[k], sd)) : 0.0f;
+      }
+    }
+  }
+}
+
 // ------------------------------------------------------------------ ingest
 // v_a = ((A[a][0] x + A[a][1] y) + A[a][2] z) + A[a][3], every operation a
 // round-to-nearest binary32 intrinsic (no contraction), then v_a * 1024
@@ -383,7 +434,13 @@ __global__ void __launch_bounds__(kThreads) rescale_kernel(const int32_t* __rest
 
 cudaError_t launch_parcellate(const int32_t* C, int32_t N, int32_t M, int32_t* label, float* frac, cudaStream_t s) {
   if (N <= 0) return cudaSuccess;
-  parcellate_kernel<<<grid_for((int64_t)N * 32), kThreads, 0, s>>>(C, N, M, label, frac);
+  const int g = grid_for((int64_t)N * 32);
+  if (M <= 32) parcellate_rows_kernel<1><<<g, kThreads, 0, s>>>(C, N, M, label, frac);
+  else if (M <= 64) parcellate_rows_kernel<2><<<g, kThreads, 0, s>>>(C, N, M, label, frac);
+  else if (M <= 128) parcellate_rows_kernel<4><<<g, kThreads, 0, s>>>(C, N, M, label, frac);
+  else if (M <= 256) parcellate_rows_kernel<8><<<g, kThreads, 0, s>>>(C, N, M, label, frac);
+  else if (M <= 512) parcellate_rows_kernel<16><<<g, kThreads, 0, s>>>(C, N, M, label, frac);
+  else parcellate_kernel<<<g, kThreads, 0, s>>>(C, N, M, label, frac);
   return cudaGetLastError();
 }
 

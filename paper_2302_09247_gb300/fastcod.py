@@ -65,7 +65,7 @@ class Stats(ctypes.Structure):
 class Profile(ctypes.Structure):
     _fields_ = [("calls", ctypes.c_int64), ("kernel_launches", ctypes.c_int64), ("ms_h2d", ctypes.c_double),
                 ("ms_prefilter", ctypes.c_double), ("ms_walk", ctypes.c_double),
-                ("ms_overflow", ctypes.c_double)]
+                ("ms_overflow", ctypes.c_double), ("aux_calls", ctypes.c_int64), ("ms_aux", ctypes.c_double)]
 
 
 class Subject(ctypes.Structure):

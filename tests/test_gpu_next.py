@@ -58,6 +58,29 @@ def test_parcellate_matches_oracle(fc, where):
                 np.testing.assert_array_equal(label2, lr)
 
 
+@pytest.mark.parametrize("n_labels", [31, 64, 100, 250, 360, 512, 600])
+def test_parcellate_row_widths(fc, n_labels):
+    # every width class of the parcellation kernels (rows held in 1, 2, 4, 8
+    # or 16 registers per lane, and the looping form past 512 labels), with
+    # many-to-one ROI maps so that rows collect large counts and ties
+    rng = np.random.default_rng(n_labels)
+    dims = (24, 20, 18)
+    roi, lab, N, M = tiny.random_volumes(rng, dims, n_roi=40, n_labels=n_labels, p_roi=0.3, p_lab=0.6,
+                                         many_to_one=True)
+    xyz, off = tiny.random_streamlines(rng, dims, 3000, max_len=14)
+    Cr, Cer, _ = oracle.connectivity(roi, lab, dims, N, M, xyz, off)
+    with fc.Context(0) as ctx:
+        ctx.set_volumes(roi, lab, dims, N, M)
+        ctx.add_streamlines(xyz, off)
+        for which, ref in ((0, Cr), (1, Cer)):
+            lr, fr = oracle.parcellate(ref)
+            label = np.full(N, -5, np.int32)
+            frac = np.full((N, M), -1, np.float32)
+            fc.fastcod_parcellate(ctx.ctx, which, label, frac)
+            np.testing.assert_array_equal(label, lr)
+            np.testing.assert_array_equal(frac.view(np.uint32), fr.view(np.uint32))
+
+
 def _affine(rng):
     A = np.zeros((3, 4), dtype=np.float32)
     A[:, :3] = (np.eye(3) / 1.25 + rng.normal(0, 0.03, (3, 3))).astype(np.float32)
@@ -191,3 +214,21 @@ def test_rescale_matches_oracle(fc, where):
         with pytest.raises(fc.FastCodError):
             fc.fastcod_rescale(ctx.ctx, np.array([[16000000, 0, 0]], np.int32), [2, 1, 1], [1, 1, 1], [0, 0, 0],
                                np.zeros((1, 3), np.int32))
+
+
+def test_profile_counts_calls_beside_the_path(fc):
+    # while profiling, each call beside the path adds its kernels' device time
+    vols, tr = synth.make_subject(0, n_streamlines=2000)
+    with fc.Context(0) as ctx:
+        ctx.set_volumes(vols.roi, vols.lab, vols.dims, vols.n_roi, vols.n_targets)
+        ctx.add_streamlines(tr.xyz, tr.offsets)
+        label = np.empty(vols.n_roi, np.int32)
+        fc.fastcod_parcellate(ctx.ctx, 0, label, None)
+        assert ctx.profile()["aux_calls"] == 0  # profiling off
+        ctx.set_option(fc.FASTCOD_OPT_PROFILE, 1)
+        fc.fastcod_parcellate(ctx.ctx, 0, label, None)
+        n = fc.upsampled_count(tr.offsets, 2)
+        fc.fastcod_upsample(ctx.ctx, tr.xyz, tr.offsets, 2, np.empty((n, 3), np.int32),
+                            np.empty(len(tr.offsets), np.int64))
+        p = ctx.profile()
+        assert p["aux_calls"] == 2 and p["ms_aux"] > 0.0
