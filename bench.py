@@ -389,6 +389,7 @@ def run_served(args):
     specs = [spec() for _ in arrivals]
     clocks = ClockSampler(local)
     clocks.start()
+    launches0 = fc.fastcod_server_kernel_launches(srv)
     ids = []
     t_start = time.perf_counter()
     for at, sp in zip(arrivals, specs):
@@ -399,6 +400,7 @@ def run_served(args):
     for rid, _ in ids:
         assert fc.fastcod_server_wait(srv, rid, 300.0) == fc.FASTCOD_OK
     clk = clocks.stop()
+    launches = fc.fastcod_server_kernel_launches(srv) - launches0
     infos = [fc.fastcod_server_request_info(srv, rid) for rid, _ in ids]
     lat = np.array([i["t_done"] - i["t_submit"] for i in infos])
     span = max(i["t_done"] for i in infos) - min(i["t_submit"] for i in infos)
@@ -424,7 +426,7 @@ def run_served(args):
         "offered_rate": args.rate,
         "saturation": {"requests": len(ids2), "subjects_per_s": len(ids2) / sat_s,
                        "streamlines_per_s": sum(c for _, c in ids2) / sat_s},
-        "clocks": clk, "generation_s": gen_s,
+        "gpu_launches": launches, "clocks": clk, "generation_s": gen_s,
     }
     print(json.dumps(line), flush=True)
     ctx.close()
@@ -508,6 +510,7 @@ def run_next(args):
     clocks.start()
     time.sleep(0.3)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches0 = ctx.profile()["kernel_launches"]
     e0.record(stream)
     for _ in range(args.steps):
         step()
@@ -515,6 +518,7 @@ def run_next(args):
     torch.cuda.synchronize()
     clk = clocks.stop()
     ms = e0.elapsed_time(e1) / args.steps
+    launches = ctx.profile()["kernel_launches"] - launches0
     # the kernels' own device time: a second, profiled pass (events around
     # each call's kernels; the calls' host-side checks and synchronisations,
     # which the timed pass above includes, fall outside)
@@ -535,7 +539,7 @@ def run_next(args):
                      "kernel_ms_per_step": kernel_ms,
                      "call_frac": alg_bytes / (ms / 1000.0) / 1e9 / peaks["hbm_gbs"],
                      "peak_source": f"{peak_kind} hbm_gbs (copy bandwidth)", "traffic": None},
-        "clocks": clk,
+        "gpu_launches": launches, "clocks": clk,
     }
     print(json.dumps(line), flush=True)
     ctx.close()

@@ -304,6 +304,10 @@ FASTCOD_API int fastcod_server_cancel(fastcod_server* srv, uint64_t request_id);
 /* Timing and counts of a request. */
 FASTCOD_API int fastcod_server_request_info(fastcod_server* srv, uint64_t request_id, fastcod_request_info* out);
 
+/* Kernels of this library the server's worker has launched so far (volume
+ * prep and near grid per admitted request, three per iteration). */
+FASTCOD_API int fastcod_server_kernel_launches(fastcod_server* srv, int64_t* out);
+
 /* Finish all admitted and queued work, stop the worker, free everything. */
 FASTCOD_API int fastcod_server_destroy(fastcod_server* srv);
 

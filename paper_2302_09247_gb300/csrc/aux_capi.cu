@@ -125,6 +125,7 @@ int validate_offsets(fastcod_ctx* c, const int64_t* d_off, int64_t ns, int64_t n
   if (int rc = state_begin(c, &st)) return rc;
   if (int rc = span_begin(c)) return rc;
   CU(fc::launch_check_offsets(d_off, ns, nv, st, c->stream));
+  c->prof.kernel_launches += 1;
   if (int rc = span_end(c, false)) return rc;
   return state_end(c, st, what);
 }
@@ -136,6 +137,7 @@ int world_to_fixed_into(fastcod_ctx* c, const float* xyz_mm, int64_t nv, const f
   if (int rc = state_begin(c, &st)) return rc;
   if (int rc = span_begin(c)) return rc;
   CU(fc::launch_world_to_fixed(static_cast<const float*>(d_in), nv, affine, d_out, st, c->stream));
+  c->prof.kernel_launches += nv > 0 ? 1 : 0;
   if (int rc = span_end(c, true)) return rc;
   return state_end(c, st, "world-mm ingest");
 }
@@ -159,6 +161,7 @@ FASTCOD_API int fastcod_parcellate(fastcod_ctx* c, int32_t which, int32_t* label
   if (int rc = span_begin(c)) return rc;
   CU(fc::launch_parcellate(which ? c->d_Cend : c->d_C, N, M, static_cast<int32_t*>(d_label),
                            static_cast<float*>(d_frac), c->stream));
+  c->prof.kernel_launches += N > 0 ? 1 : 0;
   if (int rc = span_end(c, true)) return rc;
   if (int rc = copy_out(c, label_out, d_label, (size_t)N * 4)) return rc;
   if (fractions_out)
@@ -212,6 +215,7 @@ FASTCOD_API int fastcod_upsample_factor(fastcod_ctx* c, const int32_t* xyz, int6
   if (int rc = span_begin(c)) return rc;
   CU(fc::launch_seg_max(static_cast<const int32_t*>(d_xyz), off, n_streamlines,
                         static_cast<unsigned long long*>(d_best), c->stream));
+  c->prof.kernel_launches += n_streamlines > 0 ? 1 : 0;
   if (int rc = span_end(c, true)) return rc;
   unsigned long long best = 0;
   CU(cudaMemcpyAsync(&best, d_best, 8, cudaMemcpyDeviceToHost, c->stream));
@@ -249,6 +253,7 @@ FASTCOD_API int fastcod_upsample(fastcod_ctx* c, const int32_t* xyz, int64_t n_v
   int64_t* oo = static_cast<int64_t*>(d_oo);
   if (int rc = span_begin(c)) return rc;
   CU(fc::launch_upsample_offsets(off, n_streamlines, factor, static_cast<long long*>(d_tmp), oo, c->stream));
+  c->prof.kernel_launches += 3;
   if (int rc = span_end(c, false)) return rc;
   int64_t total = 0;
   CU(cudaMemcpyAsync(&total, oo + n_streamlines, 8, cudaMemcpyDeviceToHost, c->stream));
@@ -263,6 +268,7 @@ FASTCOD_API int fastcod_upsample(fastcod_ctx* c, const int32_t* xyz, int64_t n_v
     if (int rc = span_begin(c)) return rc;
     CU(fc::launch_upsample_vertices(static_cast<const int32_t*>(d_xyz), off, n_streamlines, factor, oo,
                                     static_cast<int32_t*>(d_out), c->stream));
+    c->prof.kernel_launches += 1;
     if (int rc = span_end(c, true)) return rc;
     if (int rc = copy_out(c, xyz_out, d_out, (size_t)total * 12)) return rc;
   } else if (c->profile) {
@@ -291,6 +297,7 @@ FASTCOD_API int fastcod_rescale(fastcod_ctx* c, const int32_t* xyz, int64_t n_ve
   if (int rc = span_begin(c)) return rc;
   CU(fc::launch_rescale(static_cast<const int32_t*>(d_in), n_vertices, num, den, add, static_cast<int32_t*>(d_out), st,
                         c->stream));
+  c->prof.kernel_launches += n_vertices > 0 ? 1 : 0;
   if (int rc = span_end(c, true)) return rc;
   if (int rc = state_end(c, st, "rescale")) return rc;
   if (int rc = copy_out(c, xyz_out, d_out, (size_t)n_vertices * 12)) return rc;

@@ -66,6 +66,7 @@ struct Staged {
 }  // namespace
 
 struct fastcod_server {
+  std::atomic<int64_t> kernel_launches{0};  // this library's kernels launched by the worker
   int device = 0;
   int num_sms = 0;
   int32_t max_slots = 1;
@@ -195,6 +196,7 @@ cudaError_t setup_request(fastcod_server* S, Request* r, uint32_t** tmp, size_t*
     e = fc::launch_volume_prep(roi, lab, nvox, v, const_cast<uint32_t*>(v.code), const_cast<uint16_t*>(v.lab),
                                const_cast<uint32_t*>(v.bricks), *tmp, r->st, S->compute);
   if (e == cudaSuccess) e = fc::launch_near(v, *tmp, const_cast<uint32_t*>(v.near), S->compute);
+  if (e == cudaSuccess) S->kernel_launches += 2;
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&r->done_ev, cudaEventDisableTiming);
   return e;
 }
@@ -376,6 +378,7 @@ bool iterate(fastcod_server* S, uint32_t** tmp, size_t* tmp_cap) {
     if (e == cudaSuccess)
       e = fc::launch_walk_overflow_batch(tbl, S->lists + S->lists_cap, S->mode, S->scratch, kOverflowCtas, S->scratch_words,
                                          S->gst, S->compute);
+    if (e == cudaSuccess) S->kernel_launches += 3;
     if (e != cudaSuccess) {
       (void)cudaGetLastError();
       for (const Staged& sg : staged) sg.r->status = FASTCOD_ECUDA;
@@ -606,6 +609,12 @@ FASTCOD_API int fastcod_server_request_info(fastcod_server* S, uint64_t id, fast
   out->t_submit = r->t_submit;
   out->t_admit = r->t_admit;
   out->t_done = r->t_done;
+  return FASTCOD_OK;
+}
+
+FASTCOD_API int fastcod_server_kernel_launches(fastcod_server* S, int64_t* out) {
+  if (!S || !out) return FASTCOD_EINVAL;
+  *out = S->kernel_launches.load();
   return FASTCOD_OK;
 }
 

@@ -45,7 +45,7 @@ EXPORTED = [
     "fastcod_set_option", "fastcod_last_error", "fastcod_batch_run", "fastcod_batch_get_stats",
     "fastcod_batch_get_info", "fastcod_server_create", "fastcod_server_submit", "fastcod_server_push_chunk",
     "fastcod_server_poll", "fastcod_server_wait", "fastcod_server_cancel", "fastcod_server_request_info",
-    "fastcod_server_destroy", "fastcod_connectivity_noalloc", "fastcod_parcellate", "fastcod_world_to_fixed",
+    "fastcod_server_destroy", "fastcod_server_kernel_launches", "fastcod_connectivity_noalloc", "fastcod_parcellate", "fastcod_world_to_fixed",
     "fastcod_add_streamlines_mm", "fastcod_upsample", "fastcod_upsample_factor", "fastcod_rescale",
 ]
 
@@ -117,6 +117,7 @@ def _load():
         "fastcod_server_wait": ([vp, ctypes.c_uint64, ctypes.c_double], ctypes.c_int),
         "fastcod_server_cancel": ([vp, ctypes.c_uint64], ctypes.c_int),
         "fastcod_server_request_info": ([vp, ctypes.c_uint64, ctypes.POINTER(RequestInfo)], ctypes.c_int),
+        "fastcod_server_kernel_launches": ([vp, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
         "fastcod_server_destroy": ([vp], ctypes.c_int),
         "fastcod_connectivity_noalloc": ([ctypes.c_int, vp, vp, vp, i32, i32, i32, i32, i32, vp, i64, vp, i64, vp,
                                           vp], ctypes.c_int),
@@ -310,6 +311,12 @@ def fastcod_server_request_info(srv, rid: int) -> dict:
     info = RequestInfo()
     _scheck(lib.fastcod_server_request_info(srv, rid, ctypes.byref(info)))
     return {k: getattr(info, k) for k, _ in RequestInfo._fields_}
+
+
+def fastcod_server_kernel_launches(srv) -> int:
+    n = ctypes.c_int64()
+    _scheck(lib.fastcod_server_kernel_launches(srv, ctypes.byref(n)))
+    return int(n.value)
 
 
 def fastcod_server_destroy(srv):

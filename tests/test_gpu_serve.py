@@ -77,6 +77,10 @@ def test_alone_equals_in_the_mix(fc, subjects):
         for i, (x, o) in enumerate(_chunks(tA, 3)):
             ra.push(fc, srv, x, o, last=(i == 2))
         assert fc.fastcod_server_wait(srv, ra.id, 120.0) == fc.FASTCOD_OK
+        # one request of three chunks: volume prep + near grid, then three
+        # kernels per iteration, at least one iteration per chunk
+        n = fc.fastcod_server_kernel_launches(srv)
+        assert n >= 2 + 3 * 3 and (n - 2) % 3 == 0
         alone = ra.C.copy()
         # the same request in a mix with two others, chunks interleaved
         reqs = {k: Req(fc, srv, subjects[k][0], where=("device" if k == "B" else "host")) for k in "ABC"}
