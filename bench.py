@@ -621,6 +621,12 @@ def main():
     ctx.sync()
     st = ctx.stats()
     C_first = ctx.connectivity()
+    # the survivors' voxel steps: one more step with the count switched on
+    # (an extra kernel, kept out of the timed region)
+    ctx.set_option(fc.FASTCOD_OPT_WALKED_STEPS, 1)
+    step()
+    walked_steps = ctx.stats()["walked_steps"]
+    ctx.set_option(fc.FASTCOD_OPT_WALKED_STEPS, 0)
 
     # ---------------------------------------------------------- timed region
     ctx.set_option(fc.FASTCOD_OPT_PROFILE, 1)
@@ -721,6 +727,7 @@ def main():
             "subjects_per_s": subjects_s, "streamlines_per_s": streamlines_s,
             "voxel_steps_per_step": st["voxel_steps"], "survivors_per_step": st["survivors"],
             "overflow_per_step": st["overflow"], "pairs_per_step": st["pairs"],
+            "walked_steps_per_step": walked_steps,
             "C_sum": int(C_first.sum()),
             "roofline": roofline,
             "e2e": e2e,

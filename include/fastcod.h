@@ -116,7 +116,11 @@ enum {
    * aligned xyz; otherwise it is copied); 0 (default): page-locked xyz is
    * first copied to device memory (measured faster on GB300).  Host offsets
    * and pageable host inputs are always copied.  Results are identical. */
-  FASTCOD_OPT_HOST_IN_PLACE = 9
+  FASTCOD_OPT_HOST_IN_PLACE = 9,
+  /* 1: fastcod_add_streamlines also counts the voxel steps of the walked
+   * streamlines (fastcod_stats.walked_steps), with one more kernel that reads
+   * the survivors' vertices again; 0 (default): not counted (0). */
+  FASTCOD_OPT_WALKED_STEPS = 10
 };
 
 typedef struct fastcod_ctx fastcod_ctx;
@@ -130,6 +134,8 @@ typedef struct {
   int64_t overflow;     /* walked streamlines whose sets exceeded the on-chip
                            tables and took the exact global-memory path */
   int64_t pairs;        /* sum over streamlines of |V_s| * |T_s| (increments of C) */
+  int64_t walked_steps; /* voxel_steps of the survivors only (the streamlines walked);
+                           counted while FASTCOD_OPT_WALKED_STEPS is 1 */
 } fastcod_stats;
 
 /* Per-stage device time accumulated while FASTCOD_OPT_PROFILE is 1 (CUDA

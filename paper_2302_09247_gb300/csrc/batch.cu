@@ -518,6 +518,7 @@ FASTCOD_API int fastcod_batch_get_stats(fastcod_ctx* c, int32_t subject, fastcod
   out->survivors = (int64_t)h.survivors;
   out->overflow = (int64_t)h.overflow;
   out->pairs = (int64_t)h.pairs;
+  out->walked_steps = (int64_t)h.walked;
   return FASTCOD_OK;
 }
 

@@ -453,6 +453,10 @@ FASTCOD_API int fastcod_add_streamlines(fastcod_ctx* c, const int32_t* xyz, int6
                               c->stream));
   if (int rc = record(c, 4)) return rc;
   c->prof.kernel_launches += 3;
+  if (c->walked_steps) {
+    CU(fc::launch_walked_steps(t, c->d_surv, ns, c->d_state, c->num_sms, c->stream));
+    c->prof.kernel_launches += 1;
+  }
   c->total_streamlines += ns;
   c->total_vertices += nv;
   if (c->flags & FASTCOD_SYNC) return sync_check(c);
@@ -502,6 +506,7 @@ FASTCOD_API int fastcod_get_stats(fastcod_ctx* c, fastcod_stats* out) {
   out->survivors = (int64_t)h.survivors;
   out->overflow = (int64_t)h.overflow;
   out->pairs = (int64_t)h.pairs;
+  out->walked_steps = (int64_t)h.walked;
   return FASTCOD_OK;
 }
 
@@ -557,6 +562,10 @@ FASTCOD_API int fastcod_set_option(fastcod_ctx* c, int32_t key, int64_t value) {
     case FASTCOD_OPT_HOST_IN_PLACE:
       if (value != 0 && value != 1) break;
       c->host_in_place = (int)value;
+      return FASTCOD_OK;
+    case FASTCOD_OPT_WALKED_STEPS:
+      if (value != 0 && value != 1) break;
+      c->walked_steps = (int)value;
       return FASTCOD_OK;
     case FASTCOD_OPT_PROFILE:
       if (value != 0 && value != 1) break;

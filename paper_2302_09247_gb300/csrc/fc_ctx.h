@@ -58,6 +58,7 @@ struct fastcod_ctx {
   int near_log2 = -1;      // near grid cell: (1 << near_log2)^3 voxels; -1 = per volume
   int autotune = 1;        // batched form: tune per batch shape
   int host_in_place = 0;   // read page-locked host xyz in place (option)
+  int walked_steps = 0;    // count the survivors' voxel steps (option)
   int profile = 0;
   struct EvSet {
     cudaEvent_t e[5];

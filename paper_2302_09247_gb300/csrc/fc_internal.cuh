@@ -46,6 +46,7 @@ struct DevState {
   unsigned long long survivors;
   unsigned long long overflow;
   unsigned long long pairs;
+  unsigned long long walked;  // voxel steps of the walked (surviving) streamlines
   int32_t max_roi;        // set_volumes: max(roi) over the volume
   int32_t max_label;      // set_volumes: max(label)
 };
@@ -198,6 +199,9 @@ cudaError_t launch_walk(const Tract& t, const VolView& v, const int32_t* survivo
 cudaError_t launch_walk_overflow(const Tract& t, const VolView& v, const int32_t* overflow_list,
                                  Accum acc, uint32_t mode, uint32_t* scratch,
                                  int32_t scratch_ctas, DevState* st, cudaStream_t s);
+// Voxel steps of the survivors (warp per survivor), added to st->walked.
+cudaError_t launch_walked_steps(const Tract& t, const int32_t* survivors, int64_t survivor_cap, DevState* st,
+                                int num_sms, cudaStream_t s);
 // words of global scratch one overflow CTA needs for N rows and M labels
 int64_t overflow_scratch_words(int32_t n_roi, int32_t n_lab);
 

@@ -289,6 +289,37 @@ __global__ void __launch_bounds__(kWalkWarps * 32, kWalkMinBlocks)
   if (lane_id() == 0 && pairs_acc) atomicAdd(&st->pairs, pairs_acc);
 }
 
+// Voxel steps of the survivors (the metric's definition: per segment 1 + the
+// sum over the axes of its ends' voxel-coordinate differences; a single
+// vertex counts 1), warp per survivor, lanes over its segments.
+__global__ void __launch_bounds__(256) walked_steps_kernel(Tract t, const int32_t* __restrict__ surv,
+                                                           int64_t surv_cap, DevState* st) {
+  const uint32_t nl = st->n_long, n = st->n_survivors + nl;
+  const uint32_t lane = lane_id();
+  const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+  unsigned long long acc = 0;
+  for (uint32_t idx = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; idx < n; idx += nwarps) {
+    const int32_t s = survivor_at(surv, surv_cap, nl, idx);
+    const int64_t a = t.off[s], b = t.off[s + 1];
+    if (a < 0 || b > t.nv || b <= a) continue;
+    if (b - a == 1) {
+      acc += lane == 0 ? 1ull : 0ull;
+      continue;
+    }
+    for (int64_t j = a + lane; j + 1 < b; j += 32) {
+      int32_t p0[3], p1[3];
+      load_vertex(t.xyz, j, p0);
+      load_vertex(t.xyz, j + 1, p1);
+      acc += 1ull + (unsigned long long)(abs((p1[0] >> kUnitLog2) - (p0[0] >> kUnitLog2)) +
+                                         abs((p1[1] >> kUnitLog2) - (p0[1] >> kUnitLog2)) +
+                                         abs((p1[2] >> kUnitLog2) - (p0[2] >> kUnitLog2)));
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
+  if (lane == 0 && acc) atomicAdd(&st->walked, acc);
+}
+
 // Subject of global streamline id g (subjects' sbase ascend).
 __device__ __forceinline__ int subject_of(const BatchTable& tbl, int64_t g) {
   int lo = 0, hi = tbl.n - 1;
@@ -486,6 +517,13 @@ cudaError_t launch_walk(const Tract& t, const VolView& v, const int32_t* survivo
   if (bv) return launch_walk_k<true, false>(t, v, survivors, surv_cap, acc, mode, overflow_list, st, num_sms, s);
   if (bt) return launch_walk_k<false, true>(t, v, survivors, surv_cap, acc, mode, overflow_list, st, num_sms, s);
   return launch_walk_k<false, false>(t, v, survivors, surv_cap, acc, mode, overflow_list, st, num_sms, s);
+}
+
+cudaError_t launch_walked_steps(const Tract& t, const int32_t* survivors, int64_t survivor_cap, DevState* st,
+                                int num_sms, cudaStream_t s) {
+  if (t.ns <= 0) return cudaSuccess;
+  walked_steps_kernel<<<num_sms * 8, 256, 0, s>>>(t, survivors, survivor_cap, st);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_walk_overflow(const Tract& t, const VolView& v, const int32_t* overflow_list, Accum acc,

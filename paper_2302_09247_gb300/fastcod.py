@@ -37,6 +37,7 @@ FASTCOD_OPT_PREFILTER_CTAS = 6
 FASTCOD_OPT_NEAR_LOG2 = 7
 FASTCOD_OPT_AUTOTUNE = 8
 FASTCOD_OPT_HOST_IN_PLACE = 9
+FASTCOD_OPT_WALKED_STEPS = 10
 
 EXPORTED = [
     "fastcod_create", "fastcod_destroy", "fastcod_set_stream", "fastcod_set_volumes",
@@ -59,7 +60,7 @@ class FastCodError(RuntimeError):
 class Stats(ctypes.Structure):
     _fields_ = [("streamlines", ctypes.c_int64), ("vertices", ctypes.c_int64),
                 ("voxel_steps", ctypes.c_int64), ("survivors", ctypes.c_int64),
-                ("overflow", ctypes.c_int64), ("pairs", ctypes.c_int64)]
+                ("overflow", ctypes.c_int64), ("pairs", ctypes.c_int64), ("walked_steps", ctypes.c_int64)]
 
 
 class Profile(ctypes.Structure):

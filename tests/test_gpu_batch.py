@@ -74,6 +74,12 @@ def test_batch_matches_oracle(fc, where):
             st = fc.fastcod_batch_get_stats(ctx.ctx, i)
             assert st["voxel_steps"] == sr["voxel_steps"] and st["pairs"] == sr["pairs"]
             assert st["streamlines"] == len(sub[6]) - 1
+            # the same survivors as the plain path's
+            with fc.Context(0) as one:
+                roi, lab, dims, N, M, xyz, off = sub
+                one.set_volumes(roi, lab, dims, N, M)
+                one.add_streamlines(xyz, off)
+                assert st["survivors"] == one.stats()["survivors"]
 
 
 def test_batch_graph_replay_sees_new_data(fc):

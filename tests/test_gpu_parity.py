@@ -21,7 +21,7 @@ U = 1024
 def _opts(prefilter, staging, target=0, sampling=0):
     from paper_2302_09247_gb300 import fastcod as fc
     return {fc.FASTCOD_OPT_PREFILTER: prefilter, fc.FASTCOD_OPT_STAGING: staging,
-            fc.FASTCOD_OPT_TARGET_MODE: target, fc.FASTCOD_OPT_SAMPLING: sampling}
+            fc.FASTCOD_OPT_TARGET_MODE: target, fc.FASTCOD_OPT_SAMPLING: sampling, fc.FASTCOD_OPT_WALKED_STEPS: 1}
 
 
 def _oracle_flags(target, sampling):
@@ -36,6 +36,15 @@ def _check(roi, lab, dims, N, M, xyz, off, where="device", opts=None, chunks=1, 
     assert st["voxel_steps"] == sr["voxel_steps"]
     assert st["pairs"] == sr["pairs"]
     assert st["streamlines"] == len(off) - 1
+    # the walked streamlines' voxel steps (counted when asked): all of them
+    # without the prefilter
+    from paper_2302_09247_gb300 import fastcod as fc
+    if opts is not None and opts.get(fc.FASTCOD_OPT_WALKED_STEPS):
+        assert st["walked_steps"] <= st["voxel_steps"]
+        if not opts.get(fc.FASTCOD_OPT_PREFILTER, 1):
+            assert st["walked_steps"] == sr["voxel_steps"]
+    else:
+        assert st["walked_steps"] == 0
     return st, sr
 
 
@@ -95,6 +104,8 @@ def test_set_overflow_path():
     xyz = rng.integers(0, np.array(dims) * U, size=(n, T, 3)).reshape(-1, 3).astype(np.int32)
     off = np.arange(0, T * n + 1, T, dtype=np.int64)
     st, _ = _check(roi, lab, dims, nvox, 200, xyz, off, "device", _opts(1, 1))
+    assert st["overflow"] > 0
+    st, _ = _check(roi, lab, dims, nvox, 200, xyz, off, "device", _opts(0, 1))  # walked steps counted in full
     assert st["overflow"] > 0
 
 
