@@ -38,8 +38,8 @@ METRIC = "DDA voxel-steps/s & subjects/s for C, bit-exact; batched vs plain; p50
 # vertex count (the stream is read once, so traffic grows with the vertices).
 PREFILTER_SOURCES = ("paper_2302_09247_gb300/csrc/k_prefilter.cu", "paper_2302_09247_gb300/csrc/fc_tma.cuh",
                      "paper_2302_09247_gb300/csrc/fc_internal.cuh", "paper_2302_09247_gb300/csrc/fc_device.cuh")
-PREFILTER_TRAFFIC = {"sha256": "e995f4dc86d63df4779f09f7d17520a1d21bf77965041188195eb309d85d6538",
-                     "bytes": 2491725824, "vertices": 205420297,
+PREFILTER_TRAFFIC = {"sha256": "2934aeb0f0900d9bd96a0308033d85acf2bc0f3cff74c9e0522015ba4c85e253",
+                     "bytes": 2491427584, "vertices": 205420297,
                      "summary": "profiles/prefilter_kernel_hcp145x174x145.md"}
 
 
