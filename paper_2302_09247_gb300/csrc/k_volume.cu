@@ -28,16 +28,22 @@ __global__ void __launch_bounds__(256) volume_max_kernel(const int32_t* __restri
   }
 }
 
-// One thread per voxel; a warp covers 32 consecutive voxels of a row, so the
-// warp's ballots are the row's ROI / label bit-plane words (planes: two
-// planes of Dy*Dz rows of ceil(Dx/32) words).
-__global__ void __launch_bounds__(128) volume_prep_kernel(const int32_t* __restrict__ roi,
-                                                          const uint16_t* __restrict__ lab, VolView v,
-                                                          uint32_t* __restrict__ code,
-                                                          uint16_t* __restrict__ lab_out,
-                                                          uint32_t* __restrict__ bricks, uint32_t* __restrict__ planes,
-                                                          DevState* st) {
-  const int32_t x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
+// One thread per voxel in blocks of 8 rows x 32 voxels: a warp covers 32
+// consecutive voxels of a row (x aligned to 32), so the warp's ballots are
+// the row's ROI / label bit-plane words (planes: two planes of Dy*Dz rows of
+// ceil(Dx/32) words).  A warp's 32 voxels touch at most two brick words: their
+// bits are ORed across the warp and set with one atomic per word.
+constexpr int kPrepRows = 8;
+
+__global__ void __launch_bounds__(32 * kPrepRows) volume_prep_kernel(const int32_t* __restrict__ roi,
+                                                                     const uint16_t* __restrict__ lab, VolView v,
+                                                                     uint32_t* __restrict__ code,
+                                                                     uint16_t* __restrict__ lab_out,
+                                                                     uint32_t* __restrict__ bricks,
+                                                                     uint32_t* __restrict__ planes, DevState* st) {
+  const int32_t lane = (int32_t)threadIdx.x;
+  const int32_t x = blockIdx.x * 32 + lane, y = blockIdx.y * kPrepRows + threadIdx.y, z = blockIdx.z;
+  if (y >= v.dy) return;  // whole warps: y is the same for the warp's 32 lanes
   const bool in = x < v.dx;
   const int32_t i = x + v.dx * (y + v.dy * z);
   int32_t r = -1, l = 0;
@@ -51,21 +57,28 @@ __global__ void __launch_bounds__(128) volume_prep_kernel(const int32_t* __restr
     }
     code[i] = r >= 0 ? (kCodeRoi | (l > 0 ? kCodeRoiLabelled : 0u) | (uint32_t)r) : (uint32_t)l;
     lab_out[i] = (uint16_t)l;
-    const uint32_t bits = (r >= 0 ? 1u : 0u) | (l > 0 ? 2u : 0u);
-    if (bits) {
-      const int32_t b = (x >> kBrickLog2) + v.bx * ((y >> kBrickLog2) + v.by * (z >> kBrickLog2));
-      atomicOr(bricks + (b >> 4), bits << ((b & 15) * 2));
-    }
   }
+  // brick bits: lanes of the warp's first brick word, then of its second
+  const uint32_t bits = (r >= 0 ? 1u : 0u) | (l > 0 ? 2u : 0u);
+  const int32_t b = ((in ? x : blockIdx.x * 32) >> kBrickLog2) + v.bx * ((y >> kBrickLog2) + v.by * (z >> kBrickLog2));
+  const int32_t wi = b >> 4;
+  const uint32_t val = bits << ((b & 15) * 2);
+  // the in-range lanes are a prefix of the warp and their words do not
+  // decrease: lane 0 holds the first word, the last in-range lane the second
+  const int32_t last = min(31, v.dx - 1 - (int32_t)blockIdx.x * 32);
+  const int32_t wA = __shfl_sync(kFull, wi, 0), wB = __shfl_sync(kFull, wi, last);
+  const uint32_t oA = __reduce_or_sync(kFull, wi == wA ? val : 0u);
+  const uint32_t oB = __reduce_or_sync(kFull, wi != wA ? val : 0u);
+  if (lane == 0 && oA) atomicOr(bricks + wA, oA);
+  if (lane == 0 && oB) atomicOr(bricks + wB, oB);
   const uint32_t mr = __ballot_sync(kFull, r >= 0);
   const uint32_t mt = __ballot_sync(kFull, l > 0);
-  const int32_t wb = (v.dx + 31) >> 5;
-  const int32_t w = (x >> 5);
-  if (lane_id() == 0 && w < wb) {
+  if (lane == 0) {
+    const int32_t wb = (v.dx + 31) >> 5;
     const int64_t row = (int64_t)y + (int64_t)v.dy * z;
     const int64_t rows = (int64_t)v.dy * v.dz;
-    planes[row * wb + w] = mr;
-    planes[(rows + row) * wb + w] = mt;
+    planes[row * wb + blockIdx.x] = mr;
+    planes[(rows + row) * wb + blockIdx.x] = mt;
   }
 }
 
@@ -80,11 +93,14 @@ __device__ __forceinline__ uint32_t plane_word(const uint32_t* __restrict__ rowp
   return (w >= 0 && w < wb) ? __ldg(rowp + w) : 0u;
 }
 
-// grid (word blocks, nny, nnz)
-__global__ void __launch_bounds__(128) near_pack_kernel(const uint32_t* __restrict__ planes, VolView v,
+// One thread per near word, a flat grid over the nwx * nny * nnz words.
+__global__ void __launch_bounds__(256) near_pack_kernel(const uint32_t* __restrict__ planes, VolView v,
                                                         uint32_t* __restrict__ near) {
-  const int32_t wx = blockIdx.x * blockDim.x + threadIdx.x, cy = blockIdx.y, cz = blockIdx.z;
-  if (wx >= v.nwx) return;
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)v.nwx * v.nny * v.nnz) return;
+  const int32_t wx = (int32_t)(idx % v.nwx);
+  const int64_t t = idx / v.nwx;
+  const int32_t cy = (int32_t)(t % v.nny), cz = (int32_t)(t / v.nny);
   const int32_t cs = 1 << v.nsh;
   const int32_t wb = (v.dx + 31) >> 5;
   const int64_t rows = (int64_t)v.dy * v.dz;
@@ -122,7 +138,7 @@ __global__ void __launch_bounds__(128) near_pack_kernel(const uint32_t* __restri
     }
     word |= bits << (2 * k);
   }
-  near[wx + v.nwx * (cy + v.nny * cz)] = word;
+  near[idx] = word;
 }
 
 static int grid_for(int64_t n) {
@@ -140,8 +156,8 @@ cudaError_t launch_volume_prep(const int32_t* roi, const uint16_t* lab, int64_t 
                                uint32_t* code, uint16_t* lab_out, uint32_t* bricks, uint32_t* planes, DevState* st,
                                cudaStream_t s) {
   (void)nvox;
-  volume_prep_kernel<<<dim3((v.dx + 127) / 128, v.dy, v.dz), 128, 0, s>>>(roi, lab, v, code, lab_out, bricks, planes,
-                                                                           st);
+  volume_prep_kernel<<<dim3((v.dx + 31) / 32, (v.dy + kPrepRows - 1) / kPrepRows, v.dz), dim3(32, kPrepRows), 0, s>>>(
+      roi, lab, v, code, lab_out, bricks, planes, st);
   return cudaGetLastError();
 }
 
@@ -150,7 +166,8 @@ int64_t plane_words(int32_t dx, int32_t dy, int32_t dz) {
 }
 
 cudaError_t launch_near(const VolView& v, const uint32_t* planes, uint32_t* near, cudaStream_t s) {
-  near_pack_kernel<<<dim3((v.nwx + 127) / 128, v.nny, v.nnz), 128, 0, s>>>(planes, v, near);
+  const int64_t words = (int64_t)v.nwx * v.nny * v.nnz;
+  near_pack_kernel<<<(unsigned)((words + 255) / 256), 256, 0, s>>>(planes, v, near);
   return cudaGetLastError();
 }
 
