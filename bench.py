@@ -289,15 +289,17 @@ def run_batched(args):
             fc.fastcod_connectivity(ctx.ctx, x["C"])
             fc.fastcod_endpoint_connectivity(ctx.ctx, x["Ce"])
 
-    plain()
-    torch.cuda.synchronize()
-    k = max(1, min(args.steps, 3))
-    t0 = time.perf_counter()
-    for _ in range(k):
+    plain_s = None
+    if not args.batch_only:
         plain()
-    torch.cuda.synchronize()
-    plain_s = (time.perf_counter() - t0) / k
-    assert all(torch.equal(a, x["C"]) for a, x in zip(Cb, subs)), "batched and plain results differ"
+        torch.cuda.synchronize()
+        k = max(1, min(args.steps, 3))
+        t0 = time.perf_counter()
+        for _ in range(k):
+            plain()
+        torch.cuda.synchronize()
+        plain_s = (time.perf_counter() - t0) / k
+        assert all(torch.equal(a, x["C"]) for a, x in zip(Cb, subs)), "batched and plain results differ"
     n = len(subs)
     line = {
         "metric": METRIC, "value": n / batch_s, "unit": "subjects/s", "n_gpus": 1, "steps": args.steps,
@@ -308,8 +310,9 @@ def run_batched(args):
                    "subjects": n, "streamlines": ns_total, "vertices": nv_total, "count_scale": args.count_scale,
                    "l2": "inputs larger than L2"},
         "voxel_steps_per_s": steps_total / batch_s, "graph_ms": graph_ms / args.steps,
-        "plain_subjects_per_s": n / plain_s, "plain_ms_per_batch": 1000 * plain_s,
-        "batched_vs_plain": plain_s / batch_s,
+        "plain_subjects_per_s": n / plain_s if plain_s else None,
+        "plain_ms_per_batch": 1000 * plain_s if plain_s else None,
+        "batched_vs_plain": plain_s / batch_s if plain_s else None,
         "autotuned": {"prefilter_ctas": info["prefilter_ctas"], "near_log2": info["near_log2"],
                       "task_vertices": info["task_vertices"]},
         "gpu_launches": launches, "clocks": clk, "generation_s": gen_s,
@@ -555,6 +558,7 @@ def main():
     ap.add_argument("--config", type=int, default=1, choices=[0, 1, 2, 3, 4],
                     help="0-2: one subject (default 1, HCP-shaped); 3: batched; 4: served")
     ap.add_argument("--subjects", type=int, default=64, help="--config 3: subjects per batch")
+    ap.add_argument("--batch-only", action="store_true", help="--config 3: skip the one-call-per-subject leg")
     ap.add_argument("--count-scale", type=float, default=1.0, help="--config 3: scale of the streamline counts")
     ap.add_argument("--serve-seconds", type=float, default=15.0, help="--config 4: length of the arrival process")
     ap.add_argument("--rate", type=float, default=20.0, help="--config 4: Poisson arrivals per second")
