@@ -22,8 +22,6 @@ __device__ __forceinline__ unsigned lanemask_lt() {
   return m;
 }
 
-__device__ __forceinline__ bool coord_ok(int32_t c) { return c > -kCoordLimit && c < kCoordLimit; }
-
 // ROI row (-1 = none) and label (0 = none) of voxel (x, y, z); voxels off the
 // grid have neither (loc2region outside every region).
 __device__ __forceinline__ void voxel_lookup(const VolView& v, int32_t x, int32_t y, int32_t z,
