@@ -464,15 +464,15 @@ __global__ void __launch_bounds__(256)
   }
 }
 
-// Grid: every CTA resident at once, from the compiled kernel's occupancy.
+// CTAs per SM of a walk kernel (its grid: every CTA resident at once).
 template <typename K>
-int walk_grid(K kernel, int num_sms) {
+int walk_blocks_per_sm(K kernel) {
   int per_sm = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kWalkWarps * 32, 0) != cudaSuccess) {
     (void)cudaGetLastError();
-    per_sm = 4;
+    per_sm = kWalkMinBlocks;
   }
-  return num_sms * (per_sm > 0 ? per_sm : 1);
+  return per_sm > 0 ? per_sm : 1;
 }
 
 // Launch in stream order with programmatic stream serialisation: the kernel
@@ -496,7 +496,10 @@ cudaError_t launch_after_previous(void (*kernel)(Params...), int grid, int block
 template <bool kBitV, bool kBitT>
 cudaError_t launch_walk_k(const Tract& t, const VolView& v, const int32_t* survivors, int64_t surv_cap, Accum acc,
                           uint32_t mode, int32_t* overflow_list, DevState* st, int num_sms, cudaStream_t s) {
-  static const int grid = walk_grid(walk_kernel<kBitV, kBitT>, num_sms);
+  // CTAs per SM depend on the kernel and the architecture (one, sm_103a), so
+  // they are asked once; the grid follows the context's device
+  static const int per_sm = walk_blocks_per_sm(walk_kernel<kBitV, kBitT>);
+  const int grid = num_sms * per_sm;
   return launch_after_previous(walk_kernel<kBitV, kBitT>, grid, kWalkWarps * 32, s, t, v, survivors, surv_cap, acc,
                                mode, overflow_list, st);
 }
@@ -504,7 +507,8 @@ cudaError_t launch_walk_k(const Tract& t, const VolView& v, const int32_t* survi
 template <bool kBitV, bool kBitT>
 cudaError_t launch_walk_batch_k(const BatchTable& tbl, const int32_t* survivors, int64_t surv_cap, uint32_t mode,
                                 int32_t* overflow_list, DevState* gst, int num_sms, cudaStream_t s) {
-  static const int grid = walk_grid(walk_batch_kernel<kBitV, kBitT>, num_sms);
+  static const int per_sm = walk_blocks_per_sm(walk_batch_kernel<kBitV, kBitT>);
+  const int grid = num_sms * per_sm;
   walk_batch_kernel<kBitV, kBitT><<<grid, kWalkWarps * 32, 0, s>>>(tbl, survivors, surv_cap, mode, overflow_list, gst);
   return cudaGetLastError();
 }
