@@ -79,3 +79,5 @@ def test_reference_arm_prints_once_under_torchrun():
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["value"] > 0 and d["cpu_baseline"]["kind"] == "oracle"
     assert d["e2e"]["h2d_bytes_per_step"] == 0
+    # the CUDA arm's config (the whole tiny subject), the sample stated beside it
+    assert d["config"]["streamlines"] == 20_000 and "first 500 streamlines" in d["cpu_baseline"]["sample"]
