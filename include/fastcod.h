@@ -76,8 +76,10 @@ enum {
 
 /* fastcod_set_option keys */
 enum {
-  /* 1 (default): drop streamlines that touch no ROI brick or no target brick
-   * before the walk; 0: walk every streamline.  Results are identical. */
+  /* 1 (default): before the walk, drop the streamlines that pass near no ROI
+   * voxel or near no labelled voxel (a conservative test: the near grid at
+   * the even vertices, the brick occupancy of long segments' voxel boxes);
+   * 0: walk every streamline.  Results are identical. */
   FASTCOD_OPT_PREFILTER = 1,
   /* target rule: 0 (default) = every label the streamline passes through;
    * 1 = only the label of the last vertex (Algorithm 2 taken literally,
