@@ -193,8 +193,9 @@ def parcellate(C):
     N, M = C.shape
     label = np.empty(N, dtype=np.int32)
     frac = np.empty((N, M), dtype=np.float32)
-    if lib().oracle_parcellate(_p(C), N, M, _p(label), _p(frac)) != 0:
-        raise ValueError("oracle: negative count")
+    rc = lib().oracle_parcellate(_p(C), N, M, _p(label), _p(frac))
+    if rc != 0:
+        raise ValueError("oracle: negative count" if rc == -1 else "oracle: row sum reaches 2^62")
     return label, frac
 
 

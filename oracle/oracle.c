@@ -383,6 +383,42 @@ int oracle_streamline_sets(const int32_t* roi, const uint16_t* lab, const int32_
 
 /* ------------------------------------------------------------ parcellation */
 
+__extension__ typedef unsigned __int128 u128;
+
+static int bit_length(uint64_t x) {
+  int n = 0;
+  while (x) {
+    ++n;
+    x >>= 1;
+  }
+  return n;
+}
+
+/* The binary32 nearest to a / b (0 <= a <= b, 0 < b < 2^63), ties to even,
+ * by exact integer long division: with s chosen so that 2^23 <= a 2^s / b <
+ * 2^24, the quotient q = floor(a 2^s / b) is the significand truncated and
+ * the remainder decides the rounding (above half: up; exactly half: up when
+ * q is odd).  A carry to 2^24 moves to the next binade.  The result
+ * q 2^-s is a normal binary32 (a / b >= 2^-63), so the scaling is exact. */
+static float nearest_f32_quotient(uint64_t a, uint64_t b) {
+  if (a == 0) return 0.0f;
+  int s = 24 + bit_length(b) - bit_length(a); /* a 2^s / b lies in (2^23, 2^25) */
+  u128 num = (u128)a << s;
+  u128 q = num / b;
+  if (q >= ((u128)1 << 24)) { /* one binade too high */
+    s -= 1;
+    num = (u128)a << s;
+    q = num / b;
+  }
+  const u128 r = num - q * b;
+  if (2 * r > b || (2 * r == b && (q & 1))) q += 1;
+  if (q == ((u128)1 << 24)) {
+    q >>= 1;
+    s -= 1;
+  }
+  return ldexpf((float)(uint32_t)q, -s);
+}
+
 int oracle_parcellate(const int64_t* C, int32_t N, int32_t M, int32_t* label, float* frac) {
   for (int32_t r = 0; r < N; ++r) {
     const int64_t* row = C + (int64_t)r * M;
@@ -390,6 +426,7 @@ int oracle_parcellate(const int64_t* C, int32_t N, int32_t M, int32_t* label, fl
     int32_t arg = 0;
     for (int32_t t = 0; t < M; ++t) {
       if (row[t] < 0) return -1;
+      if (row[t] >= ((int64_t)1 << 62) - sum) return -2; /* the row sum must stay below 2^62 */
       sum += row[t];
       if (row[t] > best) {
         best = row[t];
@@ -398,11 +435,8 @@ int oracle_parcellate(const int64_t* C, int32_t N, int32_t M, int32_t* label, fl
     }
     label[r] = arg;
     if (frac) {
-      for (int32_t t = 0; t < M; ++t) {
-        /* binary64 quotient of two exact integers (< 2^53), then binary32:
-           the double rounding is innocuous since 53 >= 2 * 24 + 2 */
-        frac[(int64_t)r * M + t] = sum > 0 ? (float)((double)row[t] / (double)sum) : 0.0f;
-      }
+      for (int32_t t = 0; t < M; ++t)
+        frac[(int64_t)r * M + t] = sum > 0 ? nearest_f32_quotient((uint64_t)row[t], (uint64_t)sum) : 0.0f;
     }
   }
   return 0;

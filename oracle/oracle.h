@@ -85,8 +85,10 @@ int oracle_streamline_sets(const int32_t* roi, const uint16_t* lab, const int32_
  *   label[r] = 1 + argmax_t C[r][t], ties to the lowest label; 0 when the row
  *              is all zero;
  *   frac[r][t] = C[r][t] / sum_t C[r][t] rounded to the nearest binary32
- *              (ties to even); 0 for an all-zero row.  frac may be NULL.
- * Returns 0, or -1 when an entry is negative. */
+ *              (ties to even), decided by exact integer long division; 0 for
+ *              an all-zero row.  frac may be NULL.
+ * Returns 0, -1 when an entry is negative, or -2 when a row sum reaches
+ * 2^62. */
 int oracle_parcellate(const int64_t* C, int32_t N, int32_t M, int32_t* label, float* frac);
 
 /* World-mm streamline vertices (binary32, the form tractography writes) to

@@ -7,6 +7,7 @@ import numpy as np
 import pytest
 
 import oracle
+from tests.parcellation_cases import DOUBLE_ROUNDING_ROWS, as_matrix, midpoint_rows
 
 
 # ------------------------------------------------------------- parcellation
@@ -51,6 +52,44 @@ def test_parcellate_against_argmax_and_exact_quotients(seed):
                 assert frac[r, t] == 0.0
             else:
                 assert _nearest_f32(Fraction(int(C[r, t]), int(s[r])), frac[r, t]), (r, t)
+
+
+def test_parcellate_double_rounding_rows():
+    # the binary64 quotient rounded again to binary32 is one unit off on these
+    # rows; the fractions must be the nearest binary32 all the same
+    C = np.array(DOUBLE_ROUNDING_ROWS, dtype=np.int64)
+    label, frac = oracle.parcellate(C)
+    assert label.tolist() == [1, 1, 1]
+    for r in range(len(C)):
+        s = int(C[r].sum())
+        for t in range(C.shape[1]):
+            assert _nearest_f32(Fraction(int(C[r, t]), s), frac[r, t]), (r, t)
+        assert frac[r, 0] != np.float32(int(C[r, 0]) / s)  # not the doubly rounded value
+    assert frac[0, 0] == np.float32(0.8205847)
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_parcellate_at_and_beside_binary32_midpoints(seed):
+    # fractions exactly on a midpoint (ties to even) or 2^-55 relative beside
+    # one, in eight binades, with the answer known from the construction
+    rows, want = midpoint_rows(seed, 240, k_max=7)
+    M = max(len(r) for r in rows)
+    C = as_matrix(rows, M)
+    label, frac = oracle.parcellate(C)
+    for i, (pos, f) in enumerate(want):
+        q = Fraction(int(C[i, pos]), int(C[i].sum()))
+        assert _nearest_f32(q, f), i  # the construction itself, checked with exact rationals
+        assert frac[i, pos].view(np.uint32) == f.view(np.uint32), (i, float(frac[i, pos]), float(f))
+    for i in range(0, len(rows), 17):  # the row's other entries too
+        s = int(C[i].sum())
+        for t in range(M):
+            assert _nearest_f32(Fraction(int(C[i, t]), s), frac[i, t]), (i, t)
+
+
+def test_parcellate_rejects_row_sums_past_2_62():
+    with pytest.raises(ValueError):
+        oracle.parcellate(np.array([[2 ** 61, 2 ** 61]]))
+    oracle.parcellate(np.array([[2 ** 61, 2 ** 61 - 1]]))
 
 
 def test_parcellate_rejects_negative_counts():
