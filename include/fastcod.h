@@ -337,6 +337,15 @@ FASTCOD_API int fastcod_server_destroy(fastcod_server* srv);
  * Waits for the queued work first (ESTATE without volumes). */
 FASTCOD_API int fastcod_parcellate(fastcod_ctx* ctx, int32_t which, int32_t* label_out, float* fractions_out);
 
+/* The same outputs for a caller's int32 matrix C [N][M] (row-major, host or
+ * device memory), for instance the sum of partial matrices that several
+ * contexts or GPUs accumulated over parts of one tractogram.  Needs no
+ * volumes.  EINVAL when N < 0, M is outside [1, 65535] or an entry is
+ * negative (the message names the row); C, C_end and the statistics of the
+ * context are left as they were. */
+FASTCOD_API int fastcod_parcellate_matrix(fastcod_ctx* ctx, const int32_t* C, int32_t N, int32_t M,
+                                          int32_t* label_out, float* fractions_out);
+
 /* World-mm vertices (binary32 [n][3], the form tractography writes) to this
  * library's fixed point: v_a = ((A[a][0] x + A[a][1] y) + A[a][2] z) +
  * A[a][3], every product and sum rounded to binary32 (no fused multiply-add),

@@ -79,6 +79,8 @@ int state_end(fastcod_ctx* c, const DevState* st, const char* what) {
     case fc::kErrCoord:
       return fail(c, FASTCOD_EINVAL, "%s: coordinate not finite or outside [-2^24, 2^24) near vertex %d", what,
                   h.error_info);
+    case fc::kErrCount:
+      return fail(c, FASTCOD_EINVAL, "%s: negative count in row %d", what, h.error_info);
     default:
       return fail(c, FASTCOD_ECUDA, "%s: device error %d (%d)", what, h.error, h.error_info);
   }
@@ -160,12 +162,42 @@ FASTCOD_API int fastcod_parcellate(fastcod_ctx* c, int32_t which, int32_t* label
     if (int rc = out_dst(c, kOut2, fractions_out, (size_t)N * M * 4, &d_frac)) return rc;
   if (int rc = span_begin(c)) return rc;
   CU(fc::launch_parcellate(which ? c->d_Cend : c->d_C, N, M, static_cast<int32_t*>(d_label),
-                           static_cast<float*>(d_frac), c->stream));
+                           static_cast<float*>(d_frac), nullptr, c->stream));
   c->prof.kernel_launches += N > 0 ? 1 : 0;
   if (int rc = span_end(c, true)) return rc;
   if (int rc = copy_out(c, label_out, d_label, (size_t)N * 4)) return rc;
   if (fractions_out)
     if (int rc = copy_out(c, fractions_out, d_frac, (size_t)N * M * 4)) return rc;
+  CU(cudaStreamSynchronize(c->stream));
+  return FASTCOD_OK;
+}
+
+FASTCOD_API int fastcod_parcellate_matrix(fastcod_ctx* c, const int32_t* C, int32_t N, int32_t M,
+                                          int32_t* label_out, float* fractions_out) {
+  if (int rc = begin(c)) return rc;
+  if (N < 0 || M < 1 || M > 65535) return fail(c, FASTCOD_EINVAL, "N must be >= 0 and M in [1, 65535]");
+  if (N == 0) return FASTCOD_OK;
+  if (!C || !label_out) return fail(c, FASTCOD_EINVAL, "pointer is NULL");
+  if (int rc = sync_check(c)) return rc;
+  const size_t bytes = (size_t)N * M * 4;
+  const void* d_C = nullptr;
+  if (int rc = stage_in(c, kIn, C, bytes, &d_C)) return rc;
+  void* d_label = nullptr;
+  void* d_frac = nullptr;
+  if (int rc = out_dst(c, kOut, label_out, (size_t)N * 4, &d_label)) return rc;
+  if (fractions_out)
+    if (int rc = out_dst(c, kOut2, fractions_out, bytes, &d_frac)) return rc;
+  DevState* st = nullptr;
+  if (int rc = state_begin(c, &st)) return rc;
+  if (int rc = span_begin(c)) return rc;
+  CU(fc::launch_parcellate(static_cast<const int32_t*>(d_C), N, M, static_cast<int32_t*>(d_label),
+                           static_cast<float*>(d_frac), st, c->stream));
+  c->prof.kernel_launches += 1;
+  if (int rc = span_end(c, true)) return rc;
+  if (int rc = state_end(c, st, "parcellation")) return rc;
+  if (int rc = copy_out(c, label_out, d_label, (size_t)N * 4)) return rc;
+  if (fractions_out)
+    if (int rc = copy_out(c, fractions_out, d_frac, bytes)) return rc;
   CU(cudaStreamSynchronize(c->stream));
   return FASTCOD_OK;
 }

@@ -29,7 +29,8 @@ enum DevError : int32_t {
   kErrCoord = 2,        // coordinate outside [-2^24, 2^24)
   kErrVolume = 3,       // roi or label value out of range
   kErrTimeout = 4,      // a bounded wait gave up
-  kErrOverflowList = 5  // overflow list capacity exceeded (cannot happen by construction)
+  kErrOverflowList = 5, // overflow list capacity exceeded (cannot happen by construction)
+  kErrCount = 6         // a connectivity count given to the parcellation is negative
 };
 
 // Cumulative and per-call counters in device memory.
@@ -206,9 +207,10 @@ cudaError_t launch_walked_steps(const Tract& t, const int32_t* survivors, int64_
 int64_t overflow_scratch_words(int32_t n_roi, int32_t n_lab);
 
 // Beside the path (k_aux.cu): parcellation of an N x M matrix (frac may be
-// null), world-mm ingest, offsets check, upsampling (offsets, then
+// null; st, when given, receives kErrCount for a negative entry), world-mm ingest, offsets check, upsampling (offsets, then
 // vertices; block_tmp holds upsample_scan_blocks(ns) values), rescale.
-cudaError_t launch_parcellate(const int32_t* C, int32_t N, int32_t M, int32_t* label, float* frac, cudaStream_t s);
+cudaError_t launch_parcellate(const int32_t* C, int32_t N, int32_t M, int32_t* label, float* frac, DevState* st,
+                              cudaStream_t s);
 cudaError_t launch_world_to_fixed(const float* xyz_mm, int64_t nv, const float affine[12], int32_t* out,
                                   DevState* st, cudaStream_t s);
 cudaError_t launch_check_offsets(const int64_t* off, int64_t ns, int64_t nv, DevState* st, cudaStream_t s);

@@ -22,22 +22,72 @@ int grid_for(int64_t items, int per_thread = 1) {
 }
 
 // ------------------------------------------------------------ parcellation
+// sign(a 2^s - K b) over 128-bit integers (a, b < 2^63, K < 2^27, 0 <= s,
+// a 2^s < 2^128).
+__device__ __forceinline__ int cmp_shifted(uint64_t a, int s, uint64_t K, uint64_t b) {
+  const uint64_t lh = s >= 64 ? a << (s - 64) : (s == 0 ? 0ull : a >> (64 - s));
+  const uint64_t ll = s >= 64 ? 0ull : a << s;
+  const uint64_t rh = __umul64hi(K, b), rl = K * b;
+  if (lh != rh) return lh < rh ? -1 : 1;
+  if (ll != rl) return ll < rl ? -1 : 1;
+  return 0;
+}
+
+// sign(a / b - (x + y) / 2) for neighbouring positive binary32 values x < y:
+// their midpoint is exact in binary64 (26 significant bits); written as
+// K 2^-s with K odd, the comparison is a 2^s against K b.
+__device__ __forceinline__ int cmp_midpoint(uint64_t a, uint64_t b, float x, float y) {
+  const double mid = ((double)x + (double)y) * 0.5;
+  const uint64_t bits = (uint64_t)__double_as_longlong(mid);
+  uint64_t K = (bits & 0xfffffffffffffull) | (1ull << 52);  // mid = K 2^(e - 1075)
+  int s = 1075 - (int)((bits >> 52) & 0x7ff);
+  const int tz = __ffsll((long long)K) - 1;
+  K >>= tz;
+  s -= tz;
+  return cmp_shifted(a, s, K, b);
+}
+
+// The binary32 nearest to a / b (0 <= a <= b, 0 < b < 2^47), ties to even.
+// The binary64 quotient rounded to binary32 is within one unit of it (a
+// second rounding can cross a midpoint); the exact comparisons with the two
+// midpoints around that candidate settle it.
+__device__ __forceinline__ float quotient_rn(uint64_t a, uint64_t b) {
+  if (a == 0) return 0.0f;
+  const float f = __double2float_rn(__ddiv_rn((double)a, (double)b));
+  const uint32_t u = __float_as_uint(f);
+  const float up = __uint_as_float(u + 1), dn = __uint_as_float(u - 1);
+  const int cu = cmp_midpoint(a, b, f, up);
+  if (cu > 0 || (cu == 0 && (u & 1))) return up;
+  const int cd = cmp_midpoint(a, b, dn, f);
+  if (cd < 0 || (cd == 0 && (u & 1))) return dn;
+  return f;
+}
+
+// One entry's fraction: one binary32 division when the row sum is below 2^24
+// (both integers exact in binary32, and IEEE division rounds to nearest),
+// else the exact rule above.
+__device__ __forceinline__ float row_fraction(int32_t v, long long sum) {
+  if (sum <= 0) return 0.0f;
+  if (sum < (1ll << 24)) return __fdiv_rn((float)v, (float)sum);
+  return quotient_rn((uint64_t)v, (uint64_t)sum);
+}
+
 // One warp per row: the maximum with the lowest label on ties, the row sum
-// (64-bit), then the fractions: the binary32 nearest to count / sum.  When the
-// sum is below 2^24 both integers are exact in binary32 and one binary32
-// division (IEEE, round to nearest) gives it; otherwise the binary64 quotient
-// rounded to binary32 does (innocuous double rounding: 53 >= 2 * 24 + 2).
+// (64-bit), then the fractions: the binary32 nearest to count / sum.  With
+// st given, a negative entry is an error (kErrCount, the row).
 __global__ void __launch_bounds__(kThreads) parcellate_kernel(const int32_t* __restrict__ C, int32_t N, int32_t M,
-                                                              int32_t* __restrict__ label, float* __restrict__ frac) {
+                                                              int32_t* __restrict__ label, float* __restrict__ frac,
+                                                              DevState* st) {
   const int32_t lane = (int32_t)lane_id();
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < N; r += nwarps) {
     const int32_t* row = C + r * M;
     long long sum = 0;
-    int32_t best = 0, arg = 0x7fffffff;
+    int32_t best = 0, arg = 0x7fffffff, lo = 0;
     for (int32_t t = lane; t < M; t += 32) {
       const int32_t v = __ldg(row + t);
       sum += v;
+      lo = min(lo, v);
       if (v > best) {  // ascending t per lane: the first maximum stays
         best = v;
         arg = t;
@@ -52,17 +102,10 @@ __global__ void __launch_bounds__(kThreads) parcellate_kernel(const int32_t* __r
       }
       sum += __shfl_xor_sync(kFull, sum, o);
     }
+    if (st && __any_sync(kFull, lo < 0) && lane == 0) set_error(st, kErrCount, (int32_t)r);
     if (lane == 0) label[r] = best > 0 ? arg + 1 : 0;
-    if (frac) {
-      if (sum > 0 && sum < (1ll << 24)) {
-        const float s = (float)sum;
-        for (int32_t t = lane; t < M; t += 32) frac[r * M + t] = __fdiv_rn((float)__ldg(row + t), s);
-      } else {
-        const double s = (double)sum;
-        for (int32_t t = lane; t < M; t += 32)
-          frac[r * M + t] = sum > 0 ? __double2float_rn(__ddiv_rn((double)__ldg(row + t), s)) : 0.0f;
-      }
-    }
+    if (frac)
+      for (int32_t t = lane; t < M; t += 32) frac[r * M + t] = row_fraction(__ldg(row + t), sum);
   }
 }
 
@@ -72,7 +115,7 @@ __global__ void __launch_bounds__(kThreads) parcellate_kernel(const int32_t* __r
 template <int kPer>
 __global__ void __launch_bounds__(kThreads) parcellate_rows_kernel(const int32_t* __restrict__ C, int32_t N,
                                                                    int32_t M, int32_t* __restrict__ label,
-                                                                   float* __restrict__ frac) {
+                                                                   float* __restrict__ frac, DevState* st) {
   const int32_t lane = (int32_t)lane_id();
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < N; r += nwarps) {
@@ -81,10 +124,11 @@ __global__ void __launch_bounds__(kThreads) parcellate_rows_kernel(const int32_t
 #pragma unroll
     for (int k = 0; k < kPer; ++k) v[k] = lane + 32 * k < M ? __ldg(row + lane + 32 * k) : 0;
     long long sum = 0;
-    int32_t best = 0, arg = 0x7fffffff;
+    int32_t best = 0, arg = 0x7fffffff, lo = 0;
 #pragma unroll
     for (int k = 0; k < kPer; ++k) {
       sum += v[k];
+      lo = min(lo, v[k]);
       if (v[k] > best) {  // ascending t per lane: the first maximum stays
         best = v[k];
         arg = lane + 32 * k;
@@ -99,20 +143,13 @@ __global__ void __launch_bounds__(kThreads) parcellate_rows_kernel(const int32_t
       }
       sum += __shfl_xor_sync(kFull, sum, o);
     }
+    if (st && __any_sync(kFull, lo < 0) && lane == 0) set_error(st, kErrCount, (int32_t)r);
     if (lane == 0) label[r] = best > 0 ? arg + 1 : 0;
     if (frac) {
       float* out = frac + r * M;
-      if (sum > 0 && sum < (1ll << 24)) {
-        const float sf = (float)sum;
 #pragma unroll
-        for (int k = 0; k < kPer; ++k)
-          if (lane + 32 * k < M) out[lane + 32 * k] = __fdiv_rn((float)v[k], sf);
-      } else {
-        const double sd = (double)sum;
-#pragma unroll
-        for (int k = 0; k < kPer; ++k)
-          if (lane + 32 * k < M) out[lane + 32 * k] = sum > 0 ? __double2float_rn(__ddiv_rn((double)v[k], sd)) : 0.0f;
-      }
+      for (int k = 0; k < kPer; ++k)
+        if (lane + 32 * k < M) out[lane + 32 * k] = row_fraction(v[k], sum);
     }
   }
 }
@@ -432,15 +469,16 @@ __global__ void __launch_bounds__(kThreads) rescale_kernel(const int32_t* __rest
 
 }  // namespace
 
-cudaError_t launch_parcellate(const int32_t* C, int32_t N, int32_t M, int32_t* label, float* frac, cudaStream_t s) {
+cudaError_t launch_parcellate(const int32_t* C, int32_t N, int32_t M, int32_t* label, float* frac, DevState* st,
+                              cudaStream_t s) {
   if (N <= 0) return cudaSuccess;
   const int g = grid_for((int64_t)N * 32);
-  if (M <= 32) parcellate_rows_kernel<1><<<g, kThreads, 0, s>>>(C, N, M, label, frac);
-  else if (M <= 64) parcellate_rows_kernel<2><<<g, kThreads, 0, s>>>(C, N, M, label, frac);
-  else if (M <= 128) parcellate_rows_kernel<4><<<g, kThreads, 0, s>>>(C, N, M, label, frac);
-  else if (M <= 256) parcellate_rows_kernel<8><<<g, kThreads, 0, s>>>(C, N, M, label, frac);
-  else if (M <= 512) parcellate_rows_kernel<16><<<g, kThreads, 0, s>>>(C, N, M, label, frac);
-  else parcellate_kernel<<<g, kThreads, 0, s>>>(C, N, M, label, frac);
+  if (M <= 32) parcellate_rows_kernel<1><<<g, kThreads, 0, s>>>(C, N, M, label, frac, st);
+  else if (M <= 64) parcellate_rows_kernel<2><<<g, kThreads, 0, s>>>(C, N, M, label, frac, st);
+  else if (M <= 128) parcellate_rows_kernel<4><<<g, kThreads, 0, s>>>(C, N, M, label, frac, st);
+  else if (M <= 256) parcellate_rows_kernel<8><<<g, kThreads, 0, s>>>(C, N, M, label, frac, st);
+  else if (M <= 512) parcellate_rows_kernel<16><<<g, kThreads, 0, s>>>(C, N, M, label, frac, st);
+  else parcellate_kernel<<<g, kThreads, 0, s>>>(C, N, M, label, frac, st);
   return cudaGetLastError();
 }
 

@@ -46,7 +46,8 @@ EXPORTED = [
     "fastcod_set_option", "fastcod_last_error", "fastcod_batch_run", "fastcod_batch_get_stats",
     "fastcod_batch_get_info", "fastcod_server_create", "fastcod_server_submit", "fastcod_server_push_chunk",
     "fastcod_server_poll", "fastcod_server_wait", "fastcod_server_cancel", "fastcod_server_request_info",
-    "fastcod_server_destroy", "fastcod_server_kernel_launches", "fastcod_connectivity_noalloc", "fastcod_parcellate", "fastcod_world_to_fixed",
+    "fastcod_server_destroy", "fastcod_server_kernel_launches", "fastcod_connectivity_noalloc", "fastcod_parcellate", "fastcod_parcellate_matrix",
+    "fastcod_world_to_fixed",
     "fastcod_add_streamlines_mm", "fastcod_upsample", "fastcod_upsample_factor", "fastcod_rescale",
 ]
 
@@ -123,6 +124,7 @@ def _load():
         "fastcod_connectivity_noalloc": ([ctypes.c_int, vp, vp, vp, i32, i32, i32, i32, i32, vp, i64, vp, i64, vp,
                                           vp], ctypes.c_int),
         "fastcod_parcellate": ([vp, i32, vp, vp], ctypes.c_int),
+        "fastcod_parcellate_matrix": ([vp, vp, i32, i32, vp, vp], ctypes.c_int),
         "fastcod_world_to_fixed": ([vp, vp, i64, vp, vp], ctypes.c_int),
         "fastcod_add_streamlines_mm": ([vp, vp, i64, vp, i64, vp], ctypes.c_int),
         "fastcod_upsample": ([vp, vp, i64, vp, i64, i32, vp, i64, vp], ctypes.c_int),
@@ -338,6 +340,14 @@ def fastcod_connectivity_noalloc(device, stream, roi, lab, dims, n_roi, n_target
 
 def fastcod_parcellate(ctx, which: int, label_out, fractions_out=None):
     return _check(ctx, lib.fastcod_parcellate(ctx, int(which), _ptr(label_out), _ptr(fractions_out)))
+
+
+def fastcod_parcellate_matrix(ctx, C, label_out, fractions_out=None):
+    """Parcellation outputs of a caller's int32 [N, M] matrix (host or device)."""
+    if str(C.dtype) not in ("int32", "torch.int32") or len(C.shape) != 2:
+        raise TypeError("C must be a 2-D int32 array or tensor")
+    N, M = (int(d) for d in C.shape)
+    return _check(ctx, lib.fastcod_parcellate_matrix(ctx, _ptr(C), N, M, _ptr(label_out), _ptr(fractions_out)))
 
 
 def _affine(affine):

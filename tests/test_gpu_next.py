@@ -10,6 +10,7 @@ import oracle
 import synth
 from synth import tiny
 from tests.gpu_helpers import as_device
+from tests.parcellation_cases import DOUBLE_ROUNDING_ROWS, as_matrix, midpoint_rows
 
 pytestmark = pytest.mark.gpu
 
@@ -79,6 +80,55 @@ def test_parcellate_row_widths(fc, n_labels):
             fc.fastcod_parcellate(ctx.ctx, which, label, frac)
             np.testing.assert_array_equal(label, lr)
             np.testing.assert_array_equal(frac.view(np.uint32), fr.view(np.uint32))
+
+
+@pytest.mark.parametrize("M", [2, 70, 600])
+@pytest.mark.parametrize("where", ["host", "device"])
+def test_parcellate_matrix_midpoints(fc, M, where):
+    # a caller's matrix whose fractions lie on or 2^-55 beside binary32
+    # midpoints (row sums 2^25..2^37), the rows where a binary64 quotient
+    # rounded again to binary32 is one unit off, and small rows between them;
+    # M = 2 / 70 / 600 runs the one-register, four-register and looping kernels
+    import torch
+    k_max = {2: 0, 70: 5, 600: 7}[M]
+    rows, _ = midpoint_rows(17 + M, 300, k_max=k_max)
+    rows = [r for r in rows if len(r) <= M] + DOUBLE_ROUNDING_ROWS
+    rng = np.random.default_rng(M)
+    small = [list(rng.integers(0, 50, size=M)) for _ in range(40)] + [[0] * M]
+    C = as_matrix(rows + small, M)
+    C = C[rng.permutation(len(C))]
+    assert C.max() < 2 ** 31
+    lr, fr = oracle.parcellate(C)
+    C32 = np.ascontiguousarray(C.astype(np.int32))
+    N = len(C32)
+    with fc.Context(0) as ctx:
+        for rep in range(2):
+            if where == "host":
+                label = np.full(N, -5, np.int32)
+                frac = np.full((N, M), -1, np.float32)
+                fc.fastcod_parcellate_matrix(ctx.ctx, C32, label, frac)
+            else:
+                lt = torch.full((N,), -5, dtype=torch.int32, device="cuda:0")
+                ft = torch.full((N, M), -1.0, dtype=torch.float32, device="cuda:0")
+                fc.fastcod_parcellate_matrix(ctx.ctx, torch.from_numpy(C32).cuda(), lt, ft)
+                label, frac = lt.cpu().numpy(), ft.cpu().numpy()
+            np.testing.assert_array_equal(label, lr)
+            np.testing.assert_array_equal(frac.view(np.uint32), fr.view(np.uint32))  # bit-exact
+
+
+def test_parcellate_matrix_rejects_negative_counts(fc):
+    C = np.array([[1, 2], [3, -4], [5, 6]], dtype=np.int32)
+    label = np.zeros(3, np.int32)
+    with fc.Context(0) as ctx:
+        with pytest.raises(fc.FastCodError) as e:
+            fc.fastcod_parcellate_matrix(ctx.ctx, C, label)
+        assert e.value.code == fc.FASTCOD_EINVAL and "row 1" in str(e.value)
+        C[1, 1] = 4
+        frac = np.zeros((3, 2), np.float32)
+        fc.fastcod_parcellate_matrix(ctx.ctx, C, label, frac)  # the context still works
+        lr, fr = oracle.parcellate(C)
+        np.testing.assert_array_equal(label, lr)
+        np.testing.assert_array_equal(frac, fr)
 
 
 def _affine(rng):
