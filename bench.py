@@ -5,10 +5,19 @@
 One step = one whole pass of the hot path over one subject: zero C and C_end,
 prefilter + compaction over the full vertex stream, walk + dedup + accumulate
 of the survivors, and the exact overflow path.  The default workload is the
-HCP-shaped subject (145x174x145 @ 1.25 mm, two thalami, M = 70, 2,000,000
-streamlines), inputs resident in HBM, larger than L2 (2.4 GB vertex stream).
+high-resolution subject (260x311x260 @ 0.7 mm, two thalami, N = 39,708,
+M = 360, 5,000,000 streamlines, 9.5 GB vertex stream), inputs resident in HBM,
+larger than L2.  The same JSON line carries, measured in the same run:
+  dda      - the subject again with the prefilter off, every streamline walked:
+             the integer DDA's own voxel-steps/s;
+  batched  - 64 heterogeneous subjects in one graph-captured batch against one
+             call per subject (subjects/s of both);
+  served   - Poisson arrivals at 20/s of HCP-shaped requests: subjects/s,
+             p50/p99 latency and closed-loop saturation, every request's C and
+             C_end checked against the oracle.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+    python bench.py --config 1 --no-forms --no-dda   # the HCP-shaped subject alone
 
 Under torchrun (N > 1) every rank processes its own subject of the same shape
 (weak scaling, no data-path collective); rank 0 prints one JSON line.
@@ -233,7 +242,7 @@ def _config(cfg, vols, tr):
     return c
 
 
-def run_batched(args):
+def batched_record(args, local) -> dict:
     """64 heterogeneous subjects in one fastcod_batch_run (a CUDA graph per batch
     shape, autotuned) against one set_volumes + add_streamlines + readback per
     subject; subjects/s of both, device-resident inputs and outputs."""
@@ -242,10 +251,6 @@ def run_batched(args):
     import synth
     from paper_2302_09247_gb300 import fastcod as fc
 
-    ws, rank, local = _dist()
-    if rank != 0:
-        return 0
-    torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     subs, steps_total, nv_total, ns_total = [], 0, 0, 0
     t0 = time.perf_counter()
@@ -260,6 +265,7 @@ def run_batched(args):
                          Ce=torch.empty((vols.n_roi, vols.n_targets), dtype=torch.int32, device=dev)))
         nv_total += tr.n_vertices
         ns_total += tr.n_streamlines
+        del vols, tr
     gen_s = time.perf_counter() - t0
     objs = [fc.make_subject(x["roi"], x["lab"], x["dims"], x["N"], x["M"], x["xyz"], x["off"], x["C"], x["Ce"])
             for x in subs]
@@ -274,15 +280,16 @@ def run_batched(args):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     graph_ms = 0.0
-    for _ in range(args.steps):
+    for _ in range(args.batch_steps):
         fc.fastcod_batch_run(ctx.ctx, objs)
         graph_ms += fc.fastcod_batch_get_info(ctx.ctx)["ms_graph"]
     torch.cuda.synchronize()
-    batch_s = (time.perf_counter() - t0) / args.steps
+    batch_s = (time.perf_counter() - t0) / args.batch_steps
     clk = clocks.stop()
     info = fc.fastcod_batch_get_info(ctx.ctx)
-    launches = ctx.profile()["kernel_launches"] - launches0
+    launches = (ctx.profile()["kernel_launches"] - launches0) / args.batch_steps
     Cb = [x["C"].clone() for x in subs]
+    Ceb = [x["Ce"].clone() for x in subs]
 
     def plain():
         for x in subs:
@@ -295,55 +302,100 @@ def run_batched(args):
     if not args.batch_only:
         plain()
         torch.cuda.synchronize()
-        k = max(1, min(args.steps, 3))
+        k = max(1, min(args.batch_steps, 3))
         t0 = time.perf_counter()
         for _ in range(k):
             plain()
         torch.cuda.synchronize()
         plain_s = (time.perf_counter() - t0) / k
-        assert all(torch.equal(a, x["C"]) for a, x in zip(Cb, subs)), "batched and plain results differ"
+        assert all(torch.equal(a, x["C"]) for a, x in zip(Cb, subs)), "batched and plain C differ"
+        assert all(torch.equal(a, x["Ce"]) for a, x in zip(Ceb, subs)), "batched and plain C_end differ"
     n = len(subs)
-    line = {
-        "metric": METRIC, "value": n / batch_s, "unit": "subjects/s", "n_gpus": 1, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": 1000 * batch_s, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-        "config": {"workload": f"batched: {n} subjects (grids 96^3..145x174x145, M in 8/70/360, N 1,000..12,000), "
-                               f"{ns_total:,} streamlines, {nv_total:,} vertices, one CUDA graph per batch",
-                   "subjects": n, "streamlines": ns_total, "vertices": nv_total, "count_scale": args.count_scale,
-                   "l2": "inputs larger than L2"},
-        "voxel_steps_per_s": steps_total / batch_s, "graph_ms": graph_ms / args.steps,
+    ctx.close()
+    return {
+        "workload": f"batched: {n} subjects (grids 96^3..145x174x145, M in 8/70/360, N 1,000..12,000), "
+                    f"{ns_total:,} streamlines, {nv_total:,} vertices, one CUDA graph per batch shape",
+        "subjects": n, "streamlines": ns_total, "vertices": nv_total, "count_scale": args.count_scale,
+        "subjects_per_s": n / batch_s, "ms_per_batch": 1000 * batch_s, "steps": args.batch_steps,
+        "voxel_steps_per_s": steps_total / batch_s, "graph_ms": graph_ms / args.batch_steps,
         "plain_subjects_per_s": n / plain_s if plain_s else None,
         "plain_ms_per_batch": 1000 * plain_s if plain_s else None,
         "batched_vs_plain": plain_s / batch_s if plain_s else None,
+        "checked": "batched C and C_end equal the one-call-per-subject results" if plain_s else None,
         "autotuned": {"prefilter_ctas": info["prefilter_ctas"], "near_log2": info["near_log2"],
                       "task_vertices": info["task_vertices"]},
-        "gpu_launches": launches, "clocks": clk, "generation_s": gen_s,
+        "gpu_launches_per_batch": launches, "clocks": clk, "generation_s": gen_s,
+        "timing": "wall clock around the graph replays with a device synchronisation on both sides; inputs "
+                  "device-resident, larger than L2",
+    }
+
+
+def run_batched(args):
+    """--config 3: the batched form's own JSON line."""
+    import torch
+    ws, rank, local = _dist()
+    if rank != 0:
+        return 0
+    torch.cuda.set_device(local)
+    r = batched_record(args, local)
+    line = {
+        "metric": METRIC, "value": r["subjects_per_s"], "unit": "subjects/s", "n_gpus": 1,
+        "steps": args.batch_steps, "warmup": args.warmup, "ms_per_step": r["ms_per_batch"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": r["workload"], "subjects": r["subjects"], "streamlines": r["streamlines"],
+                   "vertices": r["vertices"], "count_scale": r["count_scale"], "l2": "inputs larger than L2"},
+        "batched": r, "gpu_launches": int(round(r["gpu_launches_per_batch"] * args.batch_steps)),
+        "clocks": r["clocks"],
     }
     print(json.dumps(line), flush=True)
-    ctx.close()
     return 0
 
 
-def run_served(args):
-    """Poisson arrivals of HCP-shaped requests (200,000..2,000,000 streamlines in
-    250,000-streamline chunks from page-locked host memory) into the served form;
-    subjects/s and p50/p99 end-to-end latency, then a closed-loop saturation run."""
-    import threading
+def served_expected(pool_subjects, block: int, threads: int):
+    """Oracle results per pool subject: prefix[k] = (C, C_end) of the first
+    k * block streamlines, int32 [k_max + 1, 2, N, M], from the oracle run on
+    every block (threads over blocks; integer sums are exact)."""
+    from concurrent.futures import ThreadPoolExecutor
 
+    import oracle
+    oracle.lib()
+    out = []
+    for vols, tr in pool_subjects:
+        nb = tr.n_streamlines // block
+
+        def one(b, vols=vols, tr=tr):
+            o = tr.offsets[b * block: (b + 1) * block + 1]
+            C, Ce, _ = oracle.connectivity(vols.roi, vols.lab, vols.dims, vols.n_roi, vols.n_targets,
+                                           tr.xyz[int(o[0]): int(o[-1])], o - o[0])
+            return C, Ce
+
+        with ThreadPoolExecutor(threads) as ex:
+            parts = list(ex.map(one, range(nb)))
+        pre = np.zeros((nb + 1, 2, vols.n_roi, vols.n_targets), dtype=np.int32)
+        for b, (C, Ce) in enumerate(parts):
+            pre[b + 1, 0] = pre[b, 0] + C
+            pre[b + 1, 1] = pre[b, 1] + Ce
+        out.append(pre)
+    return out
+
+
+def served_record(args, local) -> dict:
+    """Poisson arrivals of HCP-shaped requests (200,000..2,000,000 streamlines in
+    250,000-streamline chunks from page-locked host memory) into the served
+    form; subjects/s and p50/p99 end-to-end latency, then a closed-loop
+    saturation run.  Every request's C and C_end is compared with the oracle's
+    (sums of per-50,000-streamline oracle blocks of its pool subject)."""
     import torch
 
     import synth
     from paper_2302_09247_gb300 import fastcod as fc
 
-    ws, rank, local = _dist()
-    if rank != 0:
-        return 0
-    torch.cuda.set_device(local)
-    chunk = 250_000
-    pool = []
+    chunk, block = 250_000, 50_000
+    pool, subjects = [], []
     t0 = time.perf_counter()
     for p in range(args.pool):
         vols, tr = synth.make_subject(4, subject=p)
+        subjects.append((vols, tr))
         xyz = torch.from_numpy(tr.xyz).pin_memory()
         chunks = []
         for c in range(0, tr.n_streamlines, chunk):
@@ -354,22 +406,40 @@ def run_served(args):
                          lab=torch.from_numpy(vols.lab.view(np.int16)).pin_memory(), xyz=xyz, chunks=chunks,
                          ns=tr.n_streamlines))
     gen_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    expect = served_expected(subjects, block, max(1, min(64, os.cpu_count() or 1))) if args.serve_check else None
+    oracle_s = time.perf_counter() - t0
+    del subjects
     rng = np.random.default_rng(20)
+
+    def spec():
+        return int(rng.integers(len(pool))), block * int(rng.integers(4, 41))
+
+    arrivals = np.cumsum(rng.exponential(1.0 / args.rate, size=int(args.rate * args.serve_seconds * 1.5) + 10))
+    arrivals = arrivals[arrivals < args.serve_seconds]
+    specs = [spec() for _ in arrivals]
+    specs2 = [spec() for _ in range(4 * args.slots)]
+    warm = [(p, 4 * block) for p in range(len(pool))]
+    # page-locked outputs of every request, allocated before the arrivals
+    N, M = pool[0]["vols"].n_roi, pool[0]["vols"].n_targets
+    assert all(P["vols"].n_roi == N and P["vols"].n_targets == M for P in pool)
+    n_req = len(warm) + len(specs) + len(specs2)
+    outs = torch.empty((n_req, 2, N, M), dtype=torch.int32).pin_memory()
     ctx = fc.Context(local)
     srv = fc.fastcod_server_create(ctx.ctx, args.slots, 0)
-    keep = []
+    keep, issued = [], []
 
-    def submit(spec):
-        p, count = spec
+    def submit(sp):
+        p, count = sp
         P = pool[p]
         vols = P["vols"]
-        C = torch.empty((vols.n_roi, vols.n_targets), dtype=torch.int32).pin_memory()
-        Ce = torch.empty_like(C).pin_memory()
+        k = len(issued)
+        C, Ce = outs[k, 0], outs[k, 1]
         head = fc.make_subject(P["roi"], P["lab"], vols.dims, vols.n_roi, vols.n_targets,
                                np.zeros((0, 3), np.int32), np.zeros(1, np.int64), C, Ce)
         rid = fc.fastcod_server_submit(srv, head)
         left = count
-        for c, (v0, off) in enumerate(P["chunks"]):
+        for v0, off in P["chunks"]:
             n = min(chunk, left)
             o = off[: n + 1]
             x = P["xyz"][v0: v0 + int(o[-1])]
@@ -378,20 +448,12 @@ def run_served(args):
             keep.append((x, o))
             if left == 0:
                 break
-        keep.append((C, Ce, head))
-        return rid, count
+        keep.append(head)
+        issued.append((rid, p, count, k))
+        return rid
 
-    def spec():
-        return int(rng.integers(len(pool))), 50_000 * int(rng.integers(4, 41))
-
-    # warm-up: one request of each pool subject
-    for p in range(len(pool)):
-        rid, _ = submit((p, 200_000))
-        fc.fastcod_server_wait(srv, rid, 120.0)
-    # open loop: Poisson arrivals
-    arrivals = np.cumsum(rng.exponential(1.0 / args.rate, size=int(args.rate * args.serve_seconds * 1.5) + 10))
-    arrivals = arrivals[arrivals < args.serve_seconds]
-    specs = [spec() for _ in arrivals]
+    for sp in warm:
+        assert fc.fastcod_server_wait(srv, submit(sp), 120.0) == fc.FASTCOD_OK
     clocks = ClockSampler(local)
     clocks.start()
     launches0 = fc.fastcod_server_kernel_launches(srv)
@@ -402,39 +464,68 @@ def run_served(args):
         if d > 0:
             time.sleep(d)
         ids.append(submit(sp))
-    for rid, _ in ids:
+    for rid in ids:
         assert fc.fastcod_server_wait(srv, rid, 300.0) == fc.FASTCOD_OK
     clk = clocks.stop()
     launches = fc.fastcod_server_kernel_launches(srv) - launches0
-    infos = [fc.fastcod_server_request_info(srv, rid) for rid, _ in ids]
+    infos = [fc.fastcod_server_request_info(srv, rid) for rid in ids]
     lat = np.array([i["t_done"] - i["t_submit"] for i in infos])
+    wait = np.array([i["t_admit"] - i["t_submit"] for i in infos])
     span = max(i["t_done"] for i in infos) - min(i["t_submit"] for i in infos)
-    n_streamlines = sum(c for _, c in ids)
+    n_streamlines = sum(c for (_, _, c, _) in issued[len(warm):len(warm) + len(ids)])
     # closed loop: everything at once
-    specs2 = [spec() for _ in range(4 * args.slots)]
     t0 = time.perf_counter()
     ids2 = [submit(sp) for sp in specs2]
-    for rid, _ in ids2:
+    for rid in ids2:
         assert fc.fastcod_server_wait(srv, rid, 300.0) == fc.FASTCOD_OK
     sat_s = time.perf_counter() - t0
+    n2 = sum(c for (_, _, c, _) in issued[-len(ids2):])
     fc.fastcod_server_destroy(srv)
-    line = {
-        "metric": METRIC, "value": len(ids) / span, "unit": "subjects/s", "n_gpus": 1, "steps": len(ids),
-        "warmup": len(pool), "ms_per_step": 1000 * span / len(ids), "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-        "config": {"workload": f"served: Poisson {args.rate}/s for {args.serve_seconds}s of HCP-shaped requests "
-                               f"(200k..2M streamlines, 250k-streamline chunks from page-locked host memory, "
-                               f"pool of {len(pool)} subjects), {args.slots} slots",
-                   "requests": len(ids), "streamlines": n_streamlines},
+    ctx.close()
+    checked, bad = 0, 0
+    if expect is not None:
+        for rid, p, count, k in issued:
+            e = expect[p][count // block]
+            ok = np.array_equal(outs[k, 0].numpy(), e[0]) and np.array_equal(outs[k, 1].numpy(), e[1])
+            checked += 1
+            bad += 0 if ok else 1
+        assert bad == 0, f"{bad} of {checked} served results differ from the oracle"
+    return {
+        "workload": f"served: Poisson {args.rate}/s for {args.serve_seconds}s of HCP-shaped requests "
+                    f"(200k..2M streamlines, 250k-streamline chunks from page-locked host memory, "
+                    f"pool of {len(pool)} subjects), {args.slots} slots",
+        "requests": len(ids), "streamlines": n_streamlines, "subjects_per_s": len(ids) / span,
+        "offered_rate": args.rate, "span_s": span,
         "latency_ms": {"p50": 1000 * float(np.percentile(lat, 50)), "p99": 1000 * float(np.percentile(lat, 99)),
                        "mean": 1000 * float(lat.mean()), "max": 1000 * float(lat.max())},
-        "offered_rate": args.rate,
-        "saturation": {"requests": len(ids2), "subjects_per_s": len(ids2) / sat_s,
-                       "streamlines_per_s": sum(c for _, c in ids2) / sat_s},
-        "gpu_launches": launches, "clocks": clk, "generation_s": gen_s,
+        "admission_wait_ms": {"p50": 1000 * float(np.percentile(wait, 50)),
+                              "p99": 1000 * float(np.percentile(wait, 99))},
+        "saturation": {"requests": len(ids2), "subjects_per_s": len(ids2) / sat_s, "streamlines_per_s": n2 / sat_s},
+        "bit_exact": ({"requests_checked": checked, "mismatches": bad,
+                       "against": "oracle sums of 50,000-streamline blocks of each request's pool subject "
+                                  "(C and C_end, every request incl. warm-up and saturation)"}
+                      if expect is not None else None),
+        "gpu_launches": launches, "clocks": clk, "generation_s": gen_s, "oracle_s": oracle_s,
+        "latency": "request submit to completion (fastcod_server_request_info), host clock",
+    }
+
+
+def run_served(args):
+    """--config 4: the served form's own JSON line."""
+    import torch
+    ws, rank, local = _dist()
+    if rank != 0:
+        return 0
+    torch.cuda.set_device(local)
+    r = served_record(args, local)
+    line = {
+        "metric": METRIC, "value": r["subjects_per_s"], "unit": "subjects/s", "n_gpus": 1, "steps": r["requests"],
+        "warmup": args.pool, "ms_per_step": 1000 * r["span_s"] / r["requests"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": r["workload"], "requests": r["requests"], "streamlines": r["streamlines"]},
+        "served": r, "gpu_launches": r["gpu_launches"], "clocks": r["clocks"],
     }
     print(json.dumps(line), flush=True)
-    ctx.close()
     return 0
 
 
@@ -551,18 +642,99 @@ def run_next(args):
     return 0
 
 
+# Warp instructions the walk kernel issues per voxel step with the prefilter
+# off (every streamline walked), from ncu (smsp__inst_executed.sum over the
+# launch / the launch's voxel steps), valid only while the walk's sources are
+# the ones it was measured on.
+WALK_SOURCES = ("paper_2302_09247_gb300/csrc/k_walk.cu", "paper_2302_09247_gb300/csrc/fc_device.cuh",
+                "paper_2302_09247_gb300/csrc/fc_internal.cuh")
+WALK_INSTR = {"sha256": None, "warp_instr_per_voxel_step": None, "summary": None}
+
+
+def _sources_sha(files):
+    import hashlib
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def dda_record(ctx, step, stream, C_ref, Ce_ref, steps: int, local: int) -> dict:
+    """The walk on the whole vertex stream: the same subject with the prefilter
+    off, so that every streamline is walked and every voxel step of the metric
+    is a DDA step taken; C and C_end must not change."""
+    import torch
+
+    from paper_2302_09247_gb300 import fastcod as fc
+
+    fc.fastcod_set_option(ctx.ctx, fc.FASTCOD_OPT_PREFILTER, 0)
+    step()
+    ctx.sync()
+    st = ctx.stats()
+    assert np.array_equal(ctx.connectivity(), C_ref), "C differs with the prefilter off"
+    assert np.array_equal(ctx.endpoint_connectivity(), Ce_ref), "C_end differs with the prefilter off"
+    ctx.set_option(fc.FASTCOD_OPT_PROFILE, 1)
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / steps
+    prof = ctx.profile()
+    ctx.set_option(fc.FASTCOD_OPT_PROFILE, 0)
+    fc.fastcod_set_option(ctx.ctx, fc.FASTCOD_OPT_PREFILTER, 1)
+    walk_ms = prof["ms_walk"] / max(prof["calls"], 1)
+    vs = st["voxel_steps"]
+    rec = {"what": "prefilter off: every streamline walked (integer 3-D DDA, dedup, accumulate)",
+           "voxel_steps_per_step": vs, "walked_streamlines": st["survivors"], "ms_per_step": ms,
+           "voxel_steps_per_s": vs / (ms / 1000.0), "walk_ms_per_step": walk_ms,
+           "walk_voxel_steps_per_s": vs / (walk_ms / 1000.0), "steps": steps, "clocks": clk,
+           "checked": "C and C_end equal the prefiltered step's"}
+    sm_mhz = clk.get("sm_mhz") or 2070.0
+    props = torch.cuda.get_device_properties(local)
+    peak = props.multi_processor_count * 4 * sm_mhz * 1e6  # warp instructions issued per second
+    per_step = None
+    if WALK_INSTR["sha256"] is not None and _sources_sha(WALK_SOURCES) == WALK_INSTR["sha256"]:
+        per_step = WALK_INSTR["warp_instr_per_voxel_step"]
+    rec["roofline"] = {
+        "bound": "issue", "kernel": "walk_kernel",
+        "peak": peak, "unit": "warp-instructions/s",
+        "peak_source": f"{props.multi_processor_count} SMs x 4 schedulers x 1 warp-instruction/cycle x "
+                       f"{sm_mhz:.0f} MHz (median SM clock sampled during the region)",
+        "warp_instr_per_voxel_step": per_step,
+        "achieved": per_step * vs / (walk_ms / 1000.0) if per_step else None,
+        "frac": per_step * vs / (walk_ms / 1000.0) / peak if per_step else None,
+        "instr_source": WALK_INSTR["summary"] if per_step else "walk sources changed since the ncu capture",
+    }
+    return rec
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="fastcod", choices=["fastcod", "reference"])
-    ap.add_argument("--config", type=int, default=1, choices=[0, 1, 2, 3, 4],
-                    help="0-2: one subject (default 1, HCP-shaped); 3: batched; 4: served")
+    ap.add_argument("--config", type=int, default=2, choices=[0, 1, 2, 3, 4],
+                    help="0-2: one subject (default 2, the high-res subject, with the batched and served "
+                         "forms and the DDA measured in the same line); 3: batched; 4: served")
+    ap.add_argument("--no-forms", action="store_true", help="no batched / served sub-records")
+    ap.add_argument("--no-dda", action="store_true", help="no DDA sub-record (prefilter off)")
+    ap.add_argument("--dda-steps", type=int, default=5, help="timed steps of the DDA sub-record (prefilter off)")
+    ap.add_argument("--batch-steps", type=int, default=5, help="timed passes of the batched form")
+    ap.add_argument("--no-serve-check", dest="serve_check", action="store_false",
+                    help="skip the oracle check of the served results")
     ap.add_argument("--subjects", type=int, default=64, help="--config 3: subjects per batch")
     ap.add_argument("--batch-only", action="store_true", help="--config 3: skip the one-call-per-subject leg")
     ap.add_argument("--count-scale", type=float, default=1.0, help="--config 3: scale of the streamline counts")
-    ap.add_argument("--serve-seconds", type=float, default=15.0, help="--config 4: length of the arrival process")
+    ap.add_argument("--serve-seconds", type=float, default=10.0, help="served form: length of the arrival process")
     ap.add_argument("--rate", type=float, default=20.0, help="--config 4: Poisson arrivals per second")
     ap.add_argument("--pool", type=int, default=4, help="--config 4: pre-generated subjects")
     ap.add_argument("--slots", type=int, default=16, help="--config 4: server slots")
@@ -655,8 +827,12 @@ def main():
     ctx.set_option(fc.FASTCOD_OPT_PROFILE, 0)
     st_last = ctx.stats()
     C_last = ctx.connectivity()
+    Ce_first = ctx.endpoint_connectivity()
     assert np.array_equal(C_first, C_last), "C changed between identical steps"
     assert st_last["voxel_steps"] == st["voxel_steps"]
+    forms = not args.no_forms and ws == 1
+    dda = dda_record(ctx, step, stream, C_first, Ce_first, args.dda_steps, local) \
+        if not args.no_dda and ws == 1 else None
 
     value, t_max = weak_scaling(ws, float(st["voxel_steps"]) * args.steps, ms / 1000.0)
     ms_max = 1000.0 * t_max
@@ -680,6 +856,7 @@ def main():
 
     # ------------------------------------------------ end to end, host buffers
     e2e = None
+    xyz_h = off_h = None
     if args.e2e_steps > 0:
         xyz_h = torch.from_numpy(tr.xyz).pin_memory()
         off_h = torch.from_numpy(tr.offsets).pin_memory()
@@ -740,9 +917,18 @@ def main():
             "cpu_baseline": cpu,
             "gpu_launches": gpu_launches,
             "clocks": clk,
+            "dda": dda,
         }
-        print(json.dumps(line), flush=True)
     ctx.close()
+    if rank == 0 and forms:
+        # the batched and served forms of the metric, measured in this run
+        del xyz_d, off_d, roi_d, lab_d, xyz_h, off_h, tr
+        torch.cuda.empty_cache()
+        line["batched"] = batched_record(args, local)
+        torch.cuda.empty_cache()
+        line["served"] = served_record(args, local)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
