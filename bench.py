@@ -8,8 +8,9 @@ of the survivors, and the exact overflow path.  The default workload is the
 high-resolution subject (260x311x260 @ 0.7 mm, two thalami, N = 39,708,
 M = 360, 5,000,000 streamlines, 9.5 GB vertex stream), inputs resident in HBM,
 larger than L2.  The same JSON line carries, measured in the same run:
-  dda      - the subject again with the prefilter off, every streamline walked:
-             the integer DDA's own voxel-steps/s;
+  dda      - the subject again with the prefilter and the walk's skip of far
+             segments off, every voxel step walked: the integer DDA's own
+             voxel-steps/s;
   batched  - 64 heterogeneous subjects in one graph-captured batch against one
              call per subject (subjects/s of both);
   served   - Poisson arrivals at 20/s of HCP-shaped requests: subjects/s,
@@ -662,13 +663,15 @@ def _sources_sha(files):
 
 def dda_record(ctx, step, stream, C_ref, Ce_ref, steps: int, local: int) -> dict:
     """The walk on the whole vertex stream: the same subject with the prefilter
-    off, so that every streamline is walked and every voxel step of the metric
-    is a DDA step taken; C and C_end must not change."""
+    and the walk's skip of far segments off, so that every segment of every
+    streamline is walked voxel by voxel and every voxel step of the metric is
+    a DDA step taken; C and C_end must not change."""
     import torch
 
     from paper_2302_09247_gb300 import fastcod as fc
 
     fc.fastcod_set_option(ctx.ctx, fc.FASTCOD_OPT_PREFILTER, 0)
+    fc.fastcod_set_option(ctx.ctx, fc.FASTCOD_OPT_SEGMENT_SKIP, 0)
     step()
     ctx.sync()
     st = ctx.stats()
@@ -690,9 +693,11 @@ def dda_record(ctx, step, stream, C_ref, Ce_ref, steps: int, local: int) -> dict
     prof = ctx.profile()
     ctx.set_option(fc.FASTCOD_OPT_PROFILE, 0)
     fc.fastcod_set_option(ctx.ctx, fc.FASTCOD_OPT_PREFILTER, 1)
+    fc.fastcod_set_option(ctx.ctx, fc.FASTCOD_OPT_SEGMENT_SKIP, 1)
     walk_ms = prof["ms_walk"] / max(prof["calls"], 1)
     vs = st["voxel_steps"]
-    rec = {"what": "prefilter off: every streamline walked (integer 3-D DDA, dedup, accumulate)",
+    rec = {"what": "prefilter and segment skip off: every segment of every streamline walked voxel by voxel "
+                   "(integer 3-D DDA, code gather, dedup, accumulate)",
            "voxel_steps_per_step": vs, "walked_streamlines": st["survivors"], "ms_per_step": ms,
            "voxel_steps_per_s": vs / (ms / 1000.0), "walk_ms_per_step": walk_ms,
            "walk_voxel_steps_per_s": vs / (walk_ms / 1000.0), "steps": steps, "clocks": clk,

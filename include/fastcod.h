@@ -122,7 +122,21 @@ enum {
   /* 1: fastcod_add_streamlines also counts the voxel steps of the walked
    * streamlines (fastcod_stats.walked_steps), with one more kernel that reads
    * the survivors' vertices again; 0 (default): not counted (0). */
-  FASTCOD_OPT_WALKED_STEPS = 10
+  FASTCOD_OPT_WALKED_STEPS = 10,
+  /* 1 (default): the walk skips a short segment (end voxels at most one
+   * apart on every axis) whose start voxel's near cell holds no ROI and no
+   * labelled voxel: every voxel it visits lies within that cell's reach and
+   * counts for nothing.  0: every segment is walked voxel by voxel (with
+   * FASTCOD_OPT_PREFILTER = 0, every voxel step of the input is taken; the
+   * benchmark's measure of the integer DDA itself).  Results are identical. */
+  FASTCOD_OPT_SEGMENT_SKIP = 11,
+  /* Test hook for the bounded waits: -1 (default) off; k >= 0: the
+   * prefilter's bulk-copy loader neither copies the vertex piece k (vertices
+   * 256 k .. 256 k + 255) nor arrives on its barrier, so the wait for that
+   * piece runs out after its one-second limit.  The call then reports
+   * FASTCOD_ETIMEOUT (at the next synchronising call), no copy is left in
+   * flight, and the context stays usable after fastcod_reset. */
+  FASTCOD_OPT_TEST_WITHHOLD_PIECE = 12
 };
 
 typedef struct fastcod_ctx fastcod_ctx;

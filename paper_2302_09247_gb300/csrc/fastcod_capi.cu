@@ -445,7 +445,7 @@ FASTCOD_API int fastcod_add_streamlines(fastcod_ctx* c, const int32_t* xyz, int6
   // bulk copies stage device-resident vertices; host-resident ones are read
   // with direct loads
   CU(fc::launch_prefilter(t, v, c->prefilter != 0, c->mode, c->staging_tma != 0 && !xyz_in_place, c->prefilter_ctas,
-                          c->d_surv, ns, c->d_state, c->num_sms, c->stream));
+                          c->d_surv, ns, c->d_state, c->num_sms, c->stream, c->withhold_piece));
   if (int rc = record(c, 2)) return rc;
   CU(fc::launch_walk(t, v, c->d_surv, ns, acc, c->mode, c->d_ovf, c->d_state, c->num_sms, c->stream));
   if (int rc = record(c, 3)) return rc;
@@ -566,6 +566,14 @@ FASTCOD_API int fastcod_set_option(fastcod_ctx* c, int32_t key, int64_t value) {
     case FASTCOD_OPT_WALKED_STEPS:
       if (value != 0 && value != 1) break;
       c->walked_steps = (int)value;
+      return FASTCOD_OK;
+    case FASTCOD_OPT_SEGMENT_SKIP:
+      if (value != 0 && value != 1) break;
+      c->mode = (c->mode & ~fc::kModeWalkAll) | (value ? 0u : fc::kModeWalkAll);
+      return FASTCOD_OK;
+    case FASTCOD_OPT_TEST_WITHHOLD_PIECE:
+      if (value < -1) break;
+      c->withhold_piece = value;
       return FASTCOD_OK;
     case FASTCOD_OPT_PROFILE:
       if (value != 0 && value != 1) break;

@@ -59,6 +59,7 @@ struct fastcod_ctx {
   int autotune = 1;        // batched form: tune per batch shape
   int host_in_place = 0;   // read page-locked host xyz in place (option)
   int walked_steps = 0;    // count the survivors' voxel steps (option)
+  int64_t withhold_piece = -1;  // test hook: vertex piece the TMA loader never copies
   int profile = 0;
   struct EvSet {
     cudaEvent_t e[5];

@@ -162,6 +162,7 @@ struct BatchTask {
 // Mode bits of the walk.
 constexpr uint32_t kModeTargetEndpoint = 1u;
 constexpr uint32_t kModeVertexSampled = 2u;
+constexpr uint32_t kModeWalkAll = 4u;  // walk every segment (no skip of far short segments)
 
 // ---------------------------------------------------------------- launchers
 // Each returns the cudaError_t of the launch.
@@ -179,9 +180,11 @@ cudaError_t launch_near(const VolView& v, const uint32_t* planes, uint32_t* near
 
 // K2: prefilter + compaction (+ validation and voxel-step count).
 // ctas_per_sm: 2 or 3 (the register budget the kernel is compiled for).
+// withhold_piece: test hook (-1 off): the TMA loader skips that piece and its
+// barrier arrival, so its bounded wait runs out.
 cudaError_t launch_prefilter(const Tract& t, const VolView& v, bool prefilter, uint32_t mode,
                              bool tma, int ctas_per_sm, int32_t* survivors, int64_t survivor_cap, DevState* st,
-                             int num_sms, cudaStream_t s);
+                             int num_sms, cudaStream_t s, int64_t withhold_piece = -1);
 
 // Batched forms: every subject of the table in one launch each.
 cudaError_t launch_prefilter_batch(const BatchTable& tbl, const BatchTask* tasks, int32_t ntasks, bool prefilter,

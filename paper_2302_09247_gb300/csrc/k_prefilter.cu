@@ -555,11 +555,13 @@ struct Ring {
   TmaSmem* sm;
   uint32_t slot, phase;   // next slot to consume, and the parity it completes
   uint64_t policy;
+  int64_t withhold;       // test hook: this piece is never copied (-1: none)
 
-  __device__ __forceinline__ void init(TmaSmem* s) {
+  __device__ __forceinline__ void init(TmaSmem* s, int64_t withhold_piece = -1) {
     sm = s;
     slot = 0;
     phase = 0;
+    withhold = withhold_piece;
     policy = policy_evict_first();
     if (lane_id() == 0) {
       for (int k = 0; k < kStages; ++k) mbar_init(&sm->bar[k], 1);
@@ -572,6 +574,7 @@ struct Ring {
   // copy; at the end of the array the part that is not a multiple of 16 bytes
   // is copied with plain loads and the rest of the slot zero-filled.
   __device__ __forceinline__ void issue(const Tract& t, int64_t hq, uint32_t k) {
+    if (hq == withhold) return;  // neither copy nor arrival: the wait for this slot runs out
     const int64_t v0 = hq << kPieceLog2;
     int32_t* dst = sm->ring[k];
     const int32_t* src = t.xyz + 3 * v0;
@@ -678,14 +681,17 @@ __device__ __forceinline__ bool scan_range_tma(Scan& sc, const VolView& v, const
   if (!ok) {
     if (lane_id() == 0) set_error(sc.sst, kErrTimeout, (int32_t)sc.s_lo);
     sc.abort = true;
+    // the slot whose wait ran out is passed over (its copy, if one was ever
+    // issued, is waited for no longer); the ring's phases are no longer
+    // those of its slots, so the caller must not use it again
+    r.advance();
+    ++taken;
   }
   // no copy may be in flight when the range ends: bounded drain of the
-  // pieces issued but not consumed
+  // pieces issued but not consumed, every one of them waited for even after
+  // one wait has run out
   for (; taken < issued; ++taken) {
-    if (!r.wait()) {
-      ok = false;
-      break;
-    }
+    if (!r.wait()) ok = false;
     r.advance();
   }
   return ok;
@@ -704,7 +710,8 @@ __host__ __device__ constexpr size_t ring_offset(size_t near_bytes) { return (ne
 
 template <int kMinBlocks, bool kTma, bool kSmem>
 __global__ void __launch_bounds__(kWarps * 32, kMinBlocks) prefilter_kernel(Tract t, VolView v, int prefilter,
-                                                                           SurvList surv, DevState* st) {
+                                                                           SurvList surv, DevState* st,
+                                                                           int64_t withhold) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ WarpShared ws_all[kWarps];
   griddep_launch_dependents();  // the walk's CTAs may take SMs as this grid's CTAs end
@@ -721,7 +728,7 @@ __global__ void __launch_bounds__(kWarps * 32, kMinBlocks) prefilter_kernel(Trac
   if (kTma) {
     const size_t off = ring_offset(kSmem ? (size_t)near_words(v) * 4 : 0);
     Ring r;
-    r.init(reinterpret_cast<TmaSmem*>(smem_raw + off) + (threadIdx.x >> 5));
+    r.init(reinterpret_cast<TmaSmem*>(smem_raw + off) + (threadIdx.x >> 5), withhold);
     scan_range_tma<kSmem>(sc, v, nw, t, prefilter != 0, ws, r, surv, st);
   } else {
     scan_range_direct<kSmem>(sc, v, nw, t, prefilter != 0, ws, surv, st);
@@ -774,7 +781,7 @@ cudaError_t resident_grid(K kernel, size_t smem, int num_sms, int* grid) {
 
 template <int kMinBlocks, bool kTma, bool kSmem>
 cudaError_t launch_plain(const Tract& t, const VolView& v, bool prefilter, const SurvList& survivors, DevState* st,
-                         int num_sms, cudaStream_t s) {
+                         int num_sms, cudaStream_t s, int64_t withhold) {
   auto k = prefilter_kernel<kMinBlocks, kTma, kSmem>;
   const size_t near_bytes = kSmem ? (size_t)near_words(v) * 4 : 0;
   const size_t bytes = kTma ? ring_offset(near_bytes) + kRingBytes : near_bytes;
@@ -782,7 +789,7 @@ cudaError_t launch_plain(const Tract& t, const VolView& v, bool prefilter, const
   int grid = 0;
   if (e == cudaSuccess) e = resident_grid(k, bytes, num_sms, &grid);
   if (e != cudaSuccess) return e;
-  k<<<grid, kWarps * 32, bytes, s>>>(t, v, prefilter ? 1 : 0, survivors, st);
+  k<<<grid, kWarps * 32, bytes, s>>>(t, v, prefilter ? 1 : 0, survivors, st, withhold);
   return cudaGetLastError();
 }
 
@@ -792,14 +799,15 @@ constexpr int64_t kNearSmemWordsTma = 8192;
 
 template <int kMinBlocks>
 cudaError_t launch_one(const Tract& t, const VolView& v, bool prefilter, bool tma, const SurvList& survivors,
-                       DevState* st, int num_sms, cudaStream_t s) {
+                       DevState* st, int num_sms, cudaStream_t s, int64_t wh) {
   const int64_t nw = near_words(v);
   if (tma) {
-    if (nw <= kNearSmemWordsTma) return launch_plain<kMinBlocks, true, true>(t, v, prefilter, survivors, st, num_sms, s);
-    return launch_plain<kMinBlocks, true, false>(t, v, prefilter, survivors, st, num_sms, s);
+    if (nw <= kNearSmemWordsTma)
+      return launch_plain<kMinBlocks, true, true>(t, v, prefilter, survivors, st, num_sms, s, wh);
+    return launch_plain<kMinBlocks, true, false>(t, v, prefilter, survivors, st, num_sms, s, wh);
   }
-  if (nw <= kNearSmemWords) return launch_plain<kMinBlocks, false, true>(t, v, prefilter, survivors, st, num_sms, s);
-  return launch_plain<kMinBlocks, false, false>(t, v, prefilter, survivors, st, num_sms, s);
+  if (nw <= kNearSmemWords) return launch_plain<kMinBlocks, false, true>(t, v, prefilter, survivors, st, num_sms, s, wh);
+  return launch_plain<kMinBlocks, false, false>(t, v, prefilter, survivors, st, num_sms, s, wh);
 }
 
 template <int kMinBlocks, bool kTma>
@@ -832,12 +840,12 @@ cudaError_t launch_prefilter_batch(const BatchTable& tbl, const BatchTask* tasks
 
 cudaError_t launch_prefilter(const Tract& t, const VolView& v, bool prefilter, uint32_t mode, bool tma,
                              int ctas_per_sm, int32_t* survivor_ids, int64_t survivor_cap, DevState* st, int num_sms,
-                             cudaStream_t s) {
+                             cudaStream_t s, int64_t withhold_piece) {
   (void)mode;  // the segment and the vertex-only rules share the near test; the walk applies the rule
   if (t.ns <= 0) return cudaSuccess;
   const SurvList survivors{survivor_ids, survivor_cap};
-  if (ctas_per_sm >= 3) return launch_one<3>(t, v, prefilter, tma, survivors, st, num_sms, s);
-  return launch_one<2>(t, v, prefilter, tma, survivors, st, num_sms, s);
+  if (ctas_per_sm >= 3) return launch_one<3>(t, v, prefilter, tma, survivors, st, num_sms, s, withhold_piece);
+  return launch_one<2>(t, v, prefilter, tma, survivors, st, num_sms, s, withhold_piece);
 }
 
 }  // namespace fc

@@ -92,6 +92,15 @@ __device__ __forceinline__ void load_vertex(const int32_t* xyz, int64_t j, int32
   p[2] = __ldg(xyz + 3 * j + 2);
 }
 
+// The 16-byte units inside the vertices [a, b) of t, prefetched into L2 by the
+// bulk-copy engine: the windows after a streamline's first then load from L2
+// instead of waiting on HBM one window at a time.
+__device__ __forceinline__ void prefetch_vertices(const Tract& t, int64_t a, int64_t b) {
+  const uintptr_t lo = (reinterpret_cast<uintptr_t>(t.xyz + 3 * a) + 15) & ~(uintptr_t)15;
+  const uintptr_t hi = reinterpret_cast<uintptr_t>(t.xyz + 3 * b) & ~(uintptr_t)15;
+  if (hi > lo) bulk_prefetch_l2(reinterpret_cast<const void*>(lo), (uint32_t)min(hi - lo, (uintptr_t)0x7ffffff0u));
+}
+
 // Per-voxel code of in-grid voxel (x, y, z), or ~0u off the grid (no row, no
 // label).
 __device__ __forceinline__ int32_t voxel_lin(const VolView& v, int32_t x, int32_t y, int32_t z) {
@@ -165,6 +174,7 @@ __device__ __forceinline__ int walk_one(const VolView& v, const Tract& t, const 
   const unsigned lane = lane_id();
   const bool endpoint_mode = (mode & kModeTargetEndpoint) != 0;
   const bool point_mode = (mode & kModeVertexSampled) != 0;
+  const bool walk_all = (mode & kModeWalkAll) != 0;
   const uint64_t keep = policy_evict_last();  // code gathers and C stay in L2 across the stream
   const int64_t M = v.n_lab;
   const int64_t a = t.off[s], b = t.off[s + 1];
@@ -172,6 +182,7 @@ __device__ __forceinline__ int walk_one(const VolView& v, const Tract& t, const 
   // a streamline is skipped (the call reports the error)
   if (a < 0 || b > t.nv || b <= a) return 0;
   const int64_t T = b - a;
+  if (T > 33 && lane == 0) prefetch_vertices(t, a + 32, b);
   int nV = 0, nT = 0;
   bool fail = false;
   if (T == 1 || point_mode) {
@@ -214,7 +225,7 @@ __device__ __forceinline__ int walk_one(const VolView& v, const Tract& t, const 
         const int32_t c0x = p0[0] >> kUnitLog2, c0y = p0[1] >> kUnitLog2, c0z = p0[2] >> kUnitLog2;
         const bool shortseg = abs((p1[0] >> kUnitLog2) - c0x) <= 1 && abs((p1[1] >> kUnitLog2) - c0y) <= 1 &&
                               abs((p1[2] >> kUnitLog2) - c0z) <= 1;
-        if (shortseg && near_lookup<false>(v, v.near, c0x, c0y, c0z) == 0u) has = false;
+        if (shortseg && !walk_all && near_lookup<false>(v, v.near, c0x, c0y, c0z) == 0u) has = false;
       }
       const bool small = !has || (abs(p1[0] - p0[0]) < 65536 && abs(p1[1] - p0[1]) < 65536 &&
                                   abs(p1[2] - p0[2]) < 65536);

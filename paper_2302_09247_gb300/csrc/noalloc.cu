@@ -4,8 +4,6 @@
 // file-scope device array of fixed size; every call on a device shares it.
 #include <cuda_runtime.h>
 
-#include <mutex>
-
 #include "fc_ctx.h"
 #include "fc_device.cuh"
 
@@ -134,19 +132,18 @@ __global__ void __launch_bounds__(256) na_walk_kernel(NaArgs a, uint32_t* scratc
   }
 }
 
-std::mutex g_mu;
-uint32_t* g_scratch_ptr[64] = {};  // device address of the scratch, per device
-
-// Once per device, with that device current: the scratch's device address.
-cudaError_t scratch_address(int dev, uint32_t** out) {
-  std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_scratch_ptr[dev]) {
-    void* p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess) return e;
-    g_scratch_ptr[dev] = static_cast<uint32_t*>(p);
-  }
-  *out = g_scratch_ptr[dev];
+// The scratch's device address on the current device, looked up on every
+// call: cudaGetSymbolAddress allocates nothing and is cheap, and an address
+// cached across calls would go stale if the caller reset the device (the
+// module, and with it the array, is loaded again afterwards).  The first
+// lookup on a device loads the library's device code there (lazy module
+// loading), so the first call on a device should come before any stream
+// capture.
+cudaError_t scratch_address(uint32_t** out) {
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess) return e;
+  *out = static_cast<uint32_t*>(p);
   return cudaSuccess;
 }
 
@@ -188,7 +185,7 @@ FASTCOD_API int fastcod_connectivity_noalloc(int cuda_device, void* cuda_stream,
     if (!p || fcapi::ptr_kind(p, cuda_device) != 1)
       return na_fail(FASTCOD_EINVAL, "fastcod_connectivity_noalloc takes device memory of cuda_device only");
   uint32_t* scratch = nullptr;
-  cudaError_t e = scratch_address(cuda_device, &scratch);
+  cudaError_t e = scratch_address(&scratch);
   if (e != cudaSuccess) {
     (void)cudaGetLastError();
     return na_fail(FASTCOD_ECUDA, "cudaGetSymbolAddress of the scratch failed");

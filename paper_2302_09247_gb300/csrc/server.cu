@@ -267,6 +267,10 @@ bool iterate(fastcod_server* S, uint32_t** tmp, size_t* tmp_cap) {
       S->waiting.pop_front();
       setups.push_back(r);
     }
+    // survivor ids of one pass are int32: the chunks of a pass hold at most
+    // 2^31 - 1 streamlines (a chunk that would pass that waits for the next
+    // pass; every chunk alone is within it)
+    int64_t pass_ns = 0;
     for (Request* r : S->active) {
       if (r->state == RState::Active && r->cancel) {
         r->state = RState::Finishing;
@@ -275,6 +279,8 @@ bool iterate(fastcod_server* S, uint32_t** tmp, size_t* tmp_cap) {
         continue;
       }
       if ((r->state == RState::Active || r->state == RState::Setup) && !r->chunks.empty()) {
+        if (pass_ns + r->chunks.front().ns > 0x7fffffffLL) continue;
+        pass_ns += r->chunks.front().ns;
         work.emplace_back(r, r->chunks.front());
         r->chunks.pop_front();
         lasts.emplace_back(r, r->last_pushed && r->chunks.empty());
@@ -326,7 +332,16 @@ bool iterate(fastcod_server* S, uint32_t** tmp, size_t* tmp_cap) {
     words = std::max(words, fc::overflow_scratch_words(r->head.n_roi, r->head.n_targets));
     ntasks += (size_t)std::max<int64_t>(1, (k.nv + 65535) / 65536);
   }
-  if (!staged.empty() && total_ns < 0x7fffffffLL) {
+  if (!staged.empty() && total_ns > 0x7fffffffLL) {
+    // cannot happen (the work list is limited above); fail the requests
+    // rather than return partial results
+    for (const Staged& sg : staged) {
+      sg.r->status = FASTCOD_EINVAL;
+      if (sg.buf) cudaFreeAsync(sg.buf, S->copy);
+    }
+    staged.clear();
+  }
+  if (!staged.empty()) {
     cudaEventRecord(S->copied, S->copy);
     cudaStreamWaitEvent(S->compute, S->copied, 0);
     cudaError_t e = grow_iteration_buffers(S, (size_t)total_ns, ntasks, words);

@@ -38,6 +38,8 @@ FASTCOD_OPT_NEAR_LOG2 = 7
 FASTCOD_OPT_AUTOTUNE = 8
 FASTCOD_OPT_HOST_IN_PLACE = 9
 FASTCOD_OPT_WALKED_STEPS = 10
+FASTCOD_OPT_SEGMENT_SKIP = 11
+FASTCOD_OPT_TEST_WITHHOLD_PIECE = 12
 
 EXPORTED = [
     "fastcod_create", "fastcod_destroy", "fastcod_set_stream", "fastcod_set_volumes",

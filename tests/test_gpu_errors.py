@@ -199,3 +199,48 @@ def test_user_stream_and_reset(fc, tiny0):
         np.testing.assert_array_equal(C2, 2 * C1)
         st = ctx.stats()
         assert st["streamlines"] == tr.n_streamlines and st["vertices"] == tr.n_vertices
+
+
+@pytest.mark.parametrize("piece", [0, 5, "last"])
+def test_bounded_wait_runs_out_then_context_recovers(fc, mid, piece):
+    # the bulk-copy loader withholds one vertex piece (no copy, no barrier
+    # arrival): the warp that waits for it gives up after its one-second
+    # limit, drains its other copies and reports the timeout; nothing is
+    # faulted, and the same context then computes the right C after reset
+    vols, tr = mid
+    n_pieces = (tr.n_vertices + 255) // 256
+    k = n_pieces - 1 if piece == "last" else piece
+    ctx = _ctx_with_volumes(fc, vols)
+    try:
+        xyz, off = as_device(tr.xyz), as_device(tr.offsets)
+        ctx.set_option(fc.FASTCOD_OPT_TEST_WITHHOLD_PIECE, k)
+        ctx.add_streamlines(xyz, off)
+        with pytest.raises(fc.FastCodError) as e:
+            ctx.sync()
+        assert e.value.code == fc.FASTCOD_ETIMEOUT and "timed out" in str(e.value)
+        ctx.set_option(fc.FASTCOD_OPT_TEST_WITHHOLD_PIECE, -1)
+        ctx.reset()
+        ctx.add_streamlines(xyz, off)
+        C, Ce = ctx.connectivity(), ctx.endpoint_connectivity()
+        Cr, Cer, _ = oracle.connectivity(vols.roi, vols.lab, vols.dims, vols.n_roi, vols.n_targets, tr.xyz,
+                                         tr.offsets)
+        np.testing.assert_array_equal(C, Cr)
+        np.testing.assert_array_equal(Ce, Cer)
+    finally:
+        ctx.close()
+
+
+def test_withheld_piece_has_no_effect_on_the_direct_loader(fc, tiny0):
+    vols, tr = tiny0
+    ctx = _ctx_with_volumes(fc, vols)
+    try:
+        ctx.set_option(fc.FASTCOD_OPT_STAGING, 0)
+        ctx.set_option(fc.FASTCOD_OPT_TEST_WITHHOLD_PIECE, 0)
+        ctx.add_streamlines(as_device(tr.xyz), as_device(tr.offsets))
+        Cr, _, _ = oracle.connectivity(vols.roi, vols.lab, vols.dims, vols.n_roi, vols.n_targets, tr.xyz,
+                                       tr.offsets)
+        np.testing.assert_array_equal(ctx.connectivity(), Cr)
+        with pytest.raises(fc.FastCodError):
+            ctx.set_option(fc.FASTCOD_OPT_TEST_WITHHOLD_PIECE, -2)
+    finally:
+        ctx.close()

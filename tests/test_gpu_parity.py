@@ -18,10 +18,11 @@ pytestmark = pytest.mark.gpu
 U = 1024
 
 
-def _opts(prefilter, staging, target=0, sampling=0):
+def _opts(prefilter, staging, target=0, sampling=0, skip=1):
     from paper_2302_09247_gb300 import fastcod as fc
     return {fc.FASTCOD_OPT_PREFILTER: prefilter, fc.FASTCOD_OPT_STAGING: staging,
-            fc.FASTCOD_OPT_TARGET_MODE: target, fc.FASTCOD_OPT_SAMPLING: sampling, fc.FASTCOD_OPT_WALKED_STEPS: 1}
+            fc.FASTCOD_OPT_TARGET_MODE: target, fc.FASTCOD_OPT_SAMPLING: sampling, fc.FASTCOD_OPT_WALKED_STEPS: 1,
+            fc.FASTCOD_OPT_SEGMENT_SKIP: skip}
 
 
 def _oracle_flags(target, sampling):
@@ -67,6 +68,21 @@ def test_adversarial_tiny(seed, prefilter, staging, target, sampling):
                                          many_to_one=bool(seed % 2))
     xyz, off = tiny.random_streamlines(rng, dims, 300, max_len=40)
     _check(roi, lab, dims, N, M, xyz, off, "device", _opts(prefilter, staging, target, sampling),
+           flags=_oracle_flags(target, sampling))
+
+
+@pytest.mark.parametrize("seed", range(4))
+@pytest.mark.parametrize("prefilter", [1, 0])
+@pytest.mark.parametrize("target,sampling", [(0, 0), (1, 0)])
+def test_adversarial_tiny_every_segment_walked(seed, prefilter, target, sampling):
+    # the walk's skip of far short segments switched off: every segment is
+    # walked voxel by voxel, and the result is the same
+    rng = np.random.default_rng(2000 + seed)
+    dims = tuple(int(v) for v in rng.integers(3, 10, size=3))
+    roi, lab, N, M = tiny.random_volumes(rng, dims, n_roi=6, n_labels=int(rng.integers(1, 7)),
+                                         many_to_one=bool(seed % 2))
+    xyz, off = tiny.random_streamlines(rng, dims, 300, max_len=40)
+    _check(roi, lab, dims, N, M, xyz, off, "device", _opts(prefilter, 1, target, sampling, skip=0),
            flags=_oracle_flags(target, sampling))
 
 
@@ -152,6 +168,9 @@ def test_cfg1_subset_all_modes():
     for target, sampling in ((0, 0), (1, 0), (0, 1)):
         _check(vols.roi, vols.lab, vols.dims, vols.n_roi, vols.n_targets, tr.xyz, tr.offsets, "device",
                _opts(1, 1, target, sampling), flags=_oracle_flags(target, sampling))
+    # the benchmark's measure of the walk itself: no prefilter, no segment skip
+    _check(vols.roi, vols.lab, vols.dims, vols.n_roi, vols.n_targets, tr.xyz, tr.offsets, "device",
+           _opts(0, 1, skip=0))
 
 
 def test_cfg1_full_bench_configuration():

@@ -10,6 +10,7 @@ This file is collected last."""
 import numpy as np
 import pytest
 
+import oracle
 import synth
 from synth import tiny
 from tests.gpu_helpers import as_device, run_gpu
@@ -66,3 +67,70 @@ def test_noalloc_rejects_sizes_beyond_its_scratch_and_host_memory():
     # the entry point still works afterwards
     C, _ = _noalloc(fc, _inputs()[1])
     np.testing.assert_array_equal(C, run_gpu(*_inputs()[1], where="device")[0])
+
+
+def _adversarial():
+    # lattice-snapped vertices on planes, edges and corners, T = 0 and T = 1
+    # streamlines, points off the grid
+    rng = np.random.default_rng(78)
+    dims = (8, 6, 7)
+    roi, lab, N, M = tiny.random_volumes(rng, dims, n_roi=6, n_labels=5, many_to_one=True)
+    xyz, off = tiny.random_streamlines(rng, dims, 400, max_len=30)
+    assert (np.diff(off) == 0).any() and (np.diff(off) == 1).any()
+    return roi, lab, dims, N, M, xyz, off
+
+
+def test_noalloc_equals_the_oracle():
+    from paper_2302_09247_gb300 import fastcod as fc
+    for case in _inputs() + [_adversarial()]:
+        roi, lab, dims, N, M, xyz, off = case
+        Cr, Cer, _ = oracle.connectivity(roi, lab, dims, N, M, xyz, off)
+        for _ in range(2):
+            C, Ce = _noalloc(fc, case)
+            np.testing.assert_array_equal(C, Cr)
+            np.testing.assert_array_equal(Ce, Cer)
+
+
+def test_noalloc_rejects_invalid_input_then_recovers():
+    # each invalid input is reported; the next valid call starts from a clean
+    # scratch and gives the right result
+    import torch
+    from paper_2302_09247_gb300 import fastcod as fc
+    case = _adversarial()
+    roi, lab, dims, N, M, xyz, off = case
+    Cr, Cer, _ = oracle.connectivity(roi, lab, dims, N, M, xyz, off)
+    C = torch.zeros((N, M), dtype=torch.int32, device="cuda:0")
+    Ce = torch.zeros((N, M), dtype=torch.int32, device="cuda:0")
+    bad_off = off.copy()
+    bad_off[20], bad_off[21] = bad_off[21] + 3, bad_off[20]        # decreasing
+    bad_xyz = xyz.copy()
+    bad_xyz[len(xyz) // 2, 2] = 1 << 24                              # coordinate at 2^24
+    bad_lab = lab.copy()
+    bad_lab.reshape(-1)[11] = M + 1                                  # label > M
+    bad_roi = roi.copy()
+    bad_roi.reshape(-1)[3] = N                                       # row >= N
+    for r, l, x, o, what in ((roi, lab, xyz, bad_off, "offsets"), (roi, lab, bad_xyz, off, "coordinate"),
+                             (roi, bad_lab, xyz, off, "volume"), (bad_roi, lab, xyz, off, "volume")):
+        with pytest.raises(fc.FastCodError) as e:
+            fc.fastcod_connectivity_noalloc(0, None, as_device(r), as_device(l), dims, N, M, as_device(x),
+                                            as_device(o), C, Ce)
+        assert e.value.code == fc.FASTCOD_EINVAL and what in str(e.value), str(e.value)
+        Cv, Cev = _noalloc(fc, case)
+        np.testing.assert_array_equal(Cv, Cr)
+        np.testing.assert_array_equal(Cev, Cer)
+
+
+def test_noalloc_on_a_side_stream():
+    import torch
+    from paper_2302_09247_gb300 import fastcod as fc
+    roi, lab, dims, N, M, xyz, off = _adversarial()
+    Cr, Cer, _ = oracle.connectivity(roi, lab, dims, N, M, xyz, off)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        args = [as_device(roi), as_device(lab), as_device(xyz), as_device(off)]
+        C = torch.full((N, M), -5, dtype=torch.int32, device="cuda:0")
+        Ce = torch.full((N, M), -5, dtype=torch.int32, device="cuda:0")
+    s.synchronize()
+    fc.fastcod_connectivity_noalloc(0, s, args[0], args[1], dims, N, M, args[2], args[3], C, Ce)
+    np.testing.assert_array_equal(C.cpu().numpy(), Cr)
+    np.testing.assert_array_equal(Ce.cpu().numpy(), Cer)
