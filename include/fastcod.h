@@ -31,8 +31,10 @@
  *
  * Pointers: every input and output pointer may be host memory (pageable or
  * page-locked) or device memory of the context's device; the library tells
- * them apart with cudaPointerGetAttributes.  Device xyz pointers must be
- * 16-byte aligned.  The caller owns every buffer it passes.  Work is ordered
+ * them apart with cudaPointerGetAttributes.  Device xyz that does not start
+ * on a 16-byte boundary (4-byte alignment, as for any int32 array, is
+ * required) is first copied to an aligned buffer of the library: one more
+ * pass over the vertices.  The caller owns every buffer it passes.  Work is ordered
  * on the context's stream; device inputs and page-locked host inputs must
  * stay unchanged until the next synchronising call (fastcod_connectivity,
  * fastcod_endpoint_connectivity, fastcod_get_stats, fastcod_sync) or a sync
@@ -183,7 +185,7 @@ FASTCOD_API int fastcod_set_stream(fastcod_ctx* ctx, void* cuda_stream);
 
 /* Install the volumes (Section 2: the ROI voxel set V = {v_1..v_N} and the
  * target regions R = {R_1..R_M}; loc2region).  dims are Dx, Dy, Dz (> 0,
- * product < 2^31, Dy and Dz <= 65533).  n_roi = N (0: max(roi)+1); n_targets = M (0: max label).
+ * product < 2^31).  n_roi = N (0: max(roi)+1); n_targets = M (0: max label).
  * Requires -1 <= roi < N, label <= M, N < 2^30, M < 65536.  Zeroes C,
  * C_end and the statistics.  Blocks until the volumes are validated. */
 FASTCOD_API int fastcod_set_volumes(fastcod_ctx* ctx, const int32_t* roi_index_map,
@@ -239,7 +241,7 @@ typedef struct {
   int32_t dims[3];                /* Dx, Dy, Dz */
   int32_t n_roi;                  /* N (> 0, given explicitly) */
   int32_t n_targets;              /* M (> 0, given explicitly) */
-  const int32_t* xyz;             /* [n_vertices][3], 16-byte aligned if on the device */
+  const int32_t* xyz;             /* [n_vertices][3] (device xyz off 16 bytes is staged) */
   int64_t n_vertices;
   const int64_t* offsets;         /* [n_streamlines + 1] */
   int64_t n_streamlines;

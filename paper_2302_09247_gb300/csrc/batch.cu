@@ -298,7 +298,7 @@ int run_config(fastcod_ctx* c, const fastcod_subject* subs, int32_t n, const std
         if (e == cudaSuccess && L.lab_in[i] != SIZE_MAX)
           e = cudaMemcpyAsync(at<void>(A, L.lab_in[i]), S.target_labels, (size_t)nvox * 2, cudaMemcpyHostToDevice, c->stream);
         if (e == cudaSuccess && L.xyz_in[i] != SIZE_MAX && S.n_vertices)
-          e = cudaMemcpyAsync(at<void>(A, L.xyz_in[i]), S.xyz, (size_t)S.n_vertices * 12, cudaMemcpyHostToDevice, c->stream);
+          e = cudaMemcpyAsync(at<void>(A, L.xyz_in[i]), S.xyz, (size_t)S.n_vertices * 12, cudaMemcpyDefault, c->stream);
         if (e == cudaSuccess && L.off_in[i] != SIZE_MAX)
           e = cudaMemcpyAsync(at<void>(A, L.off_in[i]), S.offsets, (size_t)(S.n_streamlines + 1) * 8,
                               cudaMemcpyHostToDevice, c->stream);
@@ -419,8 +419,8 @@ FASTCOD_API int fastcod_batch_run(fastcod_ctx* c, const fastcod_subject* subs, i
     const fastcod_subject& S = subs[i];
     if (S.dims[0] <= 0 || S.dims[1] <= 0 || S.dims[2] <= 0)
       return fail(c, FASTCOD_EINVAL, "subject %d: grid dims must be > 0", i);
-    if ((int64_t)S.dims[0] * S.dims[1] * S.dims[2] >= ((int64_t)1 << 31) || S.dims[1] > 65533 || S.dims[2] > 65533)
-      return fail(c, FASTCOD_EINVAL, "subject %d: grid has >= 2^31 voxels or Dy, Dz > 65533", i);
+    if ((int64_t)S.dims[0] * S.dims[1] * S.dims[2] >= ((int64_t)1 << 31))
+      return fail(c, FASTCOD_EINVAL, "subject %d: grid has >= 2^31 voxels", i);
     if (S.n_roi <= 0 || S.n_roi >= (1 << 30) || S.n_targets <= 0 || S.n_targets > 65535)
       return fail(c, FASTCOD_EINVAL, "subject %d: need 0 < n_roi < 2^30 and 0 < n_targets < 65536", i);
     if (S.n_streamlines < 1 || S.n_vertices < 0 || S.n_vertices > 0x7fffffffLL)
@@ -433,8 +433,9 @@ FASTCOD_API int fastcod_batch_run(fastcod_ctx* c, const fastcod_subject* subs, i
       if (kind < 0) return fail(c, FASTCOD_EINVAL, "subject %d: input is device memory of another device", i);
       host_in[4 * i + k] = kind == 0;
     }
-    if (!host_in[4 * i + 2] && S.n_vertices && ((uintptr_t)S.xyz & 15u))
-      return fail(c, FASTCOD_EINVAL, "subject %d: device xyz must be 16-byte aligned", i);
+    // device xyz off a 16-byte boundary is staged like host input (the bulk
+    // copies of the prefilter need 16-byte aligned sources)
+    if (S.n_vertices && ((uintptr_t)S.xyz & 15u)) host_in[4 * i + 2] = true;
     if (ptr_kind(S.C_out, c->device) < 0 || ptr_kind(S.Cend_out, c->device) < 0)
       return fail(c, FASTCOD_EINVAL, "subject %d: output is device memory of another device", i);
     total_ns += S.n_streamlines;

@@ -298,7 +298,6 @@ FASTCOD_API int fastcod_set_volumes(fastcod_ctx* c, const int32_t* roi, const ui
   if (dx <= 0 || dy <= 0 || dz <= 0) return fail(c, FASTCOD_EINVAL, "grid dims must be > 0");
   const int64_t nvox = (int64_t)dx * dy * dz;
   if (nvox >= ((int64_t)1 << 31)) return fail(c, FASTCOD_EINVAL, "grid has >= 2^31 voxels");
-  if (dy > 65533 || dz > 65533) return fail(c, FASTCOD_EINVAL, "Dy and Dz must be <= 65533");
   if (!roi || !lab) return fail(c, FASTCOD_EINVAL, "volume pointer is NULL");
   if (n_roi < 0 || n_targets < 0) return fail(c, FASTCOD_EINVAL, "N and M must be >= 0");
   CU(cudaSetDevice(c->device));
@@ -395,8 +394,9 @@ FASTCOD_API int fastcod_add_streamlines(fastcod_ctx* c, const int32_t* xyz, int6
   const int kx = nv > 0 ? ptr_kind(xyz, c->device) : 1;
   const int ko = ptr_kind(offsets, c->device);
   if (kx < 0 || ko < 0) return fail(c, FASTCOD_EINVAL, "input is device memory of another device");
-  if (kx == 1 && nv > 0 && ((uintptr_t)xyz & 15u))
-    return fail(c, FASTCOD_EINVAL, "device xyz must be 16-byte aligned");
+  // device xyz off a 16-byte boundary is copied to an aligned buffer first
+  // (the prefilter's bulk copies and vector loads need aligned vertex rows)
+  const bool unaligned = kx == 1 && nv > 0 && ((uintptr_t)xyz & 15u);
   const int32_t* d_xyz = xyz;
   const int64_t* d_off = offsets;
   if (int rc = begin_profiled_call(c)) return rc;
@@ -411,10 +411,10 @@ FASTCOD_API int fastcod_add_streamlines(fastcod_ctx* c, const int32_t* xyz, int6
       xyz_in_place = true;
     }
   }
-  if (kx == 0 && !xyz_in_place) {
+  if ((kx == 0 && !xyz_in_place) || unaligned) {
     int rc = grow(c, (void**)&c->d_xyz, &c->xyz_bytes, (size_t)nv * 12 + 16);
     if (rc) return rc;
-    CU(cudaMemcpyAsync(c->d_xyz, xyz, (size_t)nv * 12, cudaMemcpyHostToDevice, c->stream));
+    CU(cudaMemcpyAsync(c->d_xyz, xyz, (size_t)nv * 12, cudaMemcpyDefault, c->stream));
     d_xyz = c->d_xyz;
   }
   if (ko == 0) {

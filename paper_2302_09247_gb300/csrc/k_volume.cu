@@ -2,8 +2,7 @@
 // label volume (uint16) build the per-voxel code, a private label copy, the
 // brick occupancy bits and the near grid, validating every voxel on the way
 // (Section 2: the ROI voxel set V and the target regions R that loc2region
-// reads).  Launch grids are (x blocks, rows, planes), so every thread knows
-// its voxel without a division.
+// reads).
 #include "fc_device.cuh"
 
 namespace fc {
@@ -32,7 +31,10 @@ __global__ void __launch_bounds__(256) volume_max_kernel(const int32_t* __restri
 // consecutive voxels of a row (x aligned to 32), so the warp's ballots are
 // the row's ROI / label bit-plane words (planes: two planes of Dy*Dz rows of
 // ceil(Dx/32) words).  A warp's 32 voxels touch at most two brick words: their
-// bits are ORed across the warp and set with one atomic per word.
+// bits are ORed across the warp and set with one atomic per word.  The grid's
+// x blocks run along x; its y and z blocks together number the (8-row group,
+// plane) pairs, ryb = ceil(Dy/8) groups per plane, so that Dy and Dz are
+// bounded only by the voxel count.
 constexpr int kPrepRows = 8;
 
 __global__ void __launch_bounds__(32 * kPrepRows) volume_prep_kernel(const int32_t* __restrict__ roi,
@@ -42,7 +44,11 @@ __global__ void __launch_bounds__(32 * kPrepRows) volume_prep_kernel(const int32
                                                                      uint32_t* __restrict__ bricks,
                                                                      uint32_t* __restrict__ planes, DevState* st) {
   const int32_t lane = (int32_t)threadIdx.x;
-  const int32_t x = blockIdx.x * 32 + lane, y = blockIdx.y * kPrepRows + threadIdx.y, z = blockIdx.z;
+  const int64_t g = (int64_t)blockIdx.z * gridDim.y + blockIdx.y;  // (row group, plane) pair
+  const int32_t ryb = (v.dy + kPrepRows - 1) / kPrepRows;
+  if (g >= (int64_t)ryb * v.dz) return;  // whole blocks
+  const int32_t z = (int32_t)(g / ryb);
+  const int32_t x = blockIdx.x * 32 + lane, y = (int32_t)(g - (int64_t)z * ryb) * kPrepRows + threadIdx.y;
   if (y >= v.dy) return;  // whole warps: y is the same for the warp's 32 lanes
   const bool in = x < v.dx;
   const int32_t i = x + v.dx * (y + v.dy * z);
@@ -156,7 +162,10 @@ cudaError_t launch_volume_prep(const int32_t* roi, const uint16_t* lab, int64_t 
                                uint32_t* code, uint16_t* lab_out, uint32_t* bricks, uint32_t* planes, DevState* st,
                                cudaStream_t s) {
   (void)nvox;
-  volume_prep_kernel<<<dim3((v.dx + 31) / 32, (v.dy + kPrepRows - 1) / kPrepRows, v.dz), dim3(32, kPrepRows), 0, s>>>(
+  const int64_t groups = (int64_t)((v.dy + kPrepRows - 1) / kPrepRows) * v.dz;  // < 2^31 / 8
+  const int64_t gy = groups < 65535 ? groups : 65535;
+  const int64_t gz = (groups + gy - 1) / gy;
+  volume_prep_kernel<<<dim3((v.dx + 31) / 32, (unsigned)gy, (unsigned)gz), dim3(32, kPrepRows), 0, s>>>(
       roi, lab, v, code, lab_out, bricks, planes, st);
   return cudaGetLastError();
 }

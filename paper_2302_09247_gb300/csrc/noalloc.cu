@@ -37,11 +37,13 @@ __device__ __forceinline__ void na_error(uint32_t* header, int32_t code, int32_t
   if (atomicCAS(h, 0, code) == 0) atomicExch(h + 1, info);
 }
 
-// grid (x blocks, Dy, Dz): every voxel's row and label in range
+// grid (x blocks, rows): every voxel's row and label in range; the grid's y
+// and z blocks together number the Dy * Dz rows
 __global__ void __launch_bounds__(128) na_validate_kernel(NaArgs a, uint32_t* scratch) {
-  const int32_t x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
-  if (x >= a.dx) return;
-  const int32_t i = x + a.dx * (y + a.dy * z);
+  const int64_t row = (int64_t)blockIdx.z * gridDim.y + blockIdx.y;
+  const int32_t x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= a.dx || row >= (int64_t)a.dy * a.dz) return;
+  const int32_t i = x + a.dx * (int32_t)row;
   const int32_t r = a.roi[i], l = (int32_t)a.lab[i];
   if (r < -1 || r >= a.n_roi || l > a.n_lab) na_error(scratch, fc::kErrVolume, i);
 }
@@ -166,8 +168,7 @@ FASTCOD_API int fastcod_connectivity_noalloc(int cuda_device, void* cuda_stream,
     (void)cudaGetLastError();
     return na_fail(FASTCOD_EINVAL, "no such CUDA device");
   }
-  if (dim_x <= 0 || dim_y <= 0 || dim_z <= 0 || dim_y > 65533 || dim_z > 65533 ||
-      (int64_t)dim_x * dim_y * dim_z >= ((int64_t)1 << 31))
+  if (dim_x <= 0 || dim_y <= 0 || dim_z <= 0 || (int64_t)dim_x * dim_y * dim_z >= ((int64_t)1 << 31))
     return na_fail(FASTCOD_EINVAL, "invalid grid dims");
   if (n_roi < 1 || n_roi > kNaMaxRoi || n_targets < 1 || n_targets > kNaMaxLabels)
     return na_fail(FASTCOD_EINVAL,
@@ -199,7 +200,9 @@ FASTCOD_API int fastcod_connectivity_noalloc(int cuda_device, void* cuda_stream,
   // the previous call's contents: the error word and any set bits start at zero
   if (e == cudaSuccess) e = cudaMemsetAsync(scratch, 0, (size_t)kNaWords * 4, s);
   if (e == cudaSuccess) {
-    na_validate_kernel<<<dim3((dim_x + 127) / 128, dim_y, dim_z), 128, 0, s>>>(a, scratch);
+    const int64_t rows = (int64_t)dim_y * dim_z, gy = rows < 65535 ? rows : 65535;
+    na_validate_kernel<<<dim3((dim_x + 127) / 128, (unsigned)gy, (unsigned)((rows + gy - 1) / gy)), 128, 0, s>>>(
+        a, scratch);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess && n_streamlines > 0) {

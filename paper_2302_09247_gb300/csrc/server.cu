@@ -313,7 +313,7 @@ bool iterate(fastcod_server* S, uint32_t** tmp, size_t* tmp_cap) {
       const size_t xb = a256((size_t)k.nv * 12 + 16);
       cudaError_t e = cudaMallocAsync(&sg.buf, xb + (size_t)(k.ns + 1) * 8, S->copy);
       if (e == cudaSuccess && k.host_xyz && k.nv) {
-        e = cudaMemcpyAsync(sg.buf, k.xyz, (size_t)k.nv * 12, cudaMemcpyHostToDevice, S->copy);
+        e = cudaMemcpyAsync(sg.buf, k.xyz, (size_t)k.nv * 12, cudaMemcpyDefault, S->copy);
         sg.t.xyz = static_cast<int32_t*>(sg.buf);
       }
       if (e == cudaSuccess && k.host_off) {
@@ -530,7 +530,7 @@ FASTCOD_API int fastcod_server_create(fastcod_ctx* c, int32_t max_slots, int64_t
 
 FASTCOD_API int fastcod_server_submit(fastcod_server* S, const fastcod_subject* h, uint64_t* id) {
   if (!S || !h || !id) return FASTCOD_EINVAL;
-  if (h->dims[0] <= 0 || h->dims[1] <= 0 || h->dims[2] <= 0 || h->dims[1] > 65533 || h->dims[2] > 65533 ||
+  if (h->dims[0] <= 0 || h->dims[1] <= 0 || h->dims[2] <= 0 ||
       (int64_t)h->dims[0] * h->dims[1] * h->dims[2] >= ((int64_t)1 << 31))
     return sfail(S, FASTCOD_EINVAL, "invalid grid dims");
   if (h->n_roi <= 0 || h->n_roi >= (1 << 30) || h->n_targets <= 0 || h->n_targets > 65535)
@@ -564,8 +564,9 @@ FASTCOD_API int fastcod_server_push_chunk(fastcod_server* S, uint64_t id, const 
   if (ns > 0) {
     const int kx = nv ? fcapi::ptr_kind(xyz, S->device) : 1, ko = fcapi::ptr_kind(offsets, S->device);
     if (kx < 0 || ko < 0) return sfail(S, FASTCOD_EINVAL, "device memory of another device");
-    if (kx == 1 && nv && ((uintptr_t)xyz & 15u)) return sfail(S, FASTCOD_EINVAL, "device xyz must be 16-byte aligned");
-    k.host_xyz = kx == 0;
+    // staged on the copy stream: host xyz, and device xyz off a 16-byte
+    // boundary (the prefilter's bulk copies need aligned sources)
+    k.host_xyz = kx == 0 || (nv && ((uintptr_t)xyz & 15u));
     k.host_off = ko == 0;
   }
   std::lock_guard<std::mutex> lk(S->mu);

@@ -244,3 +244,85 @@ def test_withheld_piece_has_no_effect_on_the_direct_loader(fc, tiny0):
             ctx.set_option(fc.FASTCOD_OPT_TEST_WITHHOLD_PIECE, -2)
     finally:
         ctx.close()
+
+
+def test_unaligned_device_xyz_is_staged(fc, tiny0):
+    # device xyz starting 4 bytes past a 16-byte boundary: the context, the
+    # batched form and the served form copy it to an aligned buffer first
+    import torch
+    vols, tr = tiny0
+    Cr, Cer, _ = oracle.connectivity(vols.roi, vols.lab, vols.dims, vols.n_roi, vols.n_targets, tr.xyz,
+                                     tr.offsets)
+    flat = torch.zeros(tr.xyz.size + 1, dtype=torch.int32, device="cuda:0")
+    flat[1:] = torch.from_numpy(tr.xyz.reshape(-1)).cuda()
+    view = flat[1:].view(-1, 3)
+    assert view.data_ptr() % 16 != 0
+    off = as_device(tr.offsets)
+    for staging in (1, 0):
+        ctx = _ctx_with_volumes(fc, vols)
+        try:
+            ctx.set_option(fc.FASTCOD_OPT_STAGING, staging)
+            ctx.add_streamlines(view, off)
+            np.testing.assert_array_equal(ctx.connectivity(), Cr)
+            np.testing.assert_array_equal(ctx.endpoint_connectivity(), Cer)
+        finally:
+            ctx.close()
+    N, M = vols.n_roi, vols.n_targets
+    C = torch.zeros((N, M), dtype=torch.int32, device="cuda:0")
+    Ce = torch.zeros_like(C)
+    with fc.Context(0) as ctx:
+        s = fc.make_subject(as_device(vols.roi), as_device(vols.lab), vols.dims, N, M, view, off, C, Ce)
+        fc.fastcod_batch_run(ctx.ctx, [s])
+        np.testing.assert_array_equal(C.cpu().numpy(), Cr)
+        np.testing.assert_array_equal(Ce.cpu().numpy(), Cer)
+        srv = fc.fastcod_server_create(ctx.ctx, 2, 0)
+        try:
+            Ch = np.zeros((N, M), np.int32)
+            Ceh = np.zeros((N, M), np.int32)
+            head = fc.make_subject(vols.roi, vols.lab, vols.dims, N, M, np.zeros((0, 3), np.int32),
+                                   np.zeros(1, np.int64), Ch, Ceh)
+            rid = fc.fastcod_server_submit(srv, head)
+            fc.fastcod_server_push_chunk(srv, rid, view, off, last=True)
+            assert fc.fastcod_server_wait(srv, rid, 60.0) == fc.FASTCOD_OK
+            np.testing.assert_array_equal(Ch, Cr)
+            np.testing.assert_array_equal(Ceh, Cer)
+        finally:
+            fc.fastcod_server_destroy(srv)
+
+
+@pytest.mark.parametrize("dims", [(1, 1, 70_000), (3, 70_000, 2), (2, 3, 66_000)])
+def test_long_thin_grids(fc, dims):
+    # Dy or Dz past the 65,535 blocks of one launch-grid dimension: bounded
+    # only by the voxel count
+    from synth import tiny
+    rng = np.random.default_rng(sum(dims))
+    roi, lab, N, M = tiny.random_volumes(rng, dims, n_roi=40, n_labels=6, p_roi=0.05, p_lab=0.1,
+                                         many_to_one=True)
+    xyz, off = tiny.random_streamlines(rng, dims, 2000, max_len=12, margin=1)
+    # streamlines within 4 voxels, placed at random voxels of the grid that
+    # coordinates can reach (|coordinate| < 2^24 units = 16,384 voxels)
+    reach = np.minimum(np.array(dims), 16_000)
+    shift = (rng.integers(0, reach, size=(len(off) - 1, 3)) * 1024).astype(np.int64)
+    xyz = (xyz.astype(np.int64) % 4096 + np.repeat(shift, np.diff(off), axis=0)).astype(np.int32)
+    Cr, Cer, _ = oracle.connectivity(roi, lab, dims, N, M, xyz, off)
+    assert Cr.sum() > 0
+    for where in ("device", "host"):
+        ctx = fc.Context(0)
+        try:
+            if where == "device":
+                ctx.set_volumes(as_device(roi), as_device(lab), dims, N, M)
+                ctx.add_streamlines(as_device(xyz), as_device(off))
+            else:
+                ctx.set_volumes(roi, lab, dims, N, M)
+                ctx.add_streamlines(xyz, off)
+            np.testing.assert_array_equal(ctx.connectivity(), Cr)
+            np.testing.assert_array_equal(ctx.endpoint_connectivity(), Cer)
+        finally:
+            ctx.close()
+    import torch
+    C = torch.zeros((N, M), dtype=torch.int32, device="cuda:0")
+    Ce = torch.zeros_like(C)
+    fc.fastcod_connectivity_noalloc(0, None, as_device(roi), as_device(lab), dims, N, M, as_device(xyz),
+                                    as_device(off), C, Ce)
+    np.testing.assert_array_equal(C.cpu().numpy(), Cr)
+    np.testing.assert_array_equal(Ce.cpu().numpy(), Cer)
