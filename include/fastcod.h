@@ -301,7 +301,16 @@ typedef struct {
 
 /* max_slots: 1..128 requests on the device at once; hbm_budget_bytes: device
  * memory the server may reserve for admitted requests (0: 90% of the free
- * memory at creation). */
+ * memory at creation).
+ *
+ * Failure injection for tests, on the host only: when the environment
+ * variable FASTCOD_FAULT holds comma-separated items "alloc:k", "h2d:k" or
+ * "cancel:k" (k >= 1) at creation, the server's k-th per-request device
+ * allocation (a request's volumes and accumulators at admission, or a host
+ * chunk's staging buffer) fails as if device memory were exhausted (the
+ * request ends with FASTCOD_ENOMEM), its k-th copy of a host chunk fails
+ * (FASTCOD_ECUDA), or its k-th submitted request is cancelled on
+ * submission (FASTCOD_ECANCELED).  The other requests are unaffected. */
 FASTCOD_API int fastcod_server_create(fastcod_ctx* ctx, int32_t max_slots, int64_t hbm_budget_bytes,
                                       fastcod_server** out);
 

@@ -39,8 +39,9 @@ struct Layout {
   size_t scratch, gstate, states, tasks, surv, ovf, staged_end;
   int64_t surv_cap;  // entries of the survivor and overflow lists
   std::vector<size_t> roi_in, lab_in, xyz_in, off_in;  // staging of host inputs (or SIZE_MAX)
-  std::vector<size_t> code, lab, bricks, C, Cend;
-  size_t planes;
+  std::vector<size_t> code, lab, bricks, C, Cend, planes;
+  size_t acc_lo, acc_hi;        // every subject's C and C_end: one span, zeroed by one memset
+  size_t bricks_lo, bricks_hi;  // every subject's brick words: one span
   std::vector<size_t> near;
   size_t total;
   int64_t scratch_words;
@@ -126,18 +127,28 @@ Layout plan(const fastcod_subject* subs, int32_t n, const std::vector<int>& host
   for (int32_t i = 0; i < n; ++i) {
     const fastcod_subject& S = subs[i];
     const int64_t nvox = (int64_t)S.dims[0] * S.dims[1] * S.dims[2];
-    const int64_t nb = (int64_t)((S.dims[0] + 3) / 4) * ((S.dims[1] + 3) / 4) * ((S.dims[2] + 3) / 4);
-    const size_t nm = (size_t)S.n_roi * (size_t)S.n_targets;
     L.code.push_back(take((size_t)nvox * 4));
     L.lab.push_back(take((size_t)nvox * 2));
-    L.bricks.push_back(take((size_t)((nb + 15) / 16) * 4));
+    L.planes.push_back(take((size_t)fc::plane_words(S.dims[0], S.dims[1], S.dims[2]) * 4));
+  }
+  L.acc_lo = o;
+  for (int32_t i = 0; i < n; ++i) {
+    const size_t nm = (size_t)subs[i].n_roi * (size_t)subs[i].n_targets;
     L.C.push_back(take(nm * 4));
     L.Cend.push_back(take(nm * 4));
   }
+  L.acc_hi = o;
+  L.bricks_lo = o;
+  for (int32_t i = 0; i < n; ++i) {
+    const fastcod_subject& S = subs[i];
+    const int64_t nb = (int64_t)((S.dims[0] + 3) / 4) * ((S.dims[1] + 3) / 4) * ((S.dims[2] + 3) / 4);
+    L.bricks.push_back(take((size_t)((nb + 15) / 16) * 4));
+  }
+  L.bricks_hi = o;
+  (void)maxplanes;
   // the configuration-dependent part last (near grids: the cell size; tasks:
   // the work granularity), so that the rest, staged inputs included, keeps
   // its place from one configuration to the next
-  L.planes = take((size_t)maxplanes * 4);
   for (int32_t i = 0; i < n; ++i) L.near.push_back(take((size_t)near_words(subs[i].dims, near_log2) * 4));
   L.tasks = take(sizeof(fc::BatchTask) * ntasks);
   L.total = o;
@@ -217,25 +228,33 @@ int capture(fastcod_ctx* c, const fastcod_subject* subs, int32_t n, const Layout
   BatchState* B = c->batch;
   void* A = B->arena;
   DevState* gst = at<DevState>(A, L.gstate);
-  CU(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+  // volume preparation of every subject: one launch for the codes, labels,
+  // bricks and bit planes, one for the near grids
+  fc::PrepTable* prep = new (std::nothrow) fc::PrepTable;
+  if (!prep) return fail(c, FASTCOD_ENOMEM, "host allocation failed");
+  memset(prep, 0, sizeof *prep);
+  prep->n = n;
+  for (int32_t i = 0; i < n; ++i) {
+    fc::PrepSubject& P = prep->s[i];
+    P.v = tbl.s[i].v;
+    P.roi = L.roi_in[i] != SIZE_MAX ? at<int32_t>(A, L.roi_in[i]) : subs[i].roi_index_map;
+    P.lab = L.lab_in[i] != SIZE_MAX ? at<uint16_t>(A, L.lab_in[i]) : subs[i].target_labels;
+    P.planes = at<uint32_t>(A, L.planes[i]);
+    P.st = tbl.s[i].st;
+  }
+  fc::prep_table_blocks(*prep);
+  const cudaError_t e0 = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+  if (e0 != cudaSuccess) {
+    delete prep;
+    CU(e0);
+  }
   cudaError_t e = cudaMemsetAsync(gst, 0, sizeof(DevState), c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(at<DevState>(A, L.states), 0, sizeof(DevState) * n, c->stream);
-  for (int32_t i = 0; i < n && e == cudaSuccess; ++i) {
-    const fastcod_subject& S = subs[i];
-    const fc::BatchSubject& bs = tbl.s[i];
-    const size_t nm = (size_t)S.n_roi * (size_t)S.n_targets;
-    const int64_t nvox = (int64_t)S.dims[0] * S.dims[1] * S.dims[2];
-    const int64_t nb = (int64_t)bs.v.bx * bs.v.by * bs.v.bz;
-    if (nm) e = cudaMemsetAsync(bs.acc.C, 0, nm * 4, c->stream);
-    if (nm && e == cudaSuccess) e = cudaMemsetAsync(bs.acc.Cend, 0, nm * 4, c->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(const_cast<uint32_t*>(bs.v.bricks), 0, (size_t)((nb + 15) / 16) * 4, c->stream);
-    const int32_t* roi = L.roi_in[i] != SIZE_MAX ? at<int32_t>(A, L.roi_in[i]) : S.roi_index_map;
-    const uint16_t* lab = L.lab_in[i] != SIZE_MAX ? at<uint16_t>(A, L.lab_in[i]) : S.target_labels;
-    if (e == cudaSuccess)
-      e = fc::launch_volume_prep(roi, lab, nvox, bs.v, const_cast<uint32_t*>(bs.v.code), const_cast<uint16_t*>(bs.v.lab),
-                                 const_cast<uint32_t*>(bs.v.bricks), at<uint32_t>(A, L.planes), bs.st, c->stream);
-    if (e == cudaSuccess) e = fc::launch_near(bs.v, at<uint32_t>(A, L.planes), const_cast<uint32_t*>(bs.v.near), c->stream);
-  }
+  if (e == cudaSuccess) e = cudaMemsetAsync(at<char>(A, L.acc_lo), 0, L.acc_hi - L.acc_lo, c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(at<char>(A, L.bricks_lo), 0, L.bricks_hi - L.bricks_lo, c->stream);
+  if (e == cudaSuccess) e = fc::launch_volume_prep_batch(*prep, c->stream);
+  if (e == cudaSuccess) e = fc::launch_near_batch(*prep, c->stream);
+  delete prep;
   if (e == cudaSuccess)
     e = fc::launch_prefilter_batch(tbl, at<fc::BatchTask>(A, L.tasks), L.ntasks, c->prefilter != 0, c->staging_tma != 0, cfg.ctas,
                                    at<int32_t>(A, L.surv), L.surv_cap, gst, c->num_sms, c->stream);
@@ -258,7 +277,7 @@ int capture(fastcod_ctx* c, const fastcod_subject* subs, int32_t n, const Layout
   return FASTCOD_OK;
 }
 
-int kernels_per_run(int32_t n) { return 2 * n + 3; }
+int kernels_per_run(int32_t n) { return n > 0 ? 5 : 0; }
 
 // Stage inputs, (re)capture when the shape changed, run the graph.
 int run_config(fastcod_ctx* c, const fastcod_subject* subs, int32_t n, const std::vector<int>& host_in,

@@ -152,6 +152,25 @@ struct BatchTable {
   BatchSubject s[kMaxBatch];
 };
 
+// Volume preparation of one subject of a batch: its inputs, its volume view
+// (outputs code, lab, bricks, near), its bit planes and counters, and the
+// first of its blocks in the batched prep and near-grid launches.
+struct PrepSubject {
+  VolView v;
+  const int32_t* roi;
+  const uint16_t* lab;
+  uint32_t* planes;
+  DevState* st;
+  int64_t prep_blk0;  // first block of the prep launch
+  int64_t near_blk0;  // first block of the near-grid launch
+};
+struct PrepTable {
+  int32_t n;
+  int32_t pad;
+  int64_t prep_blocks, near_blocks;  // blocks of the two launches
+  PrepSubject s[kMaxBatch];
+};
+
 // A prefilter task: streamlines [s_lo, s_hi) of one subject.
 struct BatchTask {
   int32_t subject;
@@ -177,6 +196,11 @@ cudaError_t launch_volume_prep(const int32_t* roi, const uint16_t* lab, int64_t 
 int64_t plane_words(int32_t dx, int32_t dy, int32_t dz);
 // Near grid from the bit planes written by launch_volume_prep.
 cudaError_t launch_near(const VolView& v, const uint32_t* planes, uint32_t* near, cudaStream_t s);
+// Both for every subject of a batch, one launch each; prep_table fills the
+// table's block counts (the bricks must be zero beforehand).
+void prep_table_blocks(PrepTable& tbl);
+cudaError_t launch_volume_prep_batch(const PrepTable& tbl, cudaStream_t s);
+cudaError_t launch_near_batch(const PrepTable& tbl, cudaStream_t s);
 
 // K2: prefilter + compaction (+ validation and voxel-step count).
 // ctas_per_sm: 2 or 3 (the register budget the kernel is compiled for).

@@ -37,18 +37,14 @@ __global__ void __launch_bounds__(256) volume_max_kernel(const int32_t* __restri
 // bounded only by the voxel count.
 constexpr int kPrepRows = 8;
 
-__global__ void __launch_bounds__(32 * kPrepRows) volume_prep_kernel(const int32_t* __restrict__ roi,
-                                                                     const uint16_t* __restrict__ lab, VolView v,
-                                                                     uint32_t* __restrict__ code,
-                                                                     uint16_t* __restrict__ lab_out,
-                                                                     uint32_t* __restrict__ bricks,
-                                                                     uint32_t* __restrict__ planes, DevState* st) {
+// The voxels of x block xb and 8-row group yb of plane z.
+__device__ __forceinline__ void prep_block(const int32_t* __restrict__ roi, const uint16_t* __restrict__ lab,
+                                           const VolView& v, uint32_t* __restrict__ code,
+                                           uint16_t* __restrict__ lab_out, uint32_t* __restrict__ bricks,
+                                           uint32_t* __restrict__ planes, DevState* st, int32_t xb, int32_t yb,
+                                           int32_t z) {
   const int32_t lane = (int32_t)threadIdx.x;
-  const int64_t g = (int64_t)blockIdx.z * gridDim.y + blockIdx.y;  // (row group, plane) pair
-  const int32_t ryb = (v.dy + kPrepRows - 1) / kPrepRows;
-  if (g >= (int64_t)ryb * v.dz) return;  // whole blocks
-  const int32_t z = (int32_t)(g / ryb);
-  const int32_t x = blockIdx.x * 32 + lane, y = (int32_t)(g - (int64_t)z * ryb) * kPrepRows + threadIdx.y;
+  const int32_t x = xb * 32 + lane, y = yb * kPrepRows + threadIdx.y;
   if (y >= v.dy) return;  // whole warps: y is the same for the warp's 32 lanes
   const bool in = x < v.dx;
   const int32_t i = x + v.dx * (y + v.dy * z);
@@ -66,12 +62,12 @@ __global__ void __launch_bounds__(32 * kPrepRows) volume_prep_kernel(const int32
   }
   // brick bits: lanes of the warp's first brick word, then of its second
   const uint32_t bits = (r >= 0 ? 1u : 0u) | (l > 0 ? 2u : 0u);
-  const int32_t b = ((in ? x : blockIdx.x * 32) >> kBrickLog2) + v.bx * ((y >> kBrickLog2) + v.by * (z >> kBrickLog2));
+  const int32_t b = ((in ? x : xb * 32) >> kBrickLog2) + v.bx * ((y >> kBrickLog2) + v.by * (z >> kBrickLog2));
   const int32_t wi = b >> 4;
   const uint32_t val = bits << ((b & 15) * 2);
   // the in-range lanes are a prefix of the warp and their words do not
   // decrease: lane 0 holds the first word, the last in-range lane the second
-  const int32_t last = min(31, v.dx - 1 - (int32_t)blockIdx.x * 32);
+  const int32_t last = min(31, v.dx - 1 - xb * 32);
   const int32_t wA = __shfl_sync(kFull, wi, 0), wB = __shfl_sync(kFull, wi, last);
   const uint32_t oA = __reduce_or_sync(kFull, wi == wA ? val : 0u);
   const uint32_t oB = __reduce_or_sync(kFull, wi != wA ? val : 0u);
@@ -83,9 +79,51 @@ __global__ void __launch_bounds__(32 * kPrepRows) volume_prep_kernel(const int32
     const int32_t wb = (v.dx + 31) >> 5;
     const int64_t row = (int64_t)y + (int64_t)v.dy * z;
     const int64_t rows = (int64_t)v.dy * v.dz;
-    planes[row * wb + blockIdx.x] = mr;
-    planes[(rows + row) * wb + blockIdx.x] = mt;
+    planes[row * wb + xb] = mr;
+    planes[(rows + row) * wb + xb] = mt;
   }
+}
+
+__device__ __forceinline__ int32_t row_groups(const VolView& v) { return (v.dy + kPrepRows - 1) / kPrepRows; }
+
+__global__ void __launch_bounds__(32 * kPrepRows) volume_prep_kernel(const int32_t* __restrict__ roi,
+                                                                     const uint16_t* __restrict__ lab, VolView v,
+                                                                     uint32_t* __restrict__ code,
+                                                                     uint16_t* __restrict__ lab_out,
+                                                                     uint32_t* __restrict__ bricks,
+                                                                     uint32_t* __restrict__ planes, DevState* st) {
+  const int64_t g = (int64_t)blockIdx.z * gridDim.y + blockIdx.y;  // (row group, plane) pair
+  const int32_t ryb = row_groups(v);
+  if (g >= (int64_t)ryb * v.dz) return;  // whole blocks
+  const int32_t z = (int32_t)(g / ryb);
+  prep_block(roi, lab, v, code, lab_out, bricks, planes, st, (int32_t)blockIdx.x, (int32_t)(g - (int64_t)z * ryb), z);
+}
+
+// The subject of batch block b: the last one whose first block is <= b.
+template <bool kNear>
+__device__ __forceinline__ int32_t subject_of(const PrepTable& tbl, int64_t b) {
+  int32_t lo = 0, hi = tbl.n - 1;
+  while (lo < hi) {
+    const int32_t mid = (lo + hi + 1) >> 1;
+    if ((kNear ? tbl.s[mid].near_blk0 : tbl.s[mid].prep_blk0) <= b) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Every subject of a batch in one launch: block b of subject i's
+// ceil(Dx/32) * ceil(Dy/8) * Dz blocks, x blocks fastest.
+__global__ void __launch_bounds__(32 * kPrepRows) volume_prep_batch_kernel(const __grid_constant__ PrepTable tbl) {
+  const int64_t b = blockIdx.x;
+  const PrepSubject& S = tbl.s[subject_of<false>(tbl, b)];
+  const VolView& v = S.v;
+  const int64_t local = b - S.prep_blk0;
+  const int32_t nxb = (v.dx + 31) / 32, ryb = row_groups(v);
+  const int64_t g = local / nxb;
+  const int32_t z = (int32_t)(g / ryb);
+  prep_block(S.roi, S.lab, v, const_cast<uint32_t*>(v.code), const_cast<uint16_t*>(v.lab),
+             const_cast<uint32_t*>(v.bricks), S.planes, S.st, (int32_t)(local - g * nxb),
+             (int32_t)(g - (int64_t)z * ryb), z);
 }
 
 // ---------------------------------------------------------------- near grid
@@ -99,10 +137,9 @@ __device__ __forceinline__ uint32_t plane_word(const uint32_t* __restrict__ rowp
   return (w >= 0 && w < wb) ? __ldg(rowp + w) : 0u;
 }
 
-// One thread per near word, a flat grid over the nwx * nny * nnz words.
-__global__ void __launch_bounds__(256) near_pack_kernel(const uint32_t* __restrict__ planes, VolView v,
-                                                        uint32_t* __restrict__ near) {
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+// Near word idx of volume v.
+__device__ __forceinline__ void near_word(const uint32_t* __restrict__ planes, const VolView& v,
+                                          uint32_t* __restrict__ near, int64_t idx) {
   if (idx >= (int64_t)v.nwx * v.nny * v.nnz) return;
   const int32_t wx = (int32_t)(idx % v.nwx);
   const int64_t t = idx / v.nwx;
@@ -147,6 +184,20 @@ __global__ void __launch_bounds__(256) near_pack_kernel(const uint32_t* __restri
   near[idx] = word;
 }
 
+// One thread per near word, a flat grid over the nwx * nny * nnz words.
+__global__ void __launch_bounds__(256) near_pack_kernel(const uint32_t* __restrict__ planes, VolView v,
+                                                        uint32_t* __restrict__ near) {
+  near_word(planes, v, near, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+// Every subject of a batch in one launch: subject i's words in blocks of 256
+// from its first block on.
+__global__ void __launch_bounds__(256) near_pack_batch_kernel(const __grid_constant__ PrepTable tbl) {
+  const int64_t b = blockIdx.x;
+  const PrepSubject& S = tbl.s[subject_of<true>(tbl, b)];
+  near_word(S.planes, S.v, const_cast<uint32_t*>(S.v.near), (b - S.near_blk0) * 256 + threadIdx.x);
+}
+
 static int grid_for(int64_t n) {
   const int64_t b = (n + 255) / 256;
   return (int)(b < 1 ? 1 : (b > 65535 ? 65535 : b));
@@ -177,6 +228,31 @@ int64_t plane_words(int32_t dx, int32_t dy, int32_t dz) {
 cudaError_t launch_near(const VolView& v, const uint32_t* planes, uint32_t* near, cudaStream_t s) {
   const int64_t words = (int64_t)v.nwx * v.nny * v.nnz;
   near_pack_kernel<<<(unsigned)((words + 255) / 256), 256, 0, s>>>(planes, v, near);
+  return cudaGetLastError();
+}
+
+void prep_table_blocks(PrepTable& tbl) {
+  int64_t pb = 0, nb = 0;
+  for (int32_t i = 0; i < tbl.n; ++i) {
+    PrepSubject& S = tbl.s[i];
+    S.prep_blk0 = pb;
+    S.near_blk0 = nb;
+    pb += (int64_t)((S.v.dx + 31) / 32) * ((S.v.dy + kPrepRows - 1) / kPrepRows) * S.v.dz;
+    nb += ((int64_t)S.v.nwx * S.v.nny * S.v.nnz + 255) / 256;
+  }
+  tbl.prep_blocks = pb;
+  tbl.near_blocks = nb;
+}
+
+cudaError_t launch_volume_prep_batch(const PrepTable& tbl, cudaStream_t s) {
+  if (tbl.n <= 0 || tbl.prep_blocks <= 0) return cudaSuccess;
+  volume_prep_batch_kernel<<<(unsigned)tbl.prep_blocks, dim3(32, kPrepRows), 0, s>>>(tbl);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_near_batch(const PrepTable& tbl, cudaStream_t s) {
+  if (tbl.n <= 0 || tbl.near_blocks <= 0) return cudaSuccess;
+  near_pack_batch_kernel<<<(unsigned)tbl.near_blocks, 256, 0, s>>>(tbl);
   return cudaGetLastError();
 }
 

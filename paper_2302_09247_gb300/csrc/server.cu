@@ -6,6 +6,7 @@
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
+#include <cstdlib>
 #include <cstring>
 #include <deque>
 #include <map>
@@ -111,11 +112,42 @@ struct fastcod_server {
   int tasks_turn = 0;
   DevState* state_pool = nullptr;
   std::vector<DevState*> free_states;
+  // host-side failure injection (FASTCOD_FAULT, read at creation): the k-th
+  // per-request device allocation, the k-th chunk copy, the k-th submitted
+  // request (0: none)
+  int64_t fault_alloc = 0, fault_h2d = 0, fault_cancel = 0;
+  int64_t n_alloc = 0, n_h2d = 0, n_submit = 0;  // worker / submit counters
 };
 
 namespace {
 
 double now_s(fastcod_server* S) { return std::chrono::duration<double>(Clock::now() - S->t0).count(); }
+
+// FASTCOD_FAULT = comma-separated "alloc:k", "h2d:k", "cancel:k" (k >= 1).
+void parse_faults(fastcod_server* S) {
+  const char* env = getenv("FASTCOD_FAULT");
+  if (!env) return;
+  std::string s(env);
+  size_t at = 0;
+  while (at < s.size()) {
+    size_t end = s.find(',', at);
+    if (end == std::string::npos) end = s.size();
+    const std::string item = s.substr(at, end - at);
+    const size_t colon = item.find(':');
+    if (colon != std::string::npos) {
+      const long long k = atoll(item.c_str() + colon + 1);
+      const std::string what = item.substr(0, colon);
+      if (k > 0 && what == "alloc") S->fault_alloc = k;
+      if (k > 0 && what == "h2d") S->fault_h2d = k;
+      if (k > 0 && what == "cancel") S->fault_cancel = k;
+    }
+    at = end + 1;
+  }
+}
+
+// Worker: whether this per-request allocation / chunk copy is the one to fail.
+bool inject_alloc(fastcod_server* S) { return S->fault_alloc && ++S->n_alloc == S->fault_alloc; }
+bool inject_h2d(fastcod_server* S) { return S->fault_h2d && ++S->n_h2d == S->fault_h2d; }
 
 int64_t near_words(const int32_t d[3], int near_log2) {
   fc::VolView v{};
@@ -145,6 +177,7 @@ cudaError_t setup_request(fastcod_server* S, Request* r, uint32_t** tmp, size_t*
   const size_t nm = (size_t)h.n_roi * (size_t)h.n_targets;
   size_t bytes = resident_bytes(h, S->near_log2);
   const size_t in_bytes = (r->host_roi ? a256(nvox * 4) : 0) + (r->host_lab ? a256(nvox * 2) : 0);
+  if (inject_alloc(S)) return cudaErrorMemoryAllocation;
   cudaError_t e = cudaMallocAsync((void**)&r->mem, bytes + in_bytes, S->compute);
   if (e != cudaSuccess) return e;
   char* p = r->mem;
@@ -292,10 +325,11 @@ bool iterate(fastcod_server* S, uint32_t** tmp, size_t* tmp_cap) {
   }
   bool did = !setups.empty() || !work.empty() || !finishing.empty();
   for (Request* r : setups) {
-    if (setup_request(S, r, tmp, tmp_cap) != cudaSuccess) {
+    const cudaError_t e = setup_request(S, r, tmp, tmp_cap);
+    if (e != cudaSuccess) {
       (void)cudaGetLastError();
       std::lock_guard<std::mutex> lk(S->mu);
-      r->status = FASTCOD_ECUDA;
+      r->status = e == cudaErrorMemoryAllocation ? FASTCOD_ENOMEM : FASTCOD_ECUDA;
     }
     r->state = RState::Active;
   }
@@ -311,7 +345,9 @@ bool iterate(fastcod_server* S, uint32_t** tmp, size_t* tmp_cap) {
     if (r->status != FASTCOD_OK) continue;
     if (k.host_xyz || k.host_off) {
       const size_t xb = a256((size_t)k.nv * 12 + 16);
-      cudaError_t e = cudaMallocAsync(&sg.buf, xb + (size_t)(k.ns + 1) * 8, S->copy);
+      cudaError_t e = inject_alloc(S) ? cudaErrorMemoryAllocation
+                                      : cudaMallocAsync(&sg.buf, xb + (size_t)(k.ns + 1) * 8, S->copy);
+      if (e == cudaSuccess && inject_h2d(S)) e = cudaErrorInvalidValue;  // the copy "fails" before it is issued
       if (e == cudaSuccess && k.host_xyz && k.nv) {
         e = cudaMemcpyAsync(sg.buf, k.xyz, (size_t)k.nv * 12, cudaMemcpyDefault, S->copy);
         sg.t.xyz = static_cast<int32_t*>(sg.buf);
@@ -323,7 +359,8 @@ bool iterate(fastcod_server* S, uint32_t** tmp, size_t* tmp_cap) {
       }
       if (e != cudaSuccess) {
         (void)cudaGetLastError();
-        r->status = FASTCOD_ECUDA;
+        r->status = e == cudaErrorMemoryAllocation ? FASTCOD_ENOMEM : FASTCOD_ECUDA;
+        if (sg.buf) cudaFreeAsync(sg.buf, S->copy);
         continue;
       }
     }
@@ -495,6 +532,7 @@ FASTCOD_API int fastcod_server_create(fastcod_ctx* c, int32_t max_slots, int64_t
   S->tma = c->staging_tma;
   S->near_log2 = c->near_log2;
   S->t0 = Clock::now();
+  parse_faults(S);
   size_t free_b = 0, total_b = 0;
   cudaMemGetInfo(&free_b, &total_b);
   S->budget = hbm_budget_bytes ? hbm_budget_bytes : (int64_t)(free_b / 10 * 9);
@@ -548,6 +586,7 @@ FASTCOD_API int fastcod_server_submit(fastcod_server* S, const fastcod_subject* 
   if (S->stop) return sfail(S, FASTCOD_ESTATE, "server is stopping");
   r->id = S->next_id++;
   r->t_submit = now_s(S);
+  if (S->fault_cancel && ++S->n_submit == S->fault_cancel) r->cancel = true;  // injected cancellation
   *id = r->id;
   S->waiting.push_back(r->id);
   S->reqs[r->id] = std::move(r);

@@ -151,3 +151,48 @@ def test_cancel_and_errors_are_isolated(fc, subjects):
     finally:
         fc.fastcod_server_destroy(srv)
         ctx.close()
+
+
+def _faulty_server(fc, ctx, spec, monkeypatch):
+    monkeypatch.setenv("FASTCOD_FAULT", spec)
+    srv = fc.fastcod_server_create(ctx.ctx, 4, 0)
+    monkeypatch.delenv("FASTCOD_FAULT")
+    return srv
+
+
+@pytest.mark.parametrize("spec,where,status", [("alloc:2", "device", "FASTCOD_ENOMEM"),
+                                               ("h2d:2", "host", "FASTCOD_ECUDA"),
+                                               ("cancel:2", "host", "FASTCOD_ECANCELED"),
+                                               ("alloc:3", "host", "FASTCOD_ENOMEM")])
+def test_injected_failure_hits_one_request(fc, subjects, monkeypatch, spec, where, status):
+    # host-side injection (no GPU fault): exactly one request of four reports
+    # the failure; the other three complete with the oracle's result
+    vA, tA = subjects["A"]
+    want = _oracle(vA, tA)
+    ctx = fc.Context(0)
+    srv = _faulty_server(fc, ctx, spec, monkeypatch)
+    try:
+        reqs = []
+        for _ in range(4):
+            r = Req(fc, srv, vA, where)
+            for i, (x, o) in enumerate(_chunks(tA, 2)):
+                r.push(fc, srv, x, o, last=(i == 1), where=where)
+            reqs.append(r)
+        got = [fc.fastcod_server_wait(srv, r.id, 120.0) for r in reqs]
+        assert sorted(got).count(getattr(fc, status)) == 1, got
+        assert got.count(fc.FASTCOD_OK) == 3, got
+        if spec.startswith(("alloc:2", "cancel:2")):
+            assert got[1] == getattr(fc, status)  # admission and submission follow arrival order
+        for r, g in zip(reqs, got):
+            if g == fc.FASTCOD_OK:
+                np.testing.assert_array_equal(r.C, want[0])
+                np.testing.assert_array_equal(r.Ce, want[1])
+        # the server keeps serving after the failure
+        r = Req(fc, srv, vA, where)
+        for i, (x, o) in enumerate(_chunks(tA, 2)):
+            r.push(fc, srv, x, o, last=(i == 1), where=where)
+        assert fc.fastcod_server_wait(srv, r.id, 120.0) == fc.FASTCOD_OK
+        np.testing.assert_array_equal(r.C, want[0])
+    finally:
+        fc.fastcod_server_destroy(srv)
+        ctx.close()
