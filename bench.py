@@ -43,14 +43,15 @@ if ROOT not in sys.path:
 METRIC = "DDA voxel-steps/s & subjects/s for C, bit-exact; batched vs plain; p50/p99 latency"
 
 # DRAM traffic (ncu dram__bytes_read.sum + dram__bytes_write.sum) of one
-# prefilter launch on the HCP-shaped subject, valid only while the prefilter's
-# sources are the ones it was measured on; other workloads scale it by their
-# vertex count (the stream is read once, so traffic grows with the vertices).
+# prefilter launch on the high-res subject's first 1,000,000 streamlines,
+# valid only while the prefilter's sources are the ones it was measured on;
+# workloads scale it by their vertex count (the stream is read once, so
+# traffic grows with the vertices).
 PREFILTER_SOURCES = ("paper_2302_09247_gb300/csrc/k_prefilter.cu", "paper_2302_09247_gb300/csrc/fc_tma.cuh",
                      "paper_2302_09247_gb300/csrc/fc_internal.cuh", "paper_2302_09247_gb300/csrc/fc_device.cuh")
-PREFILTER_TRAFFIC = {"sha256": "90368f0a61e93a59310f9fbce4ae7b2e25cdb03afa67b474c7dd9d10fc471ef7",
-                     "bytes": 2491472384, "vertices": 205420297,
-                     "summary": "profiles/prefilter_kernel_hcp145x174x145.md"}
+PREFILTER_TRAFFIC = {"sha256": "f0bcad148be77fcf2546ec01fc985126305327640893ff9b40948abd4151306b",
+                     "bytes": 1911508992, "vertices": 157754709, "workload": "high-res",
+                     "summary": "profiles/prefilter_kernel_highres260x311x260.md"}
 
 
 def prefilter_traffic(n_vertices: int):
@@ -66,7 +67,8 @@ def prefilter_traffic(n_vertices: int):
     if n_vertices == ref["vertices"]:
         return ref["bytes"], f"ncu capture of this workload ({ref['summary']})"
     return int(round(ref["bytes"] * n_vertices / ref["vertices"])), \
-        f"ncu capture of the HCP-shaped subject ({ref['summary']}) scaled by vertex count"
+        f"ncu capture of the {ref['workload']} subject's first {ref['vertices']:,} vertices " \
+        f"({ref['summary']}), scaled by vertex count"
 UNIT = "voxel-steps/s"
 
 
@@ -229,6 +231,11 @@ def run_reference(args):
     }
     print(json.dumps(line), flush=True)
     return 0
+
+
+def _digest(a) -> str:
+    import hashlib
+    return hashlib.sha256(np.ascontiguousarray(a, dtype="<i4").tobytes()).hexdigest()[:16]
 
 
 def _config(cfg, vols, tr):
@@ -917,6 +924,8 @@ def main():
             "overflow_per_step": st["overflow"], "pairs_per_step": st["pairs"],
             "walked_steps_per_step": walked_steps,
             "C_sum": int(C_first.sum()),
+            # fingerprints of the result (int32 little-endian bytes, row-major)
+            "C_sha256": _digest(C_first), "C_end_sha256": _digest(Ce_first),
             "roofline": roofline,
             "e2e": e2e,
             "cpu_baseline": cpu,

@@ -149,6 +149,7 @@ int world_to_fixed_into(fastcod_ctx* c, const float* xyz_mm, int64_t nv, const f
 extern "C" {
 
 FASTCOD_API int fastcod_parcellate(fastcod_ctx* c, int32_t which, int32_t* label_out, float* fractions_out) {
+  fcapi::Range nvtx_range("fastcod_parcellate");
   if (int rc = begin(c)) return rc;
   if (!c->has_vol) return fail(c, FASTCOD_ESTATE, "no volumes installed");
   if (which != 0 && which != 1) return fail(c, FASTCOD_EINVAL, "which must be 0 (C) or 1 (C_end)");
@@ -174,6 +175,7 @@ FASTCOD_API int fastcod_parcellate(fastcod_ctx* c, int32_t which, int32_t* label
 
 FASTCOD_API int fastcod_parcellate_matrix(fastcod_ctx* c, const int32_t* C, int32_t N, int32_t M,
                                           int32_t* label_out, float* fractions_out) {
+  fcapi::Range nvtx_range("fastcod_parcellate_matrix");
   if (int rc = begin(c)) return rc;
   if (N < 0 || M < 1 || M > 65535) return fail(c, FASTCOD_EINVAL, "N must be >= 0 and M in [1, 65535]");
   if (N == 0) return FASTCOD_OK;
@@ -204,6 +206,7 @@ FASTCOD_API int fastcod_parcellate_matrix(fastcod_ctx* c, const int32_t* C, int3
 
 FASTCOD_API int fastcod_world_to_fixed(fastcod_ctx* c, const float* xyz_mm, int64_t n_vertices,
                                        const float affine[12], int32_t* xyz_out) {
+  fcapi::Range nvtx_range("fastcod_world_to_fixed");
   if (int rc = begin(c)) return rc;
   if (n_vertices < 0 || n_vertices > 0x7fffffffLL) return fail(c, FASTCOD_EINVAL, "vertex count out of range");
   if (n_vertices == 0) return FASTCOD_OK;
@@ -218,6 +221,7 @@ FASTCOD_API int fastcod_world_to_fixed(fastcod_ctx* c, const float* xyz_mm, int6
 
 FASTCOD_API int fastcod_add_streamlines_mm(fastcod_ctx* c, const float* xyz_mm, int64_t n_vertices,
                                            const int64_t* offsets, int64_t n_streamlines, const float affine[12]) {
+  fcapi::Range nvtx_range("fastcod_add_streamlines_mm");
   if (int rc = begin(c)) return rc;
   if (!c->has_vol) return fail(c, FASTCOD_ESTATE, "fastcod_set_volumes must come first");
   if (int rc = check_streamlines(c, xyz_mm, n_vertices, offsets, n_streamlines)) return rc;
@@ -232,6 +236,7 @@ FASTCOD_API int fastcod_add_streamlines_mm(fastcod_ctx* c, const float* xyz_mm, 
 FASTCOD_API int fastcod_upsample_factor(fastcod_ctx* c, const int32_t* xyz, int64_t n_vertices,
                                         const int64_t* offsets, int64_t n_streamlines, int32_t spacing,
                                         int32_t* factor_out) {
+  fcapi::Range nvtx_range("fastcod_upsample_factor");
   if (int rc = begin(c)) return rc;
   if (int rc = check_streamlines(c, xyz, n_vertices, offsets, n_streamlines)) return rc;
   if (spacing < 1 || !factor_out) return fail(c, FASTCOD_EINVAL, "spacing must be >= 1 and factor_out set");
@@ -268,6 +273,7 @@ FASTCOD_API int fastcod_upsample_factor(fastcod_ctx* c, const int32_t* xyz, int6
 FASTCOD_API int fastcod_upsample(fastcod_ctx* c, const int32_t* xyz, int64_t n_vertices, const int64_t* offsets,
                                  int64_t n_streamlines, int32_t factor, int32_t* xyz_out, int64_t n_vertices_out,
                                  int64_t* offsets_out) {
+  fcapi::Range nvtx_range("fastcod_upsample");
   if (int rc = begin(c)) return rc;
   if (int rc = check_streamlines(c, xyz, n_vertices, offsets, n_streamlines)) return rc;
   if (factor < 1 || factor > (1 << 20)) return fail(c, FASTCOD_EINVAL, "factor must be in [1, 2^20]");
@@ -313,6 +319,7 @@ FASTCOD_API int fastcod_upsample(fastcod_ctx* c, const int32_t* xyz, int64_t n_v
 
 FASTCOD_API int fastcod_rescale(fastcod_ctx* c, const int32_t* xyz, int64_t n_vertices, const int32_t num[3],
                                 const int32_t den[3], const int64_t add[3], int32_t* xyz_out) {
+  fcapi::Range nvtx_range("fastcod_rescale");
   if (int rc = begin(c)) return rc;
   if (n_vertices < 0 || n_vertices > 0x7fffffffLL) return fail(c, FASTCOD_EINVAL, "vertex count out of range");
   if (!num || !den || !add) return fail(c, FASTCOD_EINVAL, "num, den and add are required");

@@ -428,6 +428,7 @@ void batch_free(fastcod_ctx* c) {
 extern "C" {
 
 FASTCOD_API int fastcod_batch_run(fastcod_ctx* c, const fastcod_subject* subs, int32_t n) {
+  fcapi::Range nvtx_range("fastcod_batch_run");
   if (!c) return FASTCOD_EINVAL;
   c->err.clear();
   if (!subs || n < 1 || n > fc::kMaxBatch) return fail(c, FASTCOD_EINVAL, "n_subjects must be in 1..%d", fc::kMaxBatch);

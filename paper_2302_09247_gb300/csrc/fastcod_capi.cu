@@ -293,6 +293,7 @@ FASTCOD_API int fastcod_set_stream(fastcod_ctx* c, void* s) {
 
 FASTCOD_API int fastcod_set_volumes(fastcod_ctx* c, const int32_t* roi, const uint16_t* lab, int32_t dx,
                                     int32_t dy, int32_t dz, int32_t n_roi, int32_t n_targets) {
+  fcapi::Range nvtx_range("fastcod_set_volumes");
   if (!c) return FASTCOD_EINVAL;
   c->err.clear();
   if (dx <= 0 || dy <= 0 || dz <= 0) return fail(c, FASTCOD_EINVAL, "grid dims must be > 0");
@@ -381,6 +382,7 @@ FASTCOD_API int fastcod_set_volumes(fastcod_ctx* c, const int32_t* roi, const ui
 
 FASTCOD_API int fastcod_add_streamlines(fastcod_ctx* c, const int32_t* xyz, int64_t nv, const int64_t* offsets,
                                         int64_t ns) {
+  fcapi::Range nvtx_range("fastcod_add_streamlines");
   if (!c) return FASTCOD_EINVAL;
   c->err.clear();
   if (!c->has_vol) return fail(c, FASTCOD_ESTATE, "fastcod_set_volumes must come first");
@@ -464,6 +466,7 @@ FASTCOD_API int fastcod_add_streamlines(fastcod_ctx* c, const int32_t* xyz, int6
 }
 
 FASTCOD_API int fastcod_connectivity(fastcod_ctx* c, int32_t* C_out) {
+  fcapi::Range nvtx_range("fastcod_connectivity");
   if (!c) return FASTCOD_EINVAL;
   c->err.clear();
   CU(cudaSetDevice(c->device));
@@ -471,6 +474,7 @@ FASTCOD_API int fastcod_connectivity(fastcod_ctx* c, int32_t* C_out) {
 }
 
 FASTCOD_API int fastcod_endpoint_connectivity(fastcod_ctx* c, int32_t* Cend_out) {
+  fcapi::Range nvtx_range("fastcod_endpoint_connectivity");
   if (!c) return FASTCOD_EINVAL;
   c->err.clear();
   CU(cudaSetDevice(c->device));
@@ -478,6 +482,7 @@ FASTCOD_API int fastcod_endpoint_connectivity(fastcod_ctx* c, int32_t* Cend_out)
 }
 
 FASTCOD_API int fastcod_reset(fastcod_ctx* c) {
+  fcapi::Range nvtx_range("fastcod_reset");
   if (!c) return FASTCOD_EINVAL;
   c->err.clear();
   if (!c->has_vol) return fail(c, FASTCOD_ESTATE, "no volumes installed");
@@ -521,6 +526,7 @@ FASTCOD_API int fastcod_get_profile(fastcod_ctx* c, fastcod_profile* out) {
 }
 
 FASTCOD_API int fastcod_sync(fastcod_ctx* c) {
+  fcapi::Range nvtx_range("fastcod_sync");
   if (!c) return FASTCOD_EINVAL;
   c->err.clear();
   CU(cudaSetDevice(c->device));

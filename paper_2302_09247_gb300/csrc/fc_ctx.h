@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <string>
 #include <vector>
@@ -80,6 +81,14 @@ struct fastcod_ctx {
 };
 
 namespace fcapi {
+// An NVTX range around a call of the C ABI (shown by Nsight tools; a no-op
+// when no tool is attached).
+struct Range {
+  explicit Range(const char* name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+  Range(const Range&) = delete;
+  Range& operator=(const Range&) = delete;
+};
 // Record a message on ctx (if any) and return code.
 int fail(fastcod_ctx* c, int code, const char* fmt, ...);
 // 0 = host memory, 1 = device memory of dev, -1 = device memory elsewhere.

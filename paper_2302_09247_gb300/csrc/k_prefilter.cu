@@ -555,7 +555,7 @@ struct Ring {
   TmaSmem* sm;
   uint32_t slot, phase;   // next slot to consume, and the parity it completes
   uint64_t policy;
-  int64_t withhold;       // test hook: this piece is never copied (-1: none)
+  int64_t withhold;       // test hook (kHook builds only): this piece is never copied
 
   __device__ __forceinline__ void init(TmaSmem* s, int64_t withhold_piece = -1) {
     sm = s;
@@ -573,8 +573,9 @@ struct Ring {
   // lane 0 only: copy piece hq of t into slot k.  A whole piece is one bulk
   // copy; at the end of the array the part that is not a multiple of 16 bytes
   // is copied with plain loads and the rest of the slot zero-filled.
+  template <bool kHook>
   __device__ __forceinline__ void issue(const Tract& t, int64_t hq, uint32_t k) {
-    if (hq == withhold) return;  // neither copy nor arrival: the wait for this slot runs out
+    if (kHook && hq == withhold) return;  // neither copy nor arrival: the wait for this slot runs out
     const int64_t v0 = hq << kPieceLog2;
     int32_t* dst = sm->ring[k];
     const int32_t* src = t.xyz + 3 * v0;
@@ -613,6 +614,7 @@ struct Ring {
 // Takes the next piece from the ring into p and refills its slot with piece
 // `issued` when that is still part of the range (hq_end exclusive).  False
 // when the wait timed out.
+template <bool kHook>
 __device__ __forceinline__ bool ring_take(Ring& r, const Tract& t, int64_t& issued, int64_t hq_end,
                                           int32_t (&p)[kLaneWords]) {
   if (!r.wait()) return false;
@@ -630,7 +632,7 @@ __device__ __forceinline__ bool ring_take(Ring& r, const Tract& t, int64_t& issu
   if (issued < hq_end) {
     if (lane_id() == 0) {
       fence_proxy_async_smem();
-      r.issue(t, issued, r.slot);
+      r.issue<kHook>(t, issued, r.slot);
     }
     ++issued;
   }
@@ -640,7 +642,7 @@ __device__ __forceinline__ bool ring_take(Ring& r, const Tract& t, int64_t& issu
 
 // Window loop of the TMA loader over the scan's vertex range.  Returns false
 // when a wait timed out (the error is set and the ring may not be reused).
-template <bool kSmem>
+template <bool kSmem, bool kHook = false>
 __device__ __forceinline__ bool scan_range_tma(Scan& sc, const VolView& v, const uint32_t* nw, const Tract& t,
                                                bool prefilter, WarpShared& ws, Ring& r, const SurvList& surv,
                                                DevState* gst) {
@@ -653,7 +655,7 @@ __device__ __forceinline__ bool scan_range_tma(Scan& sc, const VolView& v, const
   if (lane_id() == 0) {
     uint32_t k = r.slot;
     for (int64_t hq = hq_lo; hq < issued; ++hq) {
-      r.issue(t, hq, k);
+      r.issue<kHook>(t, hq, k);
       k = (k + 1 == (uint32_t)kStages) ? 0u : k + 1;
     }
   }
@@ -669,7 +671,7 @@ __device__ __forceinline__ bool scan_range_tma(Scan& sc, const VolView& v, const
 #pragma unroll 1
     for (int h = h_lo; h < h_hi; ++h) {
       int32_t p[kLaneWords];
-      if (!ring_take(r, t, issued, hq_end, p)) {
+      if (!ring_take<kHook>(r, t, issued, hq_end, p)) {
         ok = false;
         break;
       }
@@ -708,7 +710,7 @@ __device__ __forceinline__ void stage_near(const VolView& v, uint32_t* s_near) {
 // warps' rings at a 128-byte aligned offset.
 __host__ __device__ constexpr size_t ring_offset(size_t near_bytes) { return (near_bytes + 127) & ~(size_t)127; }
 
-template <int kMinBlocks, bool kTma, bool kSmem>
+template <int kMinBlocks, bool kTma, bool kSmem, bool kHook>
 __global__ void __launch_bounds__(kWarps * 32, kMinBlocks) prefilter_kernel(Tract t, VolView v, int prefilter,
                                                                            SurvList surv, DevState* st,
                                                                            int64_t withhold) {
@@ -729,7 +731,7 @@ __global__ void __launch_bounds__(kWarps * 32, kMinBlocks) prefilter_kernel(Trac
     const size_t off = ring_offset(kSmem ? (size_t)near_words(v) * 4 : 0);
     Ring r;
     r.init(reinterpret_cast<TmaSmem*>(smem_raw + off) + (threadIdx.x >> 5), withhold);
-    scan_range_tma<kSmem>(sc, v, nw, t, prefilter != 0, ws, r, surv, st);
+    scan_range_tma<kSmem, kHook>(sc, v, nw, t, prefilter != 0, ws, r, surv, st);
   } else {
     scan_range_direct<kSmem>(sc, v, nw, t, prefilter != 0, ws, surv, st);
   }
@@ -782,7 +784,10 @@ cudaError_t resident_grid(K kernel, size_t smem, int num_sms, int* grid) {
 template <int kMinBlocks, bool kTma, bool kSmem>
 cudaError_t launch_plain(const Tract& t, const VolView& v, bool prefilter, const SurvList& survivors, DevState* st,
                          int num_sms, cudaStream_t s, int64_t withhold) {
-  auto k = prefilter_kernel<kMinBlocks, kTma, kSmem>;
+  // the test hook has builds of its own, so that the default one carries no
+  // trace of it
+  auto k = (kTma && withhold >= 0) ? prefilter_kernel<kMinBlocks, kTma, kSmem, kTma>
+                                   : prefilter_kernel<kMinBlocks, kTma, kSmem, false>;
   const size_t near_bytes = kSmem ? (size_t)near_words(v) * 4 : 0;
   const size_t bytes = kTma ? ring_offset(near_bytes) + kRingBytes : near_bytes;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);

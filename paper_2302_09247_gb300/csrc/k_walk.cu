@@ -28,12 +28,16 @@ constexpr int kWalkWarps = 8;
 constexpr int kWalkMinBlocks = 4;
 constexpr int kHV = 512, kLimV = 256;  // V_s table slots / size limit
 constexpr int kHT = 128, kLimT = 64;   // T_s table slots / size limit
+constexpr int kLin = 256;              // visited voxels awaiting their code gathers
 
+// Every insertion round adds at most 32 keys to a list, and the limits are
+// checked after every round: the lists hold limit + 32 keys.
 struct WalkWarpSmem {
   int32_t tabV[kHV];
   int32_t listV[kLimV + 32];
   int32_t tabT[kHT];
   int32_t listT[kLimT + 32];
+  int32_t lin[kLin];
 };
 
 // The per-warp sets V_s and T_s live in tabV / tabT in one of two forms,
@@ -121,18 +125,49 @@ __device__ __forceinline__ void decode(const VolView& v, int32_t lin, uint32_t c
   }
 }
 
-// Voxels gathered per lane before their codes are read together.
-constexpr int kGather = 2;
+// The listed voxels' codes, decoded and inserted into the sets, 32 keys per
+// round with the size limits checked after each round.  Empties the list.
+// kWide: four rounds of loads in flight at once; otherwise one
+// round at a time (few registers: used inside the walk's loop, where long
+// segments may fill the list).
+template <typename S, bool kWide>
+__device__ __forceinline__ void flush_voxels(const VolView& v, WalkWarpSmem& sm, int& nL, bool endpoint_mode,
+                                             uint64_t keep, int& nV, int& nT, bool& fail) {
+  __syncwarp();
+  constexpr int kPer = kWide ? 4 : 1;
+  const int lane = (int)lane_id();
+  for (int r0 = 0; r0 < nL && !fail; r0 += 32 * kPer) {  // one pass when kWide
+    int32_t lin[kPer];
+    uint32_t code[kPer];
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) lin[k] = r0 + lane + 32 * k < nL ? sm.lin[r0 + lane + 32 * k] : -1;
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) code[k] = lin[k] >= 0 ? ldg_hint(v.code + lin[k], keep) : 0u;
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+      if (r0 + 32 * k < nL && !fail) {  // warp-uniform
+        int32_t row, lab;
+        decode(v, lin[k], code[k], row, lab);
+        if (endpoint_mode) lab = 0;
+        nV = S::insV(sm, nV, row, fail);
+        nT = S::insT(sm, nT, lab > 0 ? lab : -1, fail);
+        if (nV > kLimV || nT > kLimT) fail = true;
+      }
+    }
+  }
+  nL = 0;
+  __syncwarp();
+}
 
-// Walk the window's segments (one per lane, p0 -> p1 where has): every voxel
-// a segment enters (and, for the streamline's first segment, its start
-// voxel) goes into the sets.  Each round gathers up to kGather voxels per
-// lane with the integer walk, reads their codes with independent loads, then
-// inserts them; long segments take more rounds.
+// Walk the window's segments (one per lane, p0 -> p1 where has) and list
+// every in-grid voxel a segment enters (and, for the streamline's first
+// segment, its start voxel); the list is flushed into the sets when it
+// fills.  The walk itself has no memory dependence, so a window costs no
+// load latency beyond its vertices.
 template <typename P, typename S>
 __device__ __forceinline__ void walk_window(const VolView& v, WalkWarpSmem& sm, const int32_t p0[3],
                                             const int32_t p1[3], bool has, bool first, bool endpoint_mode,
-                                            uint64_t keep, int& nV, int& nT, bool& fail) {
+                                            uint64_t keep, int& nL, int& nV, int& nT, bool& fail) {
   SegWalk<P> w;
   bool pend = false;
   if (has) {
@@ -140,26 +175,14 @@ __device__ __forceinline__ void walk_window(const VolView& v, WalkWarpSmem& sm, 
     pend = first ? true : w.step();
   }
   while (__any_sync(kFull, pend)) {
-    int32_t lin[kGather];
-#pragma unroll
-    for (int i = 0; i < kGather; ++i) {
-      lin[i] = pend ? voxel_lin(v, w.cx, w.cy, w.cz) : -1;
-      if (pend) pend = w.step();
-    }
-    uint32_t code[kGather];
-#pragma unroll
-    for (int i = 0; i < kGather; ++i) code[i] = lin[i] >= 0 ? ldg_hint(v.code + lin[i], keep) : 0u;
-#pragma unroll
-    for (int i = 0; i < kGather; ++i) {
-      int32_t row, lab;
-      decode(v, lin[i], code[i], row, lab);
-      if (endpoint_mode) lab = 0;
-      nV = S::insV(sm, nV, row, fail);
-      nT = S::insT(sm, nT, lab > 0 ? lab : -1, fail);
-    }
-    if (nV > kLimV || nT > kLimT) {
-      fail = true;
-      break;
+    const int32_t lin = pend ? voxel_lin(v, w.cx, w.cy, w.cz) : -1;
+    const unsigned m = __ballot_sync(kFull, lin >= 0);
+    if (lin >= 0) sm.lin[nL + __popc(m & lanemask_lt())] = lin;
+    nL += __popc(m);
+    if (pend) pend = w.step();
+    if (nL > kLin - 32) {  // long segments only: windows start with room for 3 voxels a lane
+      flush_voxels<S, false>(v, sm, nL, endpoint_mode, keep, nV, nT, fail);
+      if (fail) break;
     }
   }
 }
@@ -203,9 +226,14 @@ __device__ __forceinline__ int walk_one(const VolView& v, const Tract& t, const 
   } else {
     // window i0 holds segments a+i0+lane -> a+i0+lane+1; the vertices of the
     // next window are loaded while this one is walked
+    int nL = 0;
     int32_t cur[3] = {0, 0, 0};
     if (a + lane < b) load_vertex(t.xyz, a + lane, cur);
     for (int64_t i0 = 0; i0 < T - 1 && !fail; i0 += 32) {
+      if (nL > kLin - 96) {  // room for three voxels a lane
+        flush_voxels<S, true>(v, sm, nL, endpoint_mode, keep, nV, nT, fail);
+        if (__any_sync(kFull, fail)) break;
+      }
       const int64_t j = a + i0 + lane;
       int32_t nxt[3] = {0, 0, 0};
       if (j + 32 < b) load_vertex(t.xyz, j + 32, nxt);
@@ -230,13 +258,15 @@ __device__ __forceinline__ int walk_one(const VolView& v, const Tract& t, const 
       const bool small = !has || (abs(p1[0] - p0[0]) < 65536 && abs(p1[1] - p0[1]) < 65536 &&
                                   abs(p1[2] - p0[2]) < 65536);
       if (__all_sync(kFull, small))
-        walk_window<uint32_t, S>(v, sm, p0, p1, has, j == a, endpoint_mode, keep, nV, nT, fail);
+        walk_window<uint32_t, S>(v, sm, p0, p1, has, j == a, endpoint_mode, keep, nL, nV, nT, fail);
       else
-        walk_window<unsigned long long, S>(v, sm, p0, p1, has, j == a, endpoint_mode, keep, nV, nT, fail);
+        walk_window<unsigned long long, S>(v, sm, p0, p1, has, j == a, endpoint_mode, keep, nL, nV, nT, fail);
       fail = __any_sync(kFull, fail);
 #pragma unroll
       for (int k = 0; k < 3; ++k) cur[k] = nxt[k];
     }
+    if (nL > 0 && !fail) flush_voxels<S, true>(v, sm, nL, endpoint_mode, keep, nV, nT, fail);
+    fail = __any_sync(kFull, fail);
   }
   if (endpoint_mode && !fail) {
     // T_s = {label of the last vertex}

@@ -267,6 +267,7 @@ void fail_request(fastcod_server* S, Request* r, int status) {
 // chunk of every active request, complete finished requests.  Returns true
 // when it did any work.
 bool iterate(fastcod_server* S, uint32_t** tmp, size_t* tmp_cap) {
+  fcapi::Range nvtx_range("fastcod_server pass");
   std::vector<Request*> setups, finishing;
   std::vector<std::pair<Request*, Chunk>> work;
   std::vector<std::pair<Request*, bool>> lasts;
