@@ -741,6 +741,8 @@ def main():
                          "forms and the DDA measured in the same line); 3: batched; 4: served")
     ap.add_argument("--no-forms", action="store_true", help="no batched / served sub-records")
     ap.add_argument("--no-dda", action="store_true", help="no DDA sub-record (prefilter off)")
+    ap.add_argument("--near-log2", type=int, default=None,
+                    help="near-grid cell of the plain line: (1 << n)^3 voxels, 0..3 (default: automatic)")
     ap.add_argument("--dda-steps", type=int, default=5, help="timed steps of the DDA sub-record (prefilter off)")
     ap.add_argument("--batch-steps", type=int, default=5, help="timed passes of the batched form")
     ap.add_argument("--no-serve-check", dest="serve_check", action="store_false",
@@ -797,6 +799,8 @@ def main():
     stream = torch.cuda.Stream(device=dev)
     ctx = fc.Context(local)
     fc.fastcod_set_stream(ctx.ctx, stream)
+    if args.near_log2 is not None:
+        ctx.set_option(fc.FASTCOD_OPT_NEAR_LOG2, args.near_log2)
     roi_d = torch.from_numpy(vols.roi).to(dev)
     lab_d = torch.from_numpy(vols.lab.view(np.int16)).to(dev)
     ctx.set_volumes(roi_d, lab_d, vols.dims, vols.n_roi, vols.n_targets)

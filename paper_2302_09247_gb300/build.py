@@ -1,5 +1,8 @@
 """Build libfastcod.so in-tree: one nvcc per translation unit (in parallel),
-then a shared-library link.  sm_103a only."""
+then a shared-library link.  sm_103a only.  build(checked=True) builds the
+bounds-checked variant (FASTCOD_CHECKED=1: every computed index of the
+path's gathers, scatters and list writes is tested, a failure reported as an
+error) as libfastcod_checked.so beside it."""
 from __future__ import annotations
 
 import os
@@ -10,8 +13,10 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(CSRC, "_build")
+OBJ_CHECKED = os.path.join(CSRC, "_build_checked")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libfastcod.so")
+LIB_CHECKED = os.path.join(LIBDIR, "libfastcod_checked.so")
 INCLUDE = os.path.join(ROOT, "include")
 
 SOURCES = ["fastcod_capi.cu", "batch.cu", "server.cu", "noalloc.cu", "aux_capi.cu", "k_volume.cu", "k_prefilter.cu",
@@ -31,21 +36,23 @@ def _deps():
     return hdrs + [os.path.join(INCLUDE, "fastcod.h")]
 
 
-def build(force: bool = False, ptxas_verbose: bool = False) -> str:
-    os.makedirs(OBJ, exist_ok=True)
+def build(force: bool = False, ptxas_verbose: bool = False, checked: bool = False) -> str:
+    obj_dir, lib = (OBJ_CHECKED, LIB_CHECKED) if checked else (OBJ, LIB)
+    flags = NVCC_FLAGS + (["-DFASTCOD_CHECKED=1"] if checked else [])
+    os.makedirs(obj_dir, exist_ok=True)
     os.makedirs(LIBDIR, exist_ok=True)
     dep_time = max(os.path.getmtime(d) for d in _deps())
     nvcc = _nvcc()
 
     def obj_of(src):
-        return os.path.join(OBJ, src.replace(".cu", ".o"))
+        return os.path.join(obj_dir, src.replace(".cu", ".o"))
 
     def compile_one(src):
         s = os.path.join(CSRC, src)
         o = obj_of(src)
         if not force and os.path.exists(o) and os.path.getmtime(o) >= max(os.path.getmtime(s), dep_time):
             return ""
-        cmd = [nvcc] + NVCC_FLAGS + (["-Xptxas", "-v"] if ptxas_verbose else []) + ["-c", s, "-o", o]
+        cmd = [nvcc] + flags + (["-Xptxas", "-v"] if ptxas_verbose else []) + ["-c", s, "-o", o]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {src}:\n{r.stderr}")
@@ -54,15 +61,15 @@ def build(force: bool = False, ptxas_verbose: bool = False) -> str:
     with ThreadPoolExecutor(len(SOURCES)) as ex:
         logs = list(ex.map(compile_one, SOURCES))
     objs = [obj_of(s) for s in SOURCES]
-    if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < max(os.path.getmtime(o) for o in objs):
-        tmp = LIB + f".tmp{os.getpid()}"
+    if force or not os.path.exists(lib) or os.path.getmtime(lib) < max(os.path.getmtime(o) for o in objs):
+        tmp = lib + f".tmp{os.getpid()}"
         subprocess.check_call([nvcc] + ARCH + ["-shared", "-o", tmp] + objs)
-        os.replace(tmp, LIB)
+        os.replace(tmp, lib)
     if ptxas_verbose:
         print("".join(logs))
-    return LIB
+    return lib
 
 
 if __name__ == "__main__":
     import sys
-    print(build(force="--force" in sys.argv, ptxas_verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, ptxas_verbose="-v" in sys.argv, checked="--checked" in sys.argv))

@@ -81,6 +81,8 @@ int state_end(fastcod_ctx* c, const DevState* st, const char* what) {
                   h.error_info);
     case fc::kErrCount:
       return fail(c, FASTCOD_EINVAL, "%s: negative count in row %d", what, h.error_info);
+    case fc::kErrChecked:
+      return fail(c, FASTCOD_ECUDA, "%s: bounds check failed (site %d)", what, h.error_info);
     default:
       return fail(c, FASTCOD_ECUDA, "%s: device error %d (%d)", what, h.error, h.error_info);
   }

@@ -523,6 +523,8 @@ FASTCOD_API int fastcod_batch_run(fastcod_ctx* c, const fastcod_subject* subs, i
                        : h.error == fc::kErrCoord  ? "vertex coordinate outside [-2^24, 2^24)"
                        : h.error == fc::kErrVolume ? "volume value out of range"
                                                    : "device error";
+    if (h.error == fc::kErrChecked) return fail(c, FASTCOD_ECUDA, "subject %d: bounds check failed (site %d)", i, h.error_info);
+    if (h.error == fc::kErrTimeout) return fail(c, FASTCOD_ETIMEOUT, "subject %d: device wait timed out", i);
     return fail(c, FASTCOD_EINVAL, "subject %d: %s (%d)", i, what, h.error_info);
   }
   return FASTCOD_OK;

@@ -118,6 +118,8 @@ int fcapi::sync_check(fastcod_ctx* c) {
       return fail(c, FASTCOD_EINVAL, "volume value out of range at voxel %d", h.error_info);
     case fc::kErrTimeout:
       return fail(c, FASTCOD_ETIMEOUT, "device wait timed out (warp %d)", h.error_info);
+    case fc::kErrChecked:
+      return fail(c, FASTCOD_ECUDA, "bounds check failed (site %d)", h.error_info);
     default:
       return fail(c, FASTCOD_ECUDA, "device error %d (%d)", h.error, h.error_info);
   }

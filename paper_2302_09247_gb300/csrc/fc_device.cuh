@@ -14,6 +14,30 @@ __device__ __forceinline__ void set_error(DevState* st, int32_t code, int32_t in
   if (atomicCAS(&st->error, 0, code) == 0) atomicExch(&st->error_info, info);
 }
 
+// Checked builds (FASTCOD_CHECKED=1) test every computed index of the
+// path's gathers, scatters and list writes against its array's extent: a
+// failure records kErrChecked with the site in the call's error word (st,
+// when given) and the access is skipped.  In other builds the test is the
+// constant true and compiles away.
+#ifndef FASTCOD_CHECKED
+#define FASTCOD_CHECKED 0
+#endif
+__device__ __forceinline__ bool in_bounds(int64_t i, int64_t n, DevState* st, int32_t site) {
+#if FASTCOD_CHECKED
+  if (i >= 0 && i < n) return true;
+  if (st) set_error(st, kErrChecked, site);
+  return false;
+#else
+  (void)i;
+  (void)n;
+  (void)st;
+  (void)site;
+  return true;
+#endif
+}
+
+__host__ __device__ inline int64_t voxel_count(const VolView& v) { return (int64_t)v.dx * v.dy * v.dz; }
+
 __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
 
 __device__ __forceinline__ unsigned lanemask_lt() {
@@ -25,11 +49,12 @@ __device__ __forceinline__ unsigned lanemask_lt() {
 // ROI row (-1 = none) and label (0 = none) of voxel (x, y, z); voxels off the
 // grid have neither (loc2region outside every region).
 __device__ __forceinline__ void voxel_lookup(const VolView& v, int32_t x, int32_t y, int32_t z,
-                                             int32_t& row, int32_t& lab) {
+                                             int32_t& row, int32_t& lab, DevState* ck = nullptr) {
   row = -1;
   lab = 0;
   if ((unsigned)x < (unsigned)v.dx && (unsigned)y < (unsigned)v.dy && (unsigned)z < (unsigned)v.dz) {
     const int32_t lin = x + v.dx * (y + v.dy * z);
+    if (!in_bounds(lin, voxel_count(v), ck, kSiteCode)) return;
     const uint32_t code = __ldg(v.code + lin);
     if (code & kCodeRoi) {
       row = (int32_t)(code & kCodeRowMask);
@@ -41,8 +66,10 @@ __device__ __forceinline__ void voxel_lookup(const VolView& v, int32_t x, int32_
 }
 
 // Brick bits (bit 0 ROI, bit 1 label) of brick (bx, by, bz), in range.
-__device__ __forceinline__ uint32_t brick_bits(const VolView& v, int32_t bx, int32_t by, int32_t bz) {
+__device__ __forceinline__ uint32_t brick_bits(const VolView& v, int32_t bx, int32_t by, int32_t bz,
+                                               DevState* ck = nullptr) {
   const int32_t b = bx + v.bx * (by + v.by * bz);
+  if (!in_bounds(b, (int64_t)v.bx * v.by * v.bz, ck, kSiteBrick)) return 3u;  // conservative
   return (__ldg(v.bricks + (b >> 4)) >> ((b & 15) * 2)) & 3u;
 }
 
@@ -51,7 +78,7 @@ __device__ __forceinline__ uint32_t brick_bits(const VolView& v, int32_t bx, int
 // than two bricks on an axis report both bits (long segments are rare and
 // walking them is always exact).
 __device__ __forceinline__ uint32_t box_bits(const VolView& v, int32_t lx, int32_t ly, int32_t lz,
-                                             int32_t hx, int32_t hy, int32_t hz) {
+                                             int32_t hx, int32_t hy, int32_t hz, DevState* ck = nullptr) {
   if (hx < 0 || hy < 0 || hz < 0 || lx >= v.dx || ly >= v.dy || lz >= v.dz) return 0u;
   const int32_t bx0 = max(lx, 0) >> kBrickLog2, bx1 = min(hx, v.dx - 1) >> kBrickLog2;
   const int32_t by0 = max(ly, 0) >> kBrickLog2, by1 = min(hy, v.dy - 1) >> kBrickLog2;
@@ -60,7 +87,7 @@ __device__ __forceinline__ uint32_t box_bits(const VolView& v, int32_t lx, int32
   uint32_t bits = 0;
   for (int32_t z = bz0; z <= bz1; ++z)
     for (int32_t y = by0; y <= by1; ++y)
-      for (int32_t x = bx0; x <= bx1; ++x) bits |= brick_bits(v, x, y, z);
+      for (int32_t x = bx0; x <= bx1; ++x) bits |= brick_bits(v, x, y, z, ck);
   return bits;
 }
 
@@ -70,11 +97,12 @@ __device__ __forceinline__ uint32_t box_bits(const VolView& v, int32_t lx, int32
 // shared memory (kSmem) or global memory.
 template <bool kSmem>
 __device__ __forceinline__ uint32_t near_lookup(const VolView& v, const uint32_t* nw, int32_t vx, int32_t vy,
-                                                int32_t vz) {
+                                                int32_t vz, DevState* ck = nullptr) {
   const uint32_t cx = min((uint32_t)((vx + 1) >> v.nsh), (uint32_t)v.cmx);
   const uint32_t cy = min((uint32_t)((vy + 1) >> v.nsh), (uint32_t)v.cmy);
   const uint32_t cz = min((uint32_t)((vz + 1) >> v.nsh), (uint32_t)v.cmz);
   const uint32_t w = (cx >> 4) + (uint32_t)v.nwx * (cy + (uint32_t)v.nny * cz);
+  if (!in_bounds(w, near_words(v), ck, kSiteNear)) return 3u;  // conservative
   const uint32_t word = kSmem ? nw[w] : __ldg(nw + w);
   return (word >> ((cx & 15u) << 1)) & 3u;
 }
@@ -171,7 +199,8 @@ struct SegWalk {
 // list[n..] in lane order.  Returns the new size; sets *fail when a probe
 // sequence found no slot (cannot happen while size < H).
 template <int H>
-__device__ __forceinline__ int set_insert(int32_t* tab, int32_t* list, int n, int32_t key, bool& fail) {
+__device__ __forceinline__ int set_insert(int32_t* tab, int32_t* list, int n, int32_t key, bool& fail,
+                                          int32_t cap = 0x7fffffff, DevState* ck = nullptr) {
   const unsigned want = __ballot_sync(kFull, key >= 0);
   if (want == 0u) return n;
   bool fresh = false;
@@ -190,7 +219,10 @@ __device__ __forceinline__ int set_insert(int32_t* tab, int32_t* list, int n, in
     }
   }
   const unsigned fm = __ballot_sync(kFull, fresh);
-  if (fresh) list[n + __popc(fm & lanemask_lt())] = key;
+  if (fresh) {
+    const int at = n + __popc(fm & lanemask_lt());
+    if (in_bounds(at, cap, ck, kSiteSetList)) list[at] = key;
+  }
   return n + __popc(fm);
 }
 

@@ -30,7 +30,25 @@ enum DevError : int32_t {
   kErrVolume = 3,       // roi or label value out of range
   kErrTimeout = 4,      // a bounded wait gave up
   kErrOverflowList = 5, // overflow list capacity exceeded (cannot happen by construction)
-  kErrCount = 6         // a connectivity count given to the parcellation is negative
+  kErrCount = 6,        // a connectivity count given to the parcellation is negative
+  kErrChecked = 7       // checked builds: an index failed its bounds check (error_info: the site)
+};
+
+// Sites of the bounds checks of checked builds (FASTCOD_CHECKED=1).
+enum CheckSite : int32_t {
+  kSiteSurvivorRead = 1,   // survivor id read from the list, and the id itself
+  kSiteSurvivorWrite = 2,  // survivor list append (prefilter)
+  kSiteCode = 3,           // per-voxel code gather
+  kSiteLabel = 4,          // label gather of a labelled ROI voxel
+  kSiteNear = 5,           // near-grid word
+  kSiteBrick = 6,          // brick-occupancy word
+  kSiteVoxelList = 7,      // the walk's list of visited voxels
+  kSiteSetList = 8,        // a set's key list
+  kSiteC = 9,              // C entry
+  kSiteCend = 10,          // C_end entry
+  kSiteOverflowList = 11,  // overflow list append
+  kSiteVertex = 12,        // vertex read
+  kSiteScratch = 13        // overflow path's global sets
 };
 
 // Cumulative and per-call counters in device memory.

@@ -167,7 +167,8 @@ __device__ __forceinline__ void flush_ids(int& n, const int32_t* buf, bool back,
   base = __shfl_sync(kFull, base, 0);
   for (int k = (int)lane_id(); k < n; k += 32) {  // n <= 64
     const int64_t pos = (int64_t)base + k;
-    surv.ids[back ? surv.cap - 1 - pos : pos] = buf[k];
+    const int64_t at = back ? surv.cap - 1 - pos : pos;
+    if (in_bounds(at, surv.cap, gst, kSiteSurvivorWrite)) surv.ids[at] = buf[k];
   }
   __syncwarp();
   n = 0;
@@ -177,7 +178,7 @@ __device__ __forceinline__ void flush_ids(int& n, const int32_t* buf, bool back,
 // (rare).
 __device__ __noinline__ uint32_t long_box(const uint32_t* bricks, int32_t dx, int32_t dy, int32_t dz, int32_t bx,
                                           int32_t by, int32_t lx, int32_t ly, int32_t lz, int32_t hx, int32_t hy,
-                                          int32_t hz) {
+                                          int32_t hz, DevState* ck) {
   VolView v;
   v.bricks = bricks;
   v.dx = dx;
@@ -185,7 +186,8 @@ __device__ __noinline__ uint32_t long_box(const uint32_t* bricks, int32_t dx, in
   v.dz = dz;
   v.bx = bx;
   v.by = by;
-  return box_bits(v, lx, ly, lz, hx, hy, hz);
+  v.bz = (dz + (1 << kBrickLog2) - 1) >> kBrickLog2;
+  return box_bits(v, lx, ly, lz, hx, hy, hz, ck);
 }
 
 // 1. Start of window W (first vertex, a multiple of kWin): boundaries b with
@@ -251,7 +253,7 @@ __device__ __forceinline__ uint32_t scan_piece(Scan& sc, const VolView& v, const
       const uint32_t m = 0u - ((keep8 >> k) & 1u);
       lg |= (ax | ay | az) & m;
       stp += (ax + ay + az) & m;
-      if ((k & 1) == 0) h8 |= near_lookup<kSmem>(v, nw, vx, vy, vz) << k;
+      if ((k & 1) == 0) h8 |= near_lookup<kSmem>(v, nw, vx, vy, vz, sc.sst) << k;
       qx = vx;
       qy = vy;
       qz = vz;
@@ -269,7 +271,7 @@ __device__ __forceinline__ uint32_t scan_piece(Scan& sc, const VolView& v, const
       const int32_t vx = p[3 * k] >> kUnitLog2, vy = p[3 * k + 1] >> kUnitLog2, vz = p[3 * k + 2] >> kUnitLog2;
       if (((keep8 >> k) & 1u) && (uint32_t)(abs(vx - qx) | abs(vy - qy) | abs(vz - qz)) > 1u)
         h8 |= long_box(v.bricks, v.dx, v.dy, v.dz, v.bx, v.by, min(vx, qx), min(vy, qy), min(vz, qz), max(vx, qx),
-                       max(vy, qy), max(vz, qz))
+                       max(vy, qy), max(vz, qz), sc.sst)
               << (k & ~1);
       qx = vx;
       qy = vy;

@@ -48,24 +48,30 @@ struct WalkWarpSmem {
 constexpr int32_t kBitRowsMax = 32 * kHV;
 constexpr int32_t kBitLabelsMax = 32 * kHT;  // labels 1 .. kBitLabelsMax - 1
 
-__device__ __forceinline__ int bit_insert(int32_t* tab, int32_t* list, int n, int32_t key) {
+template <int kWords, int kCap>
+__device__ __forceinline__ int bit_insert(int32_t* tab, int32_t* list, int n, int32_t key, DevState* ck) {
   bool fresh = false;
-  if (key >= 0) {
+  if (key >= 0 && in_bounds(key >> 5, kWords, ck, kSiteSetList)) {
     const uint32_t m = 1u << (key & 31);
     fresh = (atomicOr(reinterpret_cast<uint32_t*>(tab) + (key >> 5), m) & m) == 0u;
   }
   const unsigned fm = __ballot_sync(kFull, fresh);
-  if (fresh) list[n + __popc(fm & lanemask_lt())] = key;
+  if (fresh) {
+    const int at = n + __popc(fm & lanemask_lt());
+    if (in_bounds(at, kCap, ck, kSiteSetList)) list[at] = key;
+  }
   return n + __popc(fm);
 }
 
 template <bool kBitV, bool kBitT>
 struct Sets {
-  __device__ __forceinline__ static int insV(WalkWarpSmem& sm, int n, int32_t key, bool& fail) {
-    return kBitV ? bit_insert(sm.tabV, sm.listV, n, key) : set_insert<kHV>(sm.tabV, sm.listV, n, key, fail);
+  __device__ __forceinline__ static int insV(WalkWarpSmem& sm, int n, int32_t key, bool& fail, DevState* ck) {
+    return kBitV ? bit_insert<kHV, kLimV + 32>(sm.tabV, sm.listV, n, key, ck)
+                 : set_insert<kHV>(sm.tabV, sm.listV, n, key, fail, kLimV + 32, ck);
   }
-  __device__ __forceinline__ static int insT(WalkWarpSmem& sm, int n, int32_t key, bool& fail) {
-    return kBitT ? bit_insert(sm.tabT, sm.listT, n, key) : set_insert<kHT>(sm.tabT, sm.listT, n, key, fail);
+  __device__ __forceinline__ static int insT(WalkWarpSmem& sm, int n, int32_t key, bool& fail, DevState* ck) {
+    return kBitT ? bit_insert<kHT, kLimT + 32>(sm.tabT, sm.listT, n, key, ck)
+                 : set_insert<kHT>(sm.tabT, sm.listT, n, key, fail, kLimT + 32, ck);
   }
   // empty tables at kernel start
   __device__ __forceinline__ static void init(WalkWarpSmem& sm) {
@@ -113,13 +119,14 @@ __device__ __forceinline__ int32_t voxel_lin(const VolView& v, int32_t x, int32_
   return -1;
 }
 
-__device__ __forceinline__ void decode(const VolView& v, int32_t lin, uint32_t code, int32_t& row, int32_t& lab) {
+__device__ __forceinline__ void decode(const VolView& v, int32_t lin, uint32_t code, int32_t& row, int32_t& lab,
+                                       DevState* ck) {
   row = -1;
   lab = 0;
   if (lin < 0) return;
   if (code & kCodeRoi) {
     row = (int32_t)(code & kCodeRowMask);
-    if (code & kCodeRoiLabelled) lab = (int32_t)__ldg(v.lab + lin);
+    if ((code & kCodeRoiLabelled) && in_bounds(lin, voxel_count(v), ck, kSiteLabel)) lab = (int32_t)__ldg(v.lab + lin);
   } else {
     lab = (int32_t)code;
   }
@@ -132,7 +139,7 @@ __device__ __forceinline__ void decode(const VolView& v, int32_t lin, uint32_t c
 // segments may fill the list).
 template <typename S, bool kWide>
 __device__ __forceinline__ void flush_voxels(const VolView& v, WalkWarpSmem& sm, int& nL, bool endpoint_mode,
-                                             uint64_t keep, int& nV, int& nT, bool& fail) {
+                                             uint64_t keep, int& nV, int& nT, bool& fail, DevState* ck) {
   __syncwarp();
   constexpr int kPer = kWide ? 4 : 1;
   const int lane = (int)lane_id();
@@ -142,16 +149,17 @@ __device__ __forceinline__ void flush_voxels(const VolView& v, WalkWarpSmem& sm,
 #pragma unroll
     for (int k = 0; k < kPer; ++k) lin[k] = r0 + lane + 32 * k < nL ? sm.lin[r0 + lane + 32 * k] : -1;
 #pragma unroll
-    for (int k = 0; k < kPer; ++k) code[k] = lin[k] >= 0 ? ldg_hint(v.code + lin[k], keep) : 0u;
+    for (int k = 0; k < kPer; ++k)
+      code[k] = lin[k] >= 0 && in_bounds(lin[k], voxel_count(v), ck, kSiteCode) ? ldg_hint(v.code + lin[k], keep) : 0u;
 #pragma unroll
     for (int k = 0; k < kPer; ++k) {
       if (r0 + 32 * k < nL && !fail) {  // warp-uniform
         int32_t row, lab;
-        decode(v, lin[k], code[k], row, lab);
+        decode(v, lin[k], code[k], row, lab, ck);
         if (endpoint_mode) lab = 0;
-        nV = S::insV(sm, nV, row, fail);
-        nT = S::insT(sm, nT, lab > 0 ? lab : -1, fail);
-        if (nV > kLimV || nT > kLimT) fail = true;
+        nV = S::insV(sm, nV, row, fail, ck);
+        nT = S::insT(sm, nT, lab > 0 ? lab : -1, fail, ck);
+        fail = __any_sync(kFull, fail) || nV > kLimV || nT > kLimT;  // warp-uniform
       }
     }
   }
@@ -167,7 +175,7 @@ __device__ __forceinline__ void flush_voxels(const VolView& v, WalkWarpSmem& sm,
 template <typename P, typename S>
 __device__ __forceinline__ void walk_window(const VolView& v, WalkWarpSmem& sm, const int32_t p0[3],
                                             const int32_t p1[3], bool has, bool first, bool endpoint_mode,
-                                            uint64_t keep, int& nL, int& nV, int& nT, bool& fail) {
+                                            uint64_t keep, int& nL, int& nV, int& nT, bool& fail, DevState* ck) {
   SegWalk<P> w;
   bool pend = false;
   if (has) {
@@ -177,11 +185,14 @@ __device__ __forceinline__ void walk_window(const VolView& v, WalkWarpSmem& sm, 
   while (__any_sync(kFull, pend)) {
     const int32_t lin = pend ? voxel_lin(v, w.cx, w.cy, w.cz) : -1;
     const unsigned m = __ballot_sync(kFull, lin >= 0);
-    if (lin >= 0) sm.lin[nL + __popc(m & lanemask_lt())] = lin;
+    if (lin >= 0) {
+      const int at = nL + __popc(m & lanemask_lt());
+      if (in_bounds(at, kLin, ck, kSiteVoxelList)) sm.lin[at] = lin;
+    }
     nL += __popc(m);
     if (pend) pend = w.step();
     if (nL > kLin - 32) {  // long segments only: windows start with room for 3 voxels a lane
-      flush_voxels<S, false>(v, sm, nL, endpoint_mode, keep, nV, nT, fail);
+      flush_voxels<S, false>(v, sm, nL, endpoint_mode, keep, nV, nT, fail, ck);
       if (fail) break;
     }
   }
@@ -193,13 +204,14 @@ __device__ __forceinline__ void walk_window(const VolView& v, WalkWarpSmem& sm, 
 template <typename S>
 __device__ __forceinline__ int walk_one(const VolView& v, const Tract& t, const Accum& acc, uint32_t mode,
                                         WalkWarpSmem& sm, int32_t s, int32_t id, int32_t* __restrict__ ovf,
-                                        DevState* gst) {
+                                        int64_t ovf_cap, DevState* gst) {
   const unsigned lane = lane_id();
   const bool endpoint_mode = (mode & kModeTargetEndpoint) != 0;
   const bool point_mode = (mode & kModeVertexSampled) != 0;
   const bool walk_all = (mode & kModeWalkAll) != 0;
   const uint64_t keep = policy_evict_last();  // code gathers and C stay in L2 across the stream
   const int64_t M = v.n_lab;
+  if (!in_bounds(s, t.ns, gst, kSiteSurvivorRead)) return 0;
   const int64_t a = t.off[s], b = t.off[s + 1];
   // offsets the prefilter has flagged as invalid may reach this point; such
   // a streamline is skipped (the call reports the error)
@@ -215,11 +227,11 @@ __device__ __forceinline__ int walk_one(const VolView& v, const Tract& t, const 
       if (j < b) {
         int32_t p[3];
         load_vertex(t.xyz, j, p);
-        voxel_lookup(v, p[0] >> kUnitLog2, p[1] >> kUnitLog2, p[2] >> kUnitLog2, row, lab);
+        voxel_lookup(v, p[0] >> kUnitLog2, p[1] >> kUnitLog2, p[2] >> kUnitLog2, row, lab, gst);
       }
       if (endpoint_mode) lab = 0;
-      nV = S::insV(sm, nV, row, fail);
-      nT = S::insT(sm, nT, lab > 0 ? lab : -1, fail);
+      nV = S::insV(sm, nV, row, fail, gst);
+      nT = S::insT(sm, nT, lab > 0 ? lab : -1, fail, gst);
       if (nV > kLimV || nT > kLimT) fail = true;
       fail = __any_sync(kFull, fail);
     }
@@ -231,7 +243,7 @@ __device__ __forceinline__ int walk_one(const VolView& v, const Tract& t, const 
     if (a + lane < b) load_vertex(t.xyz, a + lane, cur);
     for (int64_t i0 = 0; i0 < T - 1 && !fail; i0 += 32) {
       if (nL > kLin - 96) {  // room for three voxels a lane
-        flush_voxels<S, true>(v, sm, nL, endpoint_mode, keep, nV, nT, fail);
+        flush_voxels<S, true>(v, sm, nL, endpoint_mode, keep, nV, nT, fail, gst);
         if (__any_sync(kFull, fail)) break;
       }
       const int64_t j = a + i0 + lane;
@@ -253,19 +265,19 @@ __device__ __forceinline__ int walk_one(const VolView& v, const Tract& t, const 
         const int32_t c0x = p0[0] >> kUnitLog2, c0y = p0[1] >> kUnitLog2, c0z = p0[2] >> kUnitLog2;
         const bool shortseg = abs((p1[0] >> kUnitLog2) - c0x) <= 1 && abs((p1[1] >> kUnitLog2) - c0y) <= 1 &&
                               abs((p1[2] >> kUnitLog2) - c0z) <= 1;
-        if (shortseg && !walk_all && near_lookup<false>(v, v.near, c0x, c0y, c0z) == 0u) has = false;
+        if (shortseg && !walk_all && near_lookup<false>(v, v.near, c0x, c0y, c0z, gst) == 0u) has = false;
       }
       const bool small = !has || (abs(p1[0] - p0[0]) < 65536 && abs(p1[1] - p0[1]) < 65536 &&
                                   abs(p1[2] - p0[2]) < 65536);
       if (__all_sync(kFull, small))
-        walk_window<uint32_t, S>(v, sm, p0, p1, has, j == a, endpoint_mode, keep, nL, nV, nT, fail);
+        walk_window<uint32_t, S>(v, sm, p0, p1, has, j == a, endpoint_mode, keep, nL, nV, nT, fail, gst);
       else
-        walk_window<unsigned long long, S>(v, sm, p0, p1, has, j == a, endpoint_mode, keep, nL, nV, nT, fail);
+        walk_window<unsigned long long, S>(v, sm, p0, p1, has, j == a, endpoint_mode, keep, nL, nV, nT, fail, gst);
       fail = __any_sync(kFull, fail);
 #pragma unroll
       for (int k = 0; k < 3; ++k) cur[k] = nxt[k];
     }
-    if (nL > 0 && !fail) flush_voxels<S, true>(v, sm, nL, endpoint_mode, keep, nV, nT, fail);
+    if (nL > 0 && !fail) flush_voxels<S, true>(v, sm, nL, endpoint_mode, keep, nV, nT, fail, gst);
     fail = __any_sync(kFull, fail);
   }
   if (endpoint_mode && !fail) {
@@ -274,28 +286,34 @@ __device__ __forceinline__ int walk_one(const VolView& v, const Tract& t, const 
     if (lane == 0) {
       int32_t p[3];
       load_vertex(t.xyz, b - 1, p);
-      voxel_lookup(v, p[0] >> kUnitLog2, p[1] >> kUnitLog2, p[2] >> kUnitLog2, row, lab);
+      voxel_lookup(v, p[0] >> kUnitLog2, p[1] >> kUnitLog2, p[2] >> kUnitLog2, row, lab, gst);
     }
-    nT = S::insT(sm, nT, lab > 0 ? lab : -1, fail);
+    nT = S::insT(sm, nT, lab > 0 ? lab : -1, fail, gst);
     fail = __any_sync(kFull, fail) || nT > kLimT;
   }
   __syncwarp();
   int pairs = -1;
   if (fail) {
-    if (lane == 0) ovf[atomicAdd(&gst->n_overflow, 1u)] = id;
+    if (lane == 0) {
+      const uint32_t at = atomicAdd(&gst->n_overflow, 1u);
+      if (in_bounds(at, ovf_cap, gst, kSiteOverflowList)) ovf[at] = id;
+    }
   } else {
     pairs = nV * nT;
+    const int64_t NM = (int64_t)v.n_roi * M;
     for (int p = lane; p < pairs; p += 32) {
       const int i = p / nT, k = p - i * nT;
-      red_add_hint(acc.C + (int64_t)sm.listV[i] * M + (sm.listT[k] - 1), 1, keep);
+      const int64_t e = (int64_t)sm.listV[i] * M + (sm.listT[k] - 1);
+      if (in_bounds(e, NM, gst, kSiteC)) red_add_hint(acc.C + e, 1, keep);
     }
     if (lane == 0) {
       int32_t p[3], r0, l0, r1, l1;
       load_vertex(t.xyz, a, p);
-      voxel_lookup(v, p[0] >> kUnitLog2, p[1] >> kUnitLog2, p[2] >> kUnitLog2, r0, l0);
+      voxel_lookup(v, p[0] >> kUnitLog2, p[1] >> kUnitLog2, p[2] >> kUnitLog2, r0, l0, gst);
       load_vertex(t.xyz, b - 1, p);
-      voxel_lookup(v, p[0] >> kUnitLog2, p[1] >> kUnitLog2, p[2] >> kUnitLog2, r1, l1);
-      if (r0 >= 0 && l1 >= 1) atomicAdd(acc.Cend + (int64_t)r0 * M + (l1 - 1), 1);
+      voxel_lookup(v, p[0] >> kUnitLog2, p[1] >> kUnitLog2, p[2] >> kUnitLog2, r1, l1, gst);
+      const int64_t e = (int64_t)r0 * M + (l1 - 1);
+      if (r0 >= 0 && l1 >= 1 && in_bounds(e, NM, gst, kSiteCend)) atomicAdd(acc.Cend + e, 1);
     }
   }
   S::clear(sm, nV, nT);
@@ -319,12 +337,13 @@ __global__ void __launch_bounds__(kWalkWarps * 32, kWalkMinBlocks)
   griddep_launch_dependents();
   griddep_wait();  // the prefilter's survivor list and counters
   const uint32_t nl = st->n_long, n = st->n_survivors + nl;
+  if (n > 0 && !in_bounds((int64_t)n - 1, surv_cap, st, kSiteSurvivorRead)) return;
   unsigned long long pairs_acc = 0;
   for (;;) {
     const uint32_t idx = next_survivor(st);
     if (idx >= n) break;
     const int32_t s = survivor_at(surv, surv_cap, nl, idx);
-    const int pairs = walk_one<S>(v, t, acc, mode, sm, s, s, ovf, st);
+    const int pairs = walk_one<S>(v, t, acc, mode, sm, s, s, ovf, surv_cap, st);
     if (pairs > 0) pairs_acc += (unsigned long long)pairs;
   }
   if (lane_id() == 0 && pairs_acc) atomicAdd(&st->pairs, pairs_acc);
@@ -380,12 +399,13 @@ __global__ void __launch_bounds__(kWalkWarps * 32, kWalkMinBlocks)
   WalkWarpSmem& sm = smem_all[threadIdx.x >> 5];
   S::init(sm);
   const uint32_t nl = gst->n_long, n = gst->n_survivors + nl;
+  if (n > 0 && !in_bounds((int64_t)n - 1, surv_cap, gst, kSiteSurvivorRead)) return;
   for (;;) {
     const uint32_t idx = next_survivor(gst);
     if (idx >= n) break;
     const int32_t g = survivor_at(surv, surv_cap, nl, idx);
     const BatchSubject& B = tbl.s[subject_of(tbl, g)];
-    const int pairs = walk_one<S>(B.v, B.t, B.acc, mode, sm, (int32_t)(g - B.sbase), g, ovf, gst);
+    const int pairs = walk_one<S>(B.v, B.t, B.acc, mode, sm, (int32_t)(g - B.sbase), g, ovf, surv_cap, gst);
     if (pairs > 0 && lane_id() == 0) atomicAdd(&B.st->pairs, (unsigned long long)pairs);
   }
 }
@@ -407,17 +427,23 @@ struct OvfSets {
   int32_t* lablist;
 };
 
-__device__ __forceinline__ void ovf_add(uint32_t* bits, int32_t* list, int* n, int32_t key) {
+// key < n_keys (the bitmap holds n_keys bits, the list n_keys entries)
+__device__ __forceinline__ void ovf_add(uint32_t* bits, int32_t* list, int* n, int32_t key, int64_t n_keys,
+                                        DevState* ck) {
+  if (!in_bounds(key, n_keys, ck, kSiteScratch)) return;
   const uint32_t m = 1u << (key & 31);
-  if (!(atomicOr(bits + (key >> 5), m) & m)) list[atomicAdd(n, 1)] = key;
+  if (!(atomicOr(bits + (key >> 5), m) & m)) {
+    const int at = atomicAdd(n, 1);
+    if (in_bounds(at, n_keys, ck, kSiteScratch)) list[at] = key;
+  }
 }
 
 __device__ __forceinline__ void ovf_visit(const VolView& v, const OvfSets& z, int* nV, int* nT, bool endpoint_mode,
-                                          int32_t x, int32_t y, int32_t zz) {
+                                          int32_t x, int32_t y, int32_t zz, DevState* ck) {
   int32_t row, lab;
-  voxel_lookup(v, x, y, zz, row, lab);
-  if (row >= 0) ovf_add(z.rowbits, z.rowlist, nV, row);
-  if (!endpoint_mode && lab >= 1) ovf_add(z.labbits, z.lablist, nT, lab);
+  voxel_lookup(v, x, y, zz, row, lab, ck);
+  if (row >= 0) ovf_add(z.rowbits, z.rowlist, nV, row, v.n_roi, ck);
+  if (!endpoint_mode && lab >= 1) ovf_add(z.labbits, z.lablist, nT, lab, (int64_t)v.n_lab + 1, ck);
 }
 
 // The whole CTA handles streamline s of (v, t): walk every segment, sets as
@@ -442,27 +468,29 @@ __device__ __forceinline__ void overflow_one(const VolView& v, const Tract& t, c
     int32_t p0[3];
     load_vertex(t.xyz, a + u, p0);
     if (pts) {
-      ovf_visit(v, z, nV, nT, endpoint_mode, p0[0] >> kUnitLog2, p0[1] >> kUnitLog2, p0[2] >> kUnitLog2);
+      ovf_visit(v, z, nV, nT, endpoint_mode, p0[0] >> kUnitLog2, p0[1] >> kUnitLog2, p0[2] >> kUnitLog2, sst);
     } else {
       int32_t p1[3];
       load_vertex(t.xyz, a + u + 1, p1);
       SegWalk<unsigned long long> w;
       w.init(p0, p1);
-      ovf_visit(v, z, nV, nT, endpoint_mode, w.cx, w.cy, w.cz);
-      while (w.step()) ovf_visit(v, z, nV, nT, endpoint_mode, w.cx, w.cy, w.cz);
+      ovf_visit(v, z, nV, nT, endpoint_mode, w.cx, w.cy, w.cz, sst);
+      while (w.step()) ovf_visit(v, z, nV, nT, endpoint_mode, w.cx, w.cy, w.cz, sst);
     }
   }
   if (endpoint_mode && threadIdx.x == 0 && T >= 1) {
     int32_t p[3], row, lab;
     load_vertex(t.xyz, b - 1, p);
-    voxel_lookup(v, p[0] >> kUnitLog2, p[1] >> kUnitLog2, p[2] >> kUnitLog2, row, lab);
-    if (lab >= 1) ovf_add(z.labbits, z.lablist, nT, lab);
+    voxel_lookup(v, p[0] >> kUnitLog2, p[1] >> kUnitLog2, p[2] >> kUnitLog2, row, lab, sst);
+    if (lab >= 1) ovf_add(z.labbits, z.lablist, nT, lab, (int64_t)v.n_lab + 1, sst);
   }
   __syncthreads();
   const int64_t pairs = (int64_t)(*nV) * (*nT);
+  const int64_t NM = (int64_t)v.n_roi * M;
   for (int64_t p = threadIdx.x; p < pairs; p += blockDim.x) {
     const int64_t r = p / *nT, k = p - r * *nT;
-    atomicAdd(acc.C + (int64_t)z.rowlist[r] * M + (z.lablist[k] - 1), 1);
+    const int64_t e = (int64_t)z.rowlist[r] * M + (z.lablist[k] - 1);
+    if (in_bounds(e, NM, sst, kSiteC)) atomicAdd(acc.C + e, 1);
   }
   if (threadIdx.x == 0) {
     if (pairs) atomicAdd(&sst->pairs, (unsigned long long)pairs);
@@ -470,10 +498,11 @@ __device__ __forceinline__ void overflow_one(const VolView& v, const Tract& t, c
     if (T >= 1) {
       int32_t p[3], r0, l0, r1, l1;
       load_vertex(t.xyz, a, p);
-      voxel_lookup(v, p[0] >> kUnitLog2, p[1] >> kUnitLog2, p[2] >> kUnitLog2, r0, l0);
+      voxel_lookup(v, p[0] >> kUnitLog2, p[1] >> kUnitLog2, p[2] >> kUnitLog2, r0, l0, sst);
       load_vertex(t.xyz, b - 1, p);
-      voxel_lookup(v, p[0] >> kUnitLog2, p[1] >> kUnitLog2, p[2] >> kUnitLog2, r1, l1);
-      if (r0 >= 0 && l1 >= 1) atomicAdd(acc.Cend + (int64_t)r0 * M + (l1 - 1), 1);
+      voxel_lookup(v, p[0] >> kUnitLog2, p[1] >> kUnitLog2, p[2] >> kUnitLog2, r1, l1, sst);
+      const int64_t e = (int64_t)r0 * M + (l1 - 1);
+      if (r0 >= 0 && l1 >= 1 && in_bounds(e, NM, sst, kSiteCend)) atomicAdd(acc.Cend + e, 1);
     }
   }
   __syncthreads();

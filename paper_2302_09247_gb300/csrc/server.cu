@@ -474,7 +474,9 @@ bool iterate(fastcod_server* S, uint32_t** tmp, size_t* tmp_cap) {
       }
       (void)cudaGetLastError();
       if (r->status == FASTCOD_OK && r->mem && r->host_state->error != fc::kErrNone)
-        r->status = r->host_state->error == fc::kErrTimeout ? FASTCOD_ETIMEOUT : FASTCOD_EINVAL;
+        r->status = r->host_state->error == fc::kErrTimeout   ? FASTCOD_ETIMEOUT
+                    : r->host_state->error == fc::kErrChecked ? FASTCOD_ECUDA
+                                                               : FASTCOD_EINVAL;
       S->free_states.push_back(r->host_state);
       r->host_state = nullptr;
       if (r->mem) cudaFreeAsync(r->mem, S->compute);

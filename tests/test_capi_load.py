@@ -65,3 +65,13 @@ def test_null_and_state_errors_without_gpu(lib_path):
         assert L.fastcod_create(ctypes.byref(out), 0, 0) == fc.FASTCOD_EINVAL
         assert out.value is None
         assert fc.fastcod_last_error(None) != ""
+
+
+def test_checked_build_exports_the_same_symbols(lib_path):
+    # the bounds-checked variant (FASTCOD_CHECKED=1) builds and exports the
+    # same boundary
+    from paper_2302_09247_gb300 import build
+    checked = build.build(checked=True)
+    out = subprocess.run(["nm", "-D", "--defined-only", checked], capture_output=True, text=True).stdout
+    exported = {ln.split()[-1] for ln in out.splitlines() if " T " in ln and ln.split()[-1].startswith("fastcod_")}
+    assert exported == set(_declared())
