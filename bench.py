@@ -49,8 +49,8 @@ METRIC = "DDA voxel-steps/s & subjects/s for C, bit-exact; batched vs plain; p50
 # traffic grows with the vertices).
 PREFILTER_SOURCES = ("paper_2302_09247_gb300/csrc/k_prefilter.cu", "paper_2302_09247_gb300/csrc/fc_tma.cuh",
                      "paper_2302_09247_gb300/csrc/fc_internal.cuh", "paper_2302_09247_gb300/csrc/fc_device.cuh")
-PREFILTER_TRAFFIC = {"sha256": "fa0cbb8403cdaeb1fa3c27127b9495d74bb741a0187d339391d5f71cc642a043",
-                     "bytes": 1911476992, "vertices": 157754709, "workload": "high-res",
+PREFILTER_TRAFFIC = {"sha256": "9fda845124957510a518838d56029396fbda98e705f57c2feebbdef8621dafb2",
+                     "bytes": 1911587840, "vertices": 157754709, "workload": "high-res",
                      "summary": "profiles/prefilter_kernel_highres260x311x260.md"}
 
 
@@ -656,8 +656,8 @@ def run_next(args):
 # the ones it was measured on.
 WALK_SOURCES = ("paper_2302_09247_gb300/csrc/k_walk.cu", "paper_2302_09247_gb300/csrc/fc_device.cuh",
                 "paper_2302_09247_gb300/csrc/fc_internal.cuh")
-WALK_INSTR = {"sha256": "1098d6f38db4f67879693315bba626b333208e3c7072a17073b50dee5b716acd",
-              "warp_instr_per_voxel_step": 584886662 / 54811982,
+WALK_INSTR = {"sha256": "fb328e5ffddda157f4ef2339b1638b3e17e78577d9b58d072b782734185ab24c",
+              "warp_instr_per_voxel_step": 584549628 / 54811982,
               "summary": "profiles/walk_kernel_dda_highres260x311x260.md"}
 
 
