@@ -94,6 +94,12 @@ struct fastcod_server {
 
   cudaStream_t compute = nullptr, copy = nullptr;
   cudaEvent_t copied = nullptr;
+  // stream-ordered allocations of the loop come from a pool of the server's
+  // own that keeps its memory between iterations (release threshold at the
+  // maximum) and never makes an allocation wait for another stream's free
+  // (no internal dependencies: a chunk's copy must not queue behind the
+  // compute stream); blocks whose free has completed are reused
+  cudaMemPool_t pool = nullptr;
   // iteration buffers (stream-ordered allocations on the compute stream)
   DevState* gst = nullptr;
   int32_t* lists = nullptr;  // survivors | overflow
@@ -178,7 +184,7 @@ cudaError_t setup_request(fastcod_server* S, Request* r, uint32_t** tmp, size_t*
   size_t bytes = resident_bytes(h, S->near_log2);
   const size_t in_bytes = (r->host_roi ? a256(nvox * 4) : 0) + (r->host_lab ? a256(nvox * 2) : 0);
   if (inject_alloc(S)) return cudaErrorMemoryAllocation;
-  cudaError_t e = cudaMallocAsync((void**)&r->mem, bytes + in_bytes, S->compute);
+  cudaError_t e = cudaMallocFromPoolAsync((void**)&r->mem, bytes + in_bytes, S->pool, S->compute);
   if (e != cudaSuccess) return e;
   char* p = r->mem;
   auto take = [&](size_t n) {
@@ -222,7 +228,7 @@ cudaError_t setup_request(fastcod_server* S, Request* r, uint32_t** tmp, size_t*
   const size_t need = (size_t)fc::plane_words(h.dims[0], h.dims[1], h.dims[2]) * 4;
   if (e == cudaSuccess && need > *tmp_cap) {
     if (*tmp) e = cudaFreeAsync(*tmp, S->compute);
-    if (e == cudaSuccess) e = cudaMallocAsync((void**)tmp, need, S->compute);
+    if (e == cudaSuccess) e = cudaMallocFromPoolAsync((void**)tmp, need, S->pool, S->compute);
     if (e == cudaSuccess) *tmp_cap = need;
   }
   if (e == cudaSuccess)
@@ -239,18 +245,18 @@ cudaError_t grow_iteration_buffers(fastcod_server* S, size_t entries, size_t nta
   if (entries > S->lists_cap) {
     if (S->lists) e = cudaFreeAsync(S->lists, S->compute);
     const size_t cap = std::max(entries, S->lists_cap * 2);
-    if (e == cudaSuccess) e = cudaMallocAsync((void**)&S->lists, cap * 8, S->compute);
+    if (e == cudaSuccess) e = cudaMallocFromPoolAsync((void**)&S->lists, cap * 8, S->pool, S->compute);
     if (e == cudaSuccess) S->lists_cap = cap;
   }
   if (e == cudaSuccess && ntasks > S->tasks_cap) {
     if (S->tasks) e = cudaFreeAsync(S->tasks, S->compute);
     const size_t cap = std::max(ntasks, S->tasks_cap * 2);
-    if (e == cudaSuccess) e = cudaMallocAsync((void**)&S->tasks, cap * sizeof(fc::BatchTask), S->compute);
+    if (e == cudaSuccess) e = cudaMallocFromPoolAsync((void**)&S->tasks, cap * sizeof(fc::BatchTask), S->pool, S->compute);
     if (e == cudaSuccess) S->tasks_cap = cap;
   }
   if (e == cudaSuccess && words > S->scratch_words) {
     if (S->scratch) e = cudaFreeAsync(S->scratch, S->compute);
-    if (e == cudaSuccess) e = cudaMallocAsync((void**)&S->scratch, (size_t)kOverflowCtas * words * 4, S->compute);
+    if (e == cudaSuccess) e = cudaMallocFromPoolAsync((void**)&S->scratch, (size_t)kOverflowCtas * words * 4, S->pool, S->compute);
     if (e == cudaSuccess) e = cudaMemsetAsync(S->scratch, 0, (size_t)kOverflowCtas * words * 4, S->compute);
     if (e == cudaSuccess) S->scratch_words = words;
   }
@@ -347,7 +353,7 @@ bool iterate(fastcod_server* S, uint32_t** tmp, size_t* tmp_cap) {
     if (k.host_xyz || k.host_off) {
       const size_t xb = a256((size_t)k.nv * 12 + 16);
       cudaError_t e = inject_alloc(S) ? cudaErrorMemoryAllocation
-                                      : cudaMallocAsync(&sg.buf, xb + (size_t)(k.ns + 1) * 8, S->copy);
+                                      : cudaMallocFromPoolAsync(&sg.buf, xb + (size_t)(k.ns + 1) * 8, S->pool, S->copy);
       if (e == cudaSuccess && inject_h2d(S)) e = cudaErrorInvalidValue;  // the copy "fails" before it is issued
       if (e == cudaSuccess && k.host_xyz && k.nv) {
         e = cudaMemcpyAsync(sg.buf, k.xyz, (size_t)k.nv * 12, cudaMemcpyDefault, S->copy);
@@ -541,6 +547,21 @@ FASTCOD_API int fastcod_server_create(fastcod_ctx* c, int32_t max_slots, int64_t
   S->budget = hbm_budget_bytes ? hbm_budget_bytes : (int64_t)(free_b / 10 * 9);
   S->tbl = new (std::nothrow) fc::BatchTable;
   cudaError_t e = S->tbl ? cudaSuccess : cudaErrorMemoryAllocation;
+  if (e == cudaSuccess) {
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = c->device;
+    e = cudaMemPoolCreate(&S->pool, &props);
+  }
+  if (e == cudaSuccess) {
+    uint64_t keep = ~0ull;
+    e = cudaMemPoolSetAttribute(S->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  }
+  if (e == cudaSuccess) {
+    int no = 0;
+    e = cudaMemPoolSetAttribute(S->pool, cudaMemPoolReuseAllowInternalDependencies, &no);
+  }
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->compute, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->copy, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&S->copied, cudaEventDisableTiming);
@@ -560,6 +581,7 @@ FASTCOD_API int fastcod_server_create(fastcod_ctx* c, int32_t max_slots, int64_t
       if (S->tasks_ev[k]) cudaEventDestroy(S->tasks_ev[k]);
     if (S->state_pool) cudaFreeHost(S->state_pool);
     cudaFree(S->gst);
+    if (S->pool) cudaMemPoolDestroy(S->pool);
     delete S->tbl;
     delete S;
     return fcapi::fail(c, FASTCOD_ECUDA, "server initialisation failed");
@@ -706,6 +728,7 @@ FASTCOD_API int fastcod_server_destroy(fastcod_server* S) {
   cudaFreeHost(S->state_pool);
   cudaStreamDestroy(S->compute);
   cudaStreamDestroy(S->copy);
+  cudaMemPoolDestroy(S->pool);  // released once no allocation of it is outstanding
   delete S->tbl;
   delete S;
   return FASTCOD_OK;

@@ -176,7 +176,12 @@ def test_injected_failure_hits_one_request(fc, subjects, monkeypatch, spec, wher
         for _ in range(4):
             r = Req(fc, srv, vA, where)
             for i, (x, o) in enumerate(_chunks(tA, 2)):
-                r.push(fc, srv, x, o, last=(i == 1), where=where)
+                try:
+                    r.push(fc, srv, x, o, last=(i == 1), where=where)
+                except fc.FastCodError as e:
+                    # a request cancelled on submission may already be done
+                    # when its chunks arrive: the push is refused (ESTATE)
+                    assert spec.startswith("cancel") and e.code == fc.FASTCOD_ESTATE
             reqs.append(r)
         got = [fc.fastcod_server_wait(srv, r.id, 120.0) for r in reqs]
         assert sorted(got).count(getattr(fc, status)) == 1, got
