@@ -387,6 +387,26 @@ def served_expected(pool_subjects, block: int, threads: int):
     return out
 
 
+def host_link_gbs(local, nbytes: int = 1 << 30) -> float:
+    """Host-to-device bandwidth of one page-locked copy right now (GB/s): the
+    served latency follows this shared link."""
+    import torch
+    h = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+    d = torch.empty(nbytes, dtype=torch.uint8, device=torch.device("cuda", local))
+    d.copy_(h, non_blocking=True)
+    torch.cuda.synchronize()
+    best = 0.0
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        d.copy_(h, non_blocking=True)
+        e1.record()
+        torch.cuda.synchronize()
+        best = max(best, nbytes / (e0.elapsed_time(e1) / 1000.0) / 1e9)
+    del h, d
+    return best
+
+
 def served_record(args, local) -> dict:
     """Poisson arrivals of HCP-shaped requests (200,000..2,000,000 streamlines in
     250,000-streamline chunks from page-locked host memory) into the served
@@ -462,6 +482,7 @@ def served_record(args, local) -> dict:
 
     for sp in warm:
         assert fc.fastcod_server_wait(srv, submit(sp), 120.0) == fc.FASTCOD_OK
+    link_before = host_link_gbs(local)
     clocks = ClockSampler(local)
     clocks.start()
     launches0 = fc.fastcod_server_kernel_launches(srv)
@@ -488,6 +509,7 @@ def served_record(args, local) -> dict:
         assert fc.fastcod_server_wait(srv, rid, 300.0) == fc.FASTCOD_OK
     sat_s = time.perf_counter() - t0
     n2 = sum(c for (_, _, c, _) in issued[-len(ids2):])
+    link_after = host_link_gbs(local)
     fc.fastcod_server_destroy(srv)
     ctx.close()
     checked, bad = 0, 0
@@ -508,6 +530,10 @@ def served_record(args, local) -> dict:
                        "mean": 1000 * float(lat.mean()), "max": 1000 * float(lat.max())},
         "admission_wait_ms": {"p50": 1000 * float(np.percentile(wait, 50)),
                               "p99": 1000 * float(np.percentile(wait, 99))},
+        "service_ms": {"p50": 1000 * float(np.percentile(lat - wait, 50)),
+                       "p99": 1000 * float(np.percentile(lat - wait, 99))},
+        "host_link_gbs": {"before": link_before, "after": link_after,
+                          "what": "one 1 GiB page-locked host-to-device copy, best of 3"},
         "saturation": {"requests": len(ids2), "subjects_per_s": len(ids2) / sat_s, "streamlines_per_s": n2 / sat_s},
         "bit_exact": ({"requests_checked": checked, "mismatches": bad,
                        "against": "oracle sums of 50,000-streamline blocks of each request's pool subject "
