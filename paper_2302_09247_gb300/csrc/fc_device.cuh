@@ -192,6 +192,70 @@ struct SegWalk {
   }
 };
 
+// The same walk for a segment shorter than one voxel on every axis
+// (|d_a| < 1024, so each axis crosses at most one plane).  The crossing
+// parameters num_a / den_a are brought to the common denominator
+// D = den_x den_y den_z (den = 1 for a still axis): T_a = num_a (D / den_a)
+// and D stay below 2^31, so SegWalk's cross-product comparisons become plain
+// unsigned comparisons of the T_a, and a crossing adds 1024 (D / den_a).  An
+// axis is pending while T_a < lim_a (D + 1 for an increasing axis, D for a
+// decreasing one, 0 for a still one).  Same voxels, same order, same tie
+// rule as SegWalk.
+struct SegShort {
+  int32_t cx, cy, cz;      // current voxel
+  uint32_t tx, ty, tz;     // T_a
+  uint32_t lx, ly, lz;     // pending while T_a < lim_a
+  uint32_t ux, uy, uz;     // 1024 D / den_a
+  int32_t sx, sy, sz;      // direction of each axis (-1, 0, 1)
+
+  __device__ __forceinline__ static void axis(int32_t a0, int32_t a1, int32_t& c, uint32_t& num, uint32_t& den,
+                                              int32_t& sgn) {
+    const int32_t d = a1 - a0;
+    c = a0 >> kUnitLog2;
+    sgn = d > 0 ? 1 : (d < 0 ? -1 : 0);
+    den = d > 0 ? (uint32_t)d : (d < 0 ? (uint32_t)(-d) : 1u);
+    num = d > 0 ? (uint32_t)(((c + 1) << kUnitLog2) - a0) : (d < 0 ? (uint32_t)(a0 - (c << kUnitLog2)) : 0u);
+  }
+
+  __device__ __forceinline__ void init(const int32_t p0[3], const int32_t p1[3]) {
+    uint32_t nx, ny, nz, ex, ey, ez;
+    axis(p0[0], p1[0], cx, nx, ex, sx);
+    axis(p0[1], p1[1], cy, ny, ey, sy);
+    axis(p0[2], p1[2], cz, nz, ez, sz);
+    const uint32_t dyz = ey * ez, dxz = ex * ez, dxy = ex * ey, D = ex * dyz;
+    tx = nx * dyz;
+    ty = ny * dxz;
+    tz = nz * dxy;
+    ux = dyz << kUnitLog2;
+    uy = dxz << kUnitLog2;
+    uz = dxy << kUnitLog2;
+    lx = sx > 0 ? D + 1 : (sx < 0 ? D : 0u);
+    ly = sy > 0 ? D + 1 : (sy < 0 ? D : 0u);
+    lz = sz > 0 ? D + 1 : (sz < 0 ? D : 0u);
+  }
+
+  __device__ __forceinline__ bool step() {
+    const bool q0 = tx < lx, q1 = ty < ly, q2 = tz < lz;
+    if (!(q0 || q1 || q2)) return false;
+    const uint32_t m = min(min(q0 ? tx : 0xffffffffu, q1 ? ty : 0xffffffffu), q2 ? tz : 0xffffffffu);
+    const bool t0 = q0 && tx == m, t1 = q1 && ty == m, t2 = q2 && tz == m;
+    const int32_t want = ((t0 && sx > 0) || (t1 && sy > 0) || (t2 && sz > 0)) ? 1 : -1;
+    if (t0 && sx == want) {
+      cx += want;
+      tx += ux;
+    }
+    if (t1 && sy == want) {
+      cy += want;
+      ty += uy;
+    }
+    if (t2 && sz == want) {
+      cz += want;
+      tz += uz;
+    }
+    return true;
+  }
+};
+
 // ---------------------------------------------------------------------------
 // Per-warp open-addressing set in shared memory (keys >= 0, empty = -1).
 // Lanes holding the same key are merged with __match_any_sync first; the

@@ -172,11 +172,11 @@ __device__ __forceinline__ void flush_voxels(const VolView& v, WalkWarpSmem& sm,
 // segment, its start voxel); the list is flushed into the sets when it
 // fills.  The walk itself has no memory dependence, so a window costs no
 // load latency beyond its vertices.
-template <typename P, typename S>
+template <typename W, typename S>
 __device__ __forceinline__ void walk_window(const VolView& v, WalkWarpSmem& sm, const int32_t p0[3],
                                             const int32_t p1[3], bool has, bool first, bool endpoint_mode,
                                             uint64_t keep, int& nL, int& nV, int& nT, bool& fail, DevState* ck) {
-  SegWalk<P> w;
+  W w;
   bool pend = false;
   if (has) {
     w.init(p0, p1);
@@ -267,12 +267,16 @@ __device__ __forceinline__ int walk_one(const VolView& v, const Tract& t, const 
                               abs((p1[2] >> kUnitLog2) - c0z) <= 1;
         if (shortseg && !walk_all && near_lookup<false>(v, v.near, c0x, c0y, c0z, gst) == 0u) has = false;
       }
-      const bool small = !has || (abs(p1[0] - p0[0]) < 65536 && abs(p1[1] - p0[1]) < 65536 &&
-                                  abs(p1[2] - p0[2]) < 65536);
-      if (__all_sync(kFull, small))
-        walk_window<uint32_t, S>(v, sm, p0, p1, has, j == a, endpoint_mode, keep, nL, nV, nT, fail, gst);
+      // windows whose segments are all shorter than a voxel on every axis
+      // (the common case) take the common-denominator walk; others the
+      // general one with 64-bit cross-products
+      const bool tiny = !has || (abs(p1[0] - p0[0]) < 1024 && abs(p1[1] - p0[1]) < 1024 &&
+                                 abs(p1[2] - p0[2]) < 1024);
+      if (__all_sync(kFull, tiny))
+        walk_window<SegShort, S>(v, sm, p0, p1, has, j == a, endpoint_mode, keep, nL, nV, nT, fail, gst);
       else
-        walk_window<unsigned long long, S>(v, sm, p0, p1, has, j == a, endpoint_mode, keep, nL, nV, nT, fail, gst);
+        walk_window<SegWalk<unsigned long long>, S>(v, sm, p0, p1, has, j == a, endpoint_mode, keep, nL, nV, nT,
+                                                     fail, gst);
       fail = __any_sync(kFull, fail);
 #pragma unroll
       for (int k = 0; k < 3; ++k) cur[k] = nxt[k];
