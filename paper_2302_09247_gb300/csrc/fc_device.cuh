@@ -107,6 +107,21 @@ __device__ __forceinline__ uint32_t near_lookup(const VolView& v, const uint32_t
   return (word >> ((cx & 15u) << 1)) & 3u;
 }
 
+// The same two bits at bits k and k + 1 of the result: the word is rotated
+// right by twice the cell's place (a funnel shift takes the place mod 16 for
+// free), shifted to k and masked, which folds into the caller's OR.
+template <bool kSmem>
+__device__ __forceinline__ uint32_t near_bits_at(const VolView& v, const uint32_t* nw, int32_t vx, int32_t vy,
+                                                 int32_t vz, int k, DevState* ck = nullptr) {
+  const uint32_t cx = min((uint32_t)((vx + 1) >> v.nsh), (uint32_t)v.cmx);
+  const uint32_t cy = min((uint32_t)((vy + 1) >> v.nsh), (uint32_t)v.cmy);
+  const uint32_t cz = min((uint32_t)((vz + 1) >> v.nsh), (uint32_t)v.cmz);
+  const uint32_t w = (cx >> 4) + (uint32_t)v.nwx * (cy + (uint32_t)v.nny * cz);
+  if (!in_bounds(w, near_words(v), ck, kSiteNear)) return 3u << k;  // conservative
+  const uint32_t word = kSmem ? nw[w] : __ldg(nw + w);
+  return (__funnelshift_r(word, word, cx << 1) << k) & (3u << k);
+}
+
 // ---------------------------------------------------------------------------
 // Integer walk of one segment P0 -> P1 (Amanatides & Woo, exact rational
 // events).  For axis a with d_a != 0 the next plane crossing is at

@@ -253,7 +253,7 @@ __device__ __forceinline__ uint32_t scan_piece(Scan& sc, const VolView& v, const
       const uint32_t m = 0u - ((keep8 >> k) & 1u);
       lg |= (ax | ay | az) & m;
       stp += (ax + ay + az) & m;
-      if ((k & 1) == 0) h8 |= near_lookup<kSmem>(v, nw, vx, vy, vz, sc.sst) << k;
+      if ((k & 1) == 0) h8 |= near_bits_at<kSmem>(v, nw, vx, vy, vz, k, sc.sst);
       qx = vx;
       qy = vy;
       qz = vz;

@@ -260,18 +260,22 @@ __device__ __forceinline__ int walk_one(const VolView& v, const Tract& t, const 
       // within Chebyshev distance 1 of its start voxel: when the near grid
       // shows no ROI and no labelled voxel there, it visits nothing that
       // counts and is not walked
+      // (a segment shorter than a voxel on every axis is such a segment;
+      // only longer ones need their end voxels compared)
+      const bool sub = abs(p1[0] - p0[0]) < 1024 && abs(p1[1] - p0[1]) < 1024 && abs(p1[2] - p0[2]) < 1024;
       bool has = j < b - 1;
       if (has) {
         const int32_t c0x = p0[0] >> kUnitLog2, c0y = p0[1] >> kUnitLog2, c0z = p0[2] >> kUnitLog2;
-        const bool shortseg = abs((p1[0] >> kUnitLog2) - c0x) <= 1 && abs((p1[1] >> kUnitLog2) - c0y) <= 1 &&
-                              abs((p1[2] >> kUnitLog2) - c0z) <= 1;
+        bool shortseg = sub;
+        if (!sub)
+          shortseg = abs((p1[0] >> kUnitLog2) - c0x) <= 1 && abs((p1[1] >> kUnitLog2) - c0y) <= 1 &&
+                     abs((p1[2] >> kUnitLog2) - c0z) <= 1;
         if (shortseg && !walk_all && near_lookup<false>(v, v.near, c0x, c0y, c0z, gst) == 0u) has = false;
       }
       // windows whose segments are all shorter than a voxel on every axis
       // (the common case) take the common-denominator walk; others the
       // general one with 64-bit cross-products
-      const bool tiny = !has || (abs(p1[0] - p0[0]) < 1024 && abs(p1[1] - p0[1]) < 1024 &&
-                                 abs(p1[2] - p0[2]) < 1024);
+      const bool tiny = !has || sub;
       if (__all_sync(kFull, tiny))
         walk_window<SegShort, S>(v, sm, p0, p1, has, j == a, endpoint_mode, keep, nL, nV, nT, fail, gst);
       else
