@@ -4,6 +4,7 @@
 // (Section 3, "Super-resolving connectivity features").  All are single
 // streaming passes (HBM-bound); every result is exact or rounds as stated.
 #include "fc_device.cuh"
+#include "fc_tma.cuh"
 
 namespace fc {
 
@@ -150,6 +151,70 @@ __global__ void __launch_bounds__(kThreads) parcellate_rows_kernel(const int32_t
 #pragma unroll
       for (int k = 0; k < kPer; ++k)
         if (lane + 32 * k < M) out[lane + 32 * k] = row_fraction(v[k], sum);
+    }
+  }
+}
+
+// The same for rows whose width M is a multiple of 4 with 16-byte aligned C
+// and fractions: each lane holds kV int4 (entries 128 k + 4 lane + j), one
+// 16-byte load each, and writes its fractions as float4.  The row sum is
+// warp-uniform, so the exact-quotient branch (sum at or above 2^24) is taken
+// once per row instead of once per entry; that branch re-reads the row.
+template <int kV>
+__global__ void __launch_bounds__(kThreads) parcellate_rows_vec_kernel(const int32_t* __restrict__ C, int32_t N,
+                                                                       int32_t M, int32_t* __restrict__ label,
+                                                                       float* __restrict__ frac, DevState* st) {
+  const int32_t lane = (int32_t)lane_id();
+  const int32_t M4 = M >> 2;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < N; r += nwarps) {
+    const int4* row = reinterpret_cast<const int4*>(C + r * M);
+    int4 v[kV];
+#pragma unroll
+    for (int k = 0; k < kV; ++k) v[k] = lane + 32 * k < M4 ? __ldcs(row + lane + 32 * k) : make_int4(0, 0, 0, 0);
+    long long sum = 0;
+    int32_t best = 0, arg = 0x7fffffff, lo = 0;
+#pragma unroll
+    for (int k = 0; k < kV; ++k) {
+      const int32_t e[4] = {v[k].x, v[k].y, v[k].z, v[k].w};
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        sum += e[j];
+        lo = min(lo, e[j]);
+        if (e[j] > best) {  // ascending t per lane: the first maximum stays
+          best = e[j];
+          arg = 128 * k + 4 * lane + j;
+        }
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const int32_t ob = __shfl_xor_sync(kFull, best, o), oa = __shfl_xor_sync(kFull, arg, o);
+      if (ob > best || (ob == best && oa < arg)) {
+        best = ob;
+        arg = oa;
+      }
+      sum += __shfl_xor_sync(kFull, sum, o);
+    }
+    if (st && __any_sync(kFull, lo < 0) && lane == 0) set_error(st, kErrCount, (int32_t)r);
+    if (lane == 0) label[r] = best > 0 ? arg + 1 : 0;
+    if (!frac) continue;
+    float4* out = reinterpret_cast<float4*>(frac + r * M);
+    if (sum < (1ll << 24)) {  // both integers exact in binary32: one IEEE division each
+      const float fs = (float)sum;
+#pragma unroll
+      for (int k = 0; k < kV; ++k)
+        if (lane + 32 * k < M4) {
+          float4 f;
+          f.x = sum > 0 ? __fdiv_rn((float)v[k].x, fs) : 0.0f;
+          f.y = sum > 0 ? __fdiv_rn((float)v[k].y, fs) : 0.0f;
+          f.z = sum > 0 ? __fdiv_rn((float)v[k].z, fs) : 0.0f;
+          f.w = sum > 0 ? __fdiv_rn((float)v[k].w, fs) : 0.0f;
+          __stcs(out + lane + 32 * k, f);
+        }
+    } else {  // rare: read the row again rather than hold the exact rule's registers across it
+      const int32_t* row32 = C + r * M;
+      for (int32_t t = lane; t < M; t += 32) frac[r * M + t] = row_fraction(__ldg(row32 + t), sum);
     }
   }
 }
@@ -436,6 +501,75 @@ __global__ void __launch_bounds__(kThreads) upsample_kernel(const int32_t* __res
   }
 }
 
+// Upsampled vertices for a power-of-two factor 2^L: warp per streamline.
+// The warp stages up to kStageV of the streamline's vertices in shared
+// memory (coalesced loads, all in flight at once), then each lane computes
+// output words: word k of the chunk's output is axis c = k mod 3 of point
+// P = k / 3, on the chunk's segment i = P >> L at j = P & (2^L - 1):
+// x_i[c] + floor((x_{i+1}[c] - x_i[c]) j / 2^L), an arithmetic shift of a
+// 64-bit product.  Chunks overlap by one vertex (the end of their last
+// segment); the streamline's last chunk adds its last point, P = n << L for
+// n + 1 staged vertices, which is j = 0 at the last vertex.  Stores are one
+// coalesced word per lane.  While a streamline is written, the next one's
+// vertices are requested into L2 with one bulk prefetch, so that its staging
+// loads hit L2.
+constexpr int kStageV = 256;  // vertices staged per warp (3 KB)
+
+__global__ void __launch_bounds__(kThreads) upsample_pow2_kernel(const int32_t* __restrict__ xyz,
+                                                                 const int64_t* __restrict__ off, int64_t ns,
+                                                                 int32_t flog2, const int64_t* __restrict__ out_off,
+                                                                 int32_t* __restrict__ out) {
+  __shared__ int32_t stage[kThreads / 32][3 * kStageV];
+  int32_t* sv = stage[threadIdx.x >> 5];
+  const int32_t lane = (int32_t)lane_id();
+  const uint32_t jmask = (1u << flog2) - 1u;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t s0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int64_t a = 0, b = 0, o = 0;
+  if (s0 < ns) {
+    a = off[s0];
+    b = off[s0 + 1];
+    o = out_off[s0];
+  }
+  for (int64_t s = s0; s < ns; s += nwarps) {
+    int64_t an = 0, bn = 0, on = 0;  // the next streamline's offsets, in flight
+    if (s + nwarps < ns) {
+      an = off[s + nwarps];
+      bn = off[s + nwarps + 1];
+      on = out_off[s + nwarps];
+    }
+    if (lane == 0 && bn > an) {  // the next streamline's vertices, 16-byte aligned inside
+      const uintptr_t lo = (reinterpret_cast<uintptr_t>(xyz + 3 * an) + 15) & ~(uintptr_t)15;
+      const uintptr_t hi = reinterpret_cast<uintptr_t>(xyz + 3 * bn) & ~(uintptr_t)15;
+      if (hi > lo) bulk_prefetch_l2(reinterpret_cast<const void*>(lo), (uint32_t)min(hi - lo, (uintptr_t)0x7ffffff0u));
+    }
+    const int64_t T = b - a;
+    for (int64_t c0 = 0; c0 < T; c0 += kStageV - 1) {
+      const int32_t nvc = (int32_t)min((int64_t)kStageV, T - c0);  // staged vertices
+      const bool last = c0 + nvc == T;
+      const int32_t* src = xyz + 3 * (a + c0);
+      __syncwarp();
+      const int32_t nwd = 3 * nvc;
+#pragma unroll 4
+      for (int32_t w = lane; w < nwd; w += 32) sv[w] = __ldg(src + w);
+      __syncwarp();
+      const uint32_t nout = 3u * (((uint32_t)(nvc - 1) << flog2) + (last ? 1u : 0u));  // words
+      int32_t* dst = out + 3 * (o + (c0 << flog2));
+      for (uint32_t k = (uint32_t)lane; k < nout; k += 32) {
+        const uint32_t P = k / 3u, c = k - 3u * P, i = P >> flog2, jj = P & jmask;
+        const int32_t x0 = sv[3 * i + c];
+        const int32_t x1 = jj ? sv[3 * i + 3 + c] : x0;
+        const long long dv = (long long)x1 - x0;
+        __stcs(dst + k, (int32_t)((uint32_t)x0 + (uint32_t)((dv * jj) >> flog2)));
+      }
+      if (last) break;
+    }
+    a = an;
+    b = bn;
+    o = on;
+  }
+}
+
 // Offsets [ns + 1] start at 0, do not decrease and end at nv.
 __global__ void __launch_bounds__(kThreads) check_offsets_kernel(const int64_t* __restrict__ off, int64_t ns,
                                                                  int64_t nv, DevState* st) {
@@ -473,7 +607,13 @@ cudaError_t launch_parcellate(const int32_t* C, int32_t N, int32_t M, int32_t* l
                               cudaStream_t s) {
   if (N <= 0) return cudaSuccess;
   const int g = grid_for((int64_t)N * 32);
-  if (M <= 32) parcellate_rows_kernel<1><<<g, kThreads, 0, s>>>(C, N, M, label, frac, st);
+  const bool vec = M % 4 == 0 && ((uintptr_t)C % 16 == 0) && (!frac || (uintptr_t)frac % 16 == 0);
+  if (vec && M <= 512) {
+    const auto k = M <= 128 ? parcellate_rows_vec_kernel<1>
+                   : M <= 256 ? parcellate_rows_vec_kernel<2>
+                   : M <= 384 ? parcellate_rows_vec_kernel<3> : parcellate_rows_vec_kernel<4>;
+    k<<<g, kThreads, 0, s>>>(C, N, M, label, frac, st);
+  } else if (M <= 32) parcellate_rows_kernel<1><<<g, kThreads, 0, s>>>(C, N, M, label, frac, st);
   else if (M <= 64) parcellate_rows_kernel<2><<<g, kThreads, 0, s>>>(C, N, M, label, frac, st);
   else if (M <= 128) parcellate_rows_kernel<4><<<g, kThreads, 0, s>>>(C, N, M, label, frac, st);
   else if (M <= 256) parcellate_rows_kernel<8><<<g, kThreads, 0, s>>>(C, N, M, label, frac, st);
@@ -518,7 +658,8 @@ cudaError_t launch_upsample_vertices(const int32_t* xyz, const int64_t* off, int
                                      const int64_t* out_off, int32_t* out, cudaStream_t s) {
   if (ns <= 0) return cudaSuccess;
   const int32_t flog2 = (factor & (factor - 1)) == 0 ? __builtin_ctz((unsigned)factor) : -1;
-  upsample_kernel<<<grid_for(ns * 32, 8), kThreads, 0, s>>>(xyz, off, ns, factor, flog2, out_off, out);
+  if (flog2 >= 0 && flog2 <= 20) upsample_pow2_kernel<<<grid_for(ns * 32, 8), kThreads, 0, s>>>(xyz, off, ns, flog2, out_off, out);
+  else upsample_kernel<<<grid_for(ns * 32, 8), kThreads, 0, s>>>(xyz, off, ns, factor, flog2, out_off, out);
   return cudaGetLastError();
 }
 

@@ -59,11 +59,13 @@ def test_parcellate_matches_oracle(fc, where):
                 np.testing.assert_array_equal(label2, lr)
 
 
-@pytest.mark.parametrize("n_labels", [31, 64, 100, 250, 360, 512, 600])
+@pytest.mark.parametrize("n_labels", [31, 50, 64, 70, 100, 200, 250, 360, 361, 512, 600])
 def test_parcellate_row_widths(fc, n_labels):
-    # every width class of the parcellation kernels (rows held in 1, 2, 4, 8
-    # or 16 registers per lane, and the looping form past 512 labels), with
-    # many-to-one ROI maps so that rows collect large counts and ties
+    # every width class of the parcellation kernels: widths that are a
+    # multiple of 4 read rows as int4 (1 to 4 per lane: 64, 100, 200, 360,
+    # 512), the others hold 1, 2, 4, 8 or 16 entries per lane (31, 50, 70,
+    # 250, 361), and the looping form past 512 labels; many-to-one ROI maps
+    # so that rows collect large counts and ties
     rng = np.random.default_rng(n_labels)
     dims = (24, 20, 18)
     roi, lab, N, M = tiny.random_volumes(rng, dims, n_roi=40, n_labels=n_labels, p_roi=0.3, p_lab=0.6,
@@ -82,15 +84,17 @@ def test_parcellate_row_widths(fc, n_labels):
             np.testing.assert_array_equal(frac.view(np.uint32), fr.view(np.uint32))
 
 
-@pytest.mark.parametrize("M", [2, 70, 600])
-@pytest.mark.parametrize("where", ["host", "device"])
+@pytest.mark.parametrize("M", [2, 64, 70, 360, 600])
+@pytest.mark.parametrize("where", ["host", "device", "device_unaligned"])
 def test_parcellate_matrix_midpoints(fc, M, where):
     # a caller's matrix whose fractions lie on or 2^-55 beside binary32
     # midpoints (row sums 2^25..2^37), the rows where a binary64 quotient
     # rounded again to binary32 is one unit off, and small rows between them;
-    # M = 2 / 70 / 600 runs the one-register, four-register and looping kernels
+    # M = 2 / 70 / 600 run the one-register, four-register and looping
+    # kernels, M = 64 / 360 the int4 kernels (one and three int4 per lane),
+    # and with device buffers 4 bytes off a 16-byte boundary the scalar ones
     import torch
-    k_max = {2: 0, 70: 5, 600: 7}[M]
+    k_max = {2: 0, 64: 5, 70: 5, 360: 6, 600: 7}[M]
     rows, _ = midpoint_rows(17 + M, 300, k_max=k_max)
     rows = [r for r in rows if len(r) <= M] + DOUBLE_ROUNDING_ROWS
     rng = np.random.default_rng(M)
@@ -107,10 +111,19 @@ def test_parcellate_matrix_midpoints(fc, M, where):
                 label = np.full(N, -5, np.int32)
                 frac = np.full((N, M), -1, np.float32)
                 fc.fastcod_parcellate_matrix(ctx.ctx, C32, label, frac)
-            else:
+            elif where == "device":
                 lt = torch.full((N,), -5, dtype=torch.int32, device="cuda:0")
                 ft = torch.full((N, M), -1.0, dtype=torch.float32, device="cuda:0")
                 fc.fastcod_parcellate_matrix(ctx.ctx, torch.from_numpy(C32).cuda(), lt, ft)
+                label, frac = lt.cpu().numpy(), ft.cpu().numpy()
+            else:
+                lt = torch.full((N,), -5, dtype=torch.int32, device="cuda:0")
+                fb = torch.full((N * M + 1,), -1.0, dtype=torch.float32, device="cuda:0")
+                cb = torch.zeros(N * M + 1, dtype=torch.int32, device="cuda:0")
+                cb[1:] = torch.from_numpy(C32.reshape(-1)).cuda()
+                ft, ct = fb[1:].view(N, M), cb[1:].view(N, M)
+                assert ft.data_ptr() % 16 != 0 and ct.data_ptr() % 16 != 0
+                fc.fastcod_parcellate_matrix(ctx.ctx, ct, lt, ft)
                 label, frac = lt.cpu().numpy(), ft.cpu().numpy()
             np.testing.assert_array_equal(label, lr)
             np.testing.assert_array_equal(frac.view(np.uint32), fr.view(np.uint32))  # bit-exact
@@ -182,7 +195,7 @@ def test_add_streamlines_mm_equals_fixed_point_path(fc):
     assert st["voxel_steps"] == 2 * sr["voxel_steps"]
 
 
-@pytest.mark.parametrize("factor", [1, 2, 5])
+@pytest.mark.parametrize("factor", [1, 2, 4, 5, 8])
 @pytest.mark.parametrize("where", ["host", "device"])
 def test_upsample_matches_oracle(fc, factor, where):
     import torch
@@ -209,6 +222,30 @@ def test_upsample_matches_oracle(fc, factor, where):
         bad[5], bad[6] = bad[6] + 1, bad[5]
         with pytest.raises(fc.FastCodError):  # invalid offsets
             fc.fastcod_upsample(ctx.ctx, xyz, bad, factor, out, oo)
+
+
+@pytest.mark.parametrize("factor", [1, 2, 3, 16, 300, 1024])
+def test_upsample_wide_coordinates(fc, factor):
+    # vertices anywhere in int32 (differences up to 2^32 - 1, products d j
+    # up to 2^42), streamline lengths 0..12 and 255..600 (one, two
+    # and three chunks of the power-of-two kernel's 256 staged vertices):
+    # power-of-two factors run the word-per-lane kernel, the others the
+    # segment-per-lane one (300 past its staging capacity)
+    import torch
+    rng = np.random.default_rng(900 + factor)
+    T = rng.integers(0, 13, size=200)
+    T[:8] = [0, 1, 2, 0, 255, 256, 257, 600]
+    off = np.concatenate([[0], np.cumsum(T)]).astype(np.int64)
+    xyz = rng.integers(-2 ** 31, 2 ** 31, size=(int(off[-1]), 3), dtype=np.int64).astype(np.int32)
+    xyz[:6] = [[-2 ** 31, 2 ** 31 - 1, 0], [2 ** 31 - 1, -2 ** 31, -1]] * 3
+    want_xyz, want_off = oracle.upsample(xyz, off, factor)
+    nv_out = fc.upsampled_count(off, factor)
+    with fc.Context(0) as ctx:
+        ot = torch.full((nv_out, 3), -9, dtype=torch.int32, device="cuda:0")
+        oot = torch.full((len(off),), -9, dtype=torch.int64, device="cuda:0")
+        fc.fastcod_upsample(ctx.ctx, as_device(xyz), as_device(off), factor, ot, oot)
+        np.testing.assert_array_equal(oot.cpu().numpy(), want_off)
+        np.testing.assert_array_equal(ot.cpu().numpy(), want_xyz)
 
 
 def test_upsample_factor_matches_oracle(fc):
