@@ -107,19 +107,22 @@ __device__ __forceinline__ uint32_t near_lookup(const VolView& v, const uint32_t
   return (word >> ((cx & 15u) << 1)) & 3u;
 }
 
-// The same two bits at bits k and k + 1 of the result: the word is rotated
-// right by twice the cell's place (a funnel shift takes the place mod 16 for
-// free), shifted to k and masked, which folds into the caller's OR.
+// The same two bits at bits k and k + 1 of the result (k even), for the
+// prefilter.  No per-axis clamp: for a voxel of the grown grid the index is
+// the cell's, and for any other voxel the true bits are zero (no voxel within
+// distance 1 lies in the grid), so whatever word the unclamped index reaches
+// is conservative; only the word index itself is held inside the array.  The
+// word is rotated right by twice the cell's place less k (a funnel shift
+// takes the amount mod 32), which leaves the cell's bits at k and k + 1.
 template <bool kSmem>
 __device__ __forceinline__ uint32_t near_bits_at(const VolView& v, const uint32_t* nw, int32_t vx, int32_t vy,
                                                  int32_t vz, int k, DevState* ck = nullptr) {
-  const uint32_t cx = min((uint32_t)((vx + 1) >> v.nsh), (uint32_t)v.cmx);
-  const uint32_t cy = min((uint32_t)((vy + 1) >> v.nsh), (uint32_t)v.cmy);
-  const uint32_t cz = min((uint32_t)((vz + 1) >> v.nsh), (uint32_t)v.cmz);
-  const uint32_t w = (cx >> 4) + (uint32_t)v.nwx * (cy + (uint32_t)v.nny * cz);
+  const int32_t cx = (vx + 1) >> v.nsh, cy = (vy + 1) >> v.nsh, cz = (vz + 1) >> v.nsh;
+  const uint32_t nwm = (uint32_t)near_words(v) - 1u;
+  const uint32_t w = min((uint32_t)(cx >> 4) + (uint32_t)v.nwx * ((uint32_t)cy + (uint32_t)v.nny * (uint32_t)cz), nwm);
   if (!in_bounds(w, near_words(v), ck, kSiteNear)) return 3u << k;  // conservative
   const uint32_t word = kSmem ? nw[w] : __ldg(nw + w);
-  return (__funnelshift_r(word, word, cx << 1) << k) & (3u << k);
+  return __funnelshift_r(word, word, ((uint32_t)cx << 1) - (uint32_t)k) & (3u << k);
 }
 
 // ---------------------------------------------------------------------------

@@ -27,42 +27,68 @@ __global__ void __launch_bounds__(256) volume_max_kernel(const int32_t* __restri
   }
 }
 
-// One thread per voxel in blocks of 8 rows x 32 voxels: a warp covers 32
-// consecutive voxels of a row (x aligned to 32), so the warp's ballots are
-// the row's ROI / label bit-plane words (planes: two planes of Dy*Dz rows of
-// ceil(Dx/32) words).  A warp's 32 voxels touch at most two brick words: their
-// bits are ORed across the warp and set with one atomic per word.  The grid's
-// x blocks run along x; its y and z blocks together number the (8-row group,
-// plane) pairs, ryb = ceil(Dy/8) groups per plane, so that Dy and Dz are
+// Blocks of 8 rows x 32 voxels: a warp covers 32 consecutive voxels of a row
+// (x aligned to 32) in kPrepZ consecutive planes (z aligned to kPrepZ, one
+// brick deep), one thread per (x, y) column; the thread issues the loads of
+// all its planes before it uses any, so that a warp has kPrepZ row pairs in
+// flight.  The warp's ballots are the rows' ROI / label bit-plane words
+// (planes: two planes of Dy*Dz rows of ceil(Dx/32) words).  The warp's
+// voxels touch at most two brick words: their bits, ORed over the planes and
+// across the warp, are set with one atomic per word.  The grid's x blocks run
+// along x; its y and z blocks together number the (8-row group, plane group)
+// pairs, ryb = ceil(Dy/8) row groups per plane group, so that Dy and Dz are
 // bounded only by the voxel count.
 constexpr int kPrepRows = 8;
+constexpr int kPrepZ = 1 << kBrickLog2;
 
-// The voxels of x block xb and 8-row group yb of plane z.
+__host__ __device__ __forceinline__ int32_t plane_groups(const VolView& v) { return (v.dz + kPrepZ - 1) / kPrepZ; }
+
+// The voxels of x block xb, 8-row group yb and plane group zq.
 __device__ __forceinline__ void prep_block(const int32_t* __restrict__ roi, const uint16_t* __restrict__ lab,
                                            const VolView& v, uint32_t* __restrict__ code,
                                            uint16_t* __restrict__ lab_out, uint32_t* __restrict__ bricks,
                                            uint32_t* __restrict__ planes, DevState* st, int32_t xb, int32_t yb,
-                                           int32_t z) {
+                                           int32_t zq) {
   const int32_t lane = (int32_t)threadIdx.x;
   const int32_t x = xb * 32 + lane, y = yb * kPrepRows + threadIdx.y;
   if (y >= v.dy) return;  // whole warps: y is the same for the warp's 32 lanes
   const bool in = x < v.dx;
-  const int32_t i = x + v.dx * (y + v.dy * z);
-  int32_t r = -1, l = 0;
-  if (in) {
-    r = roi[i];
-    l = (int32_t)lab[i];
-    if (r < -1 || r >= v.n_roi || l > v.n_lab) {
-      set_error(st, kErrVolume, i);
-      r = -1;
-      l = 0;
+  const int32_t z0 = zq * kPrepZ, nz = min(kPrepZ, v.dz - z0);
+  const int64_t plane = (int64_t)v.dx * v.dy;
+  const int64_t i0 = x + v.dx * ((int64_t)y + (int64_t)v.dy * z0);
+  int32_t r[kPrepZ], l[kPrepZ];
+#pragma unroll
+  for (int k = 0; k < kPrepZ; ++k) {
+    const bool ok = in && k < nz;
+    r[k] = ok ? roi[i0 + k * plane] : -1;
+    l[k] = ok ? (int32_t)lab[i0 + k * plane] : 0;
+  }
+  uint32_t bits = 0u;
+  const int32_t wb = (v.dx + 31) >> 5;
+  const int64_t rows = (int64_t)v.dy * v.dz;
+#pragma unroll
+  for (int k = 0; k < kPrepZ; ++k) {
+    if (in && k < nz) {
+      if (r[k] < -1 || r[k] >= v.n_roi || l[k] > v.n_lab) {
+        set_error(st, kErrVolume, (int32_t)(i0 + k * plane));
+        r[k] = -1;
+        l[k] = 0;
+      }
+      code[i0 + k * plane] =
+          r[k] >= 0 ? (kCodeRoi | (l[k] > 0 ? kCodeRoiLabelled : 0u) | (uint32_t)r[k]) : (uint32_t)l[k];
+      lab_out[i0 + k * plane] = (uint16_t)l[k];
     }
-    code[i] = r >= 0 ? (kCodeRoi | (l > 0 ? kCodeRoiLabelled : 0u) | (uint32_t)r) : (uint32_t)l;
-    lab_out[i] = (uint16_t)l;
+    bits |= (r[k] >= 0 ? 1u : 0u) | (l[k] > 0 ? 2u : 0u);
+    const uint32_t mr = __ballot_sync(kFull, r[k] >= 0);
+    const uint32_t mt = __ballot_sync(kFull, l[k] > 0);
+    if (lane == 0 && k < nz) {
+      const int64_t row = (int64_t)y + (int64_t)v.dy * (z0 + k);
+      planes[row * wb + xb] = mr;
+      planes[(rows + row) * wb + xb] = mt;
+    }
   }
   // brick bits: lanes of the warp's first brick word, then of its second
-  const uint32_t bits = (r >= 0 ? 1u : 0u) | (l > 0 ? 2u : 0u);
-  const int32_t b = ((in ? x : xb * 32) >> kBrickLog2) + v.bx * ((y >> kBrickLog2) + v.by * (z >> kBrickLog2));
+  const int32_t b = ((in ? x : xb * 32) >> kBrickLog2) + v.bx * ((y >> kBrickLog2) + v.by * zq);
   const int32_t wi = b >> 4;
   const uint32_t val = bits << ((b & 15) * 2);
   // the in-range lanes are a prefix of the warp and their words do not
@@ -73,18 +99,9 @@ __device__ __forceinline__ void prep_block(const int32_t* __restrict__ roi, cons
   const uint32_t oB = __reduce_or_sync(kFull, wi != wA ? val : 0u);
   if (lane == 0 && oA) atomicOr(bricks + wA, oA);
   if (lane == 0 && oB) atomicOr(bricks + wB, oB);
-  const uint32_t mr = __ballot_sync(kFull, r >= 0);
-  const uint32_t mt = __ballot_sync(kFull, l > 0);
-  if (lane == 0) {
-    const int32_t wb = (v.dx + 31) >> 5;
-    const int64_t row = (int64_t)y + (int64_t)v.dy * z;
-    const int64_t rows = (int64_t)v.dy * v.dz;
-    planes[row * wb + xb] = mr;
-    planes[(rows + row) * wb + xb] = mt;
-  }
 }
 
-__device__ __forceinline__ int32_t row_groups(const VolView& v) { return (v.dy + kPrepRows - 1) / kPrepRows; }
+__host__ __device__ __forceinline__ int32_t row_groups(const VolView& v) { return (v.dy + kPrepRows - 1) / kPrepRows; }
 
 __global__ void __launch_bounds__(32 * kPrepRows) volume_prep_kernel(const int32_t* __restrict__ roi,
                                                                      const uint16_t* __restrict__ lab, VolView v,
@@ -92,11 +109,12 @@ __global__ void __launch_bounds__(32 * kPrepRows) volume_prep_kernel(const int32
                                                                      uint16_t* __restrict__ lab_out,
                                                                      uint32_t* __restrict__ bricks,
                                                                      uint32_t* __restrict__ planes, DevState* st) {
-  const int64_t g = (int64_t)blockIdx.z * gridDim.y + blockIdx.y;  // (row group, plane) pair
+  const int64_t g = (int64_t)blockIdx.z * gridDim.y + blockIdx.y;  // (row group, plane group) pair
   const int32_t ryb = row_groups(v);
-  if (g >= (int64_t)ryb * v.dz) return;  // whole blocks
-  const int32_t z = (int32_t)(g / ryb);
-  prep_block(roi, lab, v, code, lab_out, bricks, planes, st, (int32_t)blockIdx.x, (int32_t)(g - (int64_t)z * ryb), z);
+  if (g >= (int64_t)ryb * plane_groups(v)) return;  // whole blocks
+  const int32_t zq = (int32_t)(g / ryb);
+  prep_block(roi, lab, v, code, lab_out, bricks, planes, st, (int32_t)blockIdx.x, (int32_t)(g - (int64_t)zq * ryb),
+             zq);
 }
 
 // The subject of batch block b: the last one whose first block is <= b.
@@ -112,7 +130,7 @@ __device__ __forceinline__ int32_t subject_of(const PrepTable& tbl, int64_t b) {
 }
 
 // Every subject of a batch in one launch: block b of subject i's
-// ceil(Dx/32) * ceil(Dy/8) * Dz blocks, x blocks fastest.
+// ceil(Dx/32) * ceil(Dy/8) * ceil(Dz/kPrepZ) blocks, x blocks fastest.
 __global__ void __launch_bounds__(32 * kPrepRows) volume_prep_batch_kernel(const __grid_constant__ PrepTable tbl) {
   const int64_t b = blockIdx.x;
   const PrepSubject& S = tbl.s[subject_of<false>(tbl, b)];
@@ -120,10 +138,10 @@ __global__ void __launch_bounds__(32 * kPrepRows) volume_prep_batch_kernel(const
   const int64_t local = b - S.prep_blk0;
   const int32_t nxb = (v.dx + 31) / 32, ryb = row_groups(v);
   const int64_t g = local / nxb;
-  const int32_t z = (int32_t)(g / ryb);
+  const int32_t zq = (int32_t)(g / ryb);
   prep_block(S.roi, S.lab, v, const_cast<uint32_t*>(v.code), const_cast<uint16_t*>(v.lab),
              const_cast<uint32_t*>(v.bricks), S.planes, S.st, (int32_t)(local - g * nxb),
-             (int32_t)(g - (int64_t)z * ryb), z);
+             (int32_t)(g - (int64_t)zq * ryb), zq);
 }
 
 // ---------------------------------------------------------------- near grid
@@ -213,7 +231,7 @@ cudaError_t launch_volume_prep(const int32_t* roi, const uint16_t* lab, int64_t 
                                uint32_t* code, uint16_t* lab_out, uint32_t* bricks, uint32_t* planes, DevState* st,
                                cudaStream_t s) {
   (void)nvox;
-  const int64_t groups = (int64_t)((v.dy + kPrepRows - 1) / kPrepRows) * v.dz;  // < 2^31 / 8
+  const int64_t groups = (int64_t)row_groups(v) * plane_groups(v);  // < 2^31 / 32
   const int64_t gy = groups < 65535 ? groups : 65535;
   const int64_t gz = (groups + gy - 1) / gy;
   volume_prep_kernel<<<dim3((v.dx + 31) / 32, (unsigned)gy, (unsigned)gz), dim3(32, kPrepRows), 0, s>>>(
@@ -237,7 +255,7 @@ void prep_table_blocks(PrepTable& tbl) {
     PrepSubject& S = tbl.s[i];
     S.prep_blk0 = pb;
     S.near_blk0 = nb;
-    pb += (int64_t)((S.v.dx + 31) / 32) * ((S.v.dy + kPrepRows - 1) / kPrepRows) * S.v.dz;
+    pb += (int64_t)((S.v.dx + 31) / 32) * row_groups(S.v) * plane_groups(S.v);
     nb += ((int64_t)S.v.nwx * S.v.nny * S.v.nnz + 255) / 256;
   }
   tbl.prep_blocks = pb;

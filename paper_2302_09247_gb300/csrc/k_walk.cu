@@ -236,25 +236,18 @@ __device__ __forceinline__ int walk_one(const VolView& v, const Tract& t, const 
       fail = __any_sync(kFull, fail);
     }
   } else {
-    // window i0 holds segments a+i0+lane -> a+i0+lane+1; the vertices of the
-    // next window are loaded while this one is walked
     int nL = 0;
-    int32_t cur[3] = {0, 0, 0};
-    if (a + lane < b) load_vertex(t.xyz, a + lane, cur);
     for (int64_t i0 = 0; i0 < T - 1 && !fail; i0 += 32) {
       if (nL > kLin - 96) {  // room for three voxels a lane
         flush_voxels<S, true>(v, sm, nL, endpoint_mode, keep, nV, nT, fail, gst);
         if (__any_sync(kFull, fail)) break;
       }
       const int64_t j = a + i0 + lane;
-      int32_t nxt[3] = {0, 0, 0};
-      if (j + 32 < b) load_vertex(t.xyz, j + 32, nxt);
-      int32_t p0[3] = {cur[0], cur[1], cur[2]}, p1[3];
-#pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        const int32_t dn = __shfl_down_sync(kFull, p0[k], 1);
-        const int32_t wrap = __shfl_sync(kFull, nxt[k], 0);
-        p1[k] = lane == 31 ? wrap : dn;
+      if (j + 32 < b) prefetch_l1(t.xyz + 3 * (j + 32));
+      int32_t p0[3] = {0, 0, 0}, p1[3] = {0, 0, 0};
+      if (j < b - 1) {
+        load_vertex(t.xyz, j, p0);
+        load_vertex(t.xyz, j + 1, p1);
       }
       // a segment whose end voxels differ by at most one on every axis stays
       // within Chebyshev distance 1 of its start voxel: when the near grid
@@ -282,8 +275,6 @@ __device__ __forceinline__ int walk_one(const VolView& v, const Tract& t, const 
         walk_window<SegWalk<unsigned long long>, S>(v, sm, p0, p1, has, j == a, endpoint_mode, keep, nL, nV, nT,
                                                      fail, gst);
       fail = __any_sync(kFull, fail);
-#pragma unroll
-      for (int k = 0; k < 3; ++k) cur[k] = nxt[k];
     }
     if (nL > 0 && !fail) flush_voxels<S, true>(v, sm, nL, endpoint_mode, keep, nV, nT, fail, gst);
     fail = __any_sync(kFull, fail);
