@@ -232,9 +232,12 @@ FASTCOD_API int fastcod_set_option(fastcod_ctx* ctx, int32_t key, int64_t value)
  * whole sequence captured once per batch shape as a CUDA graph and replayed.
  * Each subject's C and C_end are computed from zero, exactly as
  * fastcod_set_volumes + fastcod_add_streamlines would, and written to its
- * caller-allocated outputs.  Pointers follow the same host/device rules as
- * the single-subject calls.  The context's installed volumes and
- * accumulators are not touched. */
+ * caller-allocated outputs: outputs in device memory of the context's GPU
+ * are zeroed and accumulated in place by the pass (so no output may overlap
+ * another subject's outputs or any input of the batch), others are copied
+ * out after it.  Pointers follow the same host/device rules as the
+ * single-subject calls.  The context's installed volumes and accumulators
+ * are not touched. */
 typedef struct {
   const int32_t* roi_index_map;   /* [Dz][Dy][Dx], -1 or a row < n_roi */
   const uint16_t* target_labels;  /* [Dz][Dy][Dx], 0 or a label <= n_targets */

@@ -36,11 +36,11 @@ int64_t tasks_of(int64_t n_vertices, int task_log2) {
 
 // Sub-allocation of the batch arena (byte offsets, 256-byte aligned).
 struct Layout {
-  size_t scratch, gstate, states, tasks, surv, ovf, staged_end;
+  size_t scratch, gstate, states, surv, ovf, staged_end;
   int64_t surv_cap;  // entries of the survivor and overflow lists
   std::vector<size_t> roi_in, lab_in, xyz_in, off_in;  // staging of host inputs (or SIZE_MAX)
   std::vector<size_t> code, lab, bricks, C, Cend, planes;
-  size_t acc_lo, acc_hi;        // every subject's C and C_end: one span, zeroed by one memset
+  size_t acc_lo, acc_hi;        // every subject's C and C_end in the arena (used for outputs in host memory)
   size_t bricks_lo, bricks_hi;  // every subject's brick words: one span
   std::vector<size_t> near;
   size_t total;
@@ -58,6 +58,8 @@ struct BatchState {
   cudaGraphExec_t exec = nullptr;
   std::vector<DevState> states;
   std::vector<int64_t> ns, nv;  // per subject of the last batch
+  std::vector<char> out_dev;    // per subject: C_out and Cend_out are device memory of this device, and the
+                                // walk accumulates into them in place
   std::map<uint64_t, BatchConfig> tuned;
   bool cache_loaded = false;
   fastcod_batch_info info{};
@@ -146,11 +148,10 @@ Layout plan(const fastcod_subject* subs, int32_t n, const std::vector<int>& host
   }
   L.bricks_hi = o;
   (void)maxplanes;
-  // the configuration-dependent part last (near grids: the cell size; tasks:
-  // the work granularity), so that the rest, staged inputs included, keeps
-  // its place from one configuration to the next
+  // the configuration-dependent part last (near grids: the cell size), so
+  // that the rest, staged inputs included, keeps its place from one
+  // configuration to the next
   for (int32_t i = 0; i < n; ++i) L.near.push_back(take((size_t)near_words(subs[i].dims, near_log2) * 4));
-  L.tasks = take(sizeof(fc::BatchTask) * ntasks);
   L.total = o;
   return L;
 }
@@ -161,12 +162,12 @@ T* at(void* base, size_t off) {
 }
 
 void fill_table(fastcod_ctx* c, const fastcod_subject* subs, int32_t n, const Layout& L, int near_log2, int task_log2,
-                fc::BatchTable& tbl, std::vector<fc::BatchTask>& tasks) {
+                fc::BatchTable& tbl) {
   void* A = c->batch->arena;
+  const std::vector<char>& out_dev = c->batch->out_dev;
   memset(&tbl, 0, sizeof tbl);
   tbl.n = n;
-  tasks.clear();
-  int64_t sbase = 0;
+  int64_t sbase = 0, task0 = 0;
   for (int32_t i = 0; i < n; ++i) {
     const fastcod_subject& S = subs[i];
     fc::BatchSubject& B = tbl.s[i];
@@ -188,20 +189,17 @@ void fill_table(fastcod_ctx* c, const fastcod_subject* subs, int32_t n, const La
     B.t.off = L.off_in[i] != SIZE_MAX ? at<int64_t>(A, L.off_in[i]) : S.offsets;
     B.t.nv = S.n_vertices;
     B.t.ns = S.n_streamlines;
-    B.acc.C = at<int32_t>(A, L.C[i]);
-    B.acc.Cend = at<int32_t>(A, L.Cend[i]);
+    // device outputs are accumulated in place; host ones in the arena, copied
+    // out after the graph
+    B.acc.C = out_dev[i] ? S.C_out : at<int32_t>(A, L.C[i]);
+    B.acc.Cend = out_dev[i] ? S.Cend_out : at<int32_t>(A, L.Cend[i]);
     B.st = at<DevState>(A, L.states) + i;
     B.sbase = sbase;
     sbase += S.n_streamlines;
-    const int64_t k = tasks_of(S.n_vertices, task_log2);
-    for (int64_t j = 0; j < k; ++j) {
-      fc::BatchTask t;
-      t.subject = i;
-      t.pad = 0;
-      t.s_lo = S.n_streamlines * j / k;
-      t.s_hi = S.n_streamlines * (j + 1) / k;
-      tasks.push_back(t);
-    }
+    // its prefilter tasks, computed by the prefilter from these two numbers
+    B.task0 = task0;
+    B.ntask = tasks_of(S.n_vertices, task_log2);
+    task0 += B.ntask;
   }
 }
 
@@ -241,6 +239,9 @@ int capture(fastcod_ctx* c, const fastcod_subject* subs, int32_t n, const Layout
     P.lab = L.lab_in[i] != SIZE_MAX ? at<uint16_t>(A, L.lab_in[i]) : subs[i].target_labels;
     P.planes = at<uint32_t>(A, L.planes[i]);
     P.st = tbl.s[i].st;
+    P.zero0 = tbl.s[i].acc.C;  // zeroed by the prep launch, before the walk adds to them
+    P.zero1 = tbl.s[i].acc.Cend;
+    P.nzero = (int64_t)tbl.s[i].v.n_roi * tbl.s[i].v.n_lab;
   }
   fc::prep_table_blocks(*prep);
   const cudaError_t e0 = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
@@ -250,13 +251,12 @@ int capture(fastcod_ctx* c, const fastcod_subject* subs, int32_t n, const Layout
   }
   cudaError_t e = cudaMemsetAsync(gst, 0, sizeof(DevState), c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(at<DevState>(A, L.states), 0, sizeof(DevState) * n, c->stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(at<char>(A, L.acc_lo), 0, L.acc_hi - L.acc_lo, c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(at<char>(A, L.bricks_lo), 0, L.bricks_hi - L.bricks_lo, c->stream);
   if (e == cudaSuccess) e = fc::launch_volume_prep_batch(*prep, c->stream);
   if (e == cudaSuccess) e = fc::launch_near_batch(*prep, c->stream);
   delete prep;
   if (e == cudaSuccess)
-    e = fc::launch_prefilter_batch(tbl, at<fc::BatchTask>(A, L.tasks), L.ntasks, c->prefilter != 0, c->staging_tma != 0, cfg.ctas,
+    e = fc::launch_prefilter_batch(tbl, nullptr, L.ntasks, c->prefilter != 0, c->staging_tma != 0, cfg.ctas,
                                    at<int32_t>(A, L.surv), L.surv_cap, gst, c->num_sms, c->stream);
   if (e == cudaSuccess)
     e = fc::launch_walk_batch(tbl, at<int32_t>(A, L.surv), L.surv_cap, c->mode, at<int32_t>(A, L.ovf), gst, c->num_sms,
@@ -303,8 +303,7 @@ int run_config(fastcod_ctx* c, const fastcod_subject* subs, int32_t n, const std
   }
   fc::BatchTable* tbl = new (std::nothrow) fc::BatchTable;
   if (!tbl) return fail(c, FASTCOD_ENOMEM, "host allocation failed");
-  std::vector<fc::BatchTask> tasks;
-  fill_table(c, subs, n, L, cfg.near_log2, cfg.task_log2, *tbl, tasks);
+  fill_table(c, subs, n, L, cfg.near_log2, cfg.task_log2, *tbl);
   int rc = FASTCOD_OK;
   do {
     if (stage) {
@@ -327,13 +326,6 @@ int run_config(fastcod_ctx* c, const fastcod_subject* subs, int32_t n, const std
         }
       }
       if (rc) break;
-    }
-    // the task table depends on the configuration: uploaded on every run
-    if (cudaMemcpyAsync(at<void>(A, L.tasks), tasks.data(), sizeof(fc::BatchTask) * tasks.size(),
-                        cudaMemcpyHostToDevice, c->stream) != cudaSuccess) {
-      (void)cudaGetLastError();
-      rc = fail(c, FASTCOD_ECUDA, "batch task table copy failed");
-      break;
     }
     const uint64_t key = graph_key(*tbl, L.ntasks, cfg, c->mode, c->prefilter, c->staging_tma, A, subs, L);
     B->info.graph_reused = (B->exec && key == B->graph_key) ? 1 : 0;
@@ -435,6 +427,7 @@ FASTCOD_API int fastcod_batch_run(fastcod_ctx* c, const fastcod_subject* subs, i
   CU(cudaSetDevice(c->device));
   int64_t total_ns = 0;
   std::vector<int> host_in(4 * (size_t)n, 0);
+  std::vector<char> out_dev((size_t)n, 0);
   for (int32_t i = 0; i < n; ++i) {
     const fastcod_subject& S = subs[i];
     if (S.dims[0] <= 0 || S.dims[1] <= 0 || S.dims[2] <= 0)
@@ -456,8 +449,9 @@ FASTCOD_API int fastcod_batch_run(fastcod_ctx* c, const fastcod_subject* subs, i
     // device xyz off a 16-byte boundary is staged like host input (the bulk
     // copies of the prefilter need 16-byte aligned sources)
     if (S.n_vertices && ((uintptr_t)S.xyz & 15u)) host_in[4 * i + 2] = true;
-    if (ptr_kind(S.C_out, c->device) < 0 || ptr_kind(S.Cend_out, c->device) < 0)
-      return fail(c, FASTCOD_EINVAL, "subject %d: output is device memory of another device", i);
+    const int kc = ptr_kind(S.C_out, c->device), ke = ptr_kind(S.Cend_out, c->device);
+    if (kc < 0 || ke < 0) return fail(c, FASTCOD_EINVAL, "subject %d: output is device memory of another device", i);
+    out_dev[i] = kc == 1 && ke == 1;
     total_ns += S.n_streamlines;
   }
   if (total_ns > 0x7fffffffLL) return fail(c, FASTCOD_EINVAL, "more than 2^31-1 streamlines in one batch");
@@ -466,6 +460,7 @@ FASTCOD_API int fastcod_batch_run(fastcod_ctx* c, const fastcod_subject* subs, i
     if (!c->batch) return fail(c, FASTCOD_ENOMEM, "host allocation failed");
   }
   BatchState* B = c->batch;
+  B->out_dev = out_dev;
   B->info = fastcod_batch_info{};
   B->info.n_subjects = n;
   float ms = 0.f;
@@ -502,6 +497,7 @@ FASTCOD_API int fastcod_batch_run(fastcod_ctx* c, const fastcod_subject* subs, i
   void* A = B->arena;
   Layout L = plan(subs, n, host_in, cfg.near_log2, cfg.task_log2, total_ns);
   for (int32_t i = 0; i < n; ++i) {
+    if (out_dev[i]) continue;  // accumulated in place
     const size_t nm = (size_t)subs[i].n_roi * (size_t)subs[i].n_targets;
     CU(cudaMemcpyAsync(subs[i].C_out, at<int32_t>(A, L.C[i]), nm * 4, cudaMemcpyDefault, c->stream));
     CU(cudaMemcpyAsync(subs[i].Cend_out, at<int32_t>(A, L.Cend[i]), nm * 4, cudaMemcpyDefault, c->stream));

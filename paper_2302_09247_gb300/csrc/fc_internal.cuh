@@ -160,6 +160,7 @@ struct BatchSubject {
   Accum acc;
   DevState* st;
   int64_t sbase;
+  int64_t task0, ntask;  // its prefilter tasks (when no task table is given): [task0, task0 + ntask)
 };
 
 // Up to kMaxBatch subjects travel as one kernel parameter (constant bank).
@@ -181,6 +182,9 @@ struct PrepSubject {
   DevState* st;
   int64_t prep_blk0;  // first block of the prep launch
   int64_t near_blk0;  // first block of the near-grid launch
+  int32_t* zero0;     // optional: [nzero] words zeroed by the prep launch (the subject's C), and
+  int32_t* zero1;     // [nzero] more (its C_end); null when not wanted
+  int64_t nzero;
 };
 struct PrepTable {
   int32_t n;
@@ -195,6 +199,24 @@ struct BatchTask {
   int32_t pad;
   int64_t s_lo, s_hi;
 };
+
+// Task `task` of a batch without a task table: subject i owns tasks
+// [task0, task0 + ntask), which split its streamlines evenly by count.
+__device__ __forceinline__ BatchTask batch_task(const BatchTable& tbl, int64_t task) {
+  int32_t lo = 0, hi = tbl.n - 1;
+  while (lo < hi) {
+    const int32_t mid = (lo + hi + 1) >> 1;
+    if (tbl.s[mid].task0 <= task) lo = mid; else hi = mid - 1;
+  }
+  const BatchSubject& S = tbl.s[lo];
+  const int64_t j = task - S.task0, k = S.ntask;
+  BatchTask t;
+  t.subject = lo;
+  t.pad = 0;
+  t.s_lo = S.t.ns * j / k;
+  t.s_hi = S.t.ns * (j + 1) / k;
+  return t;
+}
 
 // Mode bits of the walk.
 constexpr uint32_t kModeTargetEndpoint = 1u;
@@ -228,7 +250,9 @@ cudaError_t launch_prefilter(const Tract& t, const VolView& v, bool prefilter, u
                              bool tma, int ctas_per_sm, int32_t* survivors, int64_t survivor_cap, DevState* st,
                              int num_sms, cudaStream_t s, int64_t withhold_piece = -1);
 
-// Batched forms: every subject of the table in one launch each.
+// Batched forms: every subject of the table in one launch each.  tasks:
+// a table of ntasks tasks, or null for the tasks the subjects' task0 / ntask
+// define.
 cudaError_t launch_prefilter_batch(const BatchTable& tbl, const BatchTask* tasks, int32_t ntasks, bool prefilter,
                                    bool tma, int ctas_per_sm, int32_t* survivors, int64_t survivor_cap,
                                    DevState* gst, int num_sms, cudaStream_t s);

@@ -756,7 +756,7 @@ __global__ void __launch_bounds__(kWarps * 32, kMinBlocks)
     if (lane_id() == 0) task = (int32_t)atomicAdd(&gst->work_task, 1u);
     task = __shfl_sync(kFull, task, 0);
     if (task >= ntasks) break;
-    const BatchTask tk = tasks[task];
+    const BatchTask tk = tasks ? tasks[task] : batch_task(tbl, task);
     const BatchSubject& S = tbl.s[tk.subject];
     Scan sc;
     if (!warp_init(S.t, tk.s_lo, tk.s_hi, sc, S.st, S.sbase)) continue;

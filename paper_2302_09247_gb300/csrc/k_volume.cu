@@ -142,6 +142,18 @@ __global__ void __launch_bounds__(32 * kPrepRows) volume_prep_batch_kernel(const
   prep_block(S.roi, S.lab, v, const_cast<uint32_t*>(v.code), const_cast<uint16_t*>(v.lab),
              const_cast<uint32_t*>(v.bricks), S.planes, S.st, (int32_t)(local - g * nxb),
              (int32_t)(g - (int64_t)zq * ryb), zq);
+  if (S.nzero > 0) {
+    // the subject's blocks share the zeroing of its accumulators (coalesced
+    // word stores, a slice per block)
+    const int64_t nb = (int64_t)nxb * ryb * plane_groups(v);
+    const int64_t per = (S.nzero + nb - 1) / nb;
+    const int64_t lo = local * per, hi = min(S.nzero, lo + per);
+    const int32_t t = (int32_t)(threadIdx.y * 32 + threadIdx.x);
+    for (int64_t i = lo + t; i < hi; i += 32 * kPrepRows) {
+      S.zero0[i] = 0;
+      S.zero1[i] = 0;
+    }
+  }
 }
 
 // ---------------------------------------------------------------- near grid

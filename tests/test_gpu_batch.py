@@ -148,3 +148,37 @@ def test_batch_errors_name_the_subject(fc):
         good = _subjects(seed_count=1, ns=500)
         outs = _run_batch(fc, ctx, good, "host")
         np.testing.assert_array_equal(outs[0][0], _oracle(good[0])[0])
+
+
+@pytest.mark.parametrize("out_where", ["device", "mixed"])
+def test_batch_outputs_in_device_memory(fc, out_where):
+    """Outputs in device memory are zeroed and accumulated in place by the
+    pass (whatever they held), on the first run and on a replay of its graph
+    with the same buffers."""
+    import torch
+    subs = _subjects(seed_count=3, ns=3000)
+    keep, objs, outs = [], [], []
+    for i, (roi, lab, dims, N, M, xyz, off) in enumerate(subs):
+        r, l, x, o = as_device(roi), as_device(lab), as_device(xyz), as_device(off)
+        if out_where == "device" or i % 2 == 0:
+            C = torch.empty((N, M), dtype=torch.int32, device="cuda:0")
+            Ce = torch.empty((N, M), dtype=torch.int32, device="cuda:0")
+        else:
+            C, Ce = np.empty((N, M), np.int32), np.empty((N, M), np.int32)
+        keep += [r, l, x, o]
+        outs.append((C, Ce))
+        objs.append(fc.make_subject(r, l, dims, N, M, x, o, C, Ce))
+    ref = [_oracle(sub)[:2] for sub in subs]
+    with fc.Context(0) as ctx:
+        ctx.set_option(fc.FASTCOD_OPT_AUTOTUNE, 0)
+        for run, fill in enumerate((-7, 123456)):
+            for C, Ce in outs:
+                C.fill(fill) if isinstance(C, np.ndarray) else C.fill_(fill)
+                Ce.fill(fill) if isinstance(Ce, np.ndarray) else Ce.fill_(fill)
+            torch.cuda.synchronize()  # the fills run on torch's stream, the pass on the context's
+            fc.fastcod_batch_run(ctx.ctx, objs)
+            assert fc.fastcod_batch_get_info(ctx.ctx)["graph_reused"] == run
+            for i, ((C, Ce), (Cr, Cer)) in enumerate(zip(outs, ref)):
+                got = [a.cpu().numpy() if isinstance(a, torch.Tensor) else a for a in (C, Ce)]
+                np.testing.assert_array_equal(got[0], Cr, err_msg=f"run {run} subject {i}")
+                np.testing.assert_array_equal(got[1], Cer, err_msg=f"run {run} subject {i}")
