@@ -474,7 +474,7 @@ FASTCOD_API int fastcod_batch_run(fastcod_ctx* c, const fastcod_subject* subs, i
       cfg = it->second;
     } else {
       // timed trials: each candidate runs twice (the first run captures its graph)
-      const BatchConfig cand[6] = {{2, -1, 16}, {2, -1, 14}, {2, -1, 18}, {3, -1, 16}, {2, 2, 16}, {2, 0, 16}};
+      const BatchConfig cand[7] = {{2, -1, 16}, {2, -1, 14}, {2, -1, 15}, {2, -1, 18}, {3, -1, 16}, {2, 2, 16}, {2, 0, 16}};
       float best = 1e30f;
       for (const BatchConfig& k : cand) {
         float t = 0.f;

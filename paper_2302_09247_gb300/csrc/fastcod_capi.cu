@@ -164,7 +164,7 @@ int zero_accumulators(fastcod_ctx* c) {
 void collect_profile(fastcod_ctx* c) {
   for (size_t k = 0; k < c->ev_used; ++k) {
     float ms[4] = {0, 0, 0, 0};
-    for (int i = 0; i < 4; ++i)
+    for (int i = c->ev_pool[k].no_h2d ? 1 : 0; i < 4; ++i)
       if (cudaEventElapsedTime(&ms[i], c->ev_pool[k].e[i], c->ev_pool[k].e[i + 1]) != cudaSuccess) {
         (void)cudaGetLastError();
         ms[i] = 0;
@@ -194,6 +194,7 @@ int begin_profiled_call(fastcod_ctx* c) {
     }
   }
   c->ev_cur = &c->ev_pool[c->ev_used++];
+  c->ev_cur->no_h2d = false;
   return FASTCOD_OK;
 }
 
@@ -404,7 +405,6 @@ FASTCOD_API int fastcod_add_streamlines(fastcod_ctx* c, const int32_t* xyz, int6
   const int32_t* d_xyz = xyz;
   const int64_t* d_off = offsets;
   if (int rc = begin_profiled_call(c)) return rc;
-  if (int rc = record(c, 0)) return rc;
   // page-locked host xyz: read in place over the host link when allowed (the
   // offsets, read with dependent loads, are always copied)
   bool xyz_in_place = false;
@@ -414,6 +414,13 @@ FASTCOD_API int fastcod_add_streamlines(fastcod_ctx* c, const int32_t* xyz, int6
       d_xyz = static_cast<const int32_t*>(m);
       xyz_in_place = true;
     }
+  }
+  // the copy stage is timed only when there is one (each recorded event costs
+  // the stream a few microseconds)
+  if ((kx == 0 && !xyz_in_place) || unaligned || ko == 0) {
+    if (int rc = record(c, 0)) return rc;
+  } else if (c->ev_cur) {
+    c->ev_cur->no_h2d = true;
   }
   if ((kx == 0 && !xyz_in_place) || unaligned) {
     int rc = grow(c, (void**)&c->d_xyz, &c->xyz_bytes, (size_t)nv * 12 + 16);

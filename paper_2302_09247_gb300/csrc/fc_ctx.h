@@ -64,6 +64,7 @@ struct fastcod_ctx {
   int profile = 0;
   struct EvSet {
     cudaEvent_t e[5];
+    bool no_h2d;  // the call copied nothing to the device: e[0] was not recorded
   };
   std::vector<EvSet> ev_pool;  // event sets of profiled calls
   size_t ev_used = 0;          // sets recorded and not yet folded into prof

@@ -109,7 +109,7 @@ def test_batch_autotune_identical_results(fc):
         a = _run_batch(fc, ctx, subs, "device")
         info = fc.fastcod_batch_get_info(ctx.ctx)
         assert info["tuned"] == 1 and info["prefilter_ctas"] in (2, 3) and -1 <= info["near_log2"] <= 3
-        assert info["task_vertices"] in (1 << 14, 1 << 16, 1 << 18)
+        assert info["task_vertices"] in (1 << 14, 1 << 15, 1 << 16, 1 << 18)
         b = _run_batch(fc, ctx, subs, "device")
         assert fc.fastcod_batch_get_info(ctx.ctx)["tuned"] == 0
     with fc.Context(0) as ctx:
