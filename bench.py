@@ -49,8 +49,8 @@ METRIC = "DDA voxel-steps/s & subjects/s for C, bit-exact; batched vs plain; p50
 # traffic grows with the vertices).
 PREFILTER_SOURCES = ("paper_2302_09247_gb300/csrc/k_prefilter.cu", "paper_2302_09247_gb300/csrc/fc_tma.cuh",
                      "paper_2302_09247_gb300/csrc/fc_internal.cuh", "paper_2302_09247_gb300/csrc/fc_device.cuh")
-PREFILTER_TRAFFIC = {"sha256": "5423f3e15a6a80d75bac83f900383b1a8acd19a2d0e885cdc2ff01d2d9f6df74",
-                     "bytes": 1911584256, "vertices": 157754709, "workload": "high-res",
+PREFILTER_TRAFFIC = {"sha256": "a8462d93402af98e63dd58cacedf843c78c9134a61d5c962fdbfb576010a2646",
+                     "bytes": 1911568896, "vertices": 157754709, "workload": "high-res",
                      "summary": "profiles/prefilter_kernel_highres260x311x260.md"}
 
 
@@ -682,8 +682,8 @@ def run_next(args):
 # the ones it was measured on.
 WALK_SOURCES = ("paper_2302_09247_gb300/csrc/k_walk.cu", "paper_2302_09247_gb300/csrc/fc_device.cuh",
                 "paper_2302_09247_gb300/csrc/fc_internal.cuh")
-WALK_INSTR = {"sha256": "02f75f2b6efaa3260177b25d3369404869fd07476b2265f7940b1289b6df0bf6",
-              "warp_instr_per_voxel_step": 520880513 / 54811982,
+WALK_INSTR = {"sha256": "5a3c904b058f894262e5ec9f6864b179a3fbfe99c86ac01c985d6765a5cd723f",
+              "warp_instr_per_voxel_step": 519023407 / 54811982,
               "summary": "profiles/walk_kernel_dda_highres260x311x260.md"}
 
 

@@ -113,7 +113,7 @@ enum {
    * task) per batch shape by timed trials on the first batch of that shape
    * (cached in the context, and in the file named by the environment
    * variable FASTCOD_TUNE_CACHE when set); 0: use the options as set, with
-   * tasks of about 65,536 vertices. */
+   * the work granularity of FASTCOD_OPT_BATCH_TASK_LOG2. */
   FASTCOD_OPT_AUTOTUNE = 8,
   /* 1: fastcod_add_streamlines reads page-locked (mapped) host xyz in place,
    * the kernels streaming it over the host link while they compute (16-byte
@@ -138,7 +138,11 @@ enum {
    * piece runs out after its one-second limit.  The call then reports
    * FASTCOD_ETIMEOUT (at the next synchronising call), no copy is left in
    * flight, and the context stays usable after fastcod_reset. */
-  FASTCOD_OPT_TEST_WITHHOLD_PIECE = 12
+  FASTCOD_OPT_TEST_WITHHOLD_PIECE = 12,
+  /* Work granularity of fastcod_batch_run's prefilter when the autotuner is
+   * off: dynamic tasks of about 2^value vertices of one subject, 12..22
+   * (default 16).  Results are identical. */
+  FASTCOD_OPT_BATCH_TASK_LOG2 = 13
 };
 
 typedef struct fastcod_ctx fastcod_ctx;

@@ -17,7 +17,6 @@ using fcapi::ptr_kind;
 
 namespace {
 
-constexpr int kTaskLog2Default = 16;  // prefilter task: about 2^16 vertices of one subject
 constexpr int32_t kOverflowCtas = 64;
 
 // What the autotuner picks per batch shape: prefilter CTAs per SM, near-grid
@@ -464,7 +463,7 @@ FASTCOD_API int fastcod_batch_run(fastcod_ctx* c, const fastcod_subject* subs, i
   B->info = fastcod_batch_info{};
   B->info.n_subjects = n;
   float ms = 0.f;
-  BatchConfig cfg{c->prefilter_ctas, c->near_log2, kTaskLog2Default};
+  BatchConfig cfg{c->prefilter_ctas, c->near_log2, c->batch_task_log2};
   bool staged = false;
   if (c->autotune) {
     load_tune_cache(B);

@@ -590,6 +590,10 @@ FASTCOD_API int fastcod_set_option(fastcod_ctx* c, int32_t key, int64_t value) {
       if (value < -1) break;
       c->withhold_piece = value;
       return FASTCOD_OK;
+    case FASTCOD_OPT_BATCH_TASK_LOG2:
+      if (value < 12 || value > 22) break;
+      c->batch_task_log2 = (int)value;
+      return FASTCOD_OK;
     case FASTCOD_OPT_PROFILE:
       if (value != 0 && value != 1) break;
       CU(cudaSetDevice(c->device));

@@ -58,6 +58,7 @@ struct fastcod_ctx {
   int prefilter_ctas = 2;
   int near_log2 = -1;      // near grid cell: (1 << near_log2)^3 voxels; -1 = per volume
   int autotune = 1;        // batched form: tune per batch shape
+  int batch_task_log2 = 16; // batched form without the autotuner: prefilter tasks of about 2^value vertices
   int host_in_place = 0;   // read page-locked host xyz in place (option)
   int walked_steps = 0;    // count the survivors' voxel steps (option)
   int64_t withhold_piece = -1;  // test hook: vertex piece the TMA loader never copies

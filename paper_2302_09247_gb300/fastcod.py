@@ -40,6 +40,7 @@ FASTCOD_OPT_HOST_IN_PLACE = 9
 FASTCOD_OPT_WALKED_STEPS = 10
 FASTCOD_OPT_SEGMENT_SKIP = 11
 FASTCOD_OPT_TEST_WITHHOLD_PIECE = 12
+FASTCOD_OPT_BATCH_TASK_LOG2 = 13
 
 EXPORTED = [
     "fastcod_create", "fastcod_destroy", "fastcod_set_stream", "fastcod_set_volumes",

@@ -66,7 +66,8 @@ def test_batch_matches_oracle(fc, where):
     with fc.Context(0) as ctx:
         outs = _run_batch(fc, ctx, subs, where)
         info = fc.fastcod_batch_get_info(ctx.ctx)
-        assert info["n_subjects"] == len(subs) and info["tasks"] >= len(subs)
+        assert info["n_subjects"] == len(subs)
+        assert info["tasks"] >= len(subs)
         for i, (sub, (C, Ce)) in enumerate(zip(subs, outs)):
             Cr, Cer, sr = _oracle(sub)
             np.testing.assert_array_equal(C, Cr, err_msg=f"subject {i}")
@@ -182,3 +183,28 @@ def test_batch_outputs_in_device_memory(fc, out_where):
                 got = [a.cpu().numpy() if isinstance(a, torch.Tensor) else a for a in (C, Ce)]
                 np.testing.assert_array_equal(got[0], Cr, err_msg=f"run {run} subject {i}")
                 np.testing.assert_array_equal(got[1], Cer, err_msg=f"run {run} subject {i}")
+
+
+def test_batch_task_granularity_option(fc):
+    """With the autotuner off, FASTCOD_OPT_BATCH_TASK_LOG2 sets the prefilter's
+    task size (here the smallest, so that subjects split into many tasks);
+    a subject without vertices lies between the others.  Every subject equals
+    the oracle; values outside 12..22 are refused."""
+    subs = _subjects(seed_count=3, ns=3000)
+    empty_off = np.zeros(6, dtype=np.int64)  # five streamlines of no vertex
+    roi, lab, dims, N, M = subs[0][:5]
+    subs.insert(2, (roi, lab, dims, N, M, np.zeros((0, 3), dtype=np.int32), empty_off))
+    with fc.Context(0) as ctx:
+        ctx.set_option(fc.FASTCOD_OPT_AUTOTUNE, 0)
+        ctx.set_option(fc.FASTCOD_OPT_BATCH_TASK_LOG2, 12)
+        outs = _run_batch(fc, ctx, subs, "device")
+        info = fc.fastcod_batch_get_info(ctx.ctx)
+        assert info["task_vertices"] == 1 << 12 and info["tasks"] > 2 * len(subs)
+        for i, (sub, (C, Ce)) in enumerate(zip(subs, outs)):
+            Cr, Cer, sr = _oracle(sub)
+            np.testing.assert_array_equal(C, Cr, err_msg=f"subject {i}")
+            np.testing.assert_array_equal(Ce, Cer, err_msg=f"subject {i}")
+            assert fc.fastcod_batch_get_stats(ctx.ctx, i)["voxel_steps"] == sr["voxel_steps"]
+        for bad in (0, 11, 23):
+            with pytest.raises(fc.FastCodError):
+                ctx.set_option(fc.FASTCOD_OPT_BATCH_TASK_LOG2, bad)
