@@ -80,6 +80,11 @@ def _peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
+# nvidia-smi's sampling interval (the profiling recipe's clocks line); each
+# sample queries the driver, which the served form's request loop feels
+CLOCK_SAMPLE_MS = 200
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled during a region."""
 
@@ -99,7 +104,7 @@ class ClockSampler:
             self.out = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "100"], stdout=self.out, stderr=subprocess.DEVNULL)
+                 "-lms", str(CLOCK_SAMPLE_MS)], stdout=self.out, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
 

@@ -308,7 +308,10 @@ typedef struct {
 
 /* max_slots: 1..128 requests on the device at once; hbm_budget_bytes: device
  * memory the server may reserve for admitted requests (0: 90% of the free
- * memory at creation).
+ * memory at creation).  Host chunks are copied into device staging buffers
+ * that the server keeps for its life and reuses (at most 2 * max_slots + 2
+ * of them, each the size of the largest chunk it held rounded up to 64 MiB;
+ * more in flight at once are freed after their pass).
  *
  * Failure injection for tests, on the host only: when the environment
  * variable FASTCOD_FAULT holds comma-separated items "alloc:k", "h2d:k" or

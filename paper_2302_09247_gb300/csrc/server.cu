@@ -9,6 +9,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <deque>
+#include <list>
 #include <map>
 #include <memory>
 #include <mutex>
@@ -57,11 +58,22 @@ struct Request {
   double t_submit = 0, t_admit = 0, t_done = 0;
 };
 
+// A device buffer that host chunks are copied into.  It is kept for the
+// server's life and handed out again once `reusable` (recorded on the
+// compute stream after the pass that read it) has completed.
+struct StageBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  cudaEvent_t reusable = nullptr;
+  bool taken = false;
+  bool keep = true;  // false: beyond the server's number of kept buffers, freed after its pass
+};
+
 // One chunk staged for the current iteration.
 struct Staged {
   Request* r;
   fc::Tract t;
-  void* buf;  // server-owned staging (nullptr: the chunk is device memory)
+  StageBuf* buf;  // server-owned staging (nullptr: the chunk is device memory)
 };
 
 }  // namespace
@@ -123,11 +135,71 @@ struct fastcod_server {
   // request (0: none)
   int64_t fault_alloc = 0, fault_h2d = 0, fault_cancel = 0;
   int64_t n_alloc = 0, n_h2d = 0, n_submit = 0;  // worker / submit counters
+  // staging buffers of host chunks, reused: an allocation per chunk from the
+  // pool could block the loop for milliseconds whenever the blocks freed by
+  // the compute stream were not yet reusable and the pool mapped new memory
+  std::list<StageBuf> stage_bufs;
+  size_t stage_kept = 0;  // buffers with keep set: at most 2 * max_slots + 2
 };
 
 namespace {
 
 double now_s(fastcod_server* S) { return std::chrono::duration<double>(Clock::now() - S->t0).count(); }
+
+// Staging buffers grow in 64 MiB steps, so that chunks of nearby sizes share
+// them.
+constexpr size_t kStageStep = (size_t)64 << 20;
+
+// A staging buffer of at least `bytes` whose last reader has finished: a kept
+// one when there is one, else a new one (from the pool, on the copy stream).
+cudaError_t stage_acquire(fastcod_server* S, size_t bytes, StageBuf** out) {
+  StageBuf* best = nullptr;
+  for (StageBuf& b : S->stage_bufs) {
+    if (b.taken || b.bytes < bytes || (best && b.bytes >= best->bytes)) continue;
+    const cudaError_t q = cudaEventQuery(b.reusable);
+    if (q == cudaErrorNotReady) {
+      (void)cudaGetLastError();
+      continue;
+    }
+    if (q != cudaSuccess) return q;
+    best = &b;
+  }
+  if (!best) {
+    StageBuf b;
+    b.bytes = (bytes + kStageStep - 1) / kStageStep * kStageStep;
+    cudaError_t e = cudaMallocFromPoolAsync(&b.p, b.bytes, S->pool, S->copy);
+    if (e != cudaSuccess) return e;
+    e = cudaEventCreateWithFlags(&b.reusable, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+      cudaFreeAsync(b.p, S->copy);
+      return e;
+    }
+    b.keep = S->stage_kept < 2 * (size_t)S->max_slots + 2;
+    if (b.keep) ++S->stage_kept;
+    S->stage_bufs.push_back(b);
+    best = &S->stage_bufs.back();
+  }
+  best->taken = true;
+  *out = best;
+  return cudaSuccess;
+}
+
+// The buffer may be handed out again once `s` has passed this point (a buffer
+// beyond the kept number is freed there instead).
+void stage_release(fastcod_server* S, StageBuf* b, cudaStream_t s) {
+  if (!b->keep) {
+    cudaFreeAsync(b->p, s);
+    cudaEventDestroy(b->reusable);
+    for (auto it = S->stage_bufs.begin(); it != S->stage_bufs.end(); ++it)
+      if (&*it == b) {
+        S->stage_bufs.erase(it);
+        break;
+      }
+    return;
+  }
+  cudaEventRecord(b->reusable, s);
+  b->taken = false;
+}
 
 // FASTCOD_FAULT = comma-separated "alloc:k", "h2d:k", "cancel:k" (k >= 1).
 void parse_faults(fastcod_server* S) {
@@ -353,21 +425,21 @@ bool iterate(fastcod_server* S, uint32_t** tmp, size_t* tmp_cap) {
     if (k.host_xyz || k.host_off) {
       const size_t xb = a256((size_t)k.nv * 12 + 16);
       cudaError_t e = inject_alloc(S) ? cudaErrorMemoryAllocation
-                                      : cudaMallocFromPoolAsync(&sg.buf, xb + (size_t)(k.ns + 1) * 8, S->pool, S->copy);
+                                      : stage_acquire(S, xb + (size_t)(k.ns + 1) * 8, &sg.buf);
       if (e == cudaSuccess && inject_h2d(S)) e = cudaErrorInvalidValue;  // the copy "fails" before it is issued
       if (e == cudaSuccess && k.host_xyz && k.nv) {
-        e = cudaMemcpyAsync(sg.buf, k.xyz, (size_t)k.nv * 12, cudaMemcpyDefault, S->copy);
-        sg.t.xyz = static_cast<int32_t*>(sg.buf);
+        e = cudaMemcpyAsync(sg.buf->p, k.xyz, (size_t)k.nv * 12, cudaMemcpyDefault, S->copy);
+        sg.t.xyz = static_cast<int32_t*>(sg.buf->p);
       }
       if (e == cudaSuccess && k.host_off) {
-        int64_t* o = reinterpret_cast<int64_t*>(static_cast<char*>(sg.buf) + xb);
+        int64_t* o = reinterpret_cast<int64_t*>(static_cast<char*>(sg.buf->p) + xb);
         e = cudaMemcpyAsync(o, k.off, (size_t)(k.ns + 1) * 8, cudaMemcpyHostToDevice, S->copy);
         sg.t.off = o;
       }
       if (e != cudaSuccess) {
         (void)cudaGetLastError();
         r->status = e == cudaErrorMemoryAllocation ? FASTCOD_ENOMEM : FASTCOD_ECUDA;
-        if (sg.buf) cudaFreeAsync(sg.buf, S->copy);
+        if (sg.buf) stage_release(S, sg.buf, S->copy);  // nothing reads it: free once the copies issued are done
         continue;
       }
     }
@@ -381,7 +453,7 @@ bool iterate(fastcod_server* S, uint32_t** tmp, size_t* tmp_cap) {
     // rather than return partial results
     for (const Staged& sg : staged) {
       sg.r->status = FASTCOD_EINVAL;
-      if (sg.buf) cudaFreeAsync(sg.buf, S->copy);
+      if (sg.buf) stage_release(S, sg.buf, S->compute);
     }
     staged.clear();
   }
@@ -443,7 +515,7 @@ bool iterate(fastcod_server* S, uint32_t** tmp, size_t* tmp_cap) {
       for (const Staged& sg : staged) sg.r->status = FASTCOD_ECUDA;
     }
     for (const Staged& sg : staged) {
-      if (sg.buf) cudaFreeAsync(sg.buf, S->compute);
+      if (sg.buf) stage_release(S, sg.buf, S->compute);
       sg.r->streamlines += sg.t.ns;
       sg.r->chunks_done += 1;
     }
@@ -715,6 +787,10 @@ FASTCOD_API int fastcod_server_destroy(fastcod_server* S) {
   for (auto& kv : S->reqs) {
     if (kv.second->mem) cudaFree(kv.second->mem);
     if (kv.second->done_ev) cudaEventDestroy(kv.second->done_ev);
+  }
+  for (StageBuf& b : S->stage_bufs) {
+    cudaFree(b.p);
+    cudaEventDestroy(b.reusable);
   }
   if (S->lists) cudaFree(S->lists);
   if (S->tasks) cudaFree(S->tasks);
