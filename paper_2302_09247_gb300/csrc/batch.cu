@@ -219,7 +219,10 @@ uint64_t graph_key(const fc::BatchTable& tbl, int32_t ntasks, const BatchConfig&
   return h;
 }
 
-// Capture the whole batch into a graph on the context's stream.
+// Capture the whole batch into a graph on the context's stream.  *exec: the
+// executable graph of the last batch, updated in place when only parameters
+// changed (new input or output addresses, new sizes of the same nodes), else
+// replaced by a new instantiation.
 int capture(fastcod_ctx* c, const fastcod_subject* subs, int32_t n, const Layout& L, const fc::BatchTable& tbl,
             const BatchConfig& cfg, cudaGraphExec_t* exec) {
   BatchState* B = c->batch;
@@ -269,6 +272,16 @@ int capture(fastcod_ctx* c, const fastcod_subject* subs, int32_t n, const Layout
     if (g) cudaGraphDestroy(g);
     (void)cudaGetLastError();
     return fail(c, FASTCOD_ECUDA, "batch graph capture failed: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
+  }
+  if (*exec) {
+    cudaGraphExecUpdateResultInfo info;
+    if (cudaGraphExecUpdate(*exec, g, &info) == cudaSuccess) {
+      cudaGraphDestroy(g);
+      return FASTCOD_OK;
+    }
+    (void)cudaGetLastError();
+    cudaGraphExecDestroy(*exec);
+    *exec = nullptr;
   }
   const cudaError_t e3 = cudaGraphInstantiate(exec, g, 0);
   cudaGraphDestroy(g);
@@ -329,10 +342,10 @@ int run_config(fastcod_ctx* c, const fastcod_subject* subs, int32_t n, const std
     const uint64_t key = graph_key(*tbl, L.ntasks, cfg, c->mode, c->prefilter, c->staging_tma, A, subs, L);
     B->info.graph_reused = (B->exec && key == B->graph_key) ? 1 : 0;
     if (!B->info.graph_reused) {
-      if (B->exec) cudaGraphExecDestroy(B->exec);
-      B->exec = nullptr;
       rc = capture(c, subs, n, L, *tbl, cfg, &B->exec);
       if (rc) {
+        if (B->exec) cudaGraphExecDestroy(B->exec);
+        B->exec = nullptr;
         B->graph_key = 0;
         break;
       }

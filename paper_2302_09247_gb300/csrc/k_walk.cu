@@ -236,6 +236,9 @@ __device__ __forceinline__ int walk_one(const VolView& v, const Tract& t, const 
       fail = __any_sync(kFull, fail);
     }
   } else {
+    // window i0 holds segments a+i0+lane -> a+i0+lane+1, both ends loaded by
+    // the lane; the next window's lines are prefetched into L1 while this one
+    // is walked, so that its loads wait on L1 rather than on L2
     int nL = 0;
     for (int64_t i0 = 0; i0 < T - 1 && !fail; i0 += 32) {
       if (nL > kLin - 96) {  // room for three voxels a lane

@@ -183,6 +183,22 @@ def test_batch_outputs_in_device_memory(fc, out_where):
                 got = [a.cpu().numpy() if isinstance(a, torch.Tensor) else a for a in (C, Ce)]
                 np.testing.assert_array_equal(got[0], Cr, err_msg=f"run {run} subject {i}")
                 np.testing.assert_array_equal(got[1], Cer, err_msg=f"run {run} subject {i}")
+        # new output buffers: the captured graph is updated to them (only its
+        # parameters change), and the old buffers keep what they held
+        old = list(outs)  # kept alive, so that the new buffers get new addresses
+        for i, (C, Ce) in enumerate(outs):
+            if isinstance(C, torch.Tensor):
+                outs[i] = (torch.full_like(C, 99), torch.full_like(Ce, 99))
+                objs[i].C_out, objs[i].Cend_out = outs[i][0].data_ptr(), outs[i][1].data_ptr()
+        torch.cuda.synchronize()
+        fc.fastcod_batch_run(ctx.ctx, objs)
+        assert fc.fastcod_batch_get_info(ctx.ctx)["graph_reused"] == 0
+        for i, ((C, Ce), (Cr, Cer), (C0, Ce0)) in enumerate(zip(outs, ref, old)):
+            got = [a.cpu().numpy() if isinstance(a, torch.Tensor) else a for a in (C, Ce)]
+            np.testing.assert_array_equal(got[0], Cr, err_msg=f"new buffers, subject {i}")
+            np.testing.assert_array_equal(got[1], Cer, err_msg=f"new buffers, subject {i}")
+            if isinstance(C0, torch.Tensor):
+                np.testing.assert_array_equal(C0.cpu().numpy(), Cr)
 
 
 def test_batch_task_granularity_option(fc):
