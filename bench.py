@@ -687,8 +687,8 @@ def run_next(args):
 # the ones it was measured on.
 WALK_SOURCES = ("paper_2302_09247_gb300/csrc/k_walk.cu", "paper_2302_09247_gb300/csrc/fc_device.cuh",
                 "paper_2302_09247_gb300/csrc/fc_internal.cuh")
-WALK_INSTR = {"sha256": "5a3c904b058f894262e5ec9f6864b179a3fbfe99c86ac01c985d6765a5cd723f",
-              "warp_instr_per_voxel_step": 519023407 / 54811982,
+WALK_INSTR = {"sha256": "55c885a557a500eb063c9bdc65d212fb672e17cf189c402ce5d5d05012e80f55",
+              "warp_instr_per_voxel_step": 519023415 / 54811982,
               "summary": "profiles/walk_kernel_dda_highres260x311x260.md"}
 
 
