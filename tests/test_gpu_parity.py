@@ -242,3 +242,30 @@ def test_batch_mixed_set_forms():
         Cr, Cer, _ = oracle.connectivity(roi, lab, dims, N, M, xyz, off)
         np.testing.assert_array_equal(C, Cr)
         np.testing.assert_array_equal(Ce, Cer)
+
+
+@pytest.mark.parametrize("dims", [(37, 11, 1), (33, 9, 2), (65, 7, 3), (20, 17, 5), (70, 13, 6)])
+def test_thin_volumes_one_call_and_batched(dims):
+    """Volume preparation takes four planes per thread and a brick's depth is
+    four planes: grids of 1, 2, 3, 5 and 6 planes, with rows that are not a
+    multiple of 32 voxels, through the single-subject call and through a
+    batch (whose preparation launch also zeroes the outputs), against the
+    oracle."""
+    import torch
+    from paper_2302_09247_gb300 import fastcod as fc
+    from tests.gpu_helpers import as_device
+
+    rng = np.random.default_rng(sum(dims))
+    roi, lab, N, M = tiny.random_volumes(rng, dims, n_roi=5, n_labels=4, p_roi=0.15, p_lab=0.25)
+    xyz, off = tiny.random_streamlines(rng, dims, 400, max_len=30)
+    _check(roi, lab, dims, N, M, xyz, off, "device", _opts(1, 1))
+    Cr, Cer, _ = oracle.connectivity(roi, lab, dims, N, M, xyz, off)
+    C = torch.full((N, M), -3, dtype=torch.int32, device="cuda:0")
+    Ce = torch.full((N, M), -3, dtype=torch.int32, device="cuda:0")
+    keep = [as_device(roi), as_device(lab), as_device(xyz), as_device(off)]
+    torch.cuda.synchronize()
+    with fc.Context(0) as ctx:
+        ctx.set_option(fc.FASTCOD_OPT_AUTOTUNE, 0)
+        fc.fastcod_batch_run(ctx.ctx, [fc.make_subject(*keep[:2], dims, N, M, keep[2], keep[3], C, Ce)])
+    np.testing.assert_array_equal(C.cpu().numpy(), Cr)
+    np.testing.assert_array_equal(Ce.cpu().numpy(), Cer)
