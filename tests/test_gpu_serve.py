@@ -201,3 +201,40 @@ def test_injected_failure_hits_one_request(fc, subjects, monkeypatch, spec, wher
     finally:
         fc.fastcod_server_destroy(srv)
         ctx.close()
+
+
+@pytest.mark.parametrize("slots", [1, 3])
+def test_staging_buffers_reused_across_chunk_sizes(fc, subjects, slots):
+    """Host chunks go through the server's kept staging buffers: requests
+    whose chunks shrink and grow (a chunk larger than any buffer held, many
+    small ones, one whole subject), from pageable and page-locked memory, one
+    after another and at once, each equal to the oracle."""
+    import torch
+    vA, tA = subjects["A"]
+    vB, tB = subjects["B"]
+    Cr, Cer = _oracle(vA, tA)
+    Br, Ber = _oracle(vB, tB)
+    plans = [("A", 12, False), ("A", 2, True), ("B", 9, False), ("A", 1, True), ("A", 5, False)]
+    ctx = fc.Context(0)
+    srv = fc.fastcod_server_create(ctx.ctx, slots, 0)
+    try:
+        for together in (False, True):
+            reqs = []
+            for k, n, pinned in plans:
+                vols, tr = subjects[k]
+                r = Req(fc, srv, vols)
+                chunks = _chunks(tr, n)
+                for i, (x, o) in enumerate(chunks):
+                    if pinned:
+                        x, o = torch.from_numpy(x).pin_memory(), torch.from_numpy(o).pin_memory()
+                    r.push(fc, srv, x, o, last=(i == n - 1))
+                reqs.append((k, r))
+                if not together:
+                    assert fc.fastcod_server_wait(srv, r.id, 120.0) == fc.FASTCOD_OK
+            for k, r in reqs:
+                assert fc.fastcod_server_wait(srv, r.id, 120.0) == fc.FASTCOD_OK
+                np.testing.assert_array_equal(r.C, Cr if k == "A" else Br, err_msg=f"{k} together={together}")
+                np.testing.assert_array_equal(r.Ce, Cer if k == "A" else Ber, err_msg=f"{k} together={together}")
+    finally:
+        fc.fastcod_server_destroy(srv)
+        ctx.close()
