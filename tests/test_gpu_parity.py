@@ -269,3 +269,39 @@ def test_thin_volumes_one_call_and_batched(dims):
         fc.fastcod_batch_run(ctx.ctx, [fc.make_subject(*keep[:2], dims, N, M, keep[2], keep[3], C, Ce)])
     np.testing.assert_array_equal(C.cpu().numpy(), Cr)
     np.testing.assert_array_equal(Ce.cpu().numpy(), Cer)
+
+
+def test_vertices_beside_and_far_off_the_grid():
+    """The prefilter's near lookup clamps only its word index: for a voxel
+    off the grown grid it may read any word, which is conservative because
+    such a voxel has no ROI or labelled neighbour.  Short walks just outside
+    each face, walks near the ends of the coordinate range, and streamlines
+    that come in from far away in one long segment, against the oracle."""
+    rng = np.random.default_rng(77)
+    dims = (24, 20, 18)
+    roi, lab, N, M = tiny.random_volumes(rng, dims, n_roi=5, n_labels=4, p_roi=0.1, p_lab=0.2)
+    lim = (1 << 24) - 1
+    pts, counts = [], []
+    for i in range(400):
+        kind = i % 4
+        c = rng.uniform(0, 1, size=3) * np.array(dims) * U
+        if kind == 1:  # beside a face, 1 to 3 voxels out
+            a = int(rng.integers(3))
+            c[a] = (-rng.uniform(0.1, 3) * U) if rng.random() < 0.5 else (dims[a] + rng.uniform(0, 3)) * U
+        elif kind == 2:  # near the ends of the coordinate range on some axes
+            for a in range(3):
+                if rng.random() < 0.6:
+                    c[a] = rng.choice([-lim + 4096, lim - 4096]) + rng.uniform(-2000, 2000)
+        T = int(rng.integers(2, 40))
+        steps = rng.integers(-512, 513, size=(T, 3))
+        v = np.clip(np.round(c) + np.cumsum(steps, axis=0), -lim, lim - 1).astype(np.int64)
+        if kind == 3:  # in from far away in one long segment
+            far = rng.choice([-lim + 100, lim - 100], size=3)
+            v = np.vstack([far, v])
+        pts.append(v)
+        counts.append(len(v))
+    off = np.zeros(len(counts) + 1, dtype=np.int64)
+    np.cumsum(counts, out=off[1:])
+    xyz = np.concatenate(pts).astype(np.int32)
+    for staging in (0, 1):
+        _check(roi, lab, dims, N, M, xyz, off, "device", _opts(1, staging))
