@@ -712,19 +712,24 @@ __device__ __forceinline__ void stage_near(const VolView& v, uint32_t* s_near) {
 // warps' rings at a 128-byte aligned offset.
 __host__ __device__ constexpr size_t ring_offset(size_t near_bytes) { return (near_bytes + 127) & ~(size_t)127; }
 
-template <int kMinBlocks, bool kTma, bool kSmem, bool kHook>
-__global__ void __launch_bounds__(kWarps * 32, kMinBlocks) prefilter_kernel(Tract t, VolView v, int prefilter,
-                                                                           SurvList surv, DevState* st,
-                                                                           int64_t withhold) {
+// kW warps per CTA, kMinBlocks CTAs per SM.  The default shape is one CTA of
+// 16 warps per SM: with two CTAs of 8 on an SM (each warp the same share of
+// the stream), the warp schedulers favoured the older CTA, which finished
+// 15-18 % before the other, and the SM then ran the second one alone, on half
+// its warps, for the end of the launch.
+template <int kW, int kMinBlocks, bool kTma, bool kSmem, bool kHook>
+__global__ void __launch_bounds__(kW * 32, kMinBlocks) prefilter_kernel(Tract t, VolView v, int prefilter,
+                                                                       SurvList surv, DevState* st,
+                                                                       int64_t withhold) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  __shared__ WarpShared ws_all[kWarps];
+  __shared__ WarpShared ws_all[kW];
   griddep_launch_dependents();  // the walk's CTAs may take SMs as this grid's CTAs end
   uint32_t* s_near = reinterpret_cast<uint32_t*>(smem_raw);
   if (kSmem) stage_near(v, s_near);
   const uint32_t* nw = kSmem ? s_near : v.near;
   WarpShared& ws = ws_all[threadIdx.x >> 5];
-  const int64_t gw = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
-  const int64_t nwarps = (int64_t)gridDim.x * kWarps;
+  const int64_t gw = (int64_t)blockIdx.x * kW + (threadIdx.x >> 5);
+  const int64_t nwarps = (int64_t)gridDim.x * kW;
   int64_t s_lo, s_hi;
   vertex_split(t.off, t.ns, t.nv, gw, nwarps, s_lo, s_hi);
   Scan sc;
@@ -775,46 +780,47 @@ constexpr size_t kRingBytes = sizeof(TmaSmem) * kWarps;
 // Grid = every CTA resident at once (one wave), from the occupancy the
 // compiled kernel really reaches.
 template <typename K>
-cudaError_t resident_grid(K kernel, size_t smem, int num_sms, int* grid) {
+cudaError_t resident_grid(K kernel, int threads, size_t smem, int num_sms, int* grid) {
   int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kWarps * 32, smem);
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem);
   if (e != cudaSuccess) return e;
   *grid = num_sms * (per_sm > 0 ? per_sm : 1);
   return cudaSuccess;
 }
 
-template <int kMinBlocks, bool kTma, bool kSmem>
+template <int kW, int kMinBlocks, bool kTma, bool kSmem>
 cudaError_t launch_plain(const Tract& t, const VolView& v, bool prefilter, const SurvList& survivors, DevState* st,
                          int num_sms, cudaStream_t s, int64_t withhold) {
   // the test hook has builds of its own, so that the default one carries no
   // trace of it
-  auto k = (kTma && withhold >= 0) ? prefilter_kernel<kMinBlocks, kTma, kSmem, kTma>
-                                   : prefilter_kernel<kMinBlocks, kTma, kSmem, false>;
+  auto k = (kTma && withhold >= 0) ? prefilter_kernel<kW, kMinBlocks, kTma, kSmem, kTma>
+                                   : prefilter_kernel<kW, kMinBlocks, kTma, kSmem, false>;
   const size_t near_bytes = kSmem ? (size_t)near_words(v) * 4 : 0;
-  const size_t bytes = kTma ? ring_offset(near_bytes) + kRingBytes : near_bytes;
+  const size_t bytes = kTma ? ring_offset(near_bytes) + sizeof(TmaSmem) * kW : near_bytes;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   int grid = 0;
-  if (e == cudaSuccess) e = resident_grid(k, bytes, num_sms, &grid);
+  if (e == cudaSuccess) e = resident_grid(k, kW * 32, bytes, num_sms, &grid);
   if (e != cudaSuccess) return e;
-  k<<<grid, kWarps * 32, bytes, s>>>(t, v, prefilter ? 1 : 0, survivors, st, withhold);
+  k<<<grid, kW * 32, bytes, s>>>(t, v, prefilter ? 1 : 0, survivors, st, withhold);
   return cudaGetLastError();
 }
 
 // Near grids up to this many words are staged in shared memory beside the
-// rings (two CTAs still fit on an SM).
+// rings of the SM's warps.
 constexpr int64_t kNearSmemWordsTma = 8192;
 
-template <int kMinBlocks>
+template <int kW, int kMinBlocks>
 cudaError_t launch_one(const Tract& t, const VolView& v, bool prefilter, bool tma, const SurvList& survivors,
                        DevState* st, int num_sms, cudaStream_t s, int64_t wh) {
   const int64_t nw = near_words(v);
   if (tma) {
     if (nw <= kNearSmemWordsTma)
-      return launch_plain<kMinBlocks, true, true>(t, v, prefilter, survivors, st, num_sms, s, wh);
-    return launch_plain<kMinBlocks, true, false>(t, v, prefilter, survivors, st, num_sms, s, wh);
+      return launch_plain<kW, kMinBlocks, true, true>(t, v, prefilter, survivors, st, num_sms, s, wh);
+    return launch_plain<kW, kMinBlocks, true, false>(t, v, prefilter, survivors, st, num_sms, s, wh);
   }
-  if (nw <= kNearSmemWords) return launch_plain<kMinBlocks, false, true>(t, v, prefilter, survivors, st, num_sms, s, wh);
-  return launch_plain<kMinBlocks, false, false>(t, v, prefilter, survivors, st, num_sms, s, wh);
+  if (nw <= kNearSmemWords)
+    return launch_plain<kW, kMinBlocks, false, true>(t, v, prefilter, survivors, st, num_sms, s, wh);
+  return launch_plain<kW, kMinBlocks, false, false>(t, v, prefilter, survivors, st, num_sms, s, wh);
 }
 
 template <int kMinBlocks, bool kTma>
@@ -824,7 +830,7 @@ cudaError_t launch_batch_one(const BatchTable& tbl, const BatchTask* tasks, int3
   const size_t bytes = kTma ? kRingBytes : 0;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   int grid = 0;
-  if (e == cudaSuccess) e = resident_grid(k, bytes, num_sms, &grid);
+  if (e == cudaSuccess) e = resident_grid(k, kWarps * 32, bytes, num_sms, &grid);
   if (e != cudaSuccess) return e;
   k<<<grid, kWarps * 32, bytes, s>>>(tbl, tasks, ntasks, prefilter ? 1 : 0, survivors, gst);
   return cudaGetLastError();
@@ -851,8 +857,10 @@ cudaError_t launch_prefilter(const Tract& t, const VolView& v, bool prefilter, u
   (void)mode;  // the segment and the vertex-only rules share the near test; the walk applies the rule
   if (t.ns <= 0) return cudaSuccess;
   const SurvList survivors{survivor_ids, survivor_cap};
-  if (ctas_per_sm >= 3) return launch_one<3>(t, v, prefilter, tma, survivors, st, num_sms, s, withhold_piece);
-  return launch_one<2>(t, v, prefilter, tma, survivors, st, num_sms, s, withhold_piece);
+  // the register budget of two 8-warp CTAs per SM as one CTA of 16 warps;
+  // that of three (80 registers) as three CTAs of 8
+  if (ctas_per_sm >= 3) return launch_one<8, 3>(t, v, prefilter, tma, survivors, st, num_sms, s, withhold_piece);
+  return launch_one<16, 1>(t, v, prefilter, tma, survivors, st, num_sms, s, withhold_piece);
 }
 
 }  // namespace fc
