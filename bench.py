@@ -49,8 +49,8 @@ METRIC = "DDA voxel-steps/s & subjects/s for C, bit-exact; batched vs plain; p50
 # traffic grows with the vertices).
 PREFILTER_SOURCES = ("paper_2302_09247_gb300/csrc/k_prefilter.cu", "paper_2302_09247_gb300/csrc/fc_tma.cuh",
                      "paper_2302_09247_gb300/csrc/fc_internal.cuh", "paper_2302_09247_gb300/csrc/fc_device.cuh")
-PREFILTER_TRAFFIC = {"sha256": "a8462d93402af98e63dd58cacedf843c78c9134a61d5c962fdbfb576010a2646",
-                     "bytes": 1911568896, "vertices": 157754709, "workload": "high-res",
+PREFILTER_TRAFFIC = {"sha256": "70b72fb97fc8f0e5418766b9fb457e7f86c81daa9ec46a6f364f474256c830cd",
+                     "bytes": 1911417856, "vertices": 157754709, "workload": "high-res",
                      "summary": "profiles/prefilter_kernel_highres260x311x260.md"}
 
 
