@@ -97,9 +97,11 @@ enum {
   /* 1: record CUDA events around every stage on the context's stream and
    * accumulate their durations (fastcod_get_profile); 0 (default): off. */
   FASTCOD_OPT_PROFILE = 5,
-  /* CTAs per SM the prefilter is compiled for: 2 (default, up to 128
-   * registers per thread) or 3 (80 registers, more resident warps).  Results
-   * are identical. */
+  /* Register budget of the prefilter, in 8-warp CTAs per SM: 2 (default: 16
+   * warps per SM at up to 128 registers a thread, run as one CTA of 16 warps
+   * by the single-subject call and as two of 8 by the batched and served
+   * forms) or 3 (24 warps at 80 registers, three CTAs of 8).  Results are
+   * identical. */
   FASTCOD_OPT_PREFILTER_CTAS = 6,
   /* cell of the near grid (the prefilter's test, and the walk's skip of
    * segments far from every ROI and labelled voxel): (1 << value)^3 voxels,
