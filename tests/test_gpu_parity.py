@@ -305,3 +305,19 @@ def test_vertices_beside_and_far_off_the_grid():
     xyz = np.concatenate(pts).astype(np.int32)
     for staging in (0, 1):
         _check(roi, lab, dims, N, M, xyz, off, "device", _opts(1, staging))
+
+
+@pytest.mark.parametrize("ctas", [2, 3])
+@pytest.mark.parametrize("staging", [1, 0])
+def test_prefilter_launch_shapes(ctas, staging):
+    """The single-subject prefilter as one CTA of 16 warps per SM (the
+    default register budget) and as three CTAs of 8 at 80 registers, with the
+    bulk-copy and the direct loader, on an HCP-shaped subset (near grid in
+    global memory) and on the tiny subject (near grid staged in shared
+    memory), against the oracle."""
+    from paper_2302_09247_gb300 import fastcod as fc
+    opts = dict(_opts(1, staging))
+    opts[fc.FASTCOD_OPT_PREFILTER_CTAS] = ctas
+    for cfg, n in ((1, 30_000), (0, 20_000)):
+        vols, tr = synth.make_subject(cfg, n_streamlines=n)
+        _check(vols.roi, vols.lab, vols.dims, vols.n_roi, vols.n_targets, tr.xyz, tr.offsets, "device", opts)
