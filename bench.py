@@ -49,8 +49,8 @@ METRIC = "DDA voxel-steps/s & subjects/s for C, bit-exact; batched vs plain; p50
 # traffic grows with the vertices).
 PREFILTER_SOURCES = ("paper_2302_09247_gb300/csrc/k_prefilter.cu", "paper_2302_09247_gb300/csrc/fc_tma.cuh",
                      "paper_2302_09247_gb300/csrc/fc_internal.cuh", "paper_2302_09247_gb300/csrc/fc_device.cuh")
-PREFILTER_TRAFFIC = {"sha256": "70b72fb97fc8f0e5418766b9fb457e7f86c81daa9ec46a6f364f474256c830cd",
-                     "bytes": 1911417856, "vertices": 157754709, "workload": "high-res",
+PREFILTER_TRAFFIC = {"sha256": "e3c96dd2aca3a0ce113e15ed2addcf4a8a58f6ed2eb59c1a51b564868699520b",
+                     "bytes": 1911535104, "vertices": 157754709, "workload": "high-res",
                      "summary": "profiles/prefilter_kernel_highres260x311x260.md"}
 
 
@@ -687,8 +687,8 @@ def run_next(args):
 # the ones it was measured on.
 WALK_SOURCES = ("paper_2302_09247_gb300/csrc/k_walk.cu", "paper_2302_09247_gb300/csrc/fc_device.cuh",
                 "paper_2302_09247_gb300/csrc/fc_internal.cuh")
-WALK_INSTR = {"sha256": "55c885a557a500eb063c9bdc65d212fb672e17cf189c402ce5d5d05012e80f55",
-              "warp_instr_per_voxel_step": 519023415 / 54811982,
+WALK_INSTR = {"sha256": "e3345e68cfa153a017e23b6b3296bfe32931559897a46f5c444e4ff3c15bad6d",
+              "warp_instr_per_voxel_step": 519023423 / 54811982,
               "summary": "profiles/walk_kernel_dda_highres260x311x260.md"}
 
 

@@ -221,6 +221,34 @@ FASTCOD_API int fastcod_get_shape(const fastcod_ctx* ctx, int32_t* n_roi, int32_
 /* Wait for all queued work and read the statistics. */
 FASTCOD_API int fastcod_get_stats(fastcod_ctx* ctx, fastcod_stats* out);
 
+/* Resume from a checkpoint.  A checkpoint of a context is its C
+ * (fastcod_connectivity), its C_end (fastcod_endpoint_connectivity) and its
+ * statistics (fastcod_get_stats), taken between fastcod_add_streamlines
+ * calls.  fastcod_restore installs one in a context whose volumes give the
+ * same N and M (the same context after a reset, or a new one, in another
+ * process for instance): C, C_end and the statistics are replaced by the
+ * checkpoint's, and later fastcod_add_streamlines calls add to them.  Each
+ * streamline adds its own terms to C and C_end (Algorithm 2, Algorithm 1)
+ * and to streamlines, vertices, voxel_steps and pairs, so a pass split at
+ * any streamline boundary, checkpointed and resumed, ends with those of one
+ * uninterrupted pass.  survivors, overflow and walked_steps count work done
+ * and can differ: the prefilter's verdict on a streamline (conservative
+ * either way) depends on where the streamline sits in its call's arrays.
+ *   C_in, Cend_in: int32 [N][M] row-major, host or device memory of the
+ *     context's device, read before the call returns (may be NULL when
+ *     N * M = 0).
+ *   stats: the checkpoint's statistics; streamlines in [0, 2^31 - 1], every
+ *     count >= 0, survivors <= streamlines, overflow <= survivors,
+ *     walked_steps <= voxel_steps.
+ * The matrices are checked on the device against what every pass
+ * satisfies: each entry in [0, stats->streamlines], the entries of C summing
+ * to stats->pairs (one increment per (v, t) pair), those of C_end to at most
+ * stats->streamlines (at most one per streamline).  A checkpoint that fails
+ * a check gives FASTCOD_EINVAL and leaves C, C_end and the statistics zero,
+ * as after fastcod_reset.  ESTATE before fastcod_set_volumes.  Blocking. */
+FASTCOD_API int fastcod_restore(fastcod_ctx* ctx, const int32_t* C_in, const int32_t* Cend_in,
+                                const fastcod_stats* stats);
+
 /* Wait for all queued work and report any device-detected error. */
 FASTCOD_API int fastcod_sync(fastcod_ctx* ctx);
 

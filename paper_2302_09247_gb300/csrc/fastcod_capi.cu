@@ -277,6 +277,7 @@ FASTCOD_API int fastcod_destroy(fastcod_ctx* c) {
   for (int i = 0; i < fastcod_ctx::kAuxSlots; ++i) cudaFree(c->d_aux[i]);
   fcapi::batch_free(c);
   cudaFree(c->d_state);
+  cudaFree(c->d_check);
   for (auto& set : c->ev_pool)
     for (int i = 0; i < 5; ++i) cudaEventDestroy(set.e[i]);
   for (cudaEvent_t e : c->aux_ev)
@@ -521,6 +522,74 @@ FASTCOD_API int fastcod_get_stats(fastcod_ctx* c, fastcod_stats* out) {
   out->overflow = (int64_t)h.overflow;
   out->pairs = (int64_t)h.pairs;
   out->walked_steps = (int64_t)h.walked;
+  return FASTCOD_OK;
+}
+
+FASTCOD_API int fastcod_restore(fastcod_ctx* c, const int32_t* C_in, const int32_t* Cend_in,
+                                const fastcod_stats* stats) {
+  fcapi::Range nvtx_range("fastcod_restore");
+  if (!c) return FASTCOD_EINVAL;
+  c->err.clear();
+  if (!c->has_vol) return fail(c, FASTCOD_ESTATE, "no volumes installed");
+  CU(cudaSetDevice(c->device));
+  // a refused checkpoint leaves the context as after fastcod_reset
+  auto refuse = [c](int rc) {
+    const std::string msg = c->err;
+    if (zero_accumulators(c) == FASTCOD_OK) (void)cudaStreamSynchronize(c->stream);
+    c->err = msg;
+    return rc;
+  };
+  if (!stats) return refuse(fail(c, FASTCOD_EINVAL, "stats is NULL"));
+  const fastcod_stats& s = *stats;
+  if (s.streamlines < 0 || s.streamlines > 0x7fffffffLL)
+    return refuse(fail(c, FASTCOD_EINVAL, "checkpoint streamlines %lld outside [0, 2^31 - 1]",
+                       (long long)s.streamlines));
+  if (s.vertices < 0 || s.voxel_steps < 0 || s.survivors < 0 || s.overflow < 0 || s.pairs < 0 ||
+      s.walked_steps < 0)
+    return refuse(fail(c, FASTCOD_EINVAL, "checkpoint with a negative count"));
+  if (s.survivors > s.streamlines || s.overflow > s.survivors || s.walked_steps > s.voxel_steps)
+    return refuse(fail(c, FASTCOD_EINVAL, "checkpoint counts inconsistent (need survivors <= streamlines, "
+                       "overflow <= survivors, walked_steps <= voxel_steps)"));
+  const size_t nm = (size_t)c->N * (size_t)c->M;
+  if (nm && (!C_in || !Cend_in)) return refuse(fail(c, FASTCOD_EINVAL, "matrix pointer is NULL"));
+  if (nm && (fcapi::ptr_kind(C_in, c->device) < 0 || fcapi::ptr_kind(Cend_in, c->device) < 0))
+    return refuse(fail(c, FASTCOD_EINVAL, "input is device memory of another device"));
+  if (int rc = zero_accumulators(c)) return rc;
+  if (int rc = grow(c, (void**)&c->d_check, &c->check_bytes, 3 * sizeof(unsigned long long))) return rc;
+  CU(cudaMemsetAsync(c->d_check, 0, 2 * sizeof(unsigned long long), c->stream));
+  CU(cudaMemsetAsync(c->d_check + 2, 0xff, sizeof(unsigned long long), c->stream));
+  if (nm) {
+    CU(cudaMemcpyAsync(c->d_C, C_in, nm * 4, cudaMemcpyDefault, c->stream));
+    CU(cudaMemcpyAsync(c->d_Cend, Cend_in, nm * 4, cudaMemcpyDefault, c->stream));
+    CU(fc::launch_checkpoint_check(c->d_C, c->d_Cend, (int64_t)nm, (int32_t)s.streamlines, c->d_check, c->stream));
+    c->prof.kernel_launches += 1;
+  }
+  unsigned long long h[3];
+  CU(cudaMemcpyAsync(h, c->d_check, sizeof h, cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  int rc = FASTCOD_OK;
+  if (h[2] != ~0ull) {
+    const bool in_c = h[2] < nm;
+    const unsigned long long k = in_c ? h[2] : h[2] - nm;
+    rc = fail(c, FASTCOD_EINVAL, "checkpoint %s[%llu][%llu] outside [0, %lld streamlines]", in_c ? "C" : "C_end",
+              k / (unsigned long long)c->M, k % (unsigned long long)c->M, (long long)s.streamlines);
+  } else if (h[0] != (unsigned long long)s.pairs) {
+    rc = fail(c, FASTCOD_EINVAL, "checkpoint C sums to %llu, its pairs count is %lld", h[0], (long long)s.pairs);
+  } else if (h[1] > (unsigned long long)s.streamlines) {
+    rc = fail(c, FASTCOD_EINVAL, "checkpoint C_end sums to %llu, more than its %lld streamlines", h[1],
+              (long long)s.streamlines);
+  }
+  if (rc) return refuse(rc);
+  // the running counts, in DevState order
+  static_assert(offsetof(DevState, walked) - offsetof(DevState, voxel_steps) == 4 * sizeof(unsigned long long),
+                "DevState counters out of order");
+  const unsigned long long cnt[5] = {(unsigned long long)s.voxel_steps, (unsigned long long)s.survivors,
+                                     (unsigned long long)s.overflow, (unsigned long long)s.pairs,
+                                     (unsigned long long)s.walked_steps};
+  CU(cudaMemcpyAsync(&c->d_state->voxel_steps, cnt, sizeof cnt, cudaMemcpyHostToDevice, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  c->total_streamlines = s.streamlines;
+  c->total_vertices = s.vertices;
   return FASTCOD_OK;
 }
 

@@ -49,6 +49,8 @@ struct fastcod_ctx {
   size_t ovf_bytes = 0;
 
   DevState* d_state = nullptr;
+  unsigned long long* d_check = nullptr;  // fastcod_restore: sums of C and C_end, first entry out of range
+  size_t check_bytes = 0;
 
   int64_t total_streamlines = 0;
   int64_t total_vertices = 0;

@@ -283,6 +283,11 @@ cudaError_t launch_parcellate(const int32_t* C, int32_t N, int32_t M, int32_t* l
 cudaError_t launch_world_to_fixed(const float* xyz_mm, int64_t nv, const float affine[12], int32_t* out,
                                   DevState* st, cudaStream_t s);
 cudaError_t launch_check_offsets(const int64_t* off, int64_t ns, int64_t nv, DevState* st, cudaStream_t s);
+// Checkpoint check: out[0] += sum of C, out[1] += sum of C_end (both [nm]),
+// out[2] = min(out[2], the first index over C then C_end, 2 nm entries,
+// whose entry lies outside [0, max_count]).
+cudaError_t launch_checkpoint_check(const int32_t* C, const int32_t* Cend, int64_t nm, int32_t max_count,
+                                    unsigned long long* out, cudaStream_t s);
 cudaError_t launch_seg_max(const int32_t* xyz, const int64_t* off, int64_t ns, unsigned long long* best,
                            cudaStream_t s);
 int64_t upsample_scan_blocks(int64_t ns);

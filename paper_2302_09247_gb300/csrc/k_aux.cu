@@ -584,6 +584,33 @@ __global__ void __launch_bounds__(kThreads) check_offsets_kernel(const int64_t* 
   }
 }
 
+// ------------------------------------------------------ checkpoint check
+__global__ void __launch_bounds__(kThreads) checkpoint_check_kernel(const int32_t* __restrict__ C,
+                                                                    const int32_t* __restrict__ Cend, int64_t nm,
+                                                                    int32_t max_count,
+                                                                    unsigned long long* __restrict__ out) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  unsigned long long sc = 0, se = 0, bad = ~0ull;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nm; k += stride) {
+    const int32_t x = __ldcs(C + k), y = __ldcs(Cend + k);
+    if (x < 0 || x > max_count) bad = min(bad, (unsigned long long)k);
+    if (y < 0 || y > max_count) bad = min(bad, (unsigned long long)(nm + k));
+    sc += (unsigned long long)max(x, 0);
+    se += (unsigned long long)max(y, 0);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    sc += __shfl_xor_sync(kFull, sc, o);
+    se += __shfl_xor_sync(kFull, se, o);
+    bad = min(bad, __shfl_xor_sync(kFull, bad, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (sc) atomicAdd(out, sc);
+    if (se) atomicAdd(out + 1, se);
+    if (bad != ~0ull) atomicMin(out + 2, bad);
+  }
+}
+
 // ----------------------------------------------------------------- rescale
 struct Rescale {
   int64_t num[3], den[3], add[3];
@@ -639,6 +666,13 @@ cudaError_t launch_seg_max(const int32_t* xyz, const int64_t* off, int64_t ns, u
 }
 
 int64_t upsample_scan_blocks(int64_t ns) { return (ns + 1 + (int64_t)kThreads * kScanItems - 1) / ((int64_t)kThreads * kScanItems); }
+
+cudaError_t launch_checkpoint_check(const int32_t* C, const int32_t* Cend, int64_t nm, int32_t max_count,
+                                    unsigned long long* out, cudaStream_t s) {
+  if (nm <= 0) return cudaSuccess;
+  checkpoint_check_kernel<<<grid_for(nm, 8), kThreads, 0, s>>>(C, Cend, nm, max_count, out);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_check_offsets(const int64_t* off, int64_t ns, int64_t nv, DevState* st, cudaStream_t s) {
   check_offsets_kernel<<<grid_for(ns + 1, 4), kThreads, 0, s>>>(off, ns, nv, st);

@@ -45,7 +45,8 @@ FASTCOD_OPT_BATCH_TASK_LOG2 = 13
 EXPORTED = [
     "fastcod_create", "fastcod_destroy", "fastcod_set_stream", "fastcod_set_volumes",
     "fastcod_add_streamlines", "fastcod_connectivity", "fastcod_endpoint_connectivity",
-    "fastcod_reset", "fastcod_get_shape", "fastcod_get_stats", "fastcod_get_profile", "fastcod_sync",
+    "fastcod_reset", "fastcod_get_shape", "fastcod_get_stats", "fastcod_restore", "fastcod_get_profile",
+    "fastcod_sync",
     "fastcod_set_option", "fastcod_last_error", "fastcod_batch_run", "fastcod_batch_get_stats",
     "fastcod_batch_get_info", "fastcod_server_create", "fastcod_server_submit", "fastcod_server_push_chunk",
     "fastcod_server_poll", "fastcod_server_wait", "fastcod_server_cancel", "fastcod_server_request_info",
@@ -108,6 +109,7 @@ def _load():
         "fastcod_reset": ([vp], ctypes.c_int),
         "fastcod_get_shape": ([vp, ctypes.POINTER(i32), ctypes.POINTER(i32)], ctypes.c_int),
         "fastcod_get_stats": ([vp, ctypes.POINTER(Stats)], ctypes.c_int),
+        "fastcod_restore": ([vp, vp, vp, ctypes.POINTER(Stats)], ctypes.c_int),
         "fastcod_get_profile": ([vp, ctypes.POINTER(Profile)], ctypes.c_int),
         "fastcod_sync": ([vp], ctypes.c_int),
         "fastcod_set_option": ([vp, i32, i64], ctypes.c_int),
@@ -217,6 +219,13 @@ def fastcod_get_stats(ctx) -> dict:
     s = Stats()
     _check(ctx, lib.fastcod_get_stats(ctx, ctypes.byref(s)))
     return {k: int(getattr(s, k)) for k, _ in Stats._fields_}
+
+
+def fastcod_restore(ctx, C, Cend, stats: dict):
+    """Install a checkpoint: C and C_end (int32 [N][M], host or device) and the
+    statistics dict fastcod_get_stats returned when they were read."""
+    s = Stats(**{k: int(stats[k]) for k, _ in Stats._fields_})
+    return _check(ctx, lib.fastcod_restore(ctx, _ptr(C), _ptr(Cend), ctypes.byref(s)))
 
 
 def fastcod_get_profile(ctx) -> dict:
@@ -449,6 +458,13 @@ class Context:
 
     def stats(self) -> dict:
         return fastcod_get_stats(self.ctx)
+
+    def checkpoint(self):
+        """(C, C_end, statistics) as host arrays and a dict."""
+        return self.connectivity(), self.endpoint_connectivity(), self.stats()
+
+    def restore(self, C, Cend, stats: dict):
+        fastcod_restore(self.ctx, C, Cend, stats)
 
     def profile(self) -> dict:
         return fastcod_get_profile(self.ctx)

@@ -55,6 +55,7 @@ def test_null_and_state_errors_without_gpu(lib_path):
     assert L.fastcod_set_volumes(None, None, None, 1, 1, 1, 0, 0) == fc.FASTCOD_EINVAL
     assert L.fastcod_add_streamlines(None, None, 0, None, 0) == fc.FASTCOD_EINVAL
     assert L.fastcod_get_shape(None, None, None) == fc.FASTCOD_EINVAL
+    assert L.fastcod_restore(None, None, None, None) == fc.FASTCOD_EINVAL
     try:
         import torch
         has_gpu = torch.cuda.is_available()
