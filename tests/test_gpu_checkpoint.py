@@ -153,3 +153,27 @@ def test_restore_needs_volumes(fc):
         assert e.value.code == fc.FASTCOD_ESTATE
     finally:
         ctx.close()
+
+
+@pytest.mark.parametrize("target,sampling", [(1, 0), (0, 1)])
+def test_resume_under_the_other_rules(fc, subject, target, sampling):
+    """The endpoint-target rule (Algorithm 2 taken literally) and the
+    vertex-sampled rule: a two-way split resumed in a fresh context equals
+    the oracle under the same rule."""
+    vols, tr, _, _, _ = subject
+    flags = (oracle.TARGET_ENDPOINT if target else 0) | (oracle.VERTEX_SAMPLED if sampling else 0)
+    Cr, Cer, sr = oracle.connectivity(vols.roi, vols.lab, vols.dims, vols.n_roi, vols.n_targets, tr.xyz,
+                                      tr.offsets, flags)
+    cut = 23_457
+    ck = None
+    for b, e in ((0, cut), (cut, tr.n_streamlines)):
+        with _ctx(fc, vols) as ctx:
+            ctx.set_option(fc.FASTCOD_OPT_TARGET_MODE, target)
+            ctx.set_option(fc.FASTCOD_OPT_SAMPLING, sampling)
+            if ck is not None:
+                ctx.restore(*ck)
+            ctx.add_streamlines(*_part(tr, b, e))
+            ck = ctx.checkpoint()
+    np.testing.assert_array_equal(ck[0], Cr)
+    np.testing.assert_array_equal(ck[1], Cer)
+    assert ck[2]["pairs"] == sr["pairs"] and ck[2]["voxel_steps"] == sr["voxel_steps"]

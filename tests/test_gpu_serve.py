@@ -238,3 +238,31 @@ def test_staging_buffers_reused_across_chunk_sizes(fc, subjects, slots):
     finally:
         fc.fastcod_server_destroy(srv)
         ctx.close()
+
+
+def test_request_split_at_a_chunk_boundary_sums_to_the_whole(fc, subjects):
+    """A request stopped after k of its chunks and resumed as a second request
+    of the remaining ones: the two results add up to the whole subject's
+    (counts add per streamline), for every split point of a 5-chunk request,
+    the two halves in flight together."""
+    vA, tA = subjects["A"]
+    Cr, Cer = _oracle(vA, tA)
+    chunks = _chunks(tA, 5)
+    ctx = fc.Context(0)
+    srv = fc.fastcod_server_create(ctx.ctx, 4, 0)
+    try:
+        for k in range(1, 5):
+            first, rest = Req(fc, srv, vA), Req(fc, srv, vA, where="device")
+            for i, (x, o) in enumerate(chunks[:k]):
+                first.push(fc, srv, x, o, last=(i == k - 1))
+            for i, (x, o) in enumerate(chunks[k:]):
+                rest.push(fc, srv, x, o, last=(i == len(chunks) - k - 1), where="device")
+            for r in (first, rest):
+                assert fc.fastcod_server_wait(srv, r.id, 120.0) == fc.FASTCOD_OK
+            np.testing.assert_array_equal(first.C + rest.C, Cr, err_msg=f"split after chunk {k}")
+            np.testing.assert_array_equal(first.Ce + rest.Ce, Cer, err_msg=f"split after chunk {k}")
+            done = [fc.fastcod_server_request_info(srv, r.id)["streamlines"] for r in (first, rest)]
+            assert sum(done) == tA.n_streamlines
+    finally:
+        fc.fastcod_server_destroy(srv)
+        ctx.close()
