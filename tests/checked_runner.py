@@ -13,7 +13,7 @@ sys.path.insert(0, ROOT)
 import oracle  # noqa: E402
 import synth  # noqa: E402
 from synth import tiny  # noqa: E402
-from tests.gpu_helpers import as_device, run_gpu  # noqa: E402
+from tests.gpu_helpers import as_device, range_end_streamlines, run_gpu  # noqa: E402
 from tests.parcellation_cases import DOUBLE_ROUNDING_ROWS, as_matrix, midpoint_rows  # noqa: E402
 
 
@@ -42,6 +42,13 @@ def main():
                     fc.FASTCOD_OPT_TARGET_MODE: target, fc.FASTCOD_OPT_SAMPLING: sampling}
             flags = (oracle.TARGET_ENDPOINT if target else 0) | (oracle.VERTEX_SAMPLED if sampling else 0)
             check(case, opts, flags)
+    # vertices at both ends of the coordinate range, prefilter on and off
+    rng = np.random.default_rng(2024)
+    dims = (20, 17, 23)
+    roi, lab, N, M = tiny.random_volumes(rng, dims, n_roi=6, n_labels=5, p_roi=0.15, p_lab=0.25)
+    xyz, off = range_end_streamlines(rng, dims)
+    for pre in (1, 0):
+        check((roi, lab, dims, N, M, xyz, off), {fc.FASTCOD_OPT_PREFILTER: pre, fc.FASTCOD_OPT_SEGMENT_SKIP: pre})
     # sets that outgrow the per-warp tables (the overflow path) and hash-set forms
     rng = np.random.default_rng(8)
     dims = (64, 40, 24)
@@ -57,6 +64,19 @@ def main():
     case = (vols.roi, vols.lab, vols.dims, vols.n_roi, vols.n_targets, tr.xyz, tr.offsets)
     check(case)
     check(case, where="host")
+    # a checkpoint after the first 40,000 streamlines, resumed in a new context
+    o = tr.offsets
+    cut = 40_000
+    with fc.Context(0) as ctx:
+        ctx.set_volumes(vols.roi, vols.lab, vols.dims, vols.n_roi, vols.n_targets)
+        ctx.add_streamlines(np.ascontiguousarray(tr.xyz[:o[cut]]), np.ascontiguousarray(o[:cut + 1]))
+        ck = ctx.checkpoint()
+    with fc.Context(0) as ctx:
+        ctx.set_volumes(vols.roi, vols.lab, vols.dims, vols.n_roi, vols.n_targets)
+        ctx.restore(*ck)
+        ctx.add_streamlines(np.ascontiguousarray(tr.xyz[o[cut]:]), np.ascontiguousarray(o[cut:] - o[cut]))
+        Cr, Cer, _ = oracle.connectivity(*case)
+        assert np.array_equal(ctx.connectivity(), Cr) and np.array_equal(ctx.endpoint_connectivity(), Cer)
     # a batch of three subjects
     subs = [synth.make_subject(3, subject=s, n_streamlines=20_000) for s in (1, 2, 3)]
     keep, objs, outs = [], [], []

@@ -11,7 +11,7 @@ import pytest
 import oracle
 import synth
 from synth import tiny
-from tests.gpu_helpers import run_gpu
+from tests.gpu_helpers import range_end_streamlines, run_gpu
 
 pytestmark = pytest.mark.gpu
 
@@ -317,30 +317,8 @@ def test_coordinates_at_the_ends_of_the_range():
     rng = np.random.default_rng(2024)
     dims = (20, 17, 23)
     roi, lab, N, M = tiny.random_volumes(rng, dims, n_roi=6, n_labels=5, p_roi=0.15, p_lab=0.25)
-    lo, hi = -(1 << 24), (1 << 24) - 1
-    inside = [int(0.5 * d * U) for d in dims]
-    lines = [
-        [[lo, lo, lo], [hi, hi, hi]],                  # the main diagonal of the range
-        [[hi, hi, hi], [lo, lo, lo]],                  # reversed
-        [[lo, inside[1], inside[2]], [hi, inside[1], inside[2]]],  # one axis, through the grid
-        [[lo, lo, inside[2]], [hi, hi, inside[2]]],    # two axes
-        [[lo, hi, 512], [1000, 1000, hi]],             # mixed signs
-        [[lo, 0, 0], [lo, 5 * U, 3 * U], [lo, 9 * U, 0]],  # in the plane x = -2^24
-        [[hi, 7 * U, 2 * U], [hi, 8 * U, 2 * U]],      # in the plane x = 2^24 - 1
-        [[lo, lo, lo]], [[hi, hi, hi]], [[lo, hi, lo]],  # single vertices at corners
-        [inside, [hi, inside[1], inside[2]]],          # out of the grid to the top end
-        [inside, [inside[0], lo, inside[2]]],          # and to the bottom end
-        [[lo, lo, lo], inside, [hi, hi, hi]],          # in from one corner, out to the other
-    ]
-    for _ in range(40):  # ordinary short walks between them
-        c = rng.uniform(0, 1, size=3) * np.array(dims) * U
-        T = int(rng.integers(2, 30))
-        lines.append((np.round(c) + np.cumsum(rng.integers(-512, 513, size=(T, 3)), axis=0)).astype(np.int64).tolist())
-    counts = [len(v) for v in lines]
-    off = np.zeros(len(counts) + 1, dtype=np.int64)
-    np.cumsum(counts, out=off[1:])
-    xyz = np.concatenate([np.asarray(v, dtype=np.int64).reshape(-1, 3) for v in lines]).astype(np.int32)
-    assert xyz.min() == lo and xyz.max() == hi
+    xyz, off = range_end_streamlines(rng, dims)
+    assert xyz.min() == -(1 << 24) and xyz.max() == (1 << 24) - 1
     for prefilter in (1, 0):
         for staging in (0, 1):
             for skip in (1, 0):
